@@ -1,0 +1,130 @@
+"""1D rules on [0, 1] used by the oracle (test infrastructure, FP64).
+
+The paper fixes tensor-product Lagrange elements on the reference cell
+[0,1]^d (Sec. 3.1, Sec. 3.4) and quadrature formulas (Sec. 3.4); the
+workloads name Gauss-Lobatto nodes and (k+1)-point Gauss quadrature.
+Everything here is the textbook definition:
+
+* Gauss-Legendre: the n roots of the Legendre polynomial P_n, weights
+  2 / ((1 - t^2) P_n'(t)^2) on [-1, 1], mapped affinely to [0, 1];
+* Gauss-Lobatto: {-1, 1} and the k-1 roots of P_k', mapped to [0, 1];
+* Lagrange basis by the product formula.
+
+Roots are found by Newton's method in FP64 from Chebyshev starting points.
+"""
+import numpy as np
+
+
+def legendre(n, t):
+    """P_n(t) and P_{n-1}(t) by the three-term recurrence (Bonnet)."""
+    t = np.asarray(t, dtype=np.float64)
+    p_prev = np.ones_like(t)
+    if n == 0:
+        return p_prev, np.zeros_like(t)
+    p = t.copy()
+    for m in range(2, n + 1):
+        p_prev, p = p, ((2 * m - 1) * t * p - (m - 1) * p_prev) / m
+    return p, p_prev
+
+
+def legendre_deriv(n, t):
+    """P_n'(t) = n (t P_n - P_{n-1}) / (t^2 - 1), valid for |t| < 1."""
+    p, pm = legendre(n, t)
+    return n * (t * p - pm) / (t * t - 1.0), p
+
+
+def _mirror(t_low, n):
+    """Full symmetric node set on [-1, 1] from its negative half (t = 0 exact in the middle)."""
+    t = np.zeros(n)
+    h = n // 2
+    t[:h] = t_low[:h]
+    t[n - h:] = -t_low[:h][::-1]
+    return t
+
+
+def gauss_legendre(n):
+    """n-point Gauss-Legendre rule on [0, 1]: (points ascending, weights).
+
+    The roots are symmetric about 0; the negative half is computed and
+    mirrored so that the rule is exactly symmetric (midpoint exactly 1/2).
+    """
+    if n < 1:
+        raise ValueError("n >= 1")
+    h = n // 2
+    t = -np.cos(np.pi * (np.arange(h) + 0.75) / (n + 0.5))  # ascending guesses
+    for _ in range(100):
+        if h == 0:
+            break
+        dp, p = legendre_deriv(n, t)
+        dt = p / dp
+        t = t - dt
+        if np.max(np.abs(dt)) < 1e-16:
+            break
+    t = _mirror(t, n)
+    dp, _ = legendre_deriv(n, t)
+    w = 2.0 / ((1.0 - t * t) * dp * dp)
+    return 0.5 * (t + 1.0), 0.5 * w
+
+
+def gauss_lobatto(k):
+    """Degree-k Gauss-Lobatto nodes (k+1 points, ascending) on [0, 1].
+
+    Interior nodes are the roots of P_k'; Newton uses P_k'' from the
+    Legendre equation (1 - t^2) P'' = 2 t P' - k (k+1) P.
+    """
+    if k < 1:
+        raise ValueError("k >= 1")
+    if k == 1:
+        return np.array([0.0, 1.0])
+    h = (k - 1) // 2  # interior roots in the negative half
+    t = -np.cos(np.pi * np.arange(1, h + 1) / k)
+    for _ in range(100):
+        if h == 0:
+            break
+        dp, p = legendre_deriv(k, t)
+        d2p = (2.0 * t * dp - k * (k + 1) * p) / (1.0 - t * t)
+        dt = dp / d2p
+        t = t - dt
+        if np.max(np.abs(dt)) < 1e-16:
+            break
+    interior = _mirror(t, k - 1)
+    nodes = np.concatenate(([-1.0], interior, [1.0]))
+    return 0.5 * (nodes + 1.0)
+
+
+def lagrange(nodes, j, x):
+    """l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m)."""
+    x = np.asarray(x, dtype=np.float64)
+    v = np.ones_like(x)
+    for m, xm in enumerate(nodes):
+        if m != j:
+            v = v * (x - xm) / (nodes[j] - xm)
+    return v
+
+
+def lagrange_deriv(nodes, j, x):
+    """l_j'(x) = sum_{m != j} 1/(x_j - x_m) prod_{l != j, m} (x - x_l)/(x_j - x_l)."""
+    x = np.asarray(x, dtype=np.float64)
+    total = np.zeros_like(x)
+    for m, xm in enumerate(nodes):
+        if m == j:
+            continue
+        term = np.full_like(x, 1.0 / (nodes[j] - xm))
+        for l, xl in enumerate(nodes):
+            if l != j and l != m:
+                term = term * (x - xl) / (nodes[j] - xl)
+        total = total + term
+    return total
+
+
+def basis_tables(k, nq):
+    """Values and derivatives of the degree-k GLL Lagrange basis at the nq Gauss points.
+
+    Returns (gll_nodes, gauss_points, gauss_weights, V, Dv) with V[q, j] =
+    l_j(xi_q) and Dv[q, j] = l_j'(xi_q).
+    """
+    nodes = gauss_lobatto(k)
+    xq, wq = gauss_legendre(nq)
+    V = np.array([[lagrange(nodes, j, x) for j in range(k + 1)] for x in xq])
+    Dv = np.array([[lagrange_deriv(nodes, j, x) for j in range(k + 1)] for x in xq])
+    return nodes, xq, wq, V, Dv
