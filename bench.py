@@ -1,0 +1,298 @@
+"""Benchmark: matrix-free Q_k Laplacian vmult on GB300.
+
+Workload: 64^3 hexahedra of the unit cube deformed by
+x -> x + 0.05 sin(pi x) sin(pi y) sin(pi z) (every component), Q4 on
+Gauss-Lobatto nodes, 5-point Gauss quadrature per direction, coefficient
+a = 1 + 0.5 sin(2 pi x) cos(2 pi y) z, homogeneous Dirichlet boundary,
+16,974,593 DoFs, seeded uniform[-1, 1] input vectors (synthetic).
+
+One step = one operator application (vmult) in FP32 (the headline) --
+the FP64 vmult, the FP64 and mixed solves and the end-to-end path are
+reported beside it.  Every step reads more than the 129 MB L2 (about
+0.92 GB per FP32 step), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(independent replicas, weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, K_DEG = 64, 4
+METRIC = "matrix-free vmult GDoF/s (FP64 vs FP32 mixed) and % HBM peak; solve p50/p99 latency"
+WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2pi y)z, Dirichlet"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def bytes_per_vmult(n_dofs, n_cells, k, s):
+    """Algorithmic bytes: src read + dst write (2 s N) and the 6-entry metric per quadrature point."""
+    return 2 * s * n_dofs + 6 * s * n_cells * (k + 1) ** 3
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds=12.0, sub=12):
+    """The FP64 oracle (assembled CSR SpMV, OpenMP) on a sub-mesh of the same workload."""
+    import numpy as np
+    from oracle import fem, mesh
+    from paper_1910_13247_gb300 import synthetic
+    verts = synthetic.deformed_vertices(sub, sub, sub)
+    om = mesh.structured_mesh(sub, sub, sub, K_DEG, verts)
+    t0 = time.perf_counter()
+    K = fem.assemble(om, K_DEG + 1, fem.COEF_TRIG, (1.0, 0.5))
+    t_asm = time.perf_counter() - t0
+    A = fem.CSR(K)
+    x = synthetic.uniform_vector(om.n_dofs, 1)
+    y = np.zeros(om.n_dofs)
+    A(x, y)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        A(x, y)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": om.n_dofs / dt / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 CSR SpMV of the oracle-assembled operator on a {sub}^3-cell sub-mesh of the same "
+                      f"workload ({om.n_dofs} DoFs, {K.nnz} nonzeros), {reps} SpMVs over {seconds:.0f} s; "
+                      f"assembly ({t_asm:.1f} s) excluded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(seconds=max(2.0, min(30.0, 0.5 * args.steps)))
+    line = {"metric": METRIC, "value": cb["value"], "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle sample: CSR SpMV on a 12^3-cell sub-mesh)"},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mfx")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve measurements")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1910_13247_gb300 import build, mfx, synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    stream = torch.cuda.current_stream()
+
+    verts = synthetic.deformed_vertices(NX, NX, NX)
+    mesh = mfx.Mesh.structured_box(NX, NX, NX, verts)
+    op = mfx.Operator(mesh, K_DEG, mfx.COEF_TRIG, (1.0, 0.5))
+    N, C = op.n_dofs, op.n_cells
+    x64 = torch.tensor(synthetic.uniform_vector(N, 1), device="cuda")
+    x32 = x64.float()
+    y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    # warm-up
+    for _ in range(max(3, args.warmup)):
+        op.vmult(x32, y32)
+    op.vmult(x64, y64)
+    barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    # timed region: K FP32 vmults, each bracketed by events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        op.vmult(x32, y32)
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    ms32 = statistics.mean(per_launch)
+    ms_per_step = total_ms / args.steps
+    value = world * N / (ms_per_step * 1e-3) / 1e9
+
+    hbm, peak_kind = peaks()
+    b32 = bytes_per_vmult(N, C, K_DEG, 4)
+    b64 = bytes_per_vmult(N, C, K_DEG, 8)
+    achieved = b32 / (ms32 * 1e-3) / 1e9
+
+    # FP64 vmult (ALU-bound on GB300: reported with its own roofline)
+    reps64 = max(10, min(200, args.steps // 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps64):
+        op.vmult(x64, y64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / reps64
+
+    # end to end through the C-ABI with host buffers: H2D of the input, vmult, D2H of the result
+    h_in = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    h_in.copy_(x32.cpu())
+    h_out = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    d_in, d_out = torch.empty_like(x32), torch.empty_like(x32)
+    n_e2e = max(5, min(100, args.steps // 20))
+    barrier()
+    e0.record(stream)
+    for _ in range(n_e2e):
+        d_in.copy_(h_in, non_blocking=True)
+        op.vmult(d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / n_e2e)
+    assert torch.equal(h_out, y32.cpu())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": N, "n_cells": C, "degree": K_DEG, "n_q_1d": K_DEG + 1,
+                   "step": "one FP32 vmult", "l2": "inputs larger than L2 (%.2f GB read+written per step)" % (b32 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "vmult (prologue + vmult_kernel), FP32",
+                     "algorithmic_bytes": b32},
+        "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N, "ms_per_step": ms_e2e},
+        "gpu_launches": 2 * args.steps,
+        "fp64": {"gdofs": N / (ms64 * 1e-3) / 1e9, "ms": ms64, "algorithmic_bytes": b64,
+                 "hbm_frac": b64 / (ms64 * 1e-3) / 1e9 / hbm},
+        "fp32_ms_per_launch": ms32,
+    }
+    if clocks:
+        line["clocks"] = clocks
+
+    if not args.no_solve:
+        line["solve"] = solve_measurements(mfx, synthetic, torch, np)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def solve_measurements(mfx, synthetic, torch, np):
+    """Latency of the 8^3 Q2 Poisson Jacobi-PCG solve (p50/p99 over repeated solves)."""
+    from oracle import fem, mesh as omesh  # noqa: F401  (forcing values only via the library's q-points)
+    out = {}
+    m = mfx.Mesh.structured_box(8, 8, 8)
+    op = mfx.Operator(m, 2, mfx.COEF_CONSTANT, (1.0, 0.0))
+    n3 = 27
+    xq = torch.empty(op.n_cells * n3 * 3, dtype=torch.float64, device="cuda")
+    op.quadrature_points(xq)
+    X = xq.view(-1, 3)
+    fq = 3 * np.pi ** 2 * torch.sin(np.pi * X[:, 0]) * torch.sin(np.pi * X[:, 1]) * torch.sin(np.pi * X[:, 2])
+    b = torch.empty(op.n_dofs, dtype=torch.float64, device="cuda")
+    op.rhs(fq.contiguous(), b)
+    x = torch.zeros_like(b)
+    lat, its = [], 0
+    for i in range(23):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.solve(b, x, tol=1e-10)
+        lat.append((time.perf_counter() - t0) * 1e3)
+        its = st["iterations"]
+    lat = sorted(lat[3:])
+    out["poisson_8x8x8_q2_jacobi_pcg"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                           "iterations": its, "rel_residual": st["rel_residual"], "runs": len(lat)}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * mfx -- matrix-free Q_k Laplacian on hexahedral meshes, GB300 (sm_103a).
+ *
+ * C-ABI of libmfx.so.  The operator is the condensed stiffness operator of
+ * the variable-coefficient Laplacian, i.e. the bilinear form of Eq. (1)
+ * (Sec. 2.4) with a coefficient a(x):
+ *
+ *     a(u, v) = integral over Omega of a(x) grad u . grad v dx,
+ *
+ * discretised with continuous tensor-product Lagrange elements of degree k
+ * on Gauss-Lobatto nodes (Sec. 3.1, Sec. 3.4), (k+1)-point Gauss quadrature
+ * per direction and a trilinear (Q1) mapping of every hexahedron
+ * (Sec. 3.4, mappings).  Following the matrix-free paradigm of Sec. 3.6,
+ * no matrix is ever formed: the operator is applied through the weak-form
+ * integrals, using the tensor-product structure of the shape functions
+ * (sum factorisation, Sec. 3.6).  Constraints (homogeneous Dirichlet on the
+ * box boundary, hanging nodes of locally refined meshes, Sec. 3.1 and
+ * Sec. 3.3) are resolved inside the operator: on constrained DoFs the
+ * operator is the identity, on free DoFs it is C^T A C where C expands free
+ * values into constrained ones.
+ *
+ * Conventions
+ *  - The library owns setup data (mesh tables, geometry) in device memory.
+ *    The caller owns every vector: contiguous device arrays of n_dofs
+ *    entries of the stated precision (double for MFX_F64, float for MFX_F32).
+ *  - Streams are passed as opaque pointers (cudaStream_t); NULL is the
+ *    legacy default stream.  vmult, diagonal and the vector calls are
+ *    asynchronous on that stream and allocate nothing.
+ *  - Errors never abort: every call returns an mfx_status; the message of
+ *    the last error of the calling thread is returned by mfx_last_error().
+ *    Asynchronous device faults surface at the next synchronising call.
+ *  - DoF indices are int32 (n_dofs < 2^31); sizes are int64.
+ */
+#ifndef MFX_H
+#define MFX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mfx_status;
+enum {
+  MFX_OK = 0,
+  MFX_EINVAL = -1,       /* bad argument (null pointer, size, range)          */
+  MFX_EUNSUPPORTED = -2, /* valid request this build does not implement        */
+  MFX_ENOMEM = -3,       /* device or host allocation failed                   */
+  MFX_ECUDA = -4,        /* a CUDA runtime call failed                         */
+  MFX_EMESH = -5,        /* invalid mesh: holes/overlaps, not 2:1 balanced     */
+  MFX_ETIMEOUT = -6,     /* a bounded device wait ran out                      */
+  MFX_EBUSY = -7,        /* no capacity (admission refused)                    */
+  MFX_NOT_CONVERGED = 1, /* iteration cap reached                              */
+  MFX_BREAKDOWN = 2      /* NaN/Inf or non-positive curvature p.Ap <= 0        */
+};
+
+typedef enum { MFX_F64 = 0, MFX_F32 = 1 } mfx_prec;
+
+enum { MFX_COEF_CONSTANT = 0, /* a = par[0]                                   */
+       MFX_COEF_TRIG = 1,     /* a = par[0] + par[1] sin(2 pi x) cos(2 pi y) z */
+       MFX_COEF_QPOINT = 2 }; /* a given at every quadrature point             */
+
+enum { MFX_PRECOND_JACOBI = 0, MFX_PRECOND_CHEBYSHEV = 1 };
+
+typedef struct mfx_mesh mfx_mesh;
+typedef struct mfx_op mfx_op;
+typedef void* mfx_stream; /* cudaStream_t */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mfx_last_error(void);
+/* Library version string. */
+const char* mfx_version(void);
+
+/*
+ * Structured box mesh of nx*ny*nz hexahedra (Sec. 3.1).
+ * vertices: host, (nx+1)(ny+1)(nz+1) x 3 doubles, lexicographic with x
+ * fastest; NULL means the unit cube lattice (i/nx, j/ny, l/nz).  Copied.
+ * Cells are lexicographic (x fastest); cell vertex v = a + 2b + 4c is the
+ * corner (a, b, c).  Every DoF on the box boundary is Dirichlet (u = 0).
+ * Errors: MFX_EINVAL for non-positive sizes or a null out pointer.
+ */
+mfx_status mfx_mesh_create_structured(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz,
+                                      const double* vertices);
+
+/*
+ * Octree mesh (local refinement with hanging nodes, Sec. 3.1, Fig. 2).
+ * coarse_vertices: as for the structured mesh (NULL = unit cube).
+ * leaves: host, n_leaves x 4 int32 (level, i, j, l), the leaf covering
+ * [i, i+1] x [j, j+1] x [l, l+1] in units of 1/(n 2^level) coarse cells;
+ * levels 0..8.  Leaves must tile the coarse box exactly and be 2:1
+ * balanced across faces and edges, else MFX_EMESH.  Cells are ordered by
+ * (coarse cell lexicographic, Morton order within the tree, x bit lowest);
+ * leaf vertices are the trilinear map of the coarse cell at the leaf's
+ * reference corners.  DoFs are numbered on first encounter (cells in order,
+ * local nodes lexicographic); coincident nodes share one DoF.  Hanging
+ * nodes are constrained to the coarse face (edge) nodes with Lagrange
+ * weights; Dirichlet takes precedence; Dirichlet masters and zero weights
+ * are dropped; masters are sorted by DoF.  Input arrays are copied.
+ */
+mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz,
+                                  const double* coarse_vertices, const int32_t* leaves,
+                                  int64_t n_leaves);
+void mfx_mesh_destroy(mfx_mesh* mesh);
+
+/*
+ * Host-only (no GPU needed): sizes of the DoF and constraint tables of the
+ * mesh at degree k (numbering and constraint rules as described above).
+ * Any output pointer may be NULL.
+ */
+mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n_cells, int64_t* n_dofs,
+                                int64_t* n_constrained, int64_t* n_masters);
+
+/*
+ * Host-only: the tables themselves, laid out as for mfx_get_tables below
+ * (caller-allocated host arrays of the sizes above; NULL skips a table).
+ * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k out of 1..8), MFX_EMESH.
+ */
+mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_dofs, int32_t* constrained,
+                           int64_t* cptr, int32_t* cmaster, double* cweight);
+
+typedef struct {
+  int32_t degree;        /* k, 1..8                                               */
+  int32_t n_q_1d;        /* quadrature points per direction; 0 or k+1 (only k+1)  */
+  int32_t coef_kind;     /* MFX_COEF_*                                            */
+  int32_t precisions;    /* bit 0: FP64 data, bit 1: FP32 data; 0 means both      */
+  double coef_par[2];    /* parameters of the coefficient                         */
+  const double* coef_qpoint; /* MFX_COEF_QPOINT: device, n_cells x n_q^3 doubles,
+                                q = q1 + n_q (q2 + n_q q3); read during create  */
+  int32_t cells_per_block;   /* 0 = autotuned default                             */
+  int32_t reserved;
+} mfx_op_desc;
+
+/*
+ * Build the operator: DoF tables and constraints on the host, then the
+ * per-quadrature-point geometry on the device in FP64 (Jacobian of the Q1
+ * map, det J, J^-1, coefficient at the physical point) merged into the
+ * symmetric 3x3 metric a |det J| w_q J^-1 J^-T (plus an FP32 copy), and the
+ * diagonal of the operator.  Synchronises the stream.
+ * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k > 8, n_q != k+1), MFX_EMESH,
+ * MFX_ENOMEM, MFX_ECUDA.
+ */
+mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc,
+                               mfx_stream stream);
+void mfx_operator_destroy(mfx_op* op);
+
+typedef struct {
+  int64_t n_dofs, n_cells, n_constrained, n_masters, n_hanging;
+  int64_t bytes_device; /* device memory owned by the operator */
+  int32_t degree, n_q_1d, structured, cells_per_block;
+} mfx_op_info;
+
+mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info);
+
+/*
+ * Host copies of the integer and constraint tables (for bit-exact checks).
+ * cell_dofs: n_cells x (k+1)^3 (local i1 + n (i2 + n i3)); constrained:
+ * n_constrained sorted DoFs; cptr: n_constrained + 1; cmaster, cweight:
+ * n_masters.  Any pointer may be NULL to skip that table.
+ */
+mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
+                          int32_t* cmaster, double* cweight);
+
+/*
+ * dst = K src (Sec. 3.6): per cell, gather with constraint resolution,
+ * interpolate to the Gauss points and take reference gradients by 1D
+ * contractions, apply the stored metric, integrate back with the
+ * transposed contractions, scatter-add; constrained rows copy src.
+ * src, dst: device, n_dofs entries of the precision, must not alias.
+ * Errors: MFX_EINVAL (null, precision not built), MFX_ECUDA (launch).
+ */
+mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, mfx_stream stream);
+
+/* diag = diagonal of K (1 on constrained rows), device, n_dofs entries. */
+mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream);
+
+/* Physical quadrature points, device, n_cells x n_q^3 x 3 doubles. */
+mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream);
+
+/*
+ * Right-hand side of the step-4 cell loop (Sec. 2.4): b_i = sum_q phi_i f_q
+ * |det J_q| w_q assembled and condensed (C^T b, 0 on constrained DoFs).
+ * fq: device, n_cells x n_q^3 doubles; b: device, n_dofs doubles.
+ */
+mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream);
+
+/*
+ * Fill constrained entries of x (device, FP64) from the free ones: hanging
+ * DoFs get their weighted masters, Dirichlet DoFs 0.
+ */
+mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream);
+
+/* ---------------------------------------------------------------- vectors */
+
+/*
+ * result[0] = sum_i a_i b_i, accumulated in FP64 in a fixed order (device
+ * scalar).  a, b: device vectors of n entries of the precision.  The
+ * reduction partials live in scratch memory owned by the operator, so
+ * calls on one operator must not overlap on the GPU.
+ */
+mfx_status mfx_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, const void* b,
+                   double* result, mfx_stream stream);
+
+/*
+ * Chebyshev-Jacobi preconditioner (smoother named in Sec. 3.5 and Sec. 6.1):
+ * z = p(D^-1 K) D^-1 r with 1 - lambda p(lambda) = T_m(s(lambda)) / T_m(s(0)),
+ * s(lambda) = (hi + lo - 2 lambda) / (hi - lo), m = degree >= 1, computed by
+ * m steps of the Chebyshev iteration from z = 0 (m - 1 operator products).
+ * r, z: device vectors of the precision (must not alias).  Uses operator
+ * workspace; calls on one operator must not overlap.
+ */
+mfx_status mfx_chebyshev(const mfx_op* op, mfx_prec prec, const void* r, void* z, int32_t degree,
+                         double lo, double hi, mfx_stream stream);
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+  double tol;            /* relative residual ||b - Kx|| <= tol ||b|| (default 1e-10) */
+  int32_t max_it;        /* iteration cap (outer cap for mixed), default 100000     */
+  int32_t precond;       /* MFX_PRECOND_JACOBI or MFX_PRECOND_CHEBYSHEV              */
+  int32_t cheb_degree;   /* Chebyshev degree (default 5)                             */
+  int32_t mixed;         /* 0: FP64 PCG; 1: FP32 PCG inside FP64 defect correction   */
+  double inner_tol;      /* inner relative tolerance for mixed (default 1e-4)        */
+  int32_t check_every;   /* convergence checked on the host every m iterations (0=auto) */
+  int32_t lanczos_steps; /* CG steps for the eigenvalue estimate (default 15)        */
+  double cheb_lo, cheb_hi; /* Chebyshev interval of D^-1 K; 0 = estimate            */
+  const double* lanczos_start; /* device start vector for the estimate; NULL = b     */
+  int32_t inner_max_it;  /* inner cap for mixed (default 10000)                      */
+  int32_t reserved;
+} mfx_solve_params;
+
+typedef struct {
+  int32_t status;        /* MFX_OK, MFX_NOT_CONVERGED or MFX_BREAKDOWN             */
+  int32_t iterations;    /* PCG iterations (FP64 solve) or outer corrections (mixed) */
+  int32_t inner_iterations; /* total FP32 PCG iterations (mixed)                    */
+  int32_t reserved;
+  double rel_residual;   /* final ||b - Kx|| / ||b|| in FP64                        */
+  double lambda_max;     /* eigenvalue estimate used for Chebyshev (0 if none)     */
+  double cheb_lo, cheb_hi;
+} mfx_solve_stats;
+
+/* Fill params with the defaults listed above. */
+void mfx_solve_params_default(mfx_solve_params* params);
+
+/*
+ * Solve K x = b (x0 = 0).  FP64 PCG with Jacobi or Chebyshev-Jacobi, or
+ * (mixed = 1) FP64 defect correction around an FP32 PCG (the single-
+ * precision solver with a double-precision correction of Sec. 6.1).  The
+ * Krylov loop runs on the device; the host reads a status word every
+ * check_every iterations.  b, x: device FP64.  Synchronises the stream.
+ */
+mfx_status mfx_solve(const mfx_op* op, const double* b, double* x, const mfx_solve_params* params,
+                     mfx_solve_stats* stats, mfx_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFX_H */

@@ -1,0 +1,397 @@
+// C-ABI entry points of libmfx (declared in include/mfx.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mfx_internal.h"
+
+namespace mfx {
+
+static thread_local std::string g_last_error;
+
+mfx_status set_error(mfx_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+mfx_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(MFX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
+                        const int32_t* skip) {
+  switch (op->n) {
+    case 2: return launch_vmult_n<2>(op, prec, src, dst, s, skip);
+    case 3: return launch_vmult_n<3>(op, prec, src, dst, s, skip);
+    case 4: return launch_vmult_n<4>(op, prec, src, dst, s, skip);
+    case 5: return launch_vmult_n<5>(op, prec, src, dst, s, skip);
+    case 6: return launch_vmult_n<6>(op, prec, src, dst, s, skip);
+    case 7: return launch_vmult_n<7>(op, prec, src, dst, s, skip);
+    case 8: return launch_vmult_n<8>(op, prec, src, dst, s, skip);
+    case 9: return launch_vmult_n<9>(op, prec, src, dst, s, skip);
+    default: return set_error(MFX_EUNSUPPORTED, "degree out of range");
+  }
+}
+
+void free_workspace(mfx_op* op);
+
+template <typename T>
+static mfx_status dev_alloc(mfx_op* op, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return MFX_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return set_error(MFX_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  op->bytes_device += (int64_t)(count * sizeof(T));
+  return MFX_OK;
+}
+
+static void destroy_op(mfx_op* op) {
+  if (!op) return;
+  free_workspace(op);
+  void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
+                  op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
+                  op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete op;
+}
+
+}  // namespace mfx
+
+using namespace mfx;
+
+#define MFX_TRY(x)                  \
+  do {                              \
+    mfx_status st_ = (x);           \
+    if (st_ != MFX_OK) {            \
+      destroy_op(op);               \
+      return st_;                   \
+    }                               \
+  } while (0)
+#define MFX_CUDA_OP(call)                          \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      mfx_status st_ = cuda_error(e_, #call);      \
+      destroy_op(op);                              \
+      return st_;                                  \
+    }                                              \
+  } while (0)
+
+extern "C" {
+
+const char* mfx_last_error(void) { return g_last_error.c_str(); }
+const char* mfx_version(void) { return "mfx 0.1 (sm_103a)"; }
+
+mfx_status mfx_mesh_create_structured(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz, const double* vertices) {
+  if (!out) return set_error(MFX_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(MFX_EINVAL, "mesh sizes must be positive");
+  auto* m = new (std::nothrow) mfx_mesh();
+  if (!m) return set_error(MFX_ENOMEM, "host allocation failed");
+  m->m.structured = true;
+  m->m.nx = nx;
+  m->m.ny = ny;
+  m->m.nz = nz;
+  const size_t nv = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  m->m.vertices.resize(3 * nv);
+  for (int l = 0; l <= nz; ++l)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        const size_t v = i + (size_t)(nx + 1) * (j + (size_t)(ny + 1) * l);
+        if (vertices) {
+          for (int d = 0; d < 3; ++d) m->m.vertices[3 * v + d] = vertices[3 * v + d];
+        } else {
+          m->m.vertices[3 * v + 0] = (double)i / nx;
+          m->m.vertices[3 * v + 1] = (double)j / ny;
+          m->m.vertices[3 * v + 2] = (double)l / nz;
+        }
+      }
+  *out = m;
+  return MFX_OK;
+}
+
+mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz, const double* coarse_vertices,
+                                  const int32_t* leaves, int64_t n_leaves) {
+  if (!out) return set_error(MFX_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || !leaves || n_leaves < 1) return set_error(MFX_EINVAL, "bad octree arguments");
+  mfx_mesh* m = nullptr;
+  mfx_status st = mfx_mesh_create_structured(&m, nx, ny, nz, coarse_vertices);
+  if (st != MFX_OK) return st;
+  m->m.structured = false;
+  m->m.leaves.assign(leaves, leaves + 4 * n_leaves);
+  st = octree_sort_and_check(&m->m);
+  if (st != MFX_OK) {
+    delete m;
+    return st;
+  }
+  *out = m;
+  return MFX_OK;
+}
+
+void mfx_mesh_destroy(mfx_mesh* mesh) { delete mesh; }
+
+mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) {
+  if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "null argument");
+  *out = nullptr;
+  const int k = desc->degree;
+  if (k < 1 || k > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
+  if (desc->n_q_1d != 0 && desc->n_q_1d != k + 1)
+    return set_error(MFX_EUNSUPPORTED, "only n_q_1d = k + 1 is implemented");
+  if (desc->coef_kind < MFX_COEF_CONSTANT || desc->coef_kind > MFX_COEF_QPOINT)
+    return set_error(MFX_EINVAL, "unknown coefficient kind");
+  if (desc->coef_kind == MFX_COEF_QPOINT && !desc->coef_qpoint)
+    return set_error(MFX_EINVAL, "MFX_COEF_QPOINT needs coef_qpoint");
+  cudaStream_t s = (cudaStream_t)stream;
+  mfx_op* op = new (std::nothrow) mfx_op();
+  if (!op) return set_error(MFX_ENOMEM, "host allocation failed");
+  op->k = k;
+  op->n = k + 1;
+  make_basis(k, &op->basis);
+  const int prec = desc->precisions ? desc->precisions : 3;
+  op->has_f64 = (prec & 1) != 0;
+  op->has_f32 = (prec & 2) != 0;
+  op->cells_per_block = desc->cells_per_block;
+  const Mesh& m = mesh->m;
+  op->nx = m.nx;
+  op->ny = m.ny;
+  op->nz = m.nz;
+  op->structured = m.structured;
+  const int n = op->n, n3 = n * n * n;
+  if (m.structured) {
+    op->n_cells = (int64_t)m.nx * m.ny * m.nz;
+    const int64_t Mx = (int64_t)k * m.nx + 1, My = (int64_t)k * m.ny + 1, Mz = (int64_t)k * m.nz + 1;
+    op->n_dofs = Mx * My * Mz;
+    if (op->n_dofs >= ((int64_t)1 << 31)) {
+      destroy_op(op);
+      return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
+    }
+    op->n_constrained = op->n_dofs - std::max<int64_t>(0, Mx - 2) * std::max<int64_t>(0, My - 2) *
+                                         std::max<int64_t>(0, Mz - 2);
+    MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size()));
+    MFX_CUDA_OP(cudaMemcpy(op->d_vertices, m.vertices.data(), m.vertices.size() * sizeof(double),
+                           cudaMemcpyHostToDevice));
+  } else {
+    MFX_TRY(octree_tables(m, k, &op->tables));
+    const OctreeTables& t = op->tables;
+    op->n_cells = t.n_cells;
+    op->n_dofs = t.n_dofs;
+    op->n_constrained = (int64_t)t.constrained.size();
+    op->n_masters = (int64_t)t.cmaster.size();
+    for (size_t r = 0; r < t.constrained.size(); ++r)
+      if (t.cptr[r + 1] > t.cptr[r]) ++op->n_hanging;
+    // encoded cell DoFs: constrained -> -(row + 1)
+    std::vector<int32_t> row_of(t.n_dofs, -1);
+    for (size_t r = 0; r < t.constrained.size(); ++r) row_of[t.constrained[r]] = (int32_t)r;
+    std::vector<int32_t> enc(t.cell_dofs.size());
+    std::vector<uint8_t> cell_hang(t.n_cells, 0);
+    for (size_t i = 0; i < enc.size(); ++i) {
+      const int32_t d = t.cell_dofs[i];
+      const int32_t r = row_of[d];
+      enc[i] = r < 0 ? d : -(r + 1);
+      if (r >= 0 && t.cptr[r + 1] > t.cptr[r]) cell_hang[i / n3] = 1;
+    }
+    std::vector<uint8_t> mask(t.n_dofs, 0);
+    for (int32_t c : t.constrained) mask[c] = 1;
+    std::vector<float> w32(t.cweight.begin(), t.cweight.end());
+    MFX_TRY(dev_alloc(op, &op->d_vertices, t.cell_vertices.size()));
+    MFX_TRY(dev_alloc(op, &op->d_cell_dofs, enc.size()));
+    MFX_TRY(dev_alloc(op, &op->d_cmask, mask.size()));
+    MFX_TRY(dev_alloc(op, &op->d_constrained, t.constrained.size()));
+    MFX_TRY(dev_alloc(op, &op->d_cptr, t.cptr.size()));
+    MFX_TRY(dev_alloc(op, &op->d_cmaster, std::max<size_t>(1, t.cmaster.size())));
+    MFX_TRY(dev_alloc(op, &op->d_cweight64, std::max<size_t>(1, t.cweight.size())));
+    MFX_TRY(dev_alloc(op, &op->d_cweight32, std::max<size_t>(1, w32.size())));
+    MFX_TRY(dev_alloc(op, &op->d_cell_hanging, cell_hang.size()));
+    MFX_CUDA_OP(cudaMemcpy(op->d_vertices, t.cell_vertices.data(), t.cell_vertices.size() * 8, cudaMemcpyHostToDevice));
+    MFX_CUDA_OP(cudaMemcpy(op->d_cell_dofs, enc.data(), enc.size() * 4, cudaMemcpyHostToDevice));
+    MFX_CUDA_OP(cudaMemcpy(op->d_cmask, mask.data(), mask.size(), cudaMemcpyHostToDevice));
+    if (!t.constrained.empty())
+      MFX_CUDA_OP(cudaMemcpy(op->d_constrained, t.constrained.data(), t.constrained.size() * 4, cudaMemcpyHostToDevice));
+    MFX_CUDA_OP(cudaMemcpy(op->d_cptr, t.cptr.data(), t.cptr.size() * 8, cudaMemcpyHostToDevice));
+    if (!t.cmaster.empty()) {
+      MFX_CUDA_OP(cudaMemcpy(op->d_cmaster, t.cmaster.data(), t.cmaster.size() * 4, cudaMemcpyHostToDevice));
+      MFX_CUDA_OP(cudaMemcpy(op->d_cweight64, t.cweight.data(), t.cweight.size() * 8, cudaMemcpyHostToDevice));
+      MFX_CUDA_OP(cudaMemcpy(op->d_cweight32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice));
+    }
+    MFX_CUDA_OP(cudaMemcpy(op->d_cell_hanging, cell_hang.data(), cell_hang.size(), cudaMemcpyHostToDevice));
+  }
+  const size_t nq = (size_t)op->n_cells * n3;
+  // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
+  MFX_TRY(dev_alloc(op, &op->d_metric64, 6 * nq));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, 6 * nq));
+  MFX_TRY(dev_alloc(op, &op->d_jxw, nq));
+  MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs)));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs)));
+  MFX_TRY(dev_alloc(op, &op->d_scalars, 64));
+  MFX_TRY(dev_alloc(op, &op->d_partials, 4096));
+  MFX_TRY(dev_alloc(op, &op->d_counter, 16));
+  MFX_CUDA_OP(cudaMemsetAsync(op->d_counter, 0, 16 * sizeof(unsigned int), s));
+  MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
+  MFX_TRY(launch_diagonal(op, s));
+  MFX_CUDA_OP(cudaStreamSynchronize(s));
+  *out = op;
+  return MFX_OK;
+}
+
+void mfx_operator_destroy(mfx_op* op) { destroy_op(op); }
+
+mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
+  if (!op || !info) return set_error(MFX_EINVAL, "null argument");
+  info->n_dofs = op->n_dofs;
+  info->n_cells = op->n_cells;
+  info->n_constrained = op->n_constrained;
+  info->n_masters = op->n_masters;
+  info->n_hanging = op->n_hanging;
+  info->bytes_device = op->bytes_device + (int64_t)op->work_bytes;
+  info->degree = op->k;
+  info->n_q_1d = op->n;
+  info->structured = op->structured ? 1 : 0;
+  info->cells_per_block = 256 / (op->n * op->n);
+  return MFX_OK;
+}
+
+static void structured_tables(int nx, int ny, int nz, int k, int32_t* cell_dofs, int32_t* constrained,
+                              int64_t* cptr) {
+  const int n = k + 1, n3 = n * n * n;
+  const int64_t Mx = (int64_t)k * nx + 1, My = (int64_t)k * ny + 1, Mz = (int64_t)k * nz + 1;
+  const int64_t C = (int64_t)nx * ny * nz;
+  if (cell_dofs) {
+    for (int64_t c = 0; c < C; ++c) {
+      const int64_t cx = c % nx, cy = (c / nx) % ny, cz = c / ((int64_t)nx * ny);
+      for (int i3 = 0; i3 < n; ++i3)
+        for (int i2 = 0; i2 < n; ++i2)
+          for (int i1 = 0; i1 < n; ++i1)
+            cell_dofs[c * n3 + i1 + n * (i2 + n * i3)] =
+                (int32_t)((cx * k + i1) + Mx * ((cy * k + i2) + My * (cz * k + i3)));
+    }
+  }
+  int64_t t = 0;
+  for (int64_t L = 0; L < Mz; ++L)
+    for (int64_t J = 0; J < My; ++J)
+      for (int64_t I = 0; I < Mx; ++I)
+        if (I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1) {
+          if (constrained) constrained[t] = (int32_t)(I + Mx * (J + My * L));
+          if (cptr) cptr[t] = 0;
+          ++t;
+        }
+  if (cptr) cptr[t] = 0;
+}
+
+static void copy_tables(const OctreeTables& tb, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
+                        int32_t* cmaster, double* cweight) {
+  if (cell_dofs) std::copy(tb.cell_dofs.begin(), tb.cell_dofs.end(), cell_dofs);
+  if (constrained) std::copy(tb.constrained.begin(), tb.constrained.end(), constrained);
+  if (cptr) std::copy(tb.cptr.begin(), tb.cptr.end(), cptr);
+  if (cmaster) std::copy(tb.cmaster.begin(), tb.cmaster.end(), cmaster);
+  if (cweight) std::copy(tb.cweight.begin(), tb.cweight.end(), cweight);
+}
+
+mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n_cells, int64_t* n_dofs,
+                                int64_t* n_constrained, int64_t* n_masters) {
+  if (!mesh) return set_error(MFX_EINVAL, "null mesh");
+  if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
+  const Mesh& m = mesh->m;
+  int64_t C, N, NC, NM;
+  if (m.structured) {
+    const int64_t k = degree, Mx = k * m.nx + 1, My = k * m.ny + 1, Mz = k * m.nz + 1;
+    C = (int64_t)m.nx * m.ny * m.nz;
+    N = Mx * My * Mz;
+    NC = N - (Mx - 2) * (My - 2) * (Mz - 2);
+    NM = 0;
+  } else {
+    OctreeTables t;
+    mfx_status st = octree_tables(m, degree, &t);
+    if (st != MFX_OK) return st;
+    C = t.n_cells;
+    N = t.n_dofs;
+    NC = (int64_t)t.constrained.size();
+    NM = (int64_t)t.cmaster.size();
+  }
+  if (n_cells) *n_cells = C;
+  if (n_dofs) *n_dofs = N;
+  if (n_constrained) *n_constrained = NC;
+  if (n_masters) *n_masters = NM;
+  return MFX_OK;
+}
+
+mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_dofs, int32_t* constrained,
+                           int64_t* cptr, int32_t* cmaster, double* cweight) {
+  if (!mesh) return set_error(MFX_EINVAL, "null mesh");
+  if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
+  const Mesh& m = mesh->m;
+  if (m.structured) {
+    structured_tables(m.nx, m.ny, m.nz, degree, cell_dofs, constrained, cptr);
+    return MFX_OK;
+  }
+  OctreeTables t;
+  mfx_status st = octree_tables(m, degree, &t);
+  if (st != MFX_OK) return st;
+  copy_tables(t, cell_dofs, constrained, cptr, cmaster, cweight);
+  return MFX_OK;
+}
+
+mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
+                          int32_t* cmaster, double* cweight) {
+  if (!op) return set_error(MFX_EINVAL, "null operator");
+  if (op->structured) {
+    structured_tables(op->nx, op->ny, op->nz, op->k, cell_dofs, constrained, cptr);
+    return MFX_OK;
+  }
+  copy_tables(op->tables, cell_dofs, constrained, cptr, cmaster, cweight);
+  return MFX_OK;
+}
+
+mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, mfx_stream stream) {
+  if (!op || !src || !dst) return set_error(MFX_EINVAL, "mfx_vmult: null argument");
+  if (src == dst) return set_error(MFX_EINVAL, "mfx_vmult: src and dst must not alias");
+  if ((prec == MFX_F64 && !op->has_f64) || (prec == MFX_F32 && !op->has_f32) || (prec != MFX_F64 && prec != MFX_F32))
+    return set_error(MFX_EINVAL, "mfx_vmult: precision not built for this operator");
+  return launch_vmult(op, prec, src, dst, (cudaStream_t)stream);
+}
+
+mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream) {
+  if (!op || !diag) return set_error(MFX_EINVAL, "mfx_diagonal: null argument");
+  const void* srcp = prec == MFX_F64 ? (const void*)op->d_diag64 : (const void*)op->d_diag32;
+  if (!srcp) return set_error(MFX_EINVAL, "mfx_diagonal: precision not built for this operator");
+  const size_t bytes = (size_t)op->n_dofs * (prec == MFX_F64 ? 8 : 4);
+  MFX_CUDA_TRY(cudaMemcpyAsync(diag, srcp, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return MFX_OK;
+}
+
+mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream) {
+  if (!op || !xq) return set_error(MFX_EINVAL, "mfx_quadrature_points: null argument");
+  return launch_qpoints(op, xq, (cudaStream_t)stream);
+}
+
+mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream) {
+  if (!op || !fq || !b) return set_error(MFX_EINVAL, "mfx_rhs: null argument");
+  return launch_rhs(op, fq, b, (cudaStream_t)stream);
+}
+
+mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream) {
+  if (!op || !x) return set_error(MFX_EINVAL, "mfx_distribute: null argument");
+  return launch_distribute(op, x, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,393 @@
+// Setup kernels: quadrature-point geometry (FP64), right-hand side,
+// diagonal and constraint distribution.
+//
+// Geometry (Sec. 3.4: mapping + quadrature; Sec. 3.6: what to precompute):
+// for every cell and Gauss point xi_q the trilinear map x(xi) of the cell's
+// eight vertices gives J = dx/dxi, det J and J^-1; with the coefficient at
+// the physical point the operator needs only the symmetric matrix
+//     G_q = a(x_q) |det J_q| w_q J_q^-1 J_q^-T
+// (six entries), stored per cell as [6][n^3] in FP64 and FP32.
+#include <algorithm>
+#include <cmath>
+
+#include "mfx_internal.h"
+
+namespace mfx {
+
+struct GeoArgs {
+  double xq[kMaxN], wq[kMaxN];
+  double S[kMaxN * kMaxN], Sd[kMaxN * kMaxN];
+  int n, k;
+  int64_t n_cells;
+  bool structured;
+  int nx, ny, nz;
+  const double* vertices;  // structured lattice or cell x 8 x 3
+  int coef_kind;
+  double par0, par1;
+  const double* coef_q;
+};
+
+__device__ __forceinline__ void cell_vertices(const GeoArgs& g, int64_t cell, double V[8][3]) {
+  if (g.structured) {
+    const int cx = (int)(cell % g.nx);
+    const int64_t rest = cell / g.nx;
+    const int cy = (int)(rest % g.ny), cz = (int)(rest / g.ny);
+    for (int v = 0; v < 8; ++v) {
+      const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
+      const int64_t idx = (cx + a) + (int64_t)(g.nx + 1) * ((cy + b) + (int64_t)(g.ny + 1) * (cz + c));
+      for (int d = 0; d < 3; ++d) V[v][d] = g.vertices[3 * idx + d];
+    }
+  } else {
+    for (int v = 0; v < 8; ++v)
+      for (int d = 0; d < 3; ++d) V[v][d] = g.vertices[cell * 24 + 3 * v + d];
+  }
+}
+
+// Trilinear map at reference point xi: x and J[i][j] = dx_i / dxi_j.
+__device__ __forceinline__ void q1_map(const double V[8][3], const double xi[3], double x[3], double J[3][3]) {
+  for (int i = 0; i < 3; ++i) {
+    x[i] = 0.0;
+    for (int j = 0; j < 3; ++j) J[i][j] = 0.0;
+  }
+  for (int v = 0; v < 8; ++v) {
+    const int c[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+    double N[3], dN[3];
+    for (int d = 0; d < 3; ++d) {
+      N[d] = c[d] ? xi[d] : 1.0 - xi[d];
+      dN[d] = c[d] ? 1.0 : -1.0;
+    }
+    const double sh = N[0] * N[1] * N[2];
+    const double gr[3] = {dN[0] * N[1] * N[2], N[0] * dN[1] * N[2], N[0] * N[1] * dN[2]};
+    for (int i = 0; i < 3; ++i) {
+      x[i] += sh * V[v][i];
+      for (int j = 0; j < 3; ++j) J[i][j] += V[v][i] * gr[j];
+    }
+  }
+}
+
+__device__ __forceinline__ double invert3(const double J[3][3], double Ji[3][3]) {
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const double id = 1.0 / det;
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+__global__ void geometry_kernel(const __grid_constant__ GeoArgs g, double* __restrict__ m64,
+                                float* __restrict__ m32, double* __restrict__ jxw) {
+  const int n = g.n, n3 = n * n * n;
+  const int64_t total = g.n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int q = (int)(idx - cell * n3);
+    const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
+    double V[8][3];
+    cell_vertices(g, cell, V);
+    const double xi[3] = {g.xq[q1], g.xq[q2], g.xq[q3]};
+    double x[3], J[3][3], Ji[3][3];
+    q1_map(V, xi, x, J);
+    const double det = invert3(J, Ji);
+    double a;
+    if (g.coef_kind == MFX_COEF_CONSTANT)
+      a = g.par0;
+    else if (g.coef_kind == MFX_COEF_TRIG)
+      a = g.par0 + g.par1 * sinpi(2.0 * x[0]) * cospi(2.0 * x[1]) * x[2];
+    else
+      a = g.coef_q[idx];
+    const double w = g.wq[q1] * g.wq[q2] * g.wq[q3];
+    const double dx = fabs(det) * w;
+    const double f = a * dx;
+    double G[6];
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+      const int r = ia[e], c = ib[e];
+      G[e] = f * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
+    }
+    const int64_t base = cell * 6 * n3 + q;
+    for (int e = 0; e < 6; ++e) {
+      if (m64) m64[base + (int64_t)e * n3] = G[e];
+      if (m32) m32[base + (int64_t)e * n3] = (float)G[e];
+    }
+    if (jxw) jxw[idx] = dx;
+  }
+}
+
+__global__ void qpoints_kernel(const __grid_constant__ GeoArgs g, double* __restrict__ out) {
+  const int n = g.n, n3 = n * n * n;
+  const int64_t total = g.n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int q = (int)(idx - cell * n3);
+    double V[8][3];
+    cell_vertices(g, cell, V);
+    const double xi[3] = {g.xq[q % n], g.xq[(q / n) % n], g.xq[q / (n * n)]};
+    double x[3], J[3][3];
+    q1_map(V, xi, x, J);
+    for (int d = 0; d < 3; ++d) out[3 * idx + d] = x[d];
+  }
+}
+
+// Global DoF of local node (i1, i2, i3) and its constraint class.
+struct DofView {
+  bool structured;
+  int nx, ny, k, Mx, My, Mz, n;
+  const int32_t* cell_dofs;
+  const int64_t* cptr;
+  const int32_t* cmaster;
+  const double* cweight;
+};
+
+// Calls f(dof, weight) for every free DoF the local node expands to.
+template <typename F>
+__device__ __forceinline__ void expand_node(const DofView& v, int64_t cell, int i1, int i2, int i3, F f) {
+  if (v.structured) {
+    const int cx = (int)(cell % v.nx);
+    const int64_t rest = cell / v.nx;
+    const int cy = (int)(rest % v.ny), cz = (int)(rest / v.ny);
+    const int I = cx * v.k + i1, J = cy * v.k + i2, L = cz * v.k + i3;
+    if (I == 0 || I == v.Mx - 1 || J == 0 || J == v.My - 1 || L == 0 || L == v.Mz - 1) return;
+    f((int64_t)I + (int64_t)v.Mx * (J + (int64_t)v.My * L), 1.0);
+  } else {
+    const int32_t e = v.cell_dofs[cell * v.n * v.n * v.n + (i3 * v.n + i2) * v.n + i1];
+    if (e >= 0) {
+      f((int64_t)e, 1.0);
+    } else {
+      const int32_t row = -e - 1;
+      for (int64_t p = v.cptr[row]; p < v.cptr[row + 1]; ++p) f((int64_t)v.cmaster[p], v.cweight[p]);
+    }
+  }
+}
+
+__global__ void rhs_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ fq,
+                           const double* __restrict__ jxw, double* __restrict__ b) {
+  const int n = g.n, n3 = n * n * n;
+  const int64_t total = g.n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int i = (int)(idx - cell * n3);
+    const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+    double s = 0.0;
+    for (int q = 0; q < n3; ++q) {
+      const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
+      const double phi = g.S[q1 * n + i1] * g.S[q2 * n + i2] * g.S[q3 * n + i3];
+      s += phi * fq[cell * n3 + q] * jxw[cell * n3 + q];
+    }
+    expand_node(v, cell, i1, i2, i3, [&](int64_t dof, double w) { atomicAdd(b + dof, w * s); });
+  }
+}
+
+// Element entry A_ij = sum_q grad_ref phi_i^T G_q grad_ref phi_j from the stored FP64 metric.
+__device__ double element_entry(const GeoArgs& g, const double* __restrict__ m64, int64_t cell, int i, int j) {
+  const int n = g.n, n3 = n * n * n;
+  const int a1 = i % n, a2 = (i / n) % n, a3 = i / (n * n);
+  const int b1 = j % n, b2 = (j / n) % n, b3 = j / (n * n);
+  const double* G = m64 + cell * 6 * n3;
+  double s = 0.0;
+  for (int q = 0; q < n3; ++q) {
+    const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
+    const double Pi[3] = {g.Sd[q1 * n + a1] * g.S[q2 * n + a2] * g.S[q3 * n + a3],
+                          g.S[q1 * n + a1] * g.Sd[q2 * n + a2] * g.S[q3 * n + a3],
+                          g.S[q1 * n + a1] * g.S[q2 * n + a2] * g.Sd[q3 * n + a3]};
+    const double Pj[3] = {g.Sd[q1 * n + b1] * g.S[q2 * n + b2] * g.S[q3 * n + b3],
+                          g.S[q1 * n + b1] * g.Sd[q2 * n + b2] * g.S[q3 * n + b3],
+                          g.S[q1 * n + b1] * g.S[q2 * n + b2] * g.Sd[q3 * n + b3]};
+    const double G00 = G[q], G01 = G[n3 + q], G02 = G[2 * n3 + q];
+    const double G11 = G[3 * n3 + q], G12 = G[4 * n3 + q], G22 = G[5 * n3 + q];
+    s += Pi[0] * (G00 * Pj[0] + G01 * Pj[1] + G02 * Pj[2]) + Pi[1] * (G01 * Pj[0] + G11 * Pj[1] + G12 * Pj[2]) +
+         Pi[2] * (G02 * Pj[0] + G12 * Pj[1] + G22 * Pj[2]);
+  }
+  return s;
+}
+
+// diag(C^T A C) on free DoFs: sum over cells and local pairs (i, j) sharing a master m of
+// w_im w_jm A_ij; cells without hanging nodes only need j = i.
+__global__ void diagonal_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ m64,
+                                const uint8_t* __restrict__ cell_hanging, double* __restrict__ diag) {
+  const int n = g.n, n3 = n * n * n;
+  const int64_t total = g.n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int i = (int)(idx - cell * n3);
+    const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+    const bool hang = cell_hanging && cell_hanging[cell];
+    if (!hang) {
+      const double aii = element_entry(g, m64, cell, i, i);
+      expand_node(v, cell, i1, i2, i3, [&](int64_t dof, double w) { atomicAdd(diag + dof, w * w * aii); });
+      continue;
+    }
+    for (int j = 0; j < n3; ++j) {
+      const int j1 = j % n, j2 = (j / n) % n, j3 = j / (n * n);
+      double aij = 0.0;
+      bool have = false;
+      expand_node(v, cell, i1, i2, i3, [&](int64_t mi, double wi) {
+        expand_node(v, cell, j1, j2, j3, [&](int64_t mj, double wj) {
+          if (mi == mj) {
+            if (!have) {
+              aij = element_entry(g, m64, cell, i, j);
+              have = true;
+            }
+            atomicAdd(diag + mi, wi * wj * aij);
+          }
+        });
+      });
+    }
+  }
+}
+
+template <typename Real>
+__global__ void diag_finish_kernel(int64_t n_dofs, bool structured, int Mx, int My, int Mz,
+                                   const uint8_t* __restrict__ cmask, const double* __restrict__ d,
+                                   double* __restrict__ d64, float* __restrict__ d32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dofs; i += (int64_t)gridDim.x * blockDim.x) {
+    bool c;
+    if (structured) {
+      const int64_t I = i % Mx, rest = i / Mx, J = rest % My, L = rest / My;
+      c = I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1;
+    } else {
+      c = cmask[i] != 0;
+    }
+    const double val = c ? 1.0 : d[i];
+    if (d64) d64[i] = val;
+    if (d32) d32[i] = (float)val;
+  }
+}
+
+__global__ void distribute_kernel(int64_t n_dofs, bool structured, int Mx, int My, int Mz, int64_t n_constrained,
+                                  const int32_t* __restrict__ constrained, const int64_t* __restrict__ cptr,
+                                  const int32_t* __restrict__ cmaster, const double* __restrict__ cweight,
+                                  double* __restrict__ x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (structured) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dofs; i += stride) {
+      const int64_t I = i % Mx, rest = i / Mx, J = rest % My, L = rest / My;
+      if (I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1) x[i] = 0.0;
+    }
+    return;
+  }
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_constrained; t += stride) {
+    double s = 0.0;
+    for (int64_t p = cptr[t]; p < cptr[t + 1]; ++p) s += cweight[p] * x[cmaster[p]];
+    x[constrained[t]] = s;
+  }
+}
+
+static GeoArgs geo_args(const mfx_op* op) {
+  GeoArgs g;
+  const int n = op->n;
+  for (int i = 0; i < n; ++i) {
+    g.xq[i] = op->basis.xq[i];
+    g.wq[i] = op->basis.wq[i];
+  }
+  for (int i = 0; i < n * n; ++i) {
+    g.S[i] = op->basis.S[i];
+    g.Sd[i] = op->basis.Sd[i];
+  }
+  g.n = n;
+  g.k = op->k;
+  g.n_cells = op->n_cells;
+  g.structured = op->structured;
+  g.nx = op->nx;
+  g.ny = op->ny;
+  g.nz = op->nz;
+  g.vertices = op->d_vertices;
+  g.coef_kind = MFX_COEF_CONSTANT;
+  g.par0 = 1.0;
+  g.par1 = 0.0;
+  g.coef_q = nullptr;
+  return g;
+}
+
+static DofView dof_view(const mfx_op* op) {
+  DofView v;
+  v.structured = op->structured;
+  v.nx = op->nx;
+  v.ny = op->ny;
+  v.k = op->k;
+  v.Mx = op->k * op->nx + 1;
+  v.My = op->k * op->ny + 1;
+  v.Mz = op->k * op->nz + 1;
+  v.n = op->n;
+  v.cell_dofs = op->d_cell_dofs;
+  v.cptr = op->d_cptr;
+  v.cmaster = op->d_cmaster;
+  v.cweight = op->d_cweight64;
+  return v;
+}
+
+static int grid_for(int64_t work) {
+  const int64_t b = (work + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)device_sm_count() * 16));
+}
+
+mfx_status launch_geometry(mfx_op* op, int coef_kind, const double* par, const double* coef_q, cudaStream_t s) {
+  GeoArgs g = geo_args(op);
+  g.coef_kind = coef_kind;
+  g.par0 = par[0];
+  g.par1 = par[1];
+  g.coef_q = coef_q;
+  const int64_t work = op->n_cells * op->n * op->n * op->n;
+  geometry_kernel<<<grid_for(work), 256, 0, s>>>(g, op->d_metric64, op->d_metric32, op->d_jxw);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s) {
+  GeoArgs g = geo_args(op);
+  const int64_t work = op->n_cells * op->n * op->n * op->n;
+  qpoints_kernel<<<grid_for(work), 256, 0, s>>>(g, xq);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s) {
+  GeoArgs g = geo_args(op);
+  MFX_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * op->n_dofs, s));
+  const int64_t work = op->n_cells * op->n * op->n * op->n;
+  rhs_kernel<<<grid_for(work), 256, 0, s>>>(g, dof_view(op), fq, op->d_jxw, b);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
+  GeoArgs g = geo_args(op);
+  double* tmp = nullptr;
+  MFX_CUDA_TRY(cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(1, op->n_dofs), s));
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(double) * op->n_dofs, s);
+  if (e == cudaSuccess) {
+    const int64_t work = op->n_cells * op->n * op->n * op->n;
+    diagonal_kernel<<<grid_for(work), 256, 0, s>>>(g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp);
+    diag_finish_kernel<double><<<grid_for(op->n_dofs), 256, 0, s>>>(
+        op->n_dofs, op->structured, op->k * op->nx + 1, op->k * op->ny + 1, op->k * op->nz + 1, op->d_cmask, tmp,
+        op->d_diag64, op->d_diag32);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(tmp, s);
+  if (e != cudaSuccess) return cuda_error(e, "diagonal");
+  return MFX_OK;
+}
+
+mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s) {
+  const int64_t work = op->structured ? op->n_dofs : op->n_constrained;
+  if (work == 0) return MFX_OK;
+  distribute_kernel<<<grid_for(work), 256, 0, s>>>(op->n_dofs, op->structured, op->k * op->nx + 1,
+                                                   op->k * op->ny + 1, op->k * op->nz + 1, op->n_constrained,
+                                                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, x);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+}  // namespace mfx

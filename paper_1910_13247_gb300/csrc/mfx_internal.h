@@ -1,0 +1,136 @@
+// Internal declarations of libmfx (host side and kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfx.h"
+
+namespace mfx {
+
+constexpr int kMaxDegree = 8;
+constexpr int kMaxN = kMaxDegree + 1;
+
+// ---------------------------------------------------------------- errors
+mfx_status set_error(mfx_status code, const std::string& msg);
+mfx_status cuda_error(cudaError_t e, const char* where);
+#define MFX_CUDA_TRY(call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::mfx::cuda_error(e_, #call); \
+  } while (0)
+
+// ----------------------------------------------------------- 1D rules
+// Gauss-Legendre points/weights on [0,1] and Gauss-Lobatto nodes on [0,1].
+void gauss_legendre(int n, double* x, double* w);
+void gauss_lobatto(int k, double* x);
+double lagrange_value(int n, const double* nodes, int j, double x);
+double lagrange_derivative(int n, const double* nodes, int j, double x);
+
+// Tables used by the kernels for degree k with n = k + 1 Gauss points:
+//   S[q][j]  = l_j(xi_q)   (GLL Lagrange basis at Gauss points)
+//   D[q][p]  = L_p'(xi_q)  (derivative of the Lagrange basis on the Gauss points)
+//   Sd[q][j] = l_j'(xi_q)  (derivative of the GLL basis at Gauss points)
+struct BasisTables {
+  int k, n;
+  double gll[kMaxN], xq[kMaxN], wq[kMaxN];
+  double S[kMaxN * kMaxN], D[kMaxN * kMaxN], Sd[kMaxN * kMaxN];
+};
+void make_basis(int k, BasisTables* t);
+
+// ----------------------------------------------------------------- mesh
+struct Mesh {
+  bool structured = true;
+  int nx = 0, ny = 0, nz = 0;
+  std::vector<double> vertices;       // structured lattice or coarse lattice
+  std::vector<int32_t> leaves;        // octree: sorted leaves, 4 per leaf
+  int max_level = 0;
+};
+
+// DoF tables of an octree mesh (host).
+struct OctreeTables {
+  int64_t n_cells = 0, n_dofs = 0;
+  std::vector<double> cell_vertices;   // n_cells x 8 x 3
+  std::vector<int32_t> cell_dofs;      // n_cells x n^3
+  std::vector<int32_t> constrained;    // sorted
+  std::vector<int64_t> cptr;           // n_constrained + 1
+  std::vector<int32_t> cmaster;
+  std::vector<double> cweight;
+};
+mfx_status octree_sort_and_check(Mesh* m);
+mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out);
+
+// ------------------------------------------------------------- operator
+struct DeviceArray {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mfx
+
+struct mfx_mesh {
+  mfx::Mesh m;
+};
+
+struct mfx_op {
+  int k = 0, n = 0;
+  int64_t n_cells = 0, n_dofs = 0, n_constrained = 0, n_masters = 0, n_hanging = 0;
+  bool structured = true;
+  int nx = 0, ny = 0, nz = 0;             // structured cells per direction
+  int cells_per_block = 0;
+  bool has_f64 = false, has_f32 = false;
+  mfx::BasisTables basis;
+  // host tables (octree) or empty (structured)
+  mfx::OctreeTables tables;
+  // device data
+  double* d_vertices = nullptr;      // structured: lattice (nx+1)(ny+1)(nz+1) x 3; else cell x 8 x 3
+  double* d_metric64 = nullptr;      // n_cells x 6 x n^3
+  float* d_metric32 = nullptr;
+  double* d_jxw = nullptr;           // n_cells x n^3 (for the right-hand side)
+  int32_t* d_cell_dofs = nullptr;    // octree: encoded cell DoFs (n_cells x n^3)
+  uint8_t* d_cmask = nullptr;        // octree: 1 on constrained DoFs
+  int32_t* d_constrained = nullptr;  // octree
+  int64_t* d_cptr = nullptr;
+  int32_t* d_cmaster = nullptr;
+  double* d_cweight64 = nullptr;
+  float* d_cweight32 = nullptr;
+  uint8_t* d_cell_hanging = nullptr; // octree: 1 if a cell touches a hanging node
+  double* d_diag64 = nullptr;
+  float* d_diag32 = nullptr;
+  // solver workspace (allocated at create)
+  void* d_work = nullptr;
+  size_t work_bytes = 0;
+  double* d_scalars = nullptr;       // device scalars for reductions / solver state
+  double* d_partials = nullptr;      // reduction partials
+  unsigned int* d_counter = nullptr; // last-block reduction counter
+  int64_t bytes_device = 0;
+};
+
+namespace mfx {
+
+// Geometry precompute (FP64) and related setup kernels (geometry.cu).
+mfx_status launch_geometry(mfx_op* op, int coef_kind, const double* par, const double* coef_q,
+                           cudaStream_t s);
+mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s);
+mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s);
+mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
+mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
+
+int device_sm_count();
+
+// vmult (vmult_k*.cu): one launcher per degree.
+mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
+                        const int32_t* skip = nullptr);
+template <int N>
+mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
+                          const int32_t* skip);
+
+// vector kernels (vector.cu)
+mfx_status launch_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, const void* b,
+                      double* result, cudaStream_t s);
+int reduction_blocks(int64_t n);
+
+}  // namespace mfx

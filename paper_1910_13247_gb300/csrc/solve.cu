@@ -1,0 +1,709 @@
+// CG / Chebyshev vector kernels and the solve drivers.
+//
+// Krylov scalars live on the device (SolveState); every reduction is a
+// two-stage deterministic sum (per-CTA partials, then the last CTA to
+// finish adds them in CTA order and updates the scalars), accumulated in
+// FP64 whatever the vector precision.  Every kernel of an iteration returns
+// immediately once the state says "done", so the host can queue a chunk of
+// iterations (captured once as a CUDA graph) and only read the status word
+// between chunks.
+//
+// Algorithms (readings of the paper: CG with a Jacobi or Chebyshev-Jacobi
+// preconditioner, Sec. 3.5 / Sec. 6.1; single-precision inner solver with
+// double-precision correction, Sec. 6.1):
+//   PCG: x0 = 0, r = b, z = P r, p = z; alpha = (r,z)/(p,Kp); x += alpha p;
+//        r -= alpha Kp; stop when ||r||_2 <= tol ||b||_2; beta = (r+,z+)/(r,z);
+//        p = z+ + beta p.
+//   Chebyshev(m) on [lo, hi] for D^-1 K: theta = (hi+lo)/2, delta = (hi-lo)/2,
+//        sigma = theta/delta, rho_0 = 1/sigma; d = D^-1 r / theta, z = d;
+//        for i = 1..m-1: rho_i = 1/(2 sigma - rho_{i-1});
+//        d = rho_i rho_{i-1} d + 2 rho_i / delta D^-1 (r - K z); z += d.
+//   lambda_max: largest eigenvalue of the Lanczos tridiagonal built from
+//        the first CG coefficients (T_ii = 1/a_i + b_{i-1}/a_{i-1},
+//        T_i,i+1 = sqrt(b_i)/a_i), by Sturm-sequence bisection.
+//   Mixed: x = 0; repeat r = b - K64 x (FP64), stop if ||r|| <= tol ||b||;
+//        solve K32 d = r/||r|| to inner_tol with FP32 PCG; x += ||r|| d.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "mfx_internal.h"
+
+namespace mfx {
+
+constexpr int kRedThreads = 256;
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxLanczos = 128;
+
+struct SolveState {
+  double rz, pq, rr, bb, tol2, alpha, beta, pad0;
+  int32_t done, status, it, max_it;
+  int32_t record, pad1, pad2, pad3;
+  double lan_alpha[kMaxLanczos], lan_beta[kMaxLanczos];
+};
+
+int reduction_blocks(int64_t n) {
+  const int64_t b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, std::min(kMaxRedBlocks, device_sm_count() * 4)));
+}
+
+// Block sum of NV values; thread 0 gets the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kRedThreads / 32];
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j][warp] = v[j];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      v[j] = lane < kRedThreads / 32 ? sh[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    }
+  }
+}
+
+// Writes the CTA partials; returns true in the last CTA, whose thread 0 then holds the totals.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter) {
+  block_sum<NV>(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) partials[blockIdx.x * NV + j] = v[j];
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[b * NV + j];
+      v[j] = s;
+    }
+    *counter = 0u;
+  }
+  return true;
+}
+
+template <typename Real>
+__global__ void dot_kernel(int64_t n, const Real* __restrict__ a, const Real* __restrict__ b, double* result,
+                           double* partials, unsigned int* counter) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)a[i] * (double)b[i];
+  if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) *result = v[0];
+}
+
+// PCG start: x = 0, r = b, bb = (b,b); with Jacobi also rz = (r, D^-1 r) and p = D^-1 r.
+template <typename Real>
+__global__ void cg_init_kernel(int64_t n, const Real* __restrict__ b, Real* __restrict__ x, Real* __restrict__ r,
+                               Real* __restrict__ p, const Real* __restrict__ dinv, bool jacobi, SolveState* st,
+                               double* partials, unsigned int* counter) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Real bi = b[i];
+    x[i] = Real(0);
+    r[i] = bi;
+    v[0] += (double)bi * (double)bi;
+    if (jacobi) {
+      const Real z = dinv[i] * bi;
+      p[i] = z;
+      v[1] += (double)bi * (double)z;
+    }
+  }
+  if (grid_sum<2>(v, partials, counter) && threadIdx.x == 0) {
+    st->bb = v[0];
+    st->rr = v[0];
+    st->rz = v[1];
+    st->it = 0;
+    st->status = MFX_OK;
+    st->done = (v[0] == 0.0) ? 1 : 0;
+    if (!isfinite(v[0])) {
+      st->done = 1;
+      st->status = MFX_BREAKDOWN;
+    }
+  }
+}
+
+// pq = (p, q); alpha = rz / pq.
+template <typename Real>
+__global__ void cg_pq_kernel(int64_t n, const Real* __restrict__ p, const Real* __restrict__ q, SolveState* st,
+                             double* partials, unsigned int* counter) {
+  if (st->done) return;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)p[i] * (double)q[i];
+  if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) {
+    st->pq = v[0];
+    if (!(v[0] > 0.0) || !isfinite(v[0])) {
+      st->status = MFX_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / v[0];
+      if (st->record && st->it < kMaxLanczos) st->lan_alpha[st->it] = st->alpha;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; rr = (r, r); with Jacobi also rz+ = (r, D^-1 r) and beta.
+template <typename Real>
+__global__ void cg_update_kernel(int64_t n, Real* __restrict__ x, Real* __restrict__ r, const Real* __restrict__ p,
+                                 const Real* __restrict__ q, const Real* __restrict__ dinv, bool jacobi,
+                                 SolveState* st, double* partials, unsigned int* counter) {
+  if (st->done) return;
+  const Real alpha = (Real)st->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const Real ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    v[0] += (double)ri * (double)ri;
+    if (jacobi) v[1] += (double)ri * (double)(dinv[i] * ri);
+  }
+  if (grid_sum<2>(v, partials, counter) && threadIdx.x == 0) {
+    st->rr = v[0];
+    st->it += 1;
+    if (!isfinite(v[0])) {
+      st->status = MFX_BREAKDOWN;
+      st->done = 1;
+    } else if (v[0] <= st->tol2 * st->bb) {
+      st->status = MFX_OK;
+      st->done = 1;
+    } else if (st->it >= st->max_it) {
+      st->status = MFX_NOT_CONVERGED;
+      st->done = 1;
+    }
+    if (jacobi) {
+      st->beta = v[1] / st->rz;
+      st->rz = v[1];
+      if (st->record && st->it - 1 < kMaxLanczos) st->lan_beta[st->it - 1] = st->beta;
+    }
+  }
+}
+
+// rz+ = (r, z); beta = rz+ / rz (Chebyshev-preconditioned CG).
+template <typename Real>
+__global__ void cg_rz_kernel(int64_t n, const Real* __restrict__ r, const Real* __restrict__ z, SolveState* st,
+                             double* partials, unsigned int* counter) {
+  if (st->done) return;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)r[i] * (double)z[i];
+  if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) {
+    st->beta = v[0] / st->rz;
+    st->rz = v[0];
+  }
+}
+
+// p = z + beta p, with z = D^-1 r (jacobi) or z given.
+template <typename Real>
+__global__ void cg_p_kernel(int64_t n, Real* __restrict__ p, const Real* __restrict__ r,
+                            const Real* __restrict__ dinv, const Real* __restrict__ z, const SolveState* st) {
+  if (st->done) return;
+  const Real beta = (Real)st->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Real zi = z ? z[i] : dinv[i] * r[i];
+    p[i] = zi + beta * p[i];
+  }
+}
+
+// Chebyshev start: d = D^-1 r / theta, z = d.
+template <typename Real>
+__global__ void cheb_init_kernel(int64_t n, const Real* __restrict__ r, const Real* __restrict__ dinv,
+                                 Real* __restrict__ d, Real* __restrict__ z, Real inv_theta, const int32_t* skip) {
+  if (skip && *skip) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Real v = dinv[i] * r[i] * inv_theta;
+    d[i] = v;
+    z[i] = v;
+  }
+}
+
+// Chebyshev step: d = c1 d + c2 D^-1 (r - Kz); z += d.
+template <typename Real>
+__global__ void cheb_step_kernel(int64_t n, const Real* __restrict__ r, const Real* __restrict__ kz,
+                                 const Real* __restrict__ dinv, Real* __restrict__ d, Real* __restrict__ z, Real c1,
+                                 Real c2, const int32_t* skip) {
+  if (skip && *skip) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Real di = c1 * d[i] + c2 * dinv[i] * (r[i] - kz[i]);
+    d[i] = di;
+    z[i] += di;
+  }
+}
+
+template <typename Real>
+__global__ void reciprocal_kernel(int64_t n, const Real* __restrict__ d, Real* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = Real(1) / d[i];
+}
+
+// r64 = b - y; out: (r, r)
+__global__ void residual_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ y,
+                                double* __restrict__ r, double* result, double* partials, unsigned int* counter) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - y[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) *result = v[0];
+}
+
+__global__ void scale_to_f32_kernel(int64_t n, const double* __restrict__ r, const double* scale_sq,
+                                    float* __restrict__ out) {
+  const double s = 1.0 / sqrt(*scale_sq);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)(r[i] * s);
+}
+
+__global__ void add_scaled_f32_kernel(int64_t n, double* __restrict__ x, const float* __restrict__ d,
+                                      const double* scale_sq) {
+  const double s = sqrt(*scale_sq);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += s * (double)d[i];
+}
+
+template <typename Real>
+__global__ void convert_kernel(int64_t n, const double* __restrict__ in, Real* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (Real)in[i];
+}
+
+// ------------------------------------------------------------------ host side
+
+static int vec_grid(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)device_sm_count() * 8));
+}
+
+mfx_status launch_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, const void* b, double* result,
+                      cudaStream_t s) {
+  const int g = reduction_blocks(n);
+  if (prec == MFX_F64)
+    dot_kernel<double><<<g, kRedThreads, 0, s>>>(n, (const double*)a, (const double*)b, result, op->d_partials,
+                                                  op->d_counter);
+  else
+    dot_kernel<float><<<g, kRedThreads, 0, s>>>(n, (const float*)a, (const float*)b, result, op->d_partials,
+                                                 op->d_counter);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+// Workspace of one precision.
+template <typename Real>
+struct Work {
+  Real *x, *r, *p, *q, *z, *d, *t, *dinv, *b;
+};
+
+struct SolveWorkspace {
+  size_t bytes = 0;
+  void* base = nullptr;
+  SolveState* st = nullptr;
+  double* scal = nullptr;  // misc FP64 device scalars
+  Work<double> w64{};
+  Work<float> w32{};
+  double* r64 = nullptr;   // mixed: FP64 residual
+  double* y64 = nullptr;   // mixed: K64 x
+  SolveState* h_st = nullptr;  // pinned host copy
+  double lambda_max[2] = {0.0, 0.0};
+  cudaStream_t stream = nullptr;  // solver stream (graph capture needs a non-default stream)
+};
+
+static SolveWorkspace* workspace(mfx_op* op) { return reinterpret_cast<SolveWorkspace*>(op->d_work); }
+
+static mfx_status ensure_workspace(mfx_op* op) {
+  if (op->d_work) return MFX_OK;
+  auto* ws = new SolveWorkspace();
+  const int64_t n = op->n_dofs;
+  const size_t n64 = (size_t)n * sizeof(double), n32 = (size_t)n * sizeof(float);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t total = al(sizeof(SolveState)) + al(64 * sizeof(double));
+  if (op->has_f64) total += 9 * al(n64);
+  if (op->has_f32) total += 9 * al(n32) + 2 * al(n64);
+  cudaError_t e = cudaMalloc(&ws->base, total);
+  if (e != cudaSuccess) {
+    delete ws;
+    return set_error(MFX_ENOMEM, "solver workspace allocation failed");
+  }
+  e = cudaMallocHost((void**)&ws->h_st, sizeof(SolveState));
+  if (e != cudaSuccess) {
+    cudaFree(ws->base);
+    delete ws;
+    return set_error(MFX_ENOMEM, "pinned status allocation failed");
+  }
+  char* p = (char*)ws->base;
+  ws->st = (SolveState*)p;
+  p += al(sizeof(SolveState));
+  ws->scal = (double*)p;
+  p += al(64 * sizeof(double));
+  if (op->has_f64) {
+    double** f[] = {&ws->w64.x, &ws->w64.r, &ws->w64.p, &ws->w64.q, &ws->w64.z,
+                    &ws->w64.d, &ws->w64.t, &ws->w64.dinv, &ws->w64.b};
+    for (auto* v : f) {
+      *v = (double*)p;
+      p += al(n64);
+    }
+  }
+  if (op->has_f32) {
+    float** f[] = {&ws->w32.x, &ws->w32.r, &ws->w32.p, &ws->w32.q, &ws->w32.z,
+                   &ws->w32.d, &ws->w32.t, &ws->w32.dinv, &ws->w32.b};
+    for (auto* v : f) {
+      *v = (float*)p;
+      p += al(n32);
+    }
+    ws->r64 = (double*)p;
+    p += al(n64);
+    ws->y64 = (double*)p;
+    p += al(n64);
+  }
+  ws->bytes = total;
+  op->d_work = ws;
+  op->work_bytes = total;
+  MFX_CUDA_TRY(cudaStreamCreateWithFlags(&ws->stream, cudaStreamNonBlocking));
+  cudaStream_t s = ws->stream;
+  // inverse diagonals
+  if (op->has_f64) reciprocal_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, op->d_diag64, ws->w64.dinv);
+  if (op->has_f32) reciprocal_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, op->d_diag32, ws->w32.dinv);
+  // one application per precision outside any capture (first-launch kernel attributes)
+  if (op->has_f64) {
+    MFX_CUDA_TRY(cudaMemsetAsync(ws->w64.p, 0, n64, s));
+    mfx_status rc = launch_vmult(op, MFX_F64, ws->w64.p, ws->w64.q, s);
+    if (rc != MFX_OK) return rc;
+  }
+  if (op->has_f32) {
+    MFX_CUDA_TRY(cudaMemsetAsync(ws->w32.p, 0, n32, s));
+    mfx_status rc = launch_vmult(op, MFX_F32, ws->w32.p, ws->w32.q, s);
+    if (rc != MFX_OK) return rc;
+  }
+  MFX_CUDA_TRY(cudaStreamSynchronize(s));
+  return MFX_OK;
+}
+
+void free_workspace(mfx_op* op) {
+  auto* ws = workspace(op);
+  if (!ws) return;
+  if (ws->stream) cudaStreamSynchronize(ws->stream);
+  cudaFree(ws->base);
+  cudaFreeHost(ws->h_st);
+  if (ws->stream) cudaStreamDestroy(ws->stream);
+  delete ws;
+  op->d_work = nullptr;
+}
+
+template <typename Real>
+static Work<Real>& work_of(SolveWorkspace* ws);
+template <>
+Work<double>& work_of<double>(SolveWorkspace* ws) { return ws->w64; }
+template <>
+Work<float>& work_of<float>(SolveWorkspace* ws) { return ws->w32; }
+
+template <typename Real>
+static constexpr mfx_prec prec_of() { return std::is_same<Real, double>::value ? MFX_F64 : MFX_F32; }
+
+// z = Chebyshev(r); uses w.d and w.t; skip: optional done flag.
+template <typename Real>
+static mfx_status cheb_apply(const mfx_op* op, Work<Real>& w, const Real* r, Real* z, int degree, double lo,
+                             double hi, const int32_t* skip, cudaStream_t s) {
+  const int64_t n = op->n_dofs;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  cheb_init_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, r, w.dinv, w.d, z, (Real)(1.0 / theta), skip);
+  for (int i = 1; i < degree; ++i) {
+    mfx_status st = launch_vmult(op, prec_of<Real>(), z, w.t, s, skip);
+    if (st != MFX_OK) return st;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    cheb_step_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, r, w.t, w.dinv, w.d, z, (Real)(rho_new * rho),
+                                                        (Real)(2.0 * rho_new / delta), skip);
+    rho = rho_new;
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+// One PCG iteration (all kernels no-op once done).
+template <typename Real>
+static mfx_status pcg_iteration(const mfx_op* op, SolveWorkspace* ws, Work<Real>& w, bool cheb, int degree,
+                                double lo, double hi, cudaStream_t s) {
+  const int64_t n = op->n_dofs;
+  const int g = reduction_blocks(n);
+  const int32_t* done = &ws->st->done;
+  mfx_status rc = launch_vmult(op, prec_of<Real>(), w.p, w.q, s, done);
+  if (rc != MFX_OK) return rc;
+  cg_pq_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.p, w.q, ws->st, op->d_partials, op->d_counter);
+  cg_update_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.x, w.r, w.p, w.q, w.dinv, !cheb, ws->st, op->d_partials,
+                                                   op->d_counter);
+  if (cheb) {
+    rc = cheb_apply<Real>(op, w, w.r, w.z, degree, lo, hi, done, s);
+    if (rc != MFX_OK) return rc;
+    cg_rz_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.r, w.z, ws->st, op->d_partials, op->d_counter);
+    cg_p_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, w.p, w.r, w.dinv, w.z, ws->st);
+  } else {
+    cg_p_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, w.p, w.r, w.dinv, nullptr, ws->st);
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+// Solve K x = b in precision Real (b, x in w.b, w.x).  Returns the final state in ws->h_st.
+template <typename Real>
+static mfx_status pcg_run(const mfx_op* op, SolveWorkspace* ws, bool cheb, int degree, double lo, double hi,
+                          double tol, int max_it, int check_every, bool record, cudaStream_t s) {
+  Work<Real>& w = work_of<Real>(ws);
+  const int64_t n = op->n_dofs;
+  const int g = reduction_blocks(n);
+  SolveState init{};
+  init.tol2 = tol * tol;
+  init.max_it = max_it;
+  init.record = record ? 1 : 0;
+  MFX_CUDA_TRY(cudaMemcpyAsync(ws->st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+  cg_init_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.b, w.x, w.r, w.p, w.dinv, !cheb, ws->st, op->d_partials,
+                                                 op->d_counter);
+  if (cheb) {
+    mfx_status rc = cheb_apply<Real>(op, w, w.r, w.p, degree, lo, hi, &ws->st->done, s);
+    if (rc != MFX_OK) return rc;
+    // rz = (r, z) with z = p
+    dot_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.r, w.p, &ws->st->rz, op->d_partials, op->d_counter);
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  // capture a chunk of iterations once, then replay it until done
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  MFX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  mfx_status rc = MFX_OK;
+  for (int i = 0; i < check_every && rc == MFX_OK; ++i) rc = pcg_iteration<Real>(op, ws, w, cheb, degree, lo, hi, s);
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (rc != MFX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphInstantiate");
+  int launched = 0;
+  for (;;) {
+    ce = cudaGraphLaunch(exec, s);
+    if (ce != cudaSuccess) break;
+    launched += check_every;
+    ce = cudaMemcpyAsync(ws->h_st, ws->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) break;
+    ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) break;
+    if (ws->h_st->done || launched >= max_it + check_every) break;
+  }
+  cudaGraphExecDestroy(exec);
+  if (ce != cudaSuccess) return cuda_error(ce, "pcg loop");
+  return MFX_OK;
+}
+
+// Largest eigenvalue of a symmetric tridiagonal matrix by Sturm-sequence bisection.
+static double tridiag_lambda_max(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // number of eigenvalues < x
+    int c = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      q = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) < m)
+      lo = mid;
+    else
+      hi = mid;
+    if (hi - lo <= 1e-15 * std::fabs(hi)) break;
+  }
+  return hi;
+}
+
+template <typename Real>
+static mfx_status estimate_lambda(const mfx_op* op, SolveWorkspace* ws, const double* start, int steps,
+                                  cudaStream_t s, double* lam) {
+  Work<Real>& w = work_of<Real>(ws);
+  const int64_t n = op->n_dofs;
+  steps = std::max(2, std::min(steps, kMaxLanczos - 1));
+  convert_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, start, w.b);
+  // constrained rows do not belong to D^-1 K on the free space: zero them
+  mfx_status rc = pcg_run<Real>(op, ws, false, 0, 0.0, 0.0, 0.0, steps, steps, true, s);
+  if (rc != MFX_OK) return rc;
+  const SolveState& h = *ws->h_st;
+  const int m = std::min(h.it, steps);
+  if (m < 1) return set_error(MFX_BREAKDOWN, "eigenvalue estimate: no CG step");
+  std::vector<double> a(m), b(std::max(0, m - 1));
+  for (int i = 0; i < m; ++i) {
+    a[i] = 1.0 / h.lan_alpha[i] + (i > 0 ? h.lan_beta[i - 1] / h.lan_alpha[i - 1] : 0.0);
+    if (i + 1 < m) b[i] = std::sqrt(h.lan_beta[i]) / h.lan_alpha[i];
+  }
+  *lam = tridiag_lambda_max(a, b);
+  return MFX_OK;
+}
+
+}  // namespace mfx
+
+using namespace mfx;
+
+extern "C" {
+
+void mfx_solve_params_default(mfx_solve_params* p) {
+  if (!p) return;
+  p->tol = 1e-10;
+  p->max_it = 100000;
+  p->precond = MFX_PRECOND_JACOBI;
+  p->cheb_degree = 5;
+  p->mixed = 0;
+  p->inner_tol = 1e-4;
+  p->check_every = 0;
+  p->lanczos_steps = 15;
+  p->cheb_lo = 0.0;
+  p->cheb_hi = 0.0;
+  p->lanczos_start = nullptr;
+  p->inner_max_it = 10000;
+  p->reserved = 0;
+}
+
+mfx_status mfx_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, const void* b, double* result,
+                   mfx_stream stream) {
+  if (!op || !a || !b || !result || n < 0 || (prec != MFX_F64 && prec != MFX_F32))
+    return set_error(MFX_EINVAL, "mfx_dot: bad arguments");
+  return launch_dot(op, prec, n, a, b, result, (cudaStream_t)stream);
+}
+
+mfx_status mfx_chebyshev(const mfx_op* op_c, mfx_prec prec, const void* r, void* z, int32_t degree, double lo,
+                         double hi, mfx_stream stream) {
+  mfx_op* op = const_cast<mfx_op*>(op_c);
+  if (!op || !r || !z || degree < 1 || !(hi > lo) || !(lo > 0.0))
+    return set_error(MFX_EINVAL, "mfx_chebyshev: bad arguments");
+  if ((prec == MFX_F64 && !op->has_f64) || (prec == MFX_F32 && !op->has_f32))
+    return set_error(MFX_EINVAL, "mfx_chebyshev: precision not built for this operator");
+  mfx_status rc = ensure_workspace(op);
+  if (rc != MFX_OK) return rc;
+  auto* ws = workspace(op);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == MFX_F64) return cheb_apply<double>(op, ws->w64, (const double*)r, (double*)z, degree, lo, hi, nullptr, s);
+  return cheb_apply<float>(op, ws->w32, (const float*)r, (float*)z, degree, lo, hi, nullptr, s);
+}
+
+mfx_status mfx_solve(const mfx_op* op_c, const double* b, double* x, const mfx_solve_params* params,
+                     mfx_solve_stats* stats, mfx_stream stream) {
+  mfx_op* op = const_cast<mfx_op*>(op_c);
+  if (!op || !b || !x || !stats) return set_error(MFX_EINVAL, "mfx_solve: null argument");
+  mfx_solve_params p;
+  mfx_solve_params_default(&p);
+  if (params) p = *params;
+  if (!(p.tol >= 0.0) || p.max_it < 1 || p.cheb_degree < 1 || (p.precond != MFX_PRECOND_JACOBI && p.precond != MFX_PRECOND_CHEBYSHEV))
+    return set_error(MFX_EINVAL, "mfx_solve: bad parameters");
+  const bool mixed = p.mixed != 0;
+  if (mixed && !(op->has_f32 && op->has_f64))
+    return set_error(MFX_EINVAL, "mfx_solve: mixed precision needs FP64 and FP32 data");
+  if (!mixed && !op->has_f64) return set_error(MFX_EINVAL, "mfx_solve: FP64 data not built");
+  mfx_status rc = ensure_workspace(op);
+  if (rc != MFX_OK) return rc;
+  auto* ws = workspace(op);
+  // order after the caller's work, then run on the solver stream (capturable)
+  MFX_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t s = ws->stream;
+  const int64_t n = op->n_dofs;
+  const int g = reduction_blocks(n);
+  const bool cheb = p.precond == MFX_PRECOND_CHEBYSHEV;
+  const int check = p.check_every > 0 ? p.check_every : 8;
+  *stats = mfx_solve_stats{};
+  const int pi = mixed ? 1 : 0;
+  double lo = p.cheb_lo, hi = p.cheb_hi;
+  if (cheb && !(hi > 0.0)) {
+    if (ws->lambda_max[pi] == 0.0 || p.lanczos_start) {
+      double lam = 0.0;
+      const double* start = p.lanczos_start ? p.lanczos_start : b;
+      rc = mixed ? estimate_lambda<float>(op, ws, start, p.lanczos_steps, s, &lam)
+                 : estimate_lambda<double>(op, ws, start, p.lanczos_steps, s, &lam);
+      if (rc != MFX_OK) return rc;
+      ws->lambda_max[pi] = lam;
+    }
+    stats->lambda_max = ws->lambda_max[pi];
+    hi = 1.2 * ws->lambda_max[pi];
+    lo = hi / 20.0;
+  }
+  stats->cheb_lo = lo;
+  stats->cheb_hi = hi;
+  if (!mixed) {
+    MFX_CUDA_TRY(cudaMemcpyAsync(ws->w64.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    rc = pcg_run<double>(op, ws, cheb, p.cheb_degree, lo, hi, p.tol, p.max_it, check, false, s);
+    if (rc != MFX_OK) return rc;
+    stats->iterations = ws->h_st->it;
+    stats->status = ws->h_st->status;
+    MFX_CUDA_TRY(cudaMemcpyAsync(x, ws->w64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    MFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    double* rr = ws->scal;      // (r, r)
+    double* bb = ws->scal + 1;  // (b, b)
+    double h[2];
+    launch_dot(op, MFX_F64, n, b, b, bb, s);
+    stats->status = MFX_NOT_CONVERGED;
+    int inner_total = 0;
+    for (int outer = 0; outer <= p.max_it; ++outer) {
+      rc = launch_vmult(op, MFX_F64, x, ws->y64, s);
+      if (rc != MFX_OK) return rc;
+      residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64, ws->r64, rr, op->d_partials, op->d_counter);
+      MFX_CUDA_TRY(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MFX_CUDA_TRY(cudaStreamSynchronize(s));
+      stats->iterations = outer;
+      if (!std::isfinite(h[0])) {
+        stats->status = MFX_BREAKDOWN;
+        break;
+      }
+      if (h[0] <= p.tol * p.tol * h[1]) {
+        stats->status = MFX_OK;
+        break;
+      }
+      if (outer == p.max_it) break;
+      scale_to_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, ws->r64, rr, ws->w32.b);
+      rc = pcg_run<float>(op, ws, cheb, p.cheb_degree, lo, hi, p.inner_tol, p.inner_max_it, check, false, s);
+      if (rc != MFX_OK) return rc;
+      inner_total += ws->h_st->it;
+      if (ws->h_st->status == MFX_BREAKDOWN) {
+        stats->status = MFX_BREAKDOWN;
+        break;
+      }
+      add_scaled_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, ws->w32.x, rr);
+    }
+    stats->inner_iterations = inner_total;
+  }
+  // true FP64 residual of the result
+  rc = launch_vmult(op, MFX_F64, x, ws->y64 ? ws->y64 : ws->w64.q, s);
+  if (rc != MFX_OK) return rc;
+  double* rr = ws->scal + 2;
+  double* bb = ws->scal + 3;
+  residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64 ? ws->y64 : ws->w64.q, ws->r64 ? ws->r64 : ws->w64.t, rr,
+                                            op->d_partials, op->d_counter);
+  launch_dot(op, MFX_F64, n, b, b, bb, s);
+  double h[2];
+  MFX_CUDA_TRY(cudaMemcpyAsync(h, rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MFX_CUDA_TRY(cudaStreamSynchronize(s));
+  stats->rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return MFX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+// Matrix-free application of the Q_k Laplacian (Sec. 3.6), one degree per
+// translation unit (MFX_N = k + 1 defined by the including file).
+//
+// Design (GB300):
+//  * a CTA of 256 threads owns CB = floor(256 / n^2) cells at a time and
+//    walks the cell range persistently (grid = resident CTAs on all SMs);
+//  * every 1D contraction is done by a thread that owns one line of one
+//    cell: it reads the n values of the line (from HBM in the gather, from
+//    shared memory otherwise), applies the n x n matrix held in the kernel
+//    parameter bank (uniform operands, no memory traffic) and writes the n
+//    results back; the cell data lives in three shared-memory cubes per
+//    cell, rows padded to an odd length so line accesses are conflict-free;
+//  * the metric (6 values per quadrature point) is streamed from HBM once,
+//    coalesced, by the thread that owns the z-line of quadrature points;
+//  * the scatter adds the cell results with fire-and-forget atomics; the
+//    constrained rows are written by a prologue kernel (identity rows).
+//
+// Steps per cell (n = k + 1 Gauss points per direction):
+//   gather (+ constraints) -> S_x -> S_y -> S_z (values at Gauss points)
+//   -> D_x, D_y, D_z (reference gradient, collocation derivative on the
+//   Gauss points) -> h = G_q grad (G = a |det J| w J^-1 J^-T)
+//   -> D_x^T h1 + D_y^T h2 + D_z^T h3 -> S_z^T -> S_y^T -> S_x^T -> scatter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mfx {
+
+template <int N, typename Real>
+struct VmultArgs {
+  Real S[N * N];  // S[q*N + j] = l_j(xi_q)
+  Real D[N * N];  // D[q*N + p] = L_p'(xi_q) on the Gauss points
+  const Real* metric;  // [cell][6][N^3]
+  int64_t n_cells;
+  // structured meshes
+  int nx, ny, nz, k, Mx, My, Mz;
+  // table meshes
+  const int32_t* cell_dofs;  // >= 0 free DoF, < 0: -(row + 1) into the constraint rows
+  const int64_t* cptr;
+  const int32_t* cmaster;
+  const Real* cweight;
+  const uint8_t* cmask;
+  int64_t n_dofs;
+  const int32_t* skip;  // optional: when *skip != 0 the launch does nothing (converged solve)
+};
+
+template <int N>
+struct VmultShape {
+  static constexpr int NP = (N % 2) ? N : N + 1;  // padded row length (odd)
+  static constexpr int N2 = N * N;
+  static constexpr int N3 = N * N * N;
+  static constexpr int THREADS = 256;
+  static constexpr int CB = THREADS / N2;         // cells per CTA step
+  static constexpr int CELL = N * N * NP;         // shared elements per cube
+};
+
+template <int N, typename Real>
+__device__ __forceinline__ void contract(const Real (&M)[N * N], const Real (&in)[N], Real (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Real s = M[i * N] * in[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) s += M[i * N + j] * in[j];
+    out[i] = s;
+  }
+}
+
+template <int N, typename Real>
+__device__ __forceinline__ void contract_t(const Real (&M)[N * N], const Real (&in)[N], Real (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Real s = M[i] * in[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) s += M[j * N + i] * in[j];
+    out[i] = s;
+  }
+}
+
+// x-line gather of cell `cell` at (i2, i3) with constraint resolution.
+template <int N, typename Real, bool STRUCT>
+__device__ __forceinline__ void gather_xline(const VmultArgs<N, Real>& a, const Real* __restrict__ src,
+                                             int64_t cell, int i2, int i3, Real (&v)[N]) {
+  if constexpr (STRUCT) {
+    const int cx = (int)(cell % a.nx);
+    const int64_t rest = cell / a.nx;
+    const int cy = (int)(rest % a.ny), cz = (int)(rest / a.ny);
+    const int J = cy * a.k + i2, L = cz * a.k + i3, I0 = cx * a.k;
+    const bool plane_bnd = (J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1);
+    const Real* row = src + (int64_t)a.Mx * (J + (int64_t)a.My * L) + I0;
+#pragma unroll
+    for (int i1 = 0; i1 < N; ++i1) {
+      const int I = I0 + i1;
+      const bool bnd = plane_bnd | (I == 0) | (I == a.Mx - 1);
+      v[i1] = bnd ? Real(0) : __ldg(row + i1);
+    }
+  } else {
+    const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
+#pragma unroll
+    for (int i1 = 0; i1 < N; ++i1) {
+      const int32_t e = __ldg(cd + i1);
+      if (e >= 0) {
+        v[i1] = __ldg(src + e);
+      } else {
+        const int32_t row = -e - 1;
+        Real s = Real(0);
+        for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) s += a.cweight[p] * __ldg(src + a.cmaster[p]);
+        v[i1] = s;
+      }
+    }
+  }
+}
+
+template <int N, typename Real, bool STRUCT>
+__device__ __forceinline__ void scatter_xline(const VmultArgs<N, Real>& a, Real* __restrict__ dst, int64_t cell,
+                                              int i2, int i3, const Real (&v)[N]) {
+  if constexpr (STRUCT) {
+    const int cx = (int)(cell % a.nx);
+    const int64_t rest = cell / a.nx;
+    const int cy = (int)(rest % a.ny), cz = (int)(rest / a.ny);
+    const int J = cy * a.k + i2, L = cz * a.k + i3, I0 = cx * a.k;
+    if ((J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1)) return;
+    Real* row = dst + (int64_t)a.Mx * (J + (int64_t)a.My * L) + I0;
+#pragma unroll
+    for (int i1 = 0; i1 < N; ++i1) {
+      const int I = I0 + i1;
+      if ((I != 0) & (I != a.Mx - 1)) atomicAdd(row + i1, v[i1]);
+    }
+  } else {
+    const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
+#pragma unroll
+    for (int i1 = 0; i1 < N; ++i1) {
+      const int32_t e = __ldg(cd + i1);
+      if (e >= 0) {
+        atomicAdd(dst + e, v[i1]);
+      } else {
+        const int32_t row = -e - 1;
+        for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) atomicAdd(dst + a.cmaster[p], a.cweight[p] * v[i1]);
+      }
+    }
+  }
+}
+
+template <int N, typename Real, bool STRUCT>
+__global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ VmultArgs<N, Real> a,
+                                                    const Real* __restrict__ src, Real* __restrict__ dst) {
+  using Sh = VmultShape<N>;
+  constexpr int NP = Sh::NP, N2 = Sh::N2, N3 = Sh::N3, CB = Sh::CB, CELL = Sh::CELL;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* buf0 = reinterpret_cast<Real*>(smem_raw);
+  Real* buf1 = buf0 + CB * CELL;
+  Real* buf2 = buf1 + CB * CELL;
+
+  const int t = threadIdx.x;
+  const int cl = t / N2;
+  const int r = t - cl * N2;
+  const int ra = r % N, rb = r / N;  // fast and slow line coordinates
+  const bool line_ok = t < CB * N2;
+  Real* B0 = buf0 + cl * CELL;
+  Real* B1 = buf1 + cl * CELL;
+  Real* B2 = buf2 + cl * CELL;
+
+  const int64_t nbatch = (a.n_cells + CB - 1) / CB;
+  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+    const int64_t cell = b * CB + cl;
+    const bool act = line_ok && cell < a.n_cells;
+    Real g3[N], t3[N];
+
+    // 1) gather + S along x: x-line (i2 = ra, i3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      gather_xline<N, Real, STRUCT>(a, src, cell, ra, rb, v);
+      contract<N, Real>(a.S, v, o);
+      Real* p = B0 + (rb * N + ra) * NP;
+#pragma unroll
+      for (int q = 0; q < N; ++q) p[q] = o[q];
+    }
+    __syncthreads();
+    // 2) S along y: y-line (q1 = ra, i3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p = B0 + rb * N * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j * NP];
+      contract<N, Real>(a.S, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[j * NP] = o[j];
+    }
+    __syncthreads();
+    // 3) S along z, then D along z in registers: z-line (q1 = ra, q2 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p = B0 + rb * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j * N * NP];
+      contract<N, Real>(a.S, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[j * N * NP] = o[j];
+      contract<N, Real>(a.D, o, g3);
+    }
+    __syncthreads();
+    // 4) D along x -> B1 (x-line q2 = ra, q3 = rb); D along y -> B2 (y-line q1 = ra, q3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      const Real* p = B0 + (rb * N + ra) * NP;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j];
+      contract<N, Real>(a.D, v, o);
+      Real* w = B1 + (rb * N + ra) * NP;
+#pragma unroll
+      for (int j = 0; j < N; ++j) w[j] = o[j];
+      const Real* py = B0 + rb * N * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = py[j * NP];
+      contract<N, Real>(a.D, v, o);
+      Real* wy = B2 + rb * N * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) wy[j * NP] = o[j];
+    }
+    __syncthreads();
+    // 5) quadrature-point metric on the z-line (q1 = ra, q2 = rb); D_z^T in registers
+    if (act) {
+      const Real* G = a.metric + cell * (6 * N3) + rb * N + ra;
+      Real h3[N];
+#pragma unroll
+      for (int q3 = 0; q3 < N; ++q3) {
+        const int off = q3 * N2;
+        const Real G00 = __ldg(G + off), G01 = __ldg(G + N3 + off), G02 = __ldg(G + 2 * N3 + off);
+        const Real G11 = __ldg(G + 3 * N3 + off), G12 = __ldg(G + 4 * N3 + off), G22 = __ldg(G + 5 * N3 + off);
+        const int sidx = (q3 * N + rb) * NP + ra;
+        const Real u1 = B1[sidx], u2 = B2[sidx], u3 = g3[q3];
+        B1[sidx] = G00 * u1 + G01 * u2 + G02 * u3;
+        B2[sidx] = G01 * u1 + G11 * u2 + G12 * u3;
+        h3[q3] = G02 * u1 + G12 * u2 + G22 * u3;
+      }
+      contract_t<N, Real>(a.D, h3, t3);
+    }
+    __syncthreads();
+    // 6) D_x^T on B1 in place (x-line q2 = ra, q3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p = B1 + (rb * N + ra) * NP;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j];
+      contract_t<N, Real>(a.D, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[j] = o[j];
+    }
+    __syncthreads();
+    // 7) D_y^T on B2, added into B1 (y-line q1 = ra, q3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p2 = B2 + rb * N * NP + ra;
+      Real* p1 = B1 + rb * N * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p2[j * NP];
+      contract_t<N, Real>(a.D, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p1[j * NP] += o[j];
+    }
+    __syncthreads();
+    // 8) add D_z^T h3, then S_z^T (z-line q1 = ra, q2 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p = B1 + rb * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j * N * NP] + t3[j];
+      contract_t<N, Real>(a.S, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[j * N * NP] = o[j];
+    }
+    __syncthreads();
+    // 9) S_y^T (y-line i1 = ra, i3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      Real* p = B1 + rb * N * NP + ra;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j * NP];
+      contract_t<N, Real>(a.S, v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) p[j * NP] = o[j];
+    }
+    __syncthreads();
+    // 10) S_x^T and scatter (x-line i2 = ra, i3 = rb)
+    if (act) {
+      Real v[N], o[N];
+      const Real* p = B1 + (rb * N + ra) * NP;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = p[j];
+      contract_t<N, Real>(a.S, v, o);
+      scatter_xline<N, Real, STRUCT>(a, dst, cell, ra, rb, o);
+    }
+    __syncthreads();
+  }
+}
+
+// dst = src on constrained rows, 0 elsewhere (identity rows of the condensed operator).
+template <int N, typename Real, bool STRUCT>
+__global__ void vmult_prologue(const __grid_constant__ VmultArgs<N, Real> a, const Real* __restrict__ src,
+                               Real* __restrict__ dst) {
+  if (a.skip && *a.skip) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_dofs; i += stride) {
+    bool c;
+    if constexpr (STRUCT) {
+      const int64_t I = i % a.Mx;
+      const int64_t rest = i / a.Mx;
+      const int64_t J = rest % a.My, L = rest / a.My;
+      c = (I == 0) | (I == a.Mx - 1) | (J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1);
+    } else {
+      c = a.cmask[i] != 0;
+    }
+    dst[i] = c ? src[i] : Real(0);
+  }
+}
+
+}  // namespace mfx

@@ -1,0 +1,9 @@
+// vmult instantiation for degree k = 4 (n = 5 points per direction).
+#include <type_traits>
+#include <algorithm>
+#include "vmult_launch.cuh"
+
+namespace mfx {
+template mfx_status launch_vmult_n<5>(const mfx_op*, mfx_prec, const void*, void*, cudaStream_t,
+                                           const int32_t*);
+}  // namespace mfx

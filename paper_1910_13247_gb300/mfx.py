@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libmfx.so (argument marshalling only).
+
+Every computation runs in the CUDA library; tensors are passed by device
+pointer and streams by handle (PyTorch provides memory and streams only).
+If the library is missing, loading raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmfx.so")
+
+F64, F32 = 0, 1
+COEF_CONSTANT, COEF_TRIG, COEF_QPOINT = 0, 1, 2
+PRECOND_JACOBI, PRECOND_CHEBYSHEV = 0, 1
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, EMESH, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+NOT_CONVERGED, BREAKDOWN = 1, 2
+
+
+class MfxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mfx error {code}: {msg}")
+        self.code = code
+
+
+class OpDesc(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("coef_kind", ctypes.c_int32),
+                ("precisions", ctypes.c_int32), ("coef_par", ctypes.c_double * 2),
+                ("coef_qpoint", ctypes.c_void_p), ("cells_per_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [("n_dofs", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_constrained", ctypes.c_int64),
+                ("n_masters", ctypes.c_int64), ("n_hanging", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
+                ("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("structured", ctypes.c_int32),
+                ("cells_per_block", ctypes.c_int32)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("cheb_degree", ctypes.c_int32), ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("lanczos_start", ctypes.c_void_p), ("inner_max_it", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libmfx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1910_13247_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    S = ctypes.c_int32
+    sig = {
+        "mfx_last_error": (ctypes.c_char_p, []),
+        "mfx_version": (ctypes.c_char_p, []),
+        "mfx_mesh_create_structured": (S, [ctypes.POINTER(_VP), S, S, S, _VP]),
+        "mfx_mesh_create_octree": (S, [ctypes.POINTER(_VP), S, S, S, _VP, _VP, ctypes.c_int64]),
+        "mfx_mesh_destroy": (None, [_VP]),
+        "mfx_mesh_table_sizes": (S, [_VP, S, _VP, _VP, _VP, _VP]),
+        "mfx_mesh_tables": (S, [_VP, S, _VP, _VP, _VP, _VP, _VP]),
+        "mfx_operator_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), _VP]),
+        "mfx_operator_destroy": (None, [_VP]),
+        "mfx_operator_info": (S, [_VP, ctypes.POINTER(OpInfo)]),
+        "mfx_get_tables": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
+        "mfx_vmult": (S, [_VP, S, _VP, _VP, _VP]),
+        "mfx_diagonal": (S, [_VP, S, _VP, _VP]),
+        "mfx_quadrature_points": (S, [_VP, _VP, _VP]),
+        "mfx_rhs": (S, [_VP, _VP, _VP, _VP]),
+        "mfx_distribute": (S, [_VP, _VP, _VP]),
+        "mfx_dot": (S, [_VP, S, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+        "mfx_chebyshev": (S, [_VP, S, _VP, _VP, S, ctypes.c_double, ctypes.c_double, _VP]),
+        "mfx_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
+        "mfx_solve": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code):
+    if code < 0:
+        raise MfxError(code, lib().mfx_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError("vectors must be float64 or float32")
+
+
+class Mesh:
+    """Host mesh description (structured box or octree)."""
+
+    def __init__(self, handle, structured):
+        self.handle = handle
+        self.structured = structured
+
+    @classmethod
+    def structured_box(cls, nx, ny, nz, vertices=None):
+        h = ctypes.c_void_p()
+        v = None
+        if vertices is not None:
+            v = np.ascontiguousarray(vertices, dtype=np.float64)
+            assert v.size == 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        check(lib().mfx_mesh_create_structured(ctypes.byref(h), nx, ny, nz,
+                                               v.ctypes.data_as(_VP) if v is not None else None))
+        return cls(h, True)
+
+    @classmethod
+    def octree(cls, nx, ny, nz, leaves, coarse_vertices=None):
+        h = ctypes.c_void_p()
+        lv = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 4)
+        v = None if coarse_vertices is None else np.ascontiguousarray(coarse_vertices, dtype=np.float64)
+        check(lib().mfx_mesh_create_octree(ctypes.byref(h), nx, ny, nz,
+                                           v.ctypes.data_as(_VP) if v is not None else None,
+                                           lv.ctypes.data_as(_VP), lv.shape[0]))
+        return cls(h, False)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfx_mesh_destroy(self.handle)
+            self.handle = None
+
+    def tables(self, degree):
+        """DoF and constraint tables at degree k, computed on the host (no GPU needed)."""
+        c, n, nc, nm = (ctypes.c_int64() for _ in range(4))
+        check(lib().mfx_mesh_table_sizes(self.handle, degree, ctypes.byref(c), ctypes.byref(n),
+                                         ctypes.byref(nc), ctypes.byref(nm)))
+        n3 = (degree + 1) ** 3
+        cd = np.zeros(c.value * n3, dtype=np.int32)
+        co = np.zeros(nc.value, dtype=np.int32)
+        cp = np.zeros(nc.value + 1, dtype=np.int64)
+        cm = np.zeros(max(1, nm.value), dtype=np.int32)
+        cw = np.zeros(max(1, nm.value), dtype=np.float64)
+        check(lib().mfx_mesh_tables(self.handle, degree, cd.ctypes.data_as(_VP), co.ctypes.data_as(_VP),
+                                    cp.ctypes.data_as(_VP), cm.ctypes.data_as(_VP), cw.ctypes.data_as(_VP)))
+        return {"n_dofs": n.value, "cell_dofs": cd.reshape(c.value, n3), "constrained": co, "cptr": cp,
+                "cmaster": cm[:nm.value], "cweight": cw[:nm.value]}
+
+
+class Operator:
+    """The condensed Q_k operator of one mesh (geometry and tables on the device)."""
+
+    def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), precisions=3,
+                 coef_qpoint=None, stream=None):
+        d = OpDesc()
+        d.degree = degree
+        d.n_q_1d = 0
+        d.coef_kind = coef_kind
+        d.precisions = precisions
+        d.coef_par[0], d.coef_par[1] = coef_par
+        d.coef_qpoint = coef_qpoint.data_ptr() if coef_qpoint is not None else None
+        d.cells_per_block = 0
+        h = ctypes.c_void_p()
+        check(lib().mfx_operator_create(ctypes.byref(h), mesh.handle, ctypes.byref(d), _stream(stream)))
+        self.handle = h
+        self.degree = degree
+        self._info = self.info()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfx_operator_destroy(self.handle)
+            self.handle = None
+
+    def info(self):
+        i = OpInfo()
+        check(lib().mfx_operator_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    @property
+    def n_dofs(self):
+        return self._info["n_dofs"]
+
+    @property
+    def n_cells(self):
+        return self._info["n_cells"]
+
+    def tables(self):
+        i = self.info()
+        n3 = (self.degree + 1) ** 3
+        cd = np.zeros(i["n_cells"] * n3, dtype=np.int32)
+        co = np.zeros(i["n_constrained"], dtype=np.int32)
+        cp = np.zeros(i["n_constrained"] + 1, dtype=np.int64)
+        cm = np.zeros(max(1, i["n_masters"]), dtype=np.int32)
+        cw = np.zeros(max(1, i["n_masters"]), dtype=np.float64)
+        check(lib().mfx_get_tables(self.handle, cd.ctypes.data_as(_VP), co.ctypes.data_as(_VP),
+                                   cp.ctypes.data_as(_VP), cm.ctypes.data_as(_VP), cw.ctypes.data_as(_VP)))
+        return {"cell_dofs": cd.reshape(i["n_cells"], n3), "constrained": co, "cptr": cp,
+                "cmaster": cm[:i["n_masters"]], "cweight": cw[:i["n_masters"]]}
+
+    def vmult(self, src, dst, stream=None):
+        assert src.is_cuda and dst.is_cuda and src.dtype == dst.dtype and src.is_contiguous() and dst.is_contiguous()
+        assert src.numel() == self.n_dofs and dst.numel() == self.n_dofs
+        check(lib().mfx_vmult(self.handle, _prec_of(src), _ptr(src), _ptr(dst), _stream(stream)))
+        return dst
+
+    def diagonal(self, out):
+        assert out.numel() == self.n_dofs
+        check(lib().mfx_diagonal(self.handle, _prec_of(out), _ptr(out), _stream()))
+        return out
+
+    def quadrature_points(self, out):
+        n3 = (self.degree + 1) ** 3
+        assert out.numel() == self.n_cells * n3 * 3 and out.dtype.itemsize == 8
+        check(lib().mfx_quadrature_points(self.handle, _ptr(out), _stream()))
+        return out
+
+    def rhs(self, fq, b):
+        check(lib().mfx_rhs(self.handle, _ptr(fq), _ptr(b), _stream()))
+        return b
+
+    def distribute(self, x):
+        check(lib().mfx_distribute(self.handle, _ptr(x), _stream()))
+        return x
+
+    def dot(self, a, b, out):
+        check(lib().mfx_dot(self.handle, _prec_of(a), a.numel(), _ptr(a), _ptr(b), _ptr(out), _stream()))
+        return out
+
+    def chebyshev(self, r, z, degree, lo, hi):
+        check(lib().mfx_chebyshev(self.handle, _prec_of(r), _ptr(r), _ptr(z), degree, lo, hi, _stream()))
+        return z
+
+    def solve(self, b, x, tol=1e-10, max_it=100000, precond=PRECOND_JACOBI, cheb_degree=5, mixed=False,
+              inner_tol=1e-4, check_every=0, lanczos_steps=15, cheb_lo=0.0, cheb_hi=0.0, lanczos_start=None,
+              inner_max_it=10000):
+        p = SolveParams()
+        lib().mfx_solve_params_default(ctypes.byref(p))
+        p.tol, p.max_it, p.precond, p.cheb_degree = tol, max_it, precond, cheb_degree
+        p.mixed, p.inner_tol, p.check_every, p.lanczos_steps = int(mixed), inner_tol, check_every, lanczos_steps
+        p.cheb_lo, p.cheb_hi = cheb_lo, cheb_hi
+        p.lanczos_start = lanczos_start.data_ptr() if lanczos_start is not None else None
+        p.inner_max_it = inner_max_it
+        st = SolveStats()
+        check(lib().mfx_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st), _stream()))
+        return st.as_dict()

@@ -1,0 +1,109 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and its
+host-side mesh/DoF/constraint tables match the oracle bit-exactly (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+from paper_1910_13247_gb300 import build as mbuild
+from paper_1910_13247_gb300 import mfx, synthetic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mbuild.build()
+    mfx.lib()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(mfx_[a-z0-9_]+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 20
+    L = mfx.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_error_strings():
+    assert b"sm_103a" in mfx.lib().mfx_version()
+    with pytest.raises(mfx.MfxError) as e:
+        mfx.Mesh.structured_box(0, 1, 1)
+    assert e.value.code == mfx.EINVAL
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_structured_tables_bit_exact(k):
+    nx, ny, nz = 3, 2, 4
+    T = mfx.Mesh.structured_box(nx, ny, nz).tables(k)
+    om = omesh.structured_mesh(nx, ny, nz, k)
+    assert T["n_dofs"] == om.n_dofs
+    assert np.array_equal(T["cell_dofs"], om.cell_dofs)
+    assert np.array_equal(T["constrained"], om.constrained)
+    assert np.array_equal(T["cptr"], om.cptr)
+
+
+@pytest.mark.parametrize("seed,nb,levels", [(0, 4, 2), (1, 4, 2), (2, 3, 1), (3, 4, 3)])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_octree_tables_bit_exact(seed, nb, levels, k):
+    if levels == 3 and k > 3:
+        pytest.skip("oracle tables take long at this size")
+    g = synthetic.rng(100 + seed)
+    leaves = synthetic.octree_leaves(nb, levels, g.uniform(0.25, 0.75, 3), float(g.uniform(0.15, 0.35)))
+    T = mfx.Mesh.octree(nb, nb, nb, leaves).tables(k)
+    om = omesh.octree_mesh(nb, nb, nb, k, leaves)
+    assert T["n_dofs"] == om.n_dofs
+    assert np.array_equal(T["cell_dofs"], om.cell_dofs)
+    assert np.array_equal(T["constrained"], om.constrained)
+    assert np.array_equal(T["cptr"], om.cptr)
+    assert np.array_equal(T["cmaster"], om.cmaster)
+    # weights: same product formula in the same order on both sides
+    assert np.array_equal(T["cweight"], om.cweight)
+
+
+def test_octree_cell_order_matches_oracle_for_shuffled_leaves():
+    leaves = synthetic.octree_leaves(3, 2, (0.5, 0.4, 0.6), 0.3)
+    perm = np.random.default_rng(0).permutation(len(leaves))
+    T = mfx.Mesh.octree(3, 3, 3, leaves[perm]).tables(2)
+    om = omesh.octree_mesh(3, 3, 3, 2, leaves)
+    assert np.array_equal(T["cell_dofs"], om.cell_dofs)
+
+
+def test_invalid_octrees_rejected_with_emesh():
+    good = synthetic.octree_leaves(2, 1, (0.25, 0.25, 0.25), 0.1)
+    mfx.Mesh.octree(2, 2, 2, good)
+    cases = {
+        "hole": good[1:],
+        "overlap": np.vstack([good, [[0, 1, 1, 1]]]),
+        "duplicate": np.vstack([good, good[:1]]),
+        "out of range": np.vstack([good[:-1], [[0, 2, 1, 1]]]),
+    }
+    # level-2 leaves next to a level-0 leaf
+    unbalanced = [lf for lf in good.tolist() if not (lf[0] == 1 and lf[1:] == [1, 0, 0])]
+    unbalanced += [[2, 2 + a, b, c] for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+    cases["unbalanced"] = np.array(unbalanced)
+    for name, lv in cases.items():
+        with pytest.raises(mfx.MfxError) as e:
+            mfx.Mesh.octree(2, 2, 2, lv)
+        assert e.value.code in (mfx.EMESH, mfx.EINVAL), name
+    with pytest.raises(omesh.MeshError):
+        omesh.octree_mesh(2, 2, 2, 1, cases["unbalanced"])
+
+
+def test_bad_degree_rejected():
+    m = mfx.Mesh.structured_box(2, 2, 2)
+    with pytest.raises(mfx.MfxError) as e:
+        m.tables(9)
+    assert e.value.code == mfx.EUNSUPPORTED

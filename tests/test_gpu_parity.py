@@ -1,0 +1,259 @@
+"""GPU parity of the CUDA path against the FP64 oracle (element by element).
+
+Tolerances: FP64 vmult / diagonal / right-hand side within 1e-12 relative,
+norm-wise and per entry against the max-norm; FP32 vmult within 1e-5
+norm-wise (single-precision arithmetic with FP32 accumulation over
+O(100) terms per entry gives about 1e-6).  Integer tables are bit-exact
+(tested on the CPU in test_abi.py).
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fem
+from oracle import mesh as omesh
+from paper_1910_13247_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mfx():
+    from paper_1910_13247_gb300 import build, mfx as m
+    build.build()
+    m.lib()
+    return m
+
+
+DEV = "cuda:0"
+
+
+def rel_err(y, ref):
+    return np.linalg.norm(y - ref) / np.linalg.norm(ref), np.abs(y - ref).max() / np.abs(ref).max()
+
+
+def run_vmult(op, x, dtype):
+    xd = torch.tensor(x, device=DEV, dtype=dtype)
+    yd = torch.empty_like(xd)
+    op.vmult(xd, yd)
+    torch.cuda.synchronize()
+    return yd.double().cpu().numpy()
+
+
+def make_pair(mfx, nx, ny, nz, k, deformed=True, coef=1):
+    verts = synthetic.deformed_vertices(nx, ny, nz) if deformed else None
+    m = mfx.Mesh.structured_box(nx, ny, nz, verts)
+    par = (1.0, 0.5) if coef == 1 else (1.0, 0.0)
+    op = mfx.Operator(m, k, coef, par)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts)
+    return op, om, par
+
+
+def test_config1_cartesian_q2_vmult(mfx):
+    op, om, par = make_pair(mfx, 8, 8, 8, 2, deformed=False, coef=0)
+    assert op.n_dofs == 4913
+    K = fem.assemble(om, 3)
+    x = synthetic.uniform_vector(om.n_dofs, 1)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12
+    e32, _ = rel_err(run_vmult(op, x, torch.float32), ref)
+    assert e32 < 1e-5
+
+
+SIZES = {1: (7, 5, 6), 2: (6, 6, 6), 3: (5, 4, 3), 4: (4, 4, 4), 5: (3, 3, 3), 6: (3, 2, 2), 7: (2, 2, 2), 8: (2, 2, 1)}
+
+
+@pytest.mark.parametrize("k", sorted(SIZES))
+def test_deformed_variable_coefficient_vmult_all_degrees(mfx, k):
+    op, om, par = make_pair(mfx, *SIZES[k], k)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, par)
+    x = synthetic.uniform_vector(om.n_dofs, 10 + k)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    e32, _ = rel_err(run_vmult(op, x, torch.float32), ref)
+    assert e32 < 1e-5, e32
+    # diagonal
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = fem.diagonal(K)
+    assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
+
+
+def test_quadrature_points_and_rhs(mfx):
+    op, om, par = make_pair(mfx, 3, 4, 2, 3)
+    X, _ = fem.quadrature_points(om, 4)
+    xq = torch.empty(op.n_cells * 64 * 3, dtype=torch.float64, device=DEV)
+    op.quadrature_points(xq)
+    assert np.abs(xq.cpu().numpy().reshape(X.shape) - X).max() < 1e-15
+    fq = synthetic.uniform_vector(op.n_cells * 64, 7)
+    b = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.rhs(torch.tensor(fq, device=DEV), b)
+    bref = fem.rhs(om, 4, fq=fq.reshape(op.n_cells, 64))
+    e2, einf = rel_err(b.cpu().numpy(), bref)
+    assert e2 < 1e-12 and einf < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_octree_vmult_with_hanging_nodes(mfx, k):
+    g = synthetic.rng(200 + k)
+    leaves = synthetic.octree_leaves(3, 2, g.uniform(0.3, 0.7, 3), 0.3)
+    verts = synthetic.deformed_vertices(3, 3, 3)
+    m = mfx.Mesh.octree(3, 3, 3, leaves, verts)
+    op = mfx.Operator(m, k, mfx.COEF_TRIG, (1.0, 0.5))
+    om = omesh.octree_mesh(3, 3, 3, k, leaves, verts)
+    assert op.info()["n_hanging"] > 0
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 20 + k)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    e32, _ = rel_err(run_vmult(op, x, torch.float32), ref)
+    assert e32 < 1e-5
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = fem.diagonal(K)
+    assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
+    # distribute fills hanging values from their masters
+    xs = torch.tensor(x, device=DEV)
+    op.distribute(xs)
+    assert np.abs(xs.cpu().numpy() - fem.distribute(om, x)).max() < 1e-14
+
+
+def test_single_cell_degenerate_meshes(mfx):
+    # one Q1 cell: every DoF is on the boundary, the operator is the identity
+    m = mfx.Mesh.structured_box(1, 1, 1)
+    op = mfx.Operator(m, 1)
+    x = synthetic.uniform_vector(8, 3)
+    assert np.array_equal(run_vmult(op, x, torch.float64), x)
+    # one Q8 cell: a single cell with 729 nodes, 343 of them free
+    op, om, par = make_pair(mfx, 1, 1, 1, 8)
+    K = fem.assemble(om, 9, fem.COEF_TRIG, par)
+    x = synthetic.uniform_vector(om.n_dofs, 4)
+    e2, _ = rel_err(run_vmult(op, x, torch.float64), K @ x)
+    assert e2 < 1e-12
+
+
+@pytest.mark.parametrize("nx,k", [(64, 4), (96, 3)])
+def test_full_size_sampled_rows(mfx, nx, k):
+    """Full-size workloads (64^3 Q4 and 96^3 Q3, deformed, variable coefficient) in the benchmark's
+    launch configuration: sampled rows against the oracle's row-by-row product."""
+    verts = synthetic.deformed_vertices(nx, nx, nx)
+    m = mfx.Mesh.structured_box(nx, nx, nx, verts)
+    op = mfx.Operator(m, k, mfx.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(op.n_dofs, 2)
+    y = run_vmult(op, x, torch.float64)
+    y32 = run_vmult(op, x, torch.float32)
+    # the oracle's sampled rows need only the cells of each DoF: build them from a sub-mesh view
+    rows = synthetic.rng(5).choice(op.n_dofs, 300, replace=False)
+    ref = sampled_rows_structured(nx, k, verts, x, rows)
+    scale = np.abs(ref).max()
+    assert np.abs(y[rows] - ref).max() < 1e-12 * scale
+    assert np.linalg.norm(y32 - y) < 1e-5 * np.linalg.norm(y)
+
+
+def sampled_rows_structured(nx, k, verts, x, rows):
+    """Oracle rows (K x)[rows] on the nx^3 structured mesh, from the element rows of each row's cells."""
+    M = k * nx + 1
+    out = np.zeros(len(rows))
+    n = k + 1
+    for t, d in enumerate(rows):
+        I, J, L = d % M, (d // M) % M, d // (M * M)
+        if min(I, J, L) == 0 or max(I, J, L) == M - 1:
+            out[t] = x[d]
+            continue
+        s = 0.0
+        for cz in {(L - 1) // k, L // k} & set(range(nx)):
+            for cy in {(J - 1) // k, J // k} & set(range(nx)):
+                for cx in {(I - 1) // k, I // k} & set(range(nx)):
+                    i1, i2, i3 = I - k * cx, J - k * cy, L - k * cz
+                    if not (0 <= i1 <= k and 0 <= i2 <= k and 0 <= i3 <= k):
+                        continue
+                    cell = omesh.structured_mesh(1, 1, 1, k, np.array(
+                        [verts[(cx + a) + (nx + 1) * ((cy + b) + (nx + 1) * (cz + e))]
+                         for e in (0, 1) for b in (0, 1) for a in (0, 1)]))
+                    row = fem.element_matrices(cell, n, fem.COEF_TRIG, (1.0, 0.5), rows=[i1 + n * (i2 + n * i3)])[0, 0]
+                    gd = np.array([(k * cx + a1) + M * ((k * cy + a2) + M * (k * cz + a3))
+                                   for a3 in range(n) for a2 in range(n) for a1 in range(n)])
+                    gI, gJ, gL = gd % M, (gd // M) % M, gd // (M * M)
+                    bnd = (np.minimum(np.minimum(gI, gJ), gL) == 0) | (np.maximum(np.maximum(gI, gJ), gL) == M - 1)
+                    s += float(row @ np.where(bnd, 0.0, x[gd]))
+        out[t] = s
+    return out
+
+
+def test_dot_and_chebyshev(mfx):
+    op, om, par = make_pair(mfx, 4, 4, 4, 3)
+    K = fem.assemble(om, 4, fem.COEF_TRIG, par)
+    a = synthetic.uniform_vector(om.n_dofs, 30)
+    b = synthetic.uniform_vector(om.n_dofs, 31)
+    out = torch.zeros(1, dtype=torch.float64, device=DEV)
+    op.dot(torch.tensor(a, device=DEV), torch.tensor(b, device=DEV), out)
+    assert abs(out.item() - a @ b) < 1e-12 * np.abs(a) @ np.abs(b)
+    d = fem.diagonal(K)
+    lo, hi = 0.1, 2.5
+    r = synthetic.uniform_vector(om.n_dofs, 32)
+    zref = fem.chebyshev(lambda v: K @ v, 1 / d, r, 5, lo, hi)
+    z = torch.empty(om.n_dofs, dtype=torch.float64, device=DEV)
+    op.chebyshev(torch.tensor(r, device=DEV), z, 5, lo, hi)
+    e2, einf = rel_err(z.cpu().numpy(), zref)
+    assert e2 < 1e-12 and einf < 1e-12
+    z32 = torch.empty(om.n_dofs, dtype=torch.float32, device=DEV)
+    op.chebyshev(torch.tensor(r, device=DEV, dtype=torch.float32), z32, 5, lo, hi)
+    assert rel_err(z32.double().cpu().numpy(), zref)[0] < 1e-5
+
+
+def test_config1_jacobi_pcg_solve(mfx):
+    op, om, par = make_pair(mfx, 8, 8, 8, 2, deformed=False, coef=0)
+    K = fem.assemble(om, 3)
+    b = fem.rhs(om, 3)
+    bd = torch.tensor(b, device=DEV)
+    x = torch.zeros_like(bd)
+    st = op.solve(bd, x, tol=1e-10)
+    assert st["status"] == 0, st
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(b - K @ xs) <= 1.0001e-10 * np.linalg.norm(b)
+    ref = fem.pcg(lambda v: K @ v, b, lambda r: r / fem.diagonal(K), tol=1e-10)
+    assert abs(st["iterations"] - ref.iterations) <= 1
+    xd = spla.spsolve(K.tocsc(), b)
+    assert np.linalg.norm(xs - xd) < 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_chebyshev_pcg_and_mixed_precision_solve(mfx, mixed):
+    op, om, par = make_pair(mfx, 6, 6, 6, 3)
+    K = fem.assemble(om, 4, fem.COEF_TRIG, par)
+    b = synthetic.gaussian_vector(om.n_dofs, 3)
+    b[om.constrained] = 0.0
+    bd = torch.tensor(b, device=DEV)
+    x = torch.zeros_like(bd)
+    st = op.solve(bd, x, tol=1e-10, precond=mfx.PRECOND_CHEBYSHEV, cheb_degree=5, mixed=mixed, inner_tol=1e-4)
+    assert st["status"] == 0, st
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(b - K @ xs) <= 1.0001e-10 * np.linalg.norm(b)
+    xd = spla.spsolve(K.tocsc(), b)
+    assert np.linalg.norm(xs - xd) < 1e-8 * np.linalg.norm(xd)
+    # the eigenvalue estimate is close to the oracle's on the same start vector
+    d = fem.diagonal(K)
+    lam = fem.lanczos_lambda_max(lambda v: K @ v, 1 / d, b, 15)
+    assert abs(st["lambda_max"] - lam) < 1e-3 * lam
+
+
+def test_solver_statuses(mfx):
+    op, om, par = make_pair(mfx, 4, 4, 4, 2)
+    b = synthetic.uniform_vector(om.n_dofs, 9)
+    b[om.constrained] = 0.0
+    bd = torch.tensor(b, device=DEV)
+    x = torch.zeros_like(bd)
+    st = op.solve(bd, x, tol=1e-10, max_it=3)
+    assert st["status"] == mfx.NOT_CONVERGED and st["iterations"] == 3
+    bn = bd.clone()
+    bn[om.n_dofs // 2] = float("nan")
+    st = op.solve(bn, x, tol=1e-10)
+    assert st["status"] == mfx.BREAKDOWN
+    z = torch.zeros_like(bd)
+    st = op.solve(z, x, tol=1e-10)
+    assert st["status"] == 0 and torch.count_nonzero(x).item() == 0
