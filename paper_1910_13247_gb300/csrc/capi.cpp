@@ -51,6 +51,34 @@ mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* 
 
 void free_workspace(mfx_op* op);
 
+mfx_status prepare_vmult(const mfx_op* op) {
+  switch (op->n) {
+    case 2: return prepare_vmult_n<2>(op);
+    case 3: return prepare_vmult_n<3>(op);
+    case 4: return prepare_vmult_n<4>(op);
+    case 5: return prepare_vmult_n<5>(op);
+    case 6: return prepare_vmult_n<6>(op);
+    case 7: return prepare_vmult_n<7>(op);
+    case 8: return prepare_vmult_n<8>(op);
+    case 9: return prepare_vmult_n<9>(op);
+    default: return set_error(MFX_EUNSUPPORTED, "degree out of range");
+  }
+}
+
+int brick_cells_for_degree(int k) {
+  switch (k + 1) {
+    case 2: return brick_cells_per_batch<2>();
+    case 3: return brick_cells_per_batch<3>();
+    case 4: return brick_cells_per_batch<4>();
+    case 5: return brick_cells_per_batch<5>();
+    case 6: return brick_cells_per_batch<6>();
+    case 7: return brick_cells_per_batch<7>();
+    case 8: return brick_cells_per_batch<8>();
+    case 9: return brick_cells_per_batch<9>();
+    default: return 0;
+  }
+}
+
 template <typename T>
 static mfx_status dev_alloc(mfx_op* op, T** p, size_t count) {
   *p = nullptr;
@@ -237,9 +265,16 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     MFX_CUDA_OP(cudaMemcpy(op->d_cell_hanging, cell_hang.data(), cell_hang.size(), cudaMemcpyHostToDevice));
   }
   const size_t nq = (size_t)op->n_cells * n3;
+  size_t metric_entries = 6 * nq;
+  if (op->structured) {
+    // structured meshes: rows of cells in batches of metric_cb, metric interleaved per batch
+    op->metric_cb = brick_cells_for_degree(k);
+    op->nchunk = (op->nx + op->metric_cb - 1) / op->metric_cb;
+    metric_entries = (size_t)op->nchunk * op->ny * op->nz * op->metric_cb * 6 * n3;
+  }
   // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
-  MFX_TRY(dev_alloc(op, &op->d_metric64, 6 * nq));
-  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, 6 * nq));
+  MFX_TRY(dev_alloc(op, &op->d_metric64, metric_entries));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, metric_entries));
   MFX_TRY(dev_alloc(op, &op->d_jxw, nq));
   MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs)));
   if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs)));
@@ -247,6 +282,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   MFX_TRY(dev_alloc(op, &op->d_partials, 4096));
   MFX_TRY(dev_alloc(op, &op->d_counter, 16));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_counter, 0, 16 * sizeof(unsigned int), s));
+  MFX_TRY(prepare_vmult(op));
   MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_diagonal(op, s));
   MFX_CUDA_OP(cudaStreamSynchronize(s));

@@ -25,7 +25,24 @@ struct GeoArgs {
   int coef_kind;
   double par0, par1;
   const double* coef_q;
+  int cb, nchunk;  // metric layout: cb = 0 -> [cell][6][q]; else [batch][6][q][cb] (structured rows)
 };
+
+// Offset of metric entry (cell, 0, q); entry e is at offset + e * metric_stride(g).
+__device__ __forceinline__ int64_t metric_offset(const GeoArgs& g, int64_t cell, int q) {
+  const int n3 = g.n * g.n * g.n;
+  if (g.cb == 0) return cell * 6 * n3 + q;
+  const int cx = (int)(cell % g.nx);
+  const int64_t rest = cell / g.nx;
+  const int cy = (int)(rest % g.ny), cz = (int)(rest / g.ny);
+  const int chunk = cx / g.cb, c = cx - chunk * g.cb;
+  const int64_t batch = chunk + (int64_t)g.nchunk * (cy + (int64_t)g.ny * cz);
+  return (batch * 6 * n3 + q) * g.cb + c;
+}
+__device__ __forceinline__ int64_t metric_stride(const GeoArgs& g) {
+  const int n3 = g.n * g.n * g.n;
+  return g.cb == 0 ? (int64_t)n3 : (int64_t)n3 * g.cb;
+}
 
 __device__ __forceinline__ void cell_vertices(const GeoArgs& g, int64_t cell, double V[8][3]) {
   if (g.structured) {
@@ -114,10 +131,10 @@ __global__ void geometry_kernel(const __grid_constant__ GeoArgs g, double* __res
       const int r = ia[e], c = ib[e];
       G[e] = f * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
     }
-    const int64_t base = cell * 6 * n3 + q;
+    const int64_t base = metric_offset(g, cell, q), st = metric_stride(g);
     for (int e = 0; e < 6; ++e) {
-      if (m64) m64[base + (int64_t)e * n3] = G[e];
-      if (m32) m32[base + (int64_t)e * n3] = (float)G[e];
+      if (m64) m64[base + e * st] = G[e];
+      if (m32) m32[base + e * st] = (float)G[e];
     }
     if (jxw) jxw[idx] = dx;
   }
@@ -194,9 +211,10 @@ __device__ double element_entry(const GeoArgs& g, const double* __restrict__ m64
   const int n = g.n, n3 = n * n * n;
   const int a1 = i % n, a2 = (i / n) % n, a3 = i / (n * n);
   const int b1 = j % n, b2 = (j / n) % n, b3 = j / (n * n);
-  const double* G = m64 + cell * 6 * n3;
+  const int64_t st = metric_stride(g);
   double s = 0.0;
   for (int q = 0; q < n3; ++q) {
+    const double* G = m64 + metric_offset(g, cell, q);
     const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
     const double Pi[3] = {g.Sd[q1 * n + a1] * g.S[q2 * n + a2] * g.S[q3 * n + a3],
                           g.S[q1 * n + a1] * g.Sd[q2 * n + a2] * g.S[q3 * n + a3],
@@ -204,8 +222,8 @@ __device__ double element_entry(const GeoArgs& g, const double* __restrict__ m64
     const double Pj[3] = {g.Sd[q1 * n + b1] * g.S[q2 * n + b2] * g.S[q3 * n + b3],
                           g.S[q1 * n + b1] * g.Sd[q2 * n + b2] * g.S[q3 * n + b3],
                           g.S[q1 * n + b1] * g.S[q2 * n + b2] * g.Sd[q3 * n + b3]};
-    const double G00 = G[q], G01 = G[n3 + q], G02 = G[2 * n3 + q];
-    const double G11 = G[3 * n3 + q], G12 = G[4 * n3 + q], G22 = G[5 * n3 + q];
+    const double G00 = G[0], G01 = G[st], G02 = G[2 * st];
+    const double G11 = G[3 * st], G12 = G[4 * st], G22 = G[5 * st];
     s += Pi[0] * (G00 * Pj[0] + G01 * Pj[1] + G02 * Pj[2]) + Pi[1] * (G01 * Pj[0] + G11 * Pj[1] + G12 * Pj[2]) +
          Pi[2] * (G02 * Pj[0] + G12 * Pj[1] + G22 * Pj[2]);
   }
@@ -308,6 +326,8 @@ static GeoArgs geo_args(const mfx_op* op) {
   g.par0 = 1.0;
   g.par1 = 0.0;
   g.coef_q = nullptr;
+  g.cb = op->metric_cb;
+  g.nchunk = op->nchunk;
   return g;
 }
 

@@ -81,6 +81,8 @@ struct mfx_op {
   bool structured = true;
   int nx = 0, ny = 0, nz = 0;             // structured cells per direction
   int cells_per_block = 0;
+  int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)
+  int nchunk = 0;                     // structured: batches per row of cells
   bool has_f64 = false, has_f32 = false;
   mfx::BasisTables basis;
   // host tables (octree) or empty (structured)
@@ -124,6 +126,12 @@ int device_sm_count();
 // vmult (vmult_k*.cu): one launcher per degree.
 mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                         const int32_t* skip = nullptr);
+template <int N>
+int brick_cells_per_batch();
+template <int N>
+mfx_status prepare_vmult_n(const mfx_op* op);
+mfx_status prepare_vmult(const mfx_op* op);
+int brick_cells_for_degree(int k);
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip);

@@ -29,8 +29,6 @@ namespace mfx {
 
 template <int N, typename Real>
 struct VmultArgs {
-  Real S[N * N];  // S[q*N + j] = l_j(xi_q)
-  Real D[N * N];  // D[q*N + p] = L_p'(xi_q) on the Gauss points
   const Real* metric;  // [cell][6][N^3]
   int64_t n_cells;
   // structured meshes
@@ -55,24 +53,40 @@ struct VmultShape {
   static constexpr int CELL = N * N * NP;         // shared elements per cube
 };
 
-template <int N, typename Real>
-__device__ __forceinline__ void contract(const Real (&M)[N * N], const Real (&in)[N], Real (&out)[N]) {
+// The 1D matrices of the translation unit's degree live in constant memory (one copy per
+// translation unit and device, uploaded when an operator of that degree is created):
+// entries [0, 81) hold S (row-major, S[q*N + j]), entries [81, 162) hold D.
+static __constant__ float c_basis32[2 * 81];
+static __constant__ double c_basis64[2 * 81];
+enum { MAT_S = 0, MAT_D = 1 };
+
+template <typename Real>
+__device__ __forceinline__ Real basis_entry(int i);
+template <>
+__device__ __forceinline__ float basis_entry<float>(int i) { return c_basis32[i]; }
+template <>
+__device__ __forceinline__ double basis_entry<double>(int i) { return c_basis64[i]; }
+
+// out = M in
+template <int N, typename Real, int MAT>
+__device__ __forceinline__ void contract(const Real (&in)[N], Real (&out)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    Real s = M[i * N] * in[0];
+    Real s = basis_entry<Real>(MAT * 81 + i * N) * in[0];
 #pragma unroll
-    for (int j = 1; j < N; ++j) s += M[i * N + j] * in[j];
+    for (int j = 1; j < N; ++j) s += basis_entry<Real>(MAT * 81 + i * N + j) * in[j];
     out[i] = s;
   }
 }
 
-template <int N, typename Real>
-__device__ __forceinline__ void contract_t(const Real (&M)[N * N], const Real (&in)[N], Real (&out)[N]) {
+// out = M^T in
+template <int N, typename Real, int MAT>
+__device__ __forceinline__ void contract_t(const Real (&in)[N], Real (&out)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    Real s = M[i] * in[0];
+    Real s = basis_entry<Real>(MAT * 81 + i) * in[0];
 #pragma unroll
-    for (int j = 1; j < N; ++j) s += M[j * N + i] * in[j];
+    for (int j = 1; j < N; ++j) s += basis_entry<Real>(MAT * 81 + j * N + i) * in[j];
     out[i] = s;
   }
 }
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
     if (act) {
       Real v[N], o[N];
       gather_xline<N, Real, STRUCT>(a, src, cell, ra, rb, v);
-      contract<N, Real>(a.S, v, o);
+      contract<N, Real, MAT_S>(v, o);
       Real* p = B0 + (rb * N + ra) * NP;
 #pragma unroll
       for (int q = 0; q < N; ++q) p[q] = o[q];
@@ -183,7 +197,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p = B0 + rb * N * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j * NP];
-      contract<N, Real>(a.S, v, o);
+      contract<N, Real, MAT_S>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p[j * NP] = o[j];
     }
@@ -194,10 +208,10 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p = B0 + rb * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j * N * NP];
-      contract<N, Real>(a.S, v, o);
+      contract<N, Real, MAT_S>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p[j * N * NP] = o[j];
-      contract<N, Real>(a.D, o, g3);
+      contract<N, Real, MAT_D>(o, g3);
     }
     __syncthreads();
     // 4) D along x -> B1 (x-line q2 = ra, q3 = rb); D along y -> B2 (y-line q1 = ra, q3 = rb)
@@ -206,14 +220,14 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       const Real* p = B0 + (rb * N + ra) * NP;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j];
-      contract<N, Real>(a.D, v, o);
+      contract<N, Real, MAT_D>(v, o);
       Real* w = B1 + (rb * N + ra) * NP;
 #pragma unroll
       for (int j = 0; j < N; ++j) w[j] = o[j];
       const Real* py = B0 + rb * N * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = py[j * NP];
-      contract<N, Real>(a.D, v, o);
+      contract<N, Real, MAT_D>(v, o);
       Real* wy = B2 + rb * N * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) wy[j * NP] = o[j];
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
         B2[sidx] = G01 * u1 + G11 * u2 + G12 * u3;
         h3[q3] = G02 * u1 + G12 * u2 + G22 * u3;
       }
-      contract_t<N, Real>(a.D, h3, t3);
+      contract_t<N, Real, MAT_D>(h3, t3);
     }
     __syncthreads();
     // 6) D_x^T on B1 in place (x-line q2 = ra, q3 = rb)
@@ -243,7 +257,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p = B1 + (rb * N + ra) * NP;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j];
-      contract_t<N, Real>(a.D, v, o);
+      contract_t<N, Real, MAT_D>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p[j] = o[j];
     }
@@ -255,7 +269,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p1 = B1 + rb * N * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p2[j * NP];
-      contract_t<N, Real>(a.D, v, o);
+      contract_t<N, Real, MAT_D>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p1[j * NP] += o[j];
     }
@@ -266,7 +280,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p = B1 + rb * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j * N * NP] + t3[j];
-      contract_t<N, Real>(a.S, v, o);
+      contract_t<N, Real, MAT_S>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p[j * N * NP] = o[j];
     }
@@ -277,7 +291,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       Real* p = B1 + rb * N * NP + ra;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j * NP];
-      contract_t<N, Real>(a.S, v, o);
+      contract_t<N, Real, MAT_S>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) p[j * NP] = o[j];
     }
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
       const Real* p = B1 + (rb * N + ra) * NP;
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j];
-      contract_t<N, Real>(a.S, v, o);
+      contract_t<N, Real, MAT_S>(v, o);
       scatter_xline<N, Real, STRUCT>(a, dst, cell, ra, rb, o);
     }
     __syncthreads();

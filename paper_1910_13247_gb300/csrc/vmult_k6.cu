@@ -6,4 +6,6 @@
 namespace mfx {
 template mfx_status launch_vmult_n<7>(const mfx_op*, mfx_prec, const void*, void*, cudaStream_t,
                                            const int32_t*);
+template int brick_cells_per_batch<7>();
+template mfx_status prepare_vmult_n<7>(const mfx_op*);
 }  // namespace mfx

@@ -6,17 +6,36 @@
 
 #include "mfx_internal.h"
 #include "vmult.cuh"
+#include "vmult_brick.cuh"
 
 namespace mfx {
 
 int device_sm_count();
 
+// Upload the 1D matrices of degree N - 1 into this translation unit's constant memory on the
+// current device (once per device; the tables depend only on the degree).
+template <int N>
+mfx_status prepare_vmult_n(const mfx_op* op) {
+  static bool done[64] = {false};
+  int dev = 0;
+  MFX_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[dev]) return MFX_OK;
+  float b32[2 * 81] = {0};
+  double b64[2 * 81] = {0};
+  for (int i = 0; i < N * N; ++i) {
+    b64[i] = op->basis.S[i];
+    b64[81 + i] = op->basis.D[i];
+    b32[i] = (float)op->basis.S[i];
+    b32[81 + i] = (float)op->basis.D[i];
+  }
+  MFX_CUDA_TRY(cudaMemcpyToSymbol(c_basis32, b32, sizeof(b32)));
+  MFX_CUDA_TRY(cudaMemcpyToSymbol(c_basis64, b64, sizeof(b64)));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return MFX_OK;
+}
+
 template <int N, typename Real>
 static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
-  for (int i = 0; i < N * N; ++i) {
-    a->S[i] = (Real)op->basis.S[i];
-    a->D[i] = (Real)op->basis.D[i];
-  }
   a->metric = std::is_same<Real, double>::value ? (const Real*)op->d_metric64 : (const Real*)op->d_metric32;
   a->n_cells = op->n_cells;
   a->nx = op->nx;
@@ -62,14 +81,49 @@ static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaSt
   return MFX_OK;
 }
 
+template <int N, typename Real>
+static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+  constexpr int CB = BrickCB<N>::value;
+  using Sh = BrickShape<N, CB>;
+  static int blocks_per_sm = -1;
+  const size_t smem = Sh::TABLE_BYTES + 3 * (size_t)Sh::CUBES * sizeof(Real);
+  auto kern = brick_vmult_kernel<N, Real, CB>;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Sh::THREADS, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  if (op->metric_cb != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
+  BrickArgs<N, Real> a;
+  a.metric = std::is_same<Real, double>::value ? (const Real*)op->d_metric64 : (const Real*)op->d_metric32;
+  a.nx = op->nx;
+  a.ny = op->ny;
+  a.nz = op->nz;
+  a.nchunk = (op->nx + CB - 1) / CB;
+  a.Mx = op->k * op->nx + 1;
+  a.My = op->k * op->ny + 1;
+  a.Mz = op->k * op->nz + 1;
+  a.n_batches = (int64_t)a.nchunk * op->ny * op->nz;
+  a.skip = skip;
+  MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(Real) * op->n_dofs, s));
+  const int grid = (int)std::min<int64_t>(a.n_batches, (int64_t)device_sm_count() * blocks_per_sm);
+  kern<<<grid, Sh::THREADS, smem, s>>>(a, src, dst);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+template <int N>
+int brick_cells_per_batch() { return BrickCB<N>::value; }
+
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip) {
   if (prec == MFX_F64) {
-    if (op->structured) return run_vmult<N, double, true>(op, (const double*)src, (double*)dst, s, skip);
+    if (op->structured) return run_brick<N, double>(op, (const double*)src, (double*)dst, s, skip);
     return run_vmult<N, double, false>(op, (const double*)src, (double*)dst, s, skip);
   }
-  if (op->structured) return run_vmult<N, float, true>(op, (const float*)src, (float*)dst, s, skip);
+  if (op->structured) return run_brick<N, float>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float, false>(op, (const float*)src, (float*)dst, s, skip);
 }
 
