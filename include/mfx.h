@@ -170,6 +170,13 @@ mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constra
  */
 mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, mfx_stream stream);
 
+/*
+ * Synchronise the stream and report device-side failures of this operator's
+ * kernels: MFX_ETIMEOUT if a bounded wait inside a kernel ran out (the word
+ * is then cleared), MFX_ECUDA for a CUDA error, else MFX_OK.
+ */
+mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream);
+
 /* diag = diagonal of K (1 on constrained rows), device, n_dofs entries. */
 mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream);
 

@@ -24,7 +24,24 @@ def _nvcc():
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) +
+                  [p for p in glob.glob(os.path.join(CSRC, "*.cpp")) if not p.endswith("gen_basis.cpp")])
+
+
+def _gen_basis_header(cuda_inc):
+    """Generate _build/basis_tables.h with the library's own host rules (compiled for the host)."""
+    hdr = os.path.join(OUT, "basis_tables.h")
+    deps = [os.path.join(CSRC, f) for f in ("gen_basis.cpp", "host_rules.cpp", "mfx_internal.h")]
+    if os.path.exists(hdr) and os.path.getmtime(hdr) >= max(os.path.getmtime(d) for d in deps):
+        return hdr
+    exe = os.path.join(OUT, "gen_basis")
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", cuda_inc, deps[0], deps[1], "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"basis generator build failed: {' '.join(cmd)}\n{r.stderr}")
+    subprocess.check_call([exe, hdr + ".tmp"])
+    os.replace(hdr + ".tmp", hdr)
+    return hdr
 
 
 def _headers():
@@ -34,14 +51,14 @@ def _headers():
 
 def _compile(src, nvcc, cuda_inc):
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
-    newest_dep = max(os.path.getmtime(h) for h in _headers() + [src])
+    newest_dep = max(os.path.getmtime(h) for h in _headers() + [src, os.path.join(OUT, "basis_tables.h")])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
     if src.endswith(".cu"):
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", OUT, "-Xcompiler", "-fPIC",
                "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-c", src, "-o", obj]
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", cuda_inc, "-c", src, "-o", obj]
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", cuda_inc, "-I", OUT, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -56,6 +73,7 @@ def build(force=False, verbose=False):
     if force:
         for o in glob.glob(os.path.join(OUT, "*.o")):
             os.remove(o)
+    _gen_basis_header(cuda_inc)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, nvcc, cuda_inc), srcs))

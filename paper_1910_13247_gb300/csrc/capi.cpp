@@ -97,7 +97,8 @@ static void destroy_op(mfx_op* op) {
   free_workspace(op);
   void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
-                  op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter};
+                  op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
+                  op->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete op;
@@ -282,6 +283,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   MFX_TRY(dev_alloc(op, &op->d_partials, 4096));
   MFX_TRY(dev_alloc(op, &op->d_counter, 16));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_counter, 0, 16 * sizeof(unsigned int), s));
+  MFX_TRY(dev_alloc(op, &op->d_err, 4));
+  MFX_CUDA_OP(cudaMemsetAsync(op->d_err, 0, 4 * sizeof(int), s));
   MFX_TRY(prepare_vmult(op));
   MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_diagonal(op, s));
@@ -404,6 +407,18 @@ mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst
   if ((prec == MFX_F64 && !op->has_f64) || (prec == MFX_F32 && !op->has_f32) || (prec != MFX_F64 && prec != MFX_F32))
     return set_error(MFX_EINVAL, "mfx_vmult: precision not built for this operator");
   return launch_vmult(op, prec, src, dst, (cudaStream_t)stream);
+}
+
+mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream) {
+  if (!op) return set_error(MFX_EINVAL, "null operator");
+  int h = 0;
+  MFX_CUDA_TRY(cudaMemcpyAsync(&h, op->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  MFX_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h) {
+    MFX_CUDA_TRY(cudaMemsetAsync(op->d_err, 0, sizeof(int), (cudaStream_t)stream));
+    return set_error(MFX_ETIMEOUT, "a bounded device wait ran out (device error word was set)");
+  }
+  return MFX_OK;
 }
 
 mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream) {

@@ -108,6 +108,7 @@ struct mfx_op {
   double* d_scalars = nullptr;       // device scalars for reductions / solver state
   double* d_partials = nullptr;      // reduction partials
   unsigned int* d_counter = nullptr; // last-block reduction counter
+  int* d_err = nullptr;              // set by a kernel whose bounded wait ran out
   int64_t bytes_device = 0;
 };
 

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "basis_tables.h"
+
 namespace mfx {
 
 template <int N, typename Real>
@@ -53,28 +55,25 @@ struct VmultShape {
   static constexpr int CELL = N * N * NP;         // shared elements per cube
 };
 
-// The 1D matrices of the translation unit's degree live in constant memory (one copy per
-// translation unit and device, uploaded when an operator of that degree is created):
-// entries [0, 81) hold S (row-major, S[q*N + j]), entries [81, 162) hold D.
-static __constant__ float c_basis32[2 * 81];
-static __constant__ double c_basis64[2 * 81];
+// The 1D matrices are compile-time constants (generated at build time from the library's
+// own rules, basis_tables.h), so every contraction is a chain of FMAs with immediate
+// operands: S[q*N + j] = l_j(xi_q) (GLL basis at Gauss points), D[q*N + p] = L_p'(xi_q)
+// (collocation derivative on the Gauss points).
 enum { MAT_S = 0, MAT_D = 1 };
 
-template <typename Real>
-__device__ __forceinline__ Real basis_entry(int i);
-template <>
-__device__ __forceinline__ float basis_entry<float>(int i) { return c_basis32[i]; }
-template <>
-__device__ __forceinline__ double basis_entry<double>(int i) { return c_basis64[i]; }
+template <int N, int MAT>
+__device__ __forceinline__ constexpr double basis_entry(int i) {
+  return MAT == MAT_S ? BasisConst<N>::S(i) : BasisConst<N>::D(i);
+}
 
 // out = M in
 template <int N, typename Real, int MAT>
 __device__ __forceinline__ void contract(const Real (&in)[N], Real (&out)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    Real s = basis_entry<Real>(MAT * 81 + i * N) * in[0];
+    Real s = Real(basis_entry<N, MAT>(i * N)) * in[0];
 #pragma unroll
-    for (int j = 1; j < N; ++j) s += basis_entry<Real>(MAT * 81 + i * N + j) * in[j];
+    for (int j = 1; j < N; ++j) s += Real(basis_entry<N, MAT>(i * N + j)) * in[j];
     out[i] = s;
   }
 }
@@ -84,9 +83,9 @@ template <int N, typename Real, int MAT>
 __device__ __forceinline__ void contract_t(const Real (&in)[N], Real (&out)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    Real s = basis_entry<Real>(MAT * 81 + i) * in[0];
+    Real s = Real(basis_entry<N, MAT>(i)) * in[0];
 #pragma unroll
-    for (int j = 1; j < N; ++j) s += basis_entry<Real>(MAT * 81 + j * N + i) * in[j];
+    for (int j = 1; j < N; ++j) s += Real(basis_entry<N, MAT>(j * N + i)) * in[j];
     out[i] = s;
   }
 }

@@ -1,23 +1,26 @@
 // Matrix-free Q_k Laplacian on structured meshes: "brick-row" kernel.
 //
 // A batch is CB consecutive cells along x in one row (cy, cz).  Per batch:
-//  0. the DoFs of the batch, (CB k + 1) x n x n lattice points, are read
-//     with coalesced row loads and written into per-cell cubes in shared
-//     memory (nodes shared by neighbouring cells are stored in both cubes;
-//     Dirichlet values read as 0);
-//  1. forward 1D contractions (Sec. 3.6, tensor-product evaluation):
-//     S_z, S_y, S_x (values at Gauss points), then D_x (registers), D_y, D_z;
-//  2. h = G_q grad at every Gauss point (G prefetched from HBM into
-//     registers at the start of the batch: 6 values per point, stored
-//     interleaved as [batch][6][q][CB] so that loads are coalesced);
-//  3. transposed contractions D^T then S^T, summed over the three gradient
-//     components;
-//  4. the cube results are summed over shared nodes and added to dst with
-//     coalesced atomic adds (Dirichlet rows get dst = src).
+//  0. the batch's DoFs, (CB k + 1) x n x n lattice points in n^2 contiguous
+//     rows of the global vector, are copied into a row-major shared-memory
+//     tile with 4/8-byte asynchronous copies (cp.async), one batch ahead
+//     for FP32 (double-buffered); Dirichlet points are stored as 0;
+//  1. forward 1D contractions (tensor-product evaluation, Sec. 3.6):
+//     S_z (reading z-lines straight from the tile), S_y, S_x (values at the
+//     Gauss points), then D_x (registers), D_y, D_z (reference gradient);
+//  2. h = G_q grad at every Gauss point, G prefetched into registers at the
+//     start of the batch (six entries per point stored as [batch][6][q][CB],
+//     so that the loads of a warp are coalesced);
+//  3. transposed contractions D^T, summed over the three components, then
+//     S_x^T, S_y^T, and S_z^T writing straight into a row-major output
+//     tile (nodes shared by neighbouring cells are summed in two passes);
+//  4. the tile is added to dst with coalesced atomic adds (Dirichlet rows
+//     get dst = src; dst is zeroed before the launch).
 // Every 1D contraction is done by a thread owning one line of one cell;
-// lanes run over cells fastest, and the cube paddings (NP, P2, CELL) were
-// chosen so that all line accesses of a warp are free of bank conflicts
-// (FP32 words).
+// lanes run over cells fastest, and the cube paddings (NP, P2, CELL) and the
+// tile skew/pitch were chosen so that the line accesses of a warp are free
+// of shared-memory bank conflicts (FP32 words; the tile phases of even n
+// keep a 1.5-way conflict).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,15 +31,15 @@
 namespace mfx {
 
 // cells per batch for each n (= k + 1)
-template <int N> struct BrickCB { static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : 8); };
+template <int N> struct BrickCB { static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : N == 8 ? 8 : 4); };
 
-template <int N, int CB>
+template <int N, int CB, typename Real>
 struct BrickShape {
   static constexpr int K = N - 1;
   static constexpr int LINES = CB * N * N;
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr bool XSWAP = (N % 2) == 0;
-  // conflict-free paddings (see the layout search in the design notes)
+  // conflict-free cube paddings
   static constexpr int NP = N;
   static constexpr int P2 = N == 2 ? (CB == 16 ? 5 : 4) : N == 3 ? 9 : N == 4 ? 17 : N == 5 ? 25 : N == 6 ? 37
                           : N == 7 ? 49 : N == 8 ? 65 : 81;
@@ -44,11 +47,16 @@ struct BrickShape {
                             : N == 4 ? (CB == 8 ? 68 : 70) : N == 5 ? (CB == 8 ? 132 : 126)
                             : N == 6 ? 222 : N == 7 ? 346 : N == 8 ? (CB == 4 ? 520 : 524) : (CB == 4 ? 744 : 732);
   static constexpr int CUBES = CB * CELL;  // elements per cube array
-  static constexpr int WMAX = CB * K + 1;  // lattice points per row of a full batch
-  static constexpr int TILE = N * N * WMAX;
-  static constexpr int TILE_ITERS = (TILE + THREADS - 1) / THREADS;
-  // bytes of shared memory before the cubes: the tile descriptor table (2 words per element)
-  static constexpr int TABLE_BYTES = (TILE * 8 + 15) / 16 * 16;
+  // row-major tile: point x of row r at r * PITCH + x + (x / K) * SKEW
+  static constexpr int WMAX = CB * K + 1;
+  static constexpr bool F32 = sizeof(Real) == 4;
+  static constexpr int SKEW = !F32 ? 0 : N == 4 ? 3 : N == 5 ? 2 : N == 6 ? 1 : N == 8 ? 5 : 0;
+  static constexpr int PITCH_MIN = WMAX + (WMAX - 1) / K * SKEW;
+  static constexpr int PITCH = !F32 ? (WMAX | 1) : (N <= 3 ? 33 : N == 9 ? 33 : 97);
+  static_assert(PITCH >= PITCH_MIN, "tile pitch too small");
+  static constexpr int TILE = N * N * PITCH;  // elements per tile buffer
+  static constexpr int NBUF = F32 ? 2 : 1;    // input tiles (double-buffered for FP32); output aliases
+  static constexpr size_t SMEM = (size_t)(NBUF * TILE + 3 * CUBES) * sizeof(Real);
 };
 
 template <int N, typename Real>
@@ -88,88 +96,96 @@ __device__ __forceinline__ BatchInfo batch_info(const Args& a, int b) {
   return bi;
 }
 
-__device__ __forceinline__ bool tile_boundary(const BatchInfo& bi, int dy, int x) {
-  return ((dy >> 23) & bi.eflags) != 0 || (x == 0 && bi.xlo) || (x == bi.Wm - 1 && bi.xhi);
+template <typename Real>
+__device__ __forceinline__ void cp_async(Real* smem, const Real* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(Real) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
 
 template <int N, typename Real, int CB>
-__global__ void __launch_bounds__(BrickShape<N, CB>::THREADS,
-                                  (sizeof(Real) == 4 ? (1024 / BrickShape<N, CB>::THREADS > 0 ? 1024 / BrickShape<N, CB>::THREADS : 1) : 1))
+__global__ void __launch_bounds__(BrickShape<N, CB, Real>::THREADS,
+                                  (sizeof(Real) == 4 ? (1024 / BrickShape<N, CB, Real>::THREADS > 0
+                                                            ? 1024 / BrickShape<N, CB, Real>::THREADS : 1) : 1))
     brick_vmult_kernel(const __grid_constant__ BrickArgs<N, Real> a, const Real* __restrict__ src,
                        Real* __restrict__ dst) {
-  using Sh = BrickShape<N, CB>;
+  using Sh = BrickShape<N, CB, Real>;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
+  constexpr int PITCH = Sh::PITCH, SKEW = Sh::SKEW, WMAX = Sh::WMAX;
   constexpr bool PREFETCH = 6 * N * (int)sizeof(Real) / 4 <= 32;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // Tile descriptors (independent of the batch): element e of the (CB K + 1) x N x N lattice tile
-  //   w0 = lattice offset x + Mx (a2 + My a3) relative to the batch's first point,
-  //   w1 = cube slot of the element | shared-with-previous-cell bit << 14 | x << 15 | edge flags << 23.
-  int2* table = reinterpret_cast<int2*>(smem_raw);
-  Real* A = reinterpret_cast<Real*>(smem_raw + Sh::TABLE_BYTES);
+  Real* tiles = reinterpret_cast<Real*>(smem_raw);
+  Real* A = tiles + Sh::NBUF * Sh::TILE;
   Real* B = A + Sh::CUBES;
   Real* C = B + Sh::CUBES;
-  const int t = threadIdx.x;
-  for (int e = t; e < Sh::TILE; e += Sh::THREADS) {
-    const int rr = e / Sh::WMAX, x = e - rr * Sh::WMAX;
-    const int a2 = rr % N, a3 = rr / N;
-    const int cc = x / K, a1 = x - cc * K;
-    const int off = a3 * P2 + a2 * NP;
-    // the last point of a row belongs to the last cell only (slot of cell cc - 1, node K)
-    const int slot = cc < CB ? cc * CELL + off + a1 : (cc - 1) * CELL + off + K;
-    const int shared_prev = (a1 == 0 && cc >= 1 && cc < CB) ? 1 : 0;
-    const int flags = (a2 == 0 ? 1 : 0) | (a2 == K ? 2 : 0) | (a3 == 0 ? 4 : 0) | (a3 == K ? 8 : 0);
-    table[e] = make_int2(x + a.Mx * (a2 + a.My * a3), slot | (shared_prev << 14) | (x << 15) | (flags << 23));
-  }
-  __syncthreads();
 
+  const int t = threadIdx.x;
   const int c = t % CB;
   const int r = t / CB;
   const int f = r % N, s = r / N;
   const bool line_ok = t < Sh::LINES;
-  // line bases
+  // line bases in the cubes
   const int xa2 = Sh::XSWAP ? s : f, xa3 = Sh::XSWAP ? f : s;
   const int xbase = c * CELL + xa3 * P2 + xa2 * NP;  // x-line (a2, a3), stride 1
   const int ybase = c * CELL + s * P2 + f;          // y-line (a1 = f, a3 = s), stride NP
   const int zbase = c * CELL + s * NP + f;          // z-line (a1 = f, a2 = s), stride P2
+  // z-line (a1 = f, a2 = s) in the tile: point x = c K + f of rows a3 N + s
+  const int zx = c * K + f;
+  const int ztile = s * PITCH + zx + (zx / K) * SKEW;  // + a3 * N * PITCH
   const int n_batches = (int)a.n_batches;
 
-  // tile values of the next batch, loaded one batch ahead (Dirichlet points read as 0)
-  Real pre[Sh::TILE_ITERS];
-  auto load_tile = [&](int bb) {
+  // issue the asynchronous copies of batch bb into tile buffer `buf` (Dirichlet points set to 0);
+  // warp w copies tile rows w, w + NWARPS, ...; lanes walk the points of the row
+  constexpr int NWARPS = Sh::THREADS / 32, XITERS = (WMAX + 31) / 32;
+  const int warp = t >> 5, lane = t & 31;
+  auto load_tile = [&](int bb, Real* buf) {
     const BatchInfo bi = batch_info<CB, K>(a, bb);
+    for (int row = warp; row < N * N; row += NWARPS) {
+      const int a2 = row % N, a3 = row / N;
+      const int rflags = (a2 == 0 ? 1 : 0) | (a2 == K ? 2 : 0) | (a3 == 0 ? 4 : 0) | (a3 == K ? 8 : 0);
+      const bool rbnd = (rflags & bi.eflags) != 0;
+      const Real* g = src + bi.gbase + a.Mx * (a2 + a.My * a3);
+      Real* p = buf + row * PITCH;
 #pragma unroll
-    for (int it = 0; it < Sh::TILE_ITERS; ++it) {
-      const int e = t + it * Sh::THREADS;
-      pre[it] = Real(0);
-      if (e < Sh::TILE) {
-        const int2 d = table[e];
-        const int x = (d.y >> 15) & 0xff;
-        if (x < bi.Wm && !tile_boundary(bi, d.y, x)) pre[it] = __ldg(src + bi.gbase + d.x);
+      for (int j = 0; j < XITERS; ++j) {
+        const int x = lane + 32 * j;
+        if (x < bi.Wm) {
+          const bool bnd = rbnd || (x == 0 && bi.xlo) || (x == bi.Wm - 1 && bi.xhi);
+          Real* q = p + x + (x / K) * SKEW;
+          if (bnd)
+            *q = Real(0);
+          else
+            cp_async(q, g + x);
+        }
       }
     }
+    cp_async_commit();
   };
-  if ((int)blockIdx.x < n_batches) load_tile(blockIdx.x);
+
+  int buf = 0;
+  if (Sh::NBUF == 2 && (int)blockIdx.x < n_batches) load_tile(blockIdx.x, tiles);
 
   for (int b = blockIdx.x; b < n_batches; b += gridDim.x) {
     const BatchInfo bi = batch_info<CB, K>(a, b);
-    const int m = bi.m, Wm = bi.Wm;
+    const int m = bi.m;
     const bool act = line_ok && c < m;
     const Real* Gb = a.metric + (int64_t)b * (6 * N3 * CB) + (xa2 * N + xa3 * N * N) * CB + c;
+    Real* T = tiles + buf * Sh::TILE;
 
-    // 0) the prefetched lattice points of this batch into the cubes
-#pragma unroll
-    for (int it = 0; it < Sh::TILE_ITERS; ++it) {
-      const int e = t + it * Sh::THREADS;
-      if (e < Sh::TILE) {
-        const int2 d = table[e];
-        const int x = (d.y >> 15) & 0xff;
-        if (x < Wm) {
-          const int slot = d.y & 0x3fff;
-          A[slot] = pre[it];
-          if ((d.y >> 14) & 1) A[slot - CELL + K] = pre[it];
-        }
-      }
+    if constexpr (Sh::NBUF == 2) {
+      // copies of the next batch go into the other buffer; this batch's copies were issued earlier
+      if (b + (int)gridDim.x < n_batches) load_tile(b + gridDim.x, tiles + (buf ^ 1) * Sh::TILE);
+      else cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      load_tile(b, T);
+      cp_async_wait<0>();
     }
     // metric of this thread's x-line, consumed four phases later
     Real G[PREFETCH ? 6 : 1][N];
@@ -180,13 +196,11 @@ __global__ void __launch_bounds__(BrickShape<N, CB>::THREADS,
         for (int q = 0; q < N; ++q) G[e][q] = __ldg(Gb + (e * N3 + q) * CB);
     }
     __syncthreads();
-    // next batch's lattice points (consumed after ten phases)
-    if (b + (int)gridDim.x < n_batches) load_tile(b + gridDim.x);
-    // 1) S along z (in place)
+    // 1) S along z: z-lines from the tile into cube A
     if (act) {
       Real v[N], o[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
+      for (int j = 0; j < N; ++j) v[j] = T[ztile + j * N * PITCH];
       contract<N, Real, MAT_S>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
@@ -286,35 +300,53 @@ __global__ void __launch_bounds__(BrickShape<N, CB>::THREADS,
       for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
     }
     __syncthreads();
-    // 9) S_z^T
+    // 9) S_z^T into the output tile (aliases this batch's input tile, consumed in step 1):
+    //    nodes with a1 < K first, then the a1 = K nodes add to the next cell's a1 = 0 node
+    Real o9[N];
     if (act) {
-      Real v[N], o[N];
+      Real v[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
-      contract_t<N, Real, MAT_S>(v, o);
+      contract_t<N, Real, MAT_S>(v, o9);
+      if (f < K) {
 #pragma unroll
-      for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
-    }
-    __syncthreads();
-    // 10) scatter: sum shared nodes, coalesced atomic adds; constrained rows copy src
-#pragma unroll 4
-    for (int e = t; e < Sh::TILE; e += Sh::THREADS) {
-      const int2 d = table[e];
-      const int x = (d.y >> 15) & 0xff;
-      if (x >= Wm) continue;
-      const int gi = bi.gbase + d.x;
-      const int slot = d.y & 0x3fff;
-      if (tile_boundary(bi, d.y, x)) {
-        dst[gi] = __ldg(src + gi);
-      } else {
-        // last point of a partial batch: only the previous (last valid) cell contributes
-        Real v = (x == Wm - 1 && m < CB) ? Real(0) : A[slot];
-        if ((d.y >> 14) & 1) v += A[slot - CELL + K];
-        red_add(dst + gi, v);
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] = o9[j];
       }
     }
     __syncthreads();
+    if (act && f == K) {
+      if (c < m - 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] += o9[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] = o9[j];
+      }
+    }
+    __syncthreads();
+    // 10) scatter: coalesced atomic adds, warp per tile row; constrained rows copy src
+    for (int row = warp; row < N * N; row += NWARPS) {
+      const int a2 = row % N, a3 = row / N;
+      const int rflags = (a2 == 0 ? 1 : 0) | (a2 == K ? 2 : 0) | (a3 == 0 ? 4 : 0) | (a3 == K ? 8 : 0);
+      const bool rbnd = (rflags & bi.eflags) != 0;
+      const int g = bi.gbase + a.Mx * (a2 + a.My * a3);
+      const Real* p = T + row * PITCH;
+#pragma unroll
+      for (int j = 0; j < XITERS; ++j) {
+        const int x = lane + 32 * j;
+        if (x < bi.Wm) {
+          const bool bnd = rbnd || (x == 0 && bi.xlo) || (x == bi.Wm - 1 && bi.xhi);
+          if (bnd)
+            dst[g + x] = __ldg(src + g + x);
+          else
+            red_add(dst + g + x, p[x + (x / K) * SKEW]);
+        }
+      }
+    }
+    __syncthreads();
+    buf ^= (Sh::NBUF - 1);
   }
+  if constexpr (Sh::NBUF == 2) cp_async_wait<0>();
 }
 
 }  // namespace mfx

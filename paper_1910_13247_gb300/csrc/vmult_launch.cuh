@@ -2,35 +2,25 @@
 #pragma once
 
 #include <algorithm>
+#include <string>
 #include <type_traits>
 
 #include "mfx_internal.h"
 #include "vmult.cuh"
 #include "vmult_brick.cuh"
+#include "vmult_brick_tma.cuh"
 
 namespace mfx {
 
 int device_sm_count();
 
-// Upload the 1D matrices of degree N - 1 into this translation unit's constant memory on the
-// current device (once per device; the tables depend only on the degree).
+// The kernels use the build-time tables; check that they match the operator's tables
+// (computed at run time by the same routines) bit for bit.
 template <int N>
 mfx_status prepare_vmult_n(const mfx_op* op) {
-  static bool done[64] = {false};
-  int dev = 0;
-  MFX_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && done[dev]) return MFX_OK;
-  float b32[2 * 81] = {0};
-  double b64[2 * 81] = {0};
-  for (int i = 0; i < N * N; ++i) {
-    b64[i] = op->basis.S[i];
-    b64[81 + i] = op->basis.D[i];
-    b32[i] = (float)op->basis.S[i];
-    b32[81 + i] = (float)op->basis.D[i];
-  }
-  MFX_CUDA_TRY(cudaMemcpyToSymbol(c_basis32, b32, sizeof(b32)));
-  MFX_CUDA_TRY(cudaMemcpyToSymbol(c_basis64, b64, sizeof(b64)));
-  if (dev >= 0 && dev < 64) done[dev] = true;
+  for (int i = 0; i < N * N; ++i)
+    if (BasisConst<N>::S(i) != op->basis.S[i] || BasisConst<N>::D(i) != op->basis.D[i])
+      return set_error(MFX_EUNSUPPORTED, "build-time basis tables differ from the run-time ones");
   return MFX_OK;
 }
 
@@ -84,9 +74,9 @@ static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaSt
 template <int N, typename Real>
 static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   constexpr int CB = BrickCB<N>::value;
-  using Sh = BrickShape<N, CB>;
+  using Sh = BrickShape<N, CB, Real>;
   static int blocks_per_sm = -1;
-  const size_t smem = Sh::TABLE_BYTES + 3 * (size_t)Sh::CUBES * sizeof(Real);
+  const size_t smem = Sh::SMEM;
   auto kern = brick_vmult_kernel<N, Real, CB>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -116,6 +106,91 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
 template <int N>
 int brick_cells_per_batch() { return BrickCB<N>::value; }
 
+// dst = src on the Dirichlet (box boundary) DoFs; one warp per lattice row (J, L).
+template <typename Real>
+__global__ void boundary_rows_kernel(int Mx, int My, int Mz, const Real* __restrict__ src, Real* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int rows = My * Mz;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
+    const int J = row % My, L = row / My;
+    const int64_t base = (int64_t)Mx * row;
+    if (J == 0 || J == My - 1 || L == 0 || L == Mz - 1) {
+      for (int I = lane; I < Mx; I += 32) dst[base + I] = src[base + I];
+    } else if (lane == 0) {
+      dst[base] = src[base];
+      dst[base + Mx - 1] = src[base + Mx - 1];
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static mfx_status encode_1d_map(CUtensorMap* map, const void* ptr, int64_t n, int box) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    MFX_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (!p || q != cudaDriverEntryPointSuccess) return set_error(MFX_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  if (((uintptr_t)ptr & 15) != 0) return set_error(MFX_EINVAL, "vectors must be 16-byte aligned");
+  const cuuint64_t dim[1] = {(cuuint64_t)n};
+  // rank 1 has no strides, but the driver expects a valid array
+  const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+  const cuuint32_t boxd[1] = {(cuuint32_t)box};
+  const cuuint32_t estr[1] = {1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<void*>(ptr), dim, strides, boxd, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(MFX_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return MFX_OK;
+}
+
+template <int N>
+static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  constexpr int CB = BrickCB<N>::value;
+  using Sh = BrickShape<N, CB, float>;
+  using Tm = TmaShape<N, CB>;
+  static int blocks_per_sm = -1;
+  const size_t smem = (size_t)(4 * Tm::TILE + 3 * Sh::CUBES + 1) * sizeof(float) + 2 * sizeof(uint64_t);
+  auto kern = brick_vmult_tma_kernel<N, CB>;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Sh::THREADS, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  if (op->metric_cb != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
+  TmaArgs<N> a;
+  mfx_status st = encode_1d_map(&a.tsrc, src, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  st = encode_1d_map(&a.tdst, dst, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  a.metric = op->d_metric32;
+  a.nx = op->nx;
+  a.ny = op->ny;
+  a.nz = op->nz;
+  a.nchunk = (op->nx + CB - 1) / CB;
+  a.Mx = op->k * op->nx + 1;
+  a.My = op->k * op->ny + 1;
+  a.Mz = op->k * op->nz + 1;
+  a.n_batches = a.nchunk * op->ny * op->nz;
+  a.err = op->d_err;
+  a.skip = skip;
+  MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
+  const int rows = a.My * a.Mz;
+  boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
+      a.Mx, a.My, a.Mz, src, dst);
+  const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
+  kern<<<grid, Sh::THREADS, smem, s>>>(a);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip) {
@@ -123,7 +198,7 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     if (op->structured) return run_brick<N, double>(op, (const double*)src, (double*)dst, s, skip);
     return run_vmult<N, double, false>(op, (const double*)src, (double*)dst, s, skip);
   }
-  if (op->structured) return run_brick<N, float>(op, (const float*)src, (float*)dst, s, skip);
+  if (op->structured) return run_brick_tma<N>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float, false>(op, (const float*)src, (float*)dst, s, skip);
 }
 

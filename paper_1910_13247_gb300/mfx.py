@@ -83,6 +83,7 @@ def lib():
         "mfx_get_tables": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "mfx_vmult": (S, [_VP, S, _VP, _VP, _VP]),
         "mfx_diagonal": (S, [_VP, S, _VP, _VP]),
+        "mfx_device_check": (S, [_VP, _VP]),
         "mfx_quadrature_points": (S, [_VP, _VP, _VP]),
         "mfx_rhs": (S, [_VP, _VP, _VP, _VP]),
         "mfx_distribute": (S, [_VP, _VP, _VP]),
@@ -229,6 +230,10 @@ class Operator:
         assert src.numel() == self.n_dofs and dst.numel() == self.n_dofs
         check(lib().mfx_vmult(self.handle, _prec_of(src), _ptr(src), _ptr(dst), _stream(stream)))
         return dst
+
+    def device_check(self):
+        """Synchronise and raise if a bounded device wait of this operator ran out."""
+        check(lib().mfx_device_check(self.handle, _stream()))
 
     def diagonal(self, out):
         assert out.numel() == self.n_dofs
