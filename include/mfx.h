@@ -208,6 +208,21 @@ mfx_status mfx_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, co
                    double* result, mfx_stream stream);
 
 /*
+ * Allocation-free variant of mfx_dot (the paper has no counterpart: this is an
+ * interface for callers that may not allocate device memory, such as code running
+ * during CUDA graph capture or inside another runtime's memory pool).  Same result
+ * as mfx_dot, without an operator: the reduction partials live in a fixed array of
+ * about 8 KB compiled into the library (kept on every GPU that loads it until exit).
+ * a, b: device vectors of n entries of the precision; result: device FP64 scalar.
+ * n above MFX_NOALLOC_MAX_N is rejected with MFX_EINVAL.  The first call on a device
+ * looks up the array's address; make it before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race and give wrong results.
+ */
+#define MFX_NOALLOC_MAX_N 2147483647LL
+mfx_status mfx_dot_noalloc(mfx_prec prec, int64_t n, const void* a, const void* b, double* result,
+                           mfx_stream stream);
+
+/*
  * Chebyshev-Jacobi preconditioner (smoother named in Sec. 3.5 and Sec. 6.1):
  * z = p(D^-1 K) D^-1 r with 1 - lambda p(lambda) = T_m(s(lambda)) / T_m(s(0)),
  * s(lambda) = (hi + lo - 2 lambda) / (hi - lo), m = degree >= 1, computed by

@@ -88,6 +88,7 @@ def lib():
         "mfx_rhs": (S, [_VP, _VP, _VP, _VP]),
         "mfx_distribute": (S, [_VP, _VP, _VP]),
         "mfx_dot": (S, [_VP, S, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+        "mfx_dot_noalloc": (S, [S, ctypes.c_int64, _VP, _VP, _VP, _VP]),
         "mfx_chebyshev": (S, [_VP, S, _VP, _VP, S, ctypes.c_double, ctypes.c_double, _VP]),
         "mfx_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
         "mfx_solve": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
@@ -123,6 +124,13 @@ def _prec_of(t):
     if t.dtype == torch.float32:
         return F32
     raise TypeError("vectors must be float64 or float32")
+
+
+def dot_noalloc(a, b, out, n=None, stream=None):
+    """out[0] = sum a_i b_i (FP64) without any device allocation (fixed library scratch)."""
+    n = a.numel() if n is None else n
+    check(lib().mfx_dot_noalloc(_prec_of(a), n, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+    return out
 
 
 class Mesh:
