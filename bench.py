@@ -31,6 +31,26 @@ METRIC = "matrix-free vmult GDoF/s (FP64 vs FP32 mixed) and % HBM peak; solve p5
 WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2pi y)z, Dirichlet"
 
 
+# DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
+# profiles/vmult_fp32_tma_q4_48cube.md (48^3 case scaled by cells).  Valid only for the kernel sources it
+# was taken from: any change to them makes the figure stale (reported as null).
+TRAFFIC_BYTES = 979.0e6
+TRAFFIC_SOURCES = {"vmult_brick_tma.cuh": "50cedac7d8f2e8a9", "vmult_brick.cuh": "aa71379d66c00ec7",
+                   "vmult.cuh": "d3511f8f3650319c"}
+
+
+def measured_traffic(nx, k):
+    import hashlib
+    if (nx, k) != (NX, K_DEG):
+        return None
+    csrc = os.path.join(ROOT, "paper_1910_13247_gb300", "csrc")
+    for name, digest in TRAFFIC_SOURCES.items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
+                return None
+    return TRAFFIC_BYTES
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -138,6 +158,7 @@ def main():
     ap.add_argument("--impl", default="mfx")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-solve", action="store_true", help="skip the solve measurements")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 96^3 Q3 mixed-precision solve")
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
     args = ap.parse_args()
@@ -250,7 +271,8 @@ def main():
                    "step": "one FP32 vmult", "l2": "inputs larger than L2 (%.2f GB read+written per step)" % (b32 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "vmult (prologue + vmult_kernel), FP32",
+                     "traffic": measured_traffic(nx, kdeg), "peak_kind": peak_kind,
+                     "kernel": "FP32 vmult (boundary_rows_kernel + brick_vmult_tma_kernel), timed together",
                      "algorithmic_bytes": b32},
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": ms_e2e},
@@ -264,6 +286,8 @@ def main():
 
     if not args.no_solve:
         line["solve"] = solve_measurements(mfx, synthetic, torch, np)
+        if not args.no_mixed:
+            line["solve"]["mixed_96x96x96_q3"] = mixed_solve_measurement(mfx, synthetic, torch, np)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -296,6 +320,37 @@ def solve_measurements(mfx, synthetic, torch, np):
     lat = sorted(lat[3:])
     out["poisson_8x8x8_q2_jacobi_pcg"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                            "iterations": its, "rel_residual": st["rel_residual"], "runs": len(lat)}
+    return out
+
+
+def mixed_solve_measurement(mfx, synthetic, torch, np):
+    """96^3 deformed Q3 with the variable coefficient: FP64 Chebyshev(5)-Jacobi PCG versus FP32 PCG with the
+    same preconditioner (to 1e-4) inside FP64 defect correction, both to a 1e-10 relative residual."""
+    nx = 96
+    m = mfx.Mesh.structured_box(nx, nx, nx, synthetic.deformed_vertices(nx, nx, nx))
+    op = mfx.Operator(m, 3, mfx.COEF_TRIG, (1.0, 0.5))
+    n = op.n_dofs
+    b = torch.tensor(synthetic.gaussian_vector(n, 3), device="cuda")
+    t = torch.tensor(synthetic.uniform_vector(n, 33), device="cuda")
+    out = {"n_dofs": n}
+    xs = {}
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        # constrained rows of b are zero: the right-hand side lives on the free DoFs
+        x = torch.zeros_like(b)
+        bb = b.clone()
+        op.distribute(bb)   # Dirichlet entries -> 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.solve(bb, x, tol=1e-10, precond=mfx.PRECOND_CHEBYSHEV, cheb_degree=5, mixed=mixed,
+                      inner_tol=1e-4, lanczos_start=t)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xs[name] = x
+        out[name] = {"seconds": dt, "status": st["status"], "iterations": st["iterations"],
+                     "inner_iterations": st["inner_iterations"], "rel_residual": st["rel_residual"],
+                     "lambda_max": st["lambda_max"]}
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["rel_difference_mixed_vs_fp64"] = float((xs["mixed"] - xs["fp64"]).norm() / xs["fp64"].norm())
     return out
 
 
