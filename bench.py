@@ -159,6 +159,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-solve", action="store_true", help="skip the solve measurements")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96^3 Q3 mixed-precision solve")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched solve")
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
     args = ap.parse_args()
@@ -288,6 +289,8 @@ def main():
         line["solve"] = solve_measurements(mfx, synthetic, torch, np)
         if not args.no_mixed:
             line["solve"]["mixed_96x96x96_q3"] = mixed_solve_measurement(mfx, synthetic, torch, np)
+        if not args.no_batch:
+            line["batched"] = batched_measurement(mfx, synthetic, torch, np)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -321,6 +324,51 @@ def solve_measurements(mfx, synthetic, torch, np):
     out["poisson_8x8x8_q2_jacobi_pcg"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                            "iterations": its, "rel_residual": st["rel_residual"], "runs": len(lat)}
     return out
+
+
+def batched_measurement(mfx, synthetic, torch, np, n_problems=64, seed=4):
+    """64 independent Poisson problems (unit cube, N^3 cells with N uniform in [4, 32], degree uniform in 1..6,
+    uniform[-1, 1] right-hand sides, FP32 inner / FP64 outer Jacobi-PCG to 1e-10) advanced together by one
+    graph launch per tick, against the same solves run one after another."""
+    g = synthetic.rng(seed)
+    Ns = g.integers(4, 33, size=n_problems)
+    ks = g.integers(1, 7, size=n_problems)
+    ops, bs = [], []
+    for i in range(n_problems):
+        op = mfx.Operator(mfx.Mesh.structured_box(int(Ns[i]), int(Ns[i]), int(Ns[i])), int(ks[i]))
+        b = torch.tensor(synthetic.uniform_vector(op.n_dofs, 1000 + i), device="cuda")
+        op.distribute(b)
+        ops.append(op)
+        bs.append(b)
+    total_dofs = sum(op.n_dofs for op in ops)
+    # one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_inner = 0
+    for op, b in zip(ops, bs):
+        st = op.solve(b, torch.zeros_like(b), tol=1e-10, mixed=True)
+        seq_inner += st["inner_iterations"] * op.n_dofs
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    # together
+    batch = mfx.Batch(n_problems, chunk=16)
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    slots = [batch.add(op, b, x, tol=1e-10, mixed=True) for op, b, x in zip(ops, bs, xs)]
+    ticks = batch.run()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    dof_iters, worst, statuses = 0, 0.0, set()
+    for op, s in zip(ops, slots):
+        done, st = batch.poll(s)
+        statuses.add(st["status"])
+        dof_iters += st["inner_iterations"] * op.n_dofs
+        worst = max(worst, st["rel_residual"])
+    return {"problems": n_problems, "total_dofs": total_dofs, "seconds": t_batch, "ticks": ticks,
+            "dof_iterations_per_s": dof_iters / t_batch, "statuses": sorted(statuses), "max_rel_residual": worst,
+            "sequential_seconds": t_seq, "speedup_over_sequential": t_seq / t_batch,
+            "sizes": {"N": [int(v) for v in Ns], "k": [int(v) for v in ks]}}
 
 
 def mixed_solve_measurement(mfx, synthetic, torch, np):

@@ -273,6 +273,33 @@ void mfx_solve_params_default(mfx_solve_params* params);
 mfx_status mfx_solve(const mfx_op* op, const double* b, double* x, const mfx_solve_params* params,
                      mfx_solve_stats* stats, mfx_stream stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/*
+ * A batch advances many independent solves together (workload: many small
+ * problems of uneven size, or a stream of requests).  Each slot holds one
+ * operator and runs the mixed-precision solve of mfx_solve (mixed = 1:
+ * FP64 residual and update, FP32 PCG inner solve) or the FP64 PCG
+ * (mixed = 0).  One call to mfx_batch_step is one scheduler tick: FP64
+ * residuals of the slots between inner solves, then ONE graph launch whose
+ * child graphs advance every slot in an inner solve by `chunk` iterations
+ * (the slots' kernels overlap on the GPU), then bookkeeping.  Problems may be
+ * added and released between ticks.  x0 = 0; stopping rules as mfx_solve.
+ * An operator may be in one active slot at a time (else MFX_EBUSY).
+ */
+typedef struct mfx_batch mfx_batch;
+mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk);
+void mfx_batch_destroy(mfx_batch* batch);
+/* Add a solve of K x = b (b, x device FP64, caller-owned until released); returns its slot. */
+mfx_status mfx_batch_add(mfx_batch* batch, const mfx_op* op, const double* b, double* x,
+                         const mfx_solve_params* params, int32_t* slot);
+/* One scheduler tick (synchronising); n_active = slots still running. */
+mfx_status mfx_batch_step(mfx_batch* batch, int32_t* n_active);
+/* done = 1 once the slot's solve has finished; stats as mfx_solve (iterations: outer for mixed). */
+mfx_status mfx_batch_poll(mfx_batch* batch, int32_t slot, int32_t* done, mfx_solve_stats* stats);
+/* Free a slot (its operator and vectors can then be reused or destroyed). */
+mfx_status mfx_batch_release(mfx_batch* batch, int32_t slot);
+
 #ifdef __cplusplus
 }
 #endif

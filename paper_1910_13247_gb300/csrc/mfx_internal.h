@@ -6,6 +6,7 @@
 
 #include <string>
 #include <vector>
+#include <cmath>
 
 #include "../../include/mfx.h"
 

@@ -707,3 +707,358 @@ mfx_status mfx_solve(const mfx_op* op_c, const double* b, double* x, const mfx_s
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches of solves
+//
+// A batch holds up to max_slots independent solves (one operator each).  A slot runs the
+// mixed-precision solve as a state machine: OUTER (FP64 residual b - K64 x and its norm; stop or
+// start an inner solve on r / ||r||), INNER (FP32 PCG, advanced `chunk` iterations per tick by a
+// captured graph), then x += ||r|| d and back to OUTER.  With mixed = 0 the INNER phase is the FP64
+// PCG on b itself.  Every tick launches one parent graph whose child nodes are the chunk graphs of
+// all slots in the INNER phase, so all active problems advance together and overlap on the GPU;
+// converged problems leave their slot, new problems can be added between ticks.
+
+namespace mfx {
+
+enum { SLOT_FREE = 0, SLOT_OUTER = 1, SLOT_INNER = 2, SLOT_DONE = 3 };
+
+struct BatchSlot {
+  mfx_op* op = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  mfx_solve_params p{};
+  int phase = SLOT_FREE;
+  bool mixed = true, cheb = false;
+  double lo = 0, hi = 0, bb = 0, rr = 0;
+  int outer = 0, inner_total = 0, status = MFX_OK;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;  // one chunk of inner iterations (ends with a copy of the state to the host)
+  double* h_scal = nullptr;     // pinned: (r, r), (b, b)
+};
+
+}  // namespace mfx
+
+struct mfx_batch {
+  std::vector<mfx::BatchSlot> slots;
+  int chunk = 8;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t parent = nullptr;
+  std::vector<int> parent_members;
+  int64_t ticks = 0;
+};
+
+namespace mfx {
+
+static void slot_release(BatchSlot& sl) {
+  if (sl.graph) cudaGraphDestroy(sl.graph);
+  sl.graph = nullptr;
+  sl.op = nullptr;
+  sl.phase = SLOT_FREE;
+}
+
+// Capture one chunk of inner PCG iterations of the slot's operator.
+template <typename Real>
+static mfx_status capture_chunk(BatchSlot& sl, int chunk) {
+  SolveWorkspace* ws = workspace(sl.op);
+  Work<Real>& w = work_of<Real>(ws);
+  cudaGraph_t g = nullptr;
+  MFX_CUDA_TRY(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
+  mfx_status rc = MFX_OK;
+  for (int i = 0; i < chunk && rc == MFX_OK; ++i)
+    rc = pcg_iteration<Real>(sl.op, ws, w, sl.cheb, sl.p.cheb_degree, sl.lo, sl.hi, sl.stream);
+  cudaMemcpyAsync(ws->h_st, ws->st, sizeof(SolveState), cudaMemcpyDeviceToHost, sl.stream);
+  cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
+  if (rc != MFX_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_error(ce, "batch chunk capture");
+  sl.graph = g;
+  return MFX_OK;
+}
+
+// Start an inner solve: FP32 on r / ||r|| (mixed) or FP64 on b.
+static mfx_status slot_start_inner(BatchSlot& sl) {
+  SolveWorkspace* ws = workspace(sl.op);
+  const int64_t n = sl.op->n_dofs;
+  const int g = reduction_blocks(n);
+  SolveState init{};
+  init.tol2 = sl.mixed ? sl.p.inner_tol * sl.p.inner_tol : sl.p.tol * sl.p.tol;
+  init.max_it = sl.mixed ? sl.p.inner_max_it : sl.p.max_it;
+  MFX_CUDA_TRY(cudaMemcpyAsync(ws->st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, sl.stream));
+  if (sl.mixed) {
+    scale_to_f32_kernel<<<vec_grid(n), 256, 0, sl.stream>>>(n, ws->r64, ws->scal, ws->w32.b);
+    cg_init_kernel<float><<<g, kRedThreads, 0, sl.stream>>>(n, ws->w32.b, ws->w32.x, ws->w32.r, ws->w32.p,
+                                                            ws->w32.dinv, !sl.cheb, ws->st, sl.op->d_partials,
+                                                            sl.op->d_counter);
+    if (sl.cheb) {
+      mfx_status rc = cheb_apply<float>(sl.op, ws->w32, ws->w32.r, ws->w32.p, sl.p.cheb_degree, sl.lo, sl.hi,
+                                        &ws->st->done, sl.stream);
+      if (rc != MFX_OK) return rc;
+      dot_kernel<float><<<g, kRedThreads, 0, sl.stream>>>(n, ws->w32.r, ws->w32.p, &ws->st->rz, sl.op->d_partials,
+                                                          sl.op->d_counter);
+    }
+  } else {
+    MFX_CUDA_TRY(cudaMemcpyAsync(ws->w64.b, sl.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, sl.stream));
+    cg_init_kernel<double><<<g, kRedThreads, 0, sl.stream>>>(n, ws->w64.b, ws->w64.x, ws->w64.r, ws->w64.p,
+                                                             ws->w64.dinv, !sl.cheb, ws->st, sl.op->d_partials,
+                                                             sl.op->d_counter);
+    if (sl.cheb) {
+      mfx_status rc = cheb_apply<double>(sl.op, ws->w64, ws->w64.r, ws->w64.p, sl.p.cheb_degree, sl.lo, sl.hi,
+                                         &ws->st->done, sl.stream);
+      if (rc != MFX_OK) return rc;
+      dot_kernel<double><<<g, kRedThreads, 0, sl.stream>>>(n, ws->w64.r, ws->w64.p, &ws->st->rz,
+                                                           sl.op->d_partials, sl.op->d_counter);
+    }
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  sl.phase = SLOT_INNER;
+  return MFX_OK;
+}
+
+// Launch the FP64 residual of an OUTER slot (result read after the tick's synchronisation).
+static mfx_status slot_launch_residual(BatchSlot& sl) {
+  SolveWorkspace* ws = workspace(sl.op);
+  const int64_t n = sl.op->n_dofs;
+  mfx_status rc = launch_vmult(sl.op, MFX_F64, sl.x, ws->y64, sl.stream);
+  if (rc != MFX_OK) return rc;
+  residual_kernel<<<reduction_blocks(n), kRedThreads, 0, sl.stream>>>(n, sl.b, ws->y64, ws->r64, ws->scal,
+                                                                      sl.op->d_partials, sl.op->d_counter);
+  MFX_CUDA_TRY(cudaMemcpyAsync(sl.h_scal, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+static mfx_status rebuild_parent(mfx_batch* bt) {
+  std::vector<int> members;
+  for (size_t i = 0; i < bt->slots.size(); ++i)
+    if (bt->slots[i].phase == SLOT_INNER) members.push_back((int)i);
+  if (bt->parent && members == bt->parent_members) return MFX_OK;
+  if (bt->parent) cudaGraphExecDestroy(bt->parent);
+  bt->parent = nullptr;
+  bt->parent_members = members;
+  if (members.empty()) return MFX_OK;
+  cudaGraph_t g = nullptr;
+  MFX_CUDA_TRY(cudaGraphCreate(&g, 0));
+  for (int i : members) {
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, bt->slots[i].graph);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_error(e, "cudaGraphAddChildGraphNode");
+    }
+  }
+  cudaError_t e = cudaGraphInstantiate(&bt->parent, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate (batch)");
+  return MFX_OK;
+}
+
+}  // namespace mfx
+
+extern "C" {
+
+mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
+  if (!out || max_slots < 1 || max_slots > 4096) return set_error(MFX_EINVAL, "mfx_batch_create: bad arguments");
+  *out = nullptr;
+  auto* bt = new mfx_batch();
+  bt->slots.resize(max_slots);
+  bt->chunk = chunk > 0 ? chunk : 8;
+  cudaError_t e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
+  for (auto& sl : bt->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_scal, 2 * sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    mfx_batch_destroy(bt);
+    return cuda_error(e, "mfx_batch_create");
+  }
+  *out = bt;
+  return MFX_OK;
+}
+
+void mfx_batch_destroy(mfx_batch* bt) {
+  if (!bt) return;
+  cudaDeviceSynchronize();
+  if (bt->parent) cudaGraphExecDestroy(bt->parent);
+  for (auto& sl : bt->slots) {
+    slot_release(sl);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.h_scal) cudaFreeHost(sl.h_scal);
+  }
+  if (bt->stream) cudaStreamDestroy(bt->stream);
+  delete bt;
+}
+
+mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, double* x,
+                         const mfx_solve_params* params, int32_t* slot_out) {
+  mfx_op* op = const_cast<mfx_op*>(op_c);
+  if (!bt || !op || !b || !x || !slot_out) return set_error(MFX_EINVAL, "mfx_batch_add: null argument");
+  mfx_solve_params p;
+  mfx_solve_params_default(&p);
+  if (params) p = *params;
+  const bool mixed = p.mixed != 0;
+  if (mixed && !(op->has_f32 && op->has_f64)) return set_error(MFX_EINVAL, "mixed solves need FP64 and FP32 data");
+  if (!op->has_f64) return set_error(MFX_EINVAL, "batch solves need FP64 data");
+  int free_slot = -1;
+  for (size_t i = 0; i < bt->slots.size(); ++i) {
+    if (bt->slots[i].phase != SLOT_FREE && bt->slots[i].op == op)
+      return set_error(MFX_EBUSY, "operator already has an active slot");
+    if (free_slot < 0 && bt->slots[i].phase == SLOT_FREE) free_slot = (int)i;
+  }
+  if (free_slot < 0) return set_error(MFX_EBUSY, "no free slot");
+  mfx_status rc = ensure_workspace(op);
+  if (rc != MFX_OK) return rc;
+  BatchSlot& sl = bt->slots[free_slot];
+  sl.op = op;
+  sl.b = b;
+  sl.x = x;
+  sl.p = p;
+  sl.mixed = mixed;
+  sl.cheb = p.precond == MFX_PRECOND_CHEBYSHEV;
+  sl.outer = 0;
+  sl.inner_total = 0;
+  sl.status = MFX_OK;
+  SolveWorkspace* ws = workspace(op);
+  if (sl.cheb) {
+    const int pi = mixed ? 1 : 0;
+    if (ws->lambda_max[pi] == 0.0) {
+      double lam = 0.0;
+      const double* start = p.lanczos_start ? p.lanczos_start : b;
+      rc = mixed ? estimate_lambda<float>(op, ws, start, p.lanczos_steps, ws->stream, &lam)
+                 : estimate_lambda<double>(op, ws, start, p.lanczos_steps, ws->stream, &lam);
+      if (rc != MFX_OK) return rc;
+      ws->lambda_max[pi] = lam;
+    }
+    sl.hi = p.cheb_hi > 0 ? p.cheb_hi : 1.2 * ws->lambda_max[pi];
+    sl.lo = p.cheb_hi > 0 ? p.cheb_lo : sl.hi / 20.0;
+  }
+  // ||b||^2 and x = 0
+  launch_dot(op, MFX_F64, op->n_dofs, b, b, ws->scal + 1, sl.stream);
+  MFX_CUDA_TRY(cudaMemcpyAsync(sl.h_scal + 1, ws->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
+  MFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * op->n_dofs, sl.stream));
+  MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
+  sl.bb = sl.h_scal[1];
+  rc = mixed ? capture_chunk<float>(sl, bt->chunk) : capture_chunk<double>(sl, bt->chunk);
+  if (rc != MFX_OK) {
+    slot_release(sl);
+    return rc;
+  }
+  if (!std::isfinite(sl.bb)) {
+    sl.phase = SLOT_DONE;
+    sl.status = MFX_BREAKDOWN;
+  } else if (sl.bb == 0.0) {
+    sl.phase = SLOT_DONE;
+  } else if (mixed) {
+    sl.phase = SLOT_OUTER;
+  } else {
+    rc = slot_start_inner(sl);
+    if (rc != MFX_OK) {
+      slot_release(sl);
+      return rc;
+    }
+  }
+  *slot_out = free_slot;
+  return MFX_OK;
+}
+
+mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
+  if (!bt) return set_error(MFX_EINVAL, "null batch");
+  // 1) outer steps: residuals of the OUTER slots, then decide
+  bool any_outer = false;
+  for (auto& sl : bt->slots)
+    if (sl.phase == SLOT_OUTER) {
+      mfx_status rc = slot_launch_residual(sl);
+      if (rc != MFX_OK) return rc;
+      any_outer = true;
+    }
+  if (any_outer) MFX_CUDA_TRY(cudaDeviceSynchronize());
+  for (auto& sl : bt->slots) {
+    if (sl.phase != SLOT_OUTER) continue;
+    sl.rr = sl.h_scal[0];
+    if (!std::isfinite(sl.rr)) {
+      sl.phase = SLOT_DONE;
+      sl.status = MFX_BREAKDOWN;
+    } else if (sl.rr <= sl.p.tol * sl.p.tol * sl.bb) {
+      sl.phase = SLOT_DONE;
+      sl.status = MFX_OK;
+    } else if (sl.outer >= sl.p.max_it) {
+      sl.phase = SLOT_DONE;
+      sl.status = MFX_NOT_CONVERGED;
+    } else {
+      mfx_status rc = slot_start_inner(sl);
+      if (rc != MFX_OK) return rc;
+    }
+  }
+  // 2) one graph launch advances every INNER slot by a chunk of iterations
+  mfx_status rc = rebuild_parent(bt);
+  if (rc != MFX_OK) return rc;
+  if (bt->parent) {
+    MFX_CUDA_TRY(cudaDeviceSynchronize());  // slot streams (inner starts) before the batch stream
+    MFX_CUDA_TRY(cudaGraphLaunch(bt->parent, bt->stream));
+    MFX_CUDA_TRY(cudaStreamSynchronize(bt->stream));
+    ++bt->ticks;
+  }
+  // 3) finished inner solves
+  int active = 0;
+  for (auto& sl : bt->slots) {
+    if (sl.phase == SLOT_INNER) {
+      SolveWorkspace* ws = workspace(sl.op);
+      const SolveState& h = *ws->h_st;
+      if (h.done) {
+        sl.inner_total += h.it;
+        if (h.status == MFX_BREAKDOWN) {
+          sl.phase = SLOT_DONE;
+          sl.status = MFX_BREAKDOWN;
+        } else if (sl.mixed) {
+          const int64_t n = sl.op->n_dofs;
+          add_scaled_f32_kernel<<<vec_grid(n), 256, 0, sl.stream>>>(n, sl.x, ws->w32.x, ws->scal);
+          sl.outer += 1;
+          sl.phase = SLOT_OUTER;
+        } else {
+          MFX_CUDA_TRY(cudaMemcpyAsync(sl.x, ws->w64.x, sizeof(double) * sl.op->n_dofs, cudaMemcpyDeviceToDevice,
+                                       sl.stream));
+          sl.status = h.status;
+          sl.phase = SLOT_DONE;
+        }
+      }
+    }
+    if (sl.phase == SLOT_OUTER || sl.phase == SLOT_INNER) ++active;
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  if (n_active) *n_active = active;
+  return MFX_OK;
+}
+
+mfx_status mfx_batch_poll(mfx_batch* bt, int32_t slot, int32_t* done, mfx_solve_stats* stats) {
+  if (!bt || slot < 0 || slot >= (int)bt->slots.size() || !done) return set_error(MFX_EINVAL, "mfx_batch_poll");
+  const BatchSlot& sl = bt->slots[slot];
+  if (sl.phase == SLOT_FREE) return set_error(MFX_EINVAL, "slot is free");
+  *done = sl.phase == SLOT_DONE ? 1 : 0;
+  if (stats) {
+    *stats = mfx_solve_stats{};
+    stats->status = sl.status;
+    stats->iterations = sl.mixed ? sl.outer : sl.inner_total;
+    stats->inner_iterations = sl.mixed ? sl.inner_total : 0;
+    stats->rel_residual = sl.bb > 0 ? std::sqrt(sl.rr / sl.bb) : 0.0;
+    stats->cheb_lo = sl.lo;
+    stats->cheb_hi = sl.hi;
+  }
+  return MFX_OK;
+}
+
+mfx_status mfx_batch_release(mfx_batch* bt, int32_t slot) {
+  if (!bt || slot < 0 || slot >= (int)bt->slots.size()) return set_error(MFX_EINVAL, "mfx_batch_release");
+  BatchSlot& sl = bt->slots[slot];
+  if (sl.stream) MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
+  if (bt->parent) {
+    // the parent graph holds a copy of this slot's chunk; rebuild it on the next step
+    cudaGraphExecDestroy(bt->parent);
+    bt->parent = nullptr;
+    bt->parent_members.clear();
+  }
+  slot_release(sl);
+  return MFX_OK;
+}
+
+}  // extern "C"

@@ -92,6 +92,12 @@ def lib():
         "mfx_chebyshev": (S, [_VP, S, _VP, _VP, S, ctypes.c_double, ctypes.c_double, _VP]),
         "mfx_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
         "mfx_solve": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
+        "mfx_batch_create": (S, [ctypes.POINTER(_VP), S, S]),
+        "mfx_batch_destroy": (None, [_VP]),
+        "mfx_batch_add": (S, [_VP, _VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(S)]),
+        "mfx_batch_step": (S, [_VP, ctypes.POINTER(S)]),
+        "mfx_batch_poll": (S, [_VP, S, ctypes.POINTER(S), ctypes.POINTER(SolveStats)]),
+        "mfx_batch_release": (S, [_VP, S]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -270,6 +276,9 @@ class Operator:
         check(lib().mfx_chebyshev(self.handle, _prec_of(r), _ptr(r), _ptr(z), degree, lo, hi, _stream()))
         return z
 
+    def solve_params(self, **kw):
+        return make_params(**kw)
+
     def solve(self, b, x, tol=1e-10, max_it=100000, precond=PRECOND_JACOBI, cheb_degree=5, mixed=False,
               inner_tol=1e-4, check_every=0, lanczos_steps=15, cheb_lo=0.0, cheb_hi=0.0, lanczos_start=None,
               inner_max_it=10000):
@@ -283,3 +292,58 @@ class Operator:
         st = SolveStats()
         check(lib().mfx_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st), _stream()))
         return st.as_dict()
+
+
+def make_params(tol=1e-10, max_it=100000, precond=PRECOND_JACOBI, cheb_degree=5, mixed=False, inner_tol=1e-4,
+                check_every=0, lanczos_steps=15, cheb_lo=0.0, cheb_hi=0.0, lanczos_start=None, inner_max_it=10000):
+    p = SolveParams()
+    lib().mfx_solve_params_default(ctypes.byref(p))
+    p.tol, p.max_it, p.precond, p.cheb_degree = tol, max_it, precond, cheb_degree
+    p.mixed, p.inner_tol, p.check_every, p.lanczos_steps = int(mixed), inner_tol, check_every, lanczos_steps
+    p.cheb_lo, p.cheb_hi = cheb_lo, cheb_hi
+    p.lanczos_start = lanczos_start.data_ptr() if lanczos_start is not None else None
+    p.inner_max_it = inner_max_it
+    return p
+
+
+class Batch:
+    """Slots of independent solves advanced together, one graph launch per tick (mfx_batch_*)."""
+
+    def __init__(self, max_slots, chunk=8):
+        h = ctypes.c_void_p()
+        check(lib().mfx_batch_create(ctypes.byref(h), max_slots, chunk))
+        self.handle = h
+        self._keep = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfx_batch_destroy(self.handle)
+            self.handle = None
+
+    def add(self, op, b, x, **kw):
+        p = make_params(**kw)
+        slot = ctypes.c_int32()
+        check(lib().mfx_batch_add(self.handle, op.handle, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(slot)))
+        self._keep[slot.value] = (op, b, x)
+        return slot.value
+
+    def step(self):
+        n = ctypes.c_int32()
+        check(lib().mfx_batch_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, slot):
+        done = ctypes.c_int32()
+        st = SolveStats()
+        check(lib().mfx_batch_poll(self.handle, slot, ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), st.as_dict()
+
+    def release(self, slot):
+        check(lib().mfx_batch_release(self.handle, slot))
+        self._keep.pop(slot, None)
+
+    def run(self, max_ticks=1000000):
+        ticks = 0
+        while self.step() > 0 and ticks < max_ticks:
+            ticks += 1
+        return ticks
