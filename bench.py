@@ -160,6 +160,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solve measurements")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96^3 Q3 mixed-precision solve")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched solve")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
     args = ap.parse_args()
@@ -291,6 +293,8 @@ def main():
             line["solve"]["mixed_96x96x96_q3"] = mixed_solve_measurement(mfx, synthetic, torch, np)
         if not args.no_batch:
             line["batched"] = batched_measurement(mfx, synthetic, torch, np)
+        if not args.no_serve:
+            line["serving"] = serving_measurement(args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -323,6 +327,17 @@ def solve_measurements(mfx, synthetic, torch, np):
     lat = sorted(lat[3:])
     out["poisson_8x8x8_q2_jacobi_pcg"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                            "iterations": its, "rel_residual": st["rel_residual"], "runs": len(lat)}
+    return out
+
+
+def serving_measurement(n_requests, rate=200.0, seed=5):
+    """Poisson arrivals (200/s) of octree Poisson solves, degree 1..8, sizes log-uniform in 1e3..1e7 DoFs
+    (clamped by the mesh generator), tol 1e-10, continuous batching under a 64 GB device-memory budget."""
+    from paper_1910_13247_gb300 import serve
+    reqs = serve.make_requests(n_requests, rate=rate, seed=seed)
+    server = serve.Server(budget_bytes=64 << 30, max_slots=32, chunk=16)
+    out = server.run(reqs, time_limit=240.0)
+    out["budget_bytes"] = 64 << 30
     return out
 
 

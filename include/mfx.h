@@ -295,6 +295,15 @@ mfx_status mfx_batch_add(mfx_batch* batch, const mfx_op* op, const double* b, do
                          const mfx_solve_params* params, int32_t* slot);
 /* One scheduler tick (synchronising); n_active = slots still running. */
 mfx_status mfx_batch_step(mfx_batch* batch, int32_t* n_active);
+/*
+ * Independent stepping (for mixes of very different problems): every slot
+ * whose previous work has finished takes its next step at once (residual,
+ * stopping decision, inner start, next chunk of iterations), each slot on
+ * its own stream; the call does not wait for the GPU.  Call it repeatedly;
+ * n_active = slots still running.  Do not mix with mfx_batch_step on the
+ * same slots while work is in flight.
+ */
+mfx_status mfx_batch_advance(mfx_batch* batch, int32_t* n_active);
 /* done = 1 once the slot's solve has finished; stats as mfx_solve (iterations: outer for mixed). */
 mfx_status mfx_batch_poll(mfx_batch* batch, int32_t slot, int32_t* done, mfx_solve_stats* stats);
 /* Free a slot (its operator and vectors can then be reused or destroyed). */

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <unordered_map>
+#include <utility>
 
 #include "mfx_internal.h"
 
@@ -144,31 +145,57 @@ mfx_status octree_sort_and_check(Mesh* m) {
 
 namespace {
 
-// Per-dimension node identity: rational position (units of 2^-(Lmax+1) coarse cells) or
-// (level, index, local node) for an irrational GLL node.
-struct DimKey {
-  uint32_t tag;  // 0 rational, 1 irrational
-  uint32_t a, b, c;
-  bool operator==(const DimKey& o) const { return tag == o.tag && a == o.a && b == o.b && c == o.c; }
-};
-
+// Per-dimension node identity packed in 32 bits: bit 31 clear -> rational position in units of
+// 2^-(Lmax+1) coarse cells (GLL nodes 0, 1/2 and 1 of a cell); bit 31 set -> interior GLL node a of
+// the level-L cell row I: (L << 27) | (I << 4) | a (I < 2^23, a < 16).
 struct NodeKey {
-  DimKey d[3];
+  uint32_t d[3];
   bool operator==(const NodeKey& o) const { return d[0] == o.d[0] && d[1] == o.d[1] && d[2] == o.d[2]; }
 };
 
-struct NodeKeyHash {
-  size_t operator()(const NodeKey& k) const {
-    uint64_t h = 1469598103934665603ull;
-    for (int i = 0; i < 3; ++i) {
-      const uint32_t w[4] = {k.d[i].tag, k.d[i].a, k.d[i].b, k.d[i].c};
-      for (uint32_t v : w) {
-        h ^= v;
-        h *= 1099511628211ull;
-      }
-    }
-    return (size_t)h;
+inline bool irrational(uint32_t dk) { return (dk >> 31) != 0; }
+
+// Flat open-addressing table NodeKey -> DoF (linear probing, power-of-two capacity).
+class NodeTable {
+ public:
+  explicit NodeTable(size_t expected) {
+    size_t cap = 16;
+    while (cap < 2 * expected + 16) cap <<= 1;
+    keys_.assign(cap, NodeKey{{~0u, ~0u, ~0u}});
+    vals_.assign(cap, -1);
+    mask_ = cap - 1;
   }
+  size_t slot(const NodeKey& k) const { return hash(k) & mask_; }
+  void prefetch(size_t h) const {
+    __builtin_prefetch(&keys_[h]);
+    __builtin_prefetch(&vals_[h]);
+  }
+  // DoF of the key (whose home slot is h), inserting `next` if absent; returns (dof, inserted).
+  std::pair<int32_t, bool> find_or_insert(const NodeKey& k, size_t h, int32_t next) {
+    for (;;) {
+      if (vals_[h] < 0) {
+        keys_[h] = k;
+        vals_[h] = next;
+        return {next, true};
+      }
+      if (keys_[h] == k) return {vals_[h], false};
+      h = (h + 1) & mask_;
+    }
+  }
+
+ private:
+  static size_t hash(const NodeKey& k) {
+    uint64_t x = ((uint64_t)k.d[0] << 32) ^ ((uint64_t)k.d[1] * 0x9E3779B97F4A7C15ull) ^ (uint64_t)k.d[2];
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return (size_t)x;
+  }
+  std::vector<NodeKey> keys_;
+  std::vector<int32_t> vals_;
+  size_t mask_ = 0;
 };
 
 }  // namespace
@@ -209,24 +236,14 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     }
   }
   const uint32_t R2 = 1u << (Lmax + 1);
-  auto dim_key = [&](int L, int64_t I, int a) {
-    DimKey d{};
-    if (a == 0) {
-      d.tag = 0;
-      d.a = (uint32_t)(I * (R2 >> L));
-    } else if (a == k) {
-      d.tag = 0;
-      d.a = (uint32_t)((I + 1) * (R2 >> L));
-    } else if (2 * a == k) {
-      d.tag = 0;
-      d.a = (uint32_t)((2 * I + 1) * (R2 >> (L + 1)));
-    } else {
-      d.tag = 1;
-      d.a = (uint32_t)L;
-      d.b = (uint32_t)I;
-      d.c = (uint32_t)a;
-    }
-    return d;
+  if ((uint64_t)std::max(m.nx, std::max(m.ny, m.nz)) * R2 >= (1ull << 31) ||
+      ((uint64_t)std::max(m.nx, std::max(m.ny, m.nz)) << Lmax) >= (1ull << 23))
+    return set_error(MFX_EUNSUPPORTED, "octree too large for the node keys");
+  auto dim_key = [&](int L, int64_t I, int a) -> uint32_t {
+    if (a == 0) return (uint32_t)(I * (R2 >> L));
+    if (a == k) return (uint32_t)((I + 1) * (R2 >> L));
+    if (2 * a == k) return (uint32_t)((2 * I + 1) * (R2 >> (L + 1)));
+    return (1u << 31) | ((uint32_t)L << 27) | ((uint32_t)I << 4) | (uint32_t)a;
   };
   auto node_key = [&](int64_t c, int a1, int a2, int a3) {
     const auto& lf = t.leaves[c];
@@ -236,35 +253,51 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     key.d[2] = dim_key(lf[0], lf[3], a3);
     return key;
   };
-  std::unordered_map<NodeKey, int32_t, NodeKeyHash> dof_of;
-  dof_of.reserve((size_t)C * (k * k * k + 3 * k * k) + 16);
+  // nodes whose three per-dimension keys are all interior GLL nodes belong to one cell only
+  int interior_1d = 0;
+  for (int a = 0; a <= k; ++a)
+    if (a != 0 && a != k && 2 * a != k) ++interior_1d;
+  // shared (non-interior) node visits; each distinct shared node is visited about twice or more
+  const size_t shared_visits = (size_t)C * (size_t)(n3 - interior_1d * interior_1d * interior_1d);
+  NodeTable dof_of(shared_visits / 2 + 64);
   out->cell_dofs.assign(C * n3, 0);
   std::vector<NodeKey> keys_by_dof;
-  for (int64_t c = 0; c < C; ++c)
+  keys_by_dof.reserve((size_t)C * n3 / 2 + 16);
+  // keys of one cell, with their home slots prefetched before the (sequential) first-encounter pass
+  std::vector<NodeKey> ck(n3);
+  std::vector<size_t> cs(n3);
+  for (int64_t c = 0; c < C; ++c) {
     for (int a3 = 0; a3 < n; ++a3)
       for (int a2 = 0; a2 < n; ++a2)
         for (int a1 = 0; a1 < n; ++a1) {
-          const NodeKey key = node_key(c, a1, a2, a3);
-          auto it = dof_of.find(key);
-          int32_t dof;
-          if (it == dof_of.end()) {
-            dof = (int32_t)keys_by_dof.size();
-            if (keys_by_dof.size() >= (size_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
-            dof_of.emplace(key, dof);
-            keys_by_dof.push_back(key);
-          } else {
-            dof = it->second;
-          }
-          out->cell_dofs[c * n3 + a1 + n * (a2 + n * a3)] = dof;
+          const int li = a1 + n * (a2 + n * a3);
+          ck[li] = node_key(c, a1, a2, a3);
+          cs[li] = dof_of.slot(ck[li]);
+          dof_of.prefetch(cs[li]);
         }
+    for (int li = 0; li < n3; ++li) {
+      const NodeKey& key = ck[li];
+      if (keys_by_dof.size() >= (size_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
+      const int32_t next = (int32_t)keys_by_dof.size();
+      int32_t dof = next;
+      if (!(irrational(key.d[0]) && irrational(key.d[1]) && irrational(key.d[2]))) {
+        auto r = dof_of.find_or_insert(key, cs[li], next);
+        dof = r.first;
+        if (r.second) keys_by_dof.push_back(key);
+      } else {
+        keys_by_dof.push_back(key);
+      }
+      out->cell_dofs[c * n3 + li] = dof;
+    }
+  }
   const int64_t N = (int64_t)keys_by_dof.size();
   out->n_dofs = N;
   const uint32_t ext[3] = {(uint32_t)m.nx * R2, (uint32_t)m.ny * R2, (uint32_t)m.nz * R2};
   std::vector<uint8_t> dirichlet(N, 0);
   for (int64_t d = 0; d < N; ++d)
     for (int e = 0; e < 3; ++e) {
-      const DimKey& dk = keys_by_dof[d].d[e];
-      if (dk.tag == 0 && (dk.a == 0 || dk.a == ext[e])) dirichlet[d] = 1;
+      const uint32_t dk = keys_by_dof[d].d[e];
+      if (!irrational(dk) && (dk == 0 || dk == ext[e])) dirichlet[d] = 1;
     }
   // hanging constraints
   std::map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;

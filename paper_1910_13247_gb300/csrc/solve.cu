@@ -733,6 +733,10 @@ struct BatchSlot {
   int outer = 0, inner_total = 0, status = MFX_OK;
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;  // one chunk of inner iterations (ends with a copy of the state to the host)
+  cudaGraphExec_t exec = nullptr;  // the same chunk, for independent (asynchronous) stepping
+  cudaEvent_t event = nullptr;     // completion of the slot's last launched work
+  bool busy = false;               // work in flight (asynchronous stepping)
+  bool residual_pending = false;   // OUTER: residual launched, norm not read yet
   double* h_scal = nullptr;     // pinned: (r, r), (b, b)
 };
 
@@ -750,8 +754,12 @@ struct mfx_batch {
 namespace mfx {
 
 static void slot_release(BatchSlot& sl) {
+  if (sl.exec) cudaGraphExecDestroy(sl.exec);
+  sl.exec = nullptr;
   if (sl.graph) cudaGraphDestroy(sl.graph);
   sl.graph = nullptr;
+  sl.busy = false;
+  sl.residual_pending = false;
   sl.op = nullptr;
   sl.phase = SLOT_FREE;
 }
@@ -774,6 +782,8 @@ static mfx_status capture_chunk(BatchSlot& sl, int chunk) {
   }
   if (ce != cudaSuccess) return cuda_error(ce, "batch chunk capture");
   sl.graph = g;
+  ce = cudaGraphInstantiate(&sl.exec, g, 0);
+  if (ce != cudaSuccess) return cuda_error(ce, "batch chunk instantiate");
   return MFX_OK;
 }
 
@@ -868,6 +878,7 @@ mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
   for (auto& sl : bt->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_scal, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     mfx_batch_destroy(bt);
@@ -884,6 +895,7 @@ void mfx_batch_destroy(mfx_batch* bt) {
   for (auto& sl : bt->slots) {
     slot_release(sl);
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.event) cudaEventDestroy(sl.event);
     if (sl.h_scal) cudaFreeHost(sl.h_scal);
   }
   if (bt->stream) cudaStreamDestroy(bt->stream);
@@ -957,6 +969,7 @@ mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, dou
       slot_release(sl);
       return rc;
     }
+    ws->h_st->done = 0;  // the first independent step launches the first chunk
   }
   *slot_out = free_slot;
   return MFX_OK;
@@ -1026,6 +1039,82 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
     if (sl.phase == SLOT_OUTER || sl.phase == SLOT_INNER) ++active;
   }
   MFX_CUDA_TRY(cudaGetLastError());
+  if (n_active) *n_active = active;
+  return MFX_OK;
+}
+
+// Independent stepping: every slot whose previous work has finished takes its next step right
+// away (residual, decision, inner start, next chunk), each on its own stream; nothing waits.
+mfx_status mfx_batch_advance(mfx_batch* bt, int32_t* n_active) {
+  if (!bt) return set_error(MFX_EINVAL, "null batch");
+  int active = 0;
+  for (auto& sl : bt->slots) {
+    if (sl.phase == SLOT_OUTER || sl.phase == SLOT_INNER) ++active;
+    if (sl.phase != SLOT_OUTER && sl.phase != SLOT_INNER) continue;
+    if (sl.busy) {
+      const cudaError_t q = cudaEventQuery(sl.event);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_error(q, "mfx_batch_advance");
+      sl.busy = false;
+    }
+    mfx_status rc = MFX_OK;
+    if (sl.phase == SLOT_OUTER) {
+      if (!sl.residual_pending) {
+        rc = slot_launch_residual(sl);
+        if (rc != MFX_OK) return rc;
+        sl.residual_pending = true;
+      } else {
+        sl.residual_pending = false;
+        sl.rr = sl.h_scal[0];
+        if (!std::isfinite(sl.rr)) {
+          sl.phase = SLOT_DONE;
+          sl.status = MFX_BREAKDOWN;
+        } else if (sl.rr <= sl.p.tol * sl.p.tol * sl.bb) {
+          sl.phase = SLOT_DONE;
+          sl.status = MFX_OK;
+        } else if (sl.outer >= sl.p.max_it) {
+          sl.phase = SLOT_DONE;
+          sl.status = MFX_NOT_CONVERGED;
+        } else {
+          rc = slot_start_inner(sl);
+          if (rc != MFX_OK) return rc;
+          MFX_CUDA_TRY(cudaGraphLaunch(sl.exec, sl.stream));
+        }
+      }
+    } else {  // INNER: a chunk finished
+      SolveWorkspace* ws = workspace(sl.op);
+      const SolveState& h = *ws->h_st;
+      if (!h.done) {
+        MFX_CUDA_TRY(cudaGraphLaunch(sl.exec, sl.stream));
+      } else {
+        sl.inner_total += h.it;
+        if (h.status == MFX_BREAKDOWN) {
+          sl.phase = SLOT_DONE;
+          sl.status = MFX_BREAKDOWN;
+        } else if (sl.mixed) {
+          const int64_t n = sl.op->n_dofs;
+          add_scaled_f32_kernel<<<vec_grid(n), 256, 0, sl.stream>>>(n, sl.x, ws->w32.x, ws->scal);
+          sl.outer += 1;
+          sl.phase = SLOT_OUTER;
+          rc = slot_launch_residual(sl);
+          if (rc != MFX_OK) return rc;
+          sl.residual_pending = true;
+        } else {
+          MFX_CUDA_TRY(cudaMemcpyAsync(sl.x, ws->w64.x, sizeof(double) * sl.op->n_dofs, cudaMemcpyDeviceToDevice,
+                                       sl.stream));
+          sl.status = h.status;
+          sl.phase = SLOT_DONE;
+        }
+      }
+    }
+    if (sl.phase == SLOT_OUTER || sl.phase == SLOT_INNER) {
+      MFX_CUDA_TRY(cudaEventRecord(sl.event, sl.stream));
+      sl.busy = true;
+    } else {
+      MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));  // results complete before the slot reports done
+      --active;
+    }
+  }
   if (n_active) *n_active = active;
   return MFX_OK;
 }

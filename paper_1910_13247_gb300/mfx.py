@@ -96,6 +96,7 @@ def lib():
         "mfx_batch_destroy": (None, [_VP]),
         "mfx_batch_add": (S, [_VP, _VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(S)]),
         "mfx_batch_step": (S, [_VP, ctypes.POINTER(S)]),
+        "mfx_batch_advance": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_poll": (S, [_VP, S, ctypes.POINTER(S), ctypes.POINTER(SolveStats)]),
         "mfx_batch_release": (S, [_VP, S]),
     }
@@ -330,6 +331,12 @@ class Batch:
     def step(self):
         n = ctypes.c_int32()
         check(lib().mfx_batch_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def advance(self):
+        """Independent stepping: each finished slot takes its next step; returns active slots."""
+        n = ctypes.c_int32()
+        check(lib().mfx_batch_advance(self.handle, ctypes.byref(n)))
         return n.value
 
     def poll(self, slot):

@@ -46,75 +46,74 @@ def deformed_vertices(nx, ny, nz, amp=0.05):
     return v + s[:, None]
 
 
-def _neighbour_shifts():
-    shifts = []
-    for d in range(3):
-        for sgn in (1, -1):
-            s = [0, 0, 0]
-            s[d] = sgn
-            shifts.append(s)
+def _dilate_faces_edges(a):
+    """out[v] = a[v] or a[w] for every face or edge neighbour w of v (same level)."""
+    out = a.copy()
+    Z, Y, X = a.shape
     for d1 in range(3):
-        for d2 in range(d1 + 1, 3):
-            for s1 in (1, -1):
+        for s1 in (1, -1):
+            sh = [0, 0, 0]
+            sh[d1] = s1
+            shifts = [tuple(sh)]
+            for d2 in range(d1 + 1, 3):
                 for s2 in (1, -1):
-                    s = [0, 0, 0]
-                    s[d1] = s1
-                    s[d2] = s2
-                    shifts.append(s)
-    return shifts
-
-
-def _max_neighbour_level(lev):
-    """Per finest voxel, the largest level among its face/edge neighbour voxels."""
-    out = lev.copy()
-    Z, Y, X = lev.shape
-    for sx, sy, sz in _neighbour_shifts():
-        src = lev[max(0, sz):Z + min(0, sz), max(0, sy):Y + min(0, sy), max(0, sx):X + min(0, sx)]
-        dst = out[max(0, -sz):Z - max(0, sz), max(0, -sy):Y - max(0, sy), max(0, -sx):X - max(0, sx)]
-        np.maximum(dst, src, out=dst)
+                    sh2 = list(sh)
+                    sh2[d2] = s2
+                    shifts.append(tuple(sh2))
+            for sz, sy, sx in [(v[2], v[1], v[0]) for v in shifts]:
+                src = a[max(0, sz):Z + min(0, sz), max(0, sy):Y + min(0, sy), max(0, sx):X + min(0, sx)]
+                dst = out[max(0, -sz):Z - max(0, sz), max(0, -sy):Y - max(0, sy), max(0, -sx):X - max(0, sx)]
+                np.logical_or(dst, src, out=dst)
     return out
 
 
+def _children_any(a):
+    """Level-L array: any of the 8 level-(L+1) children set."""
+    Z, Y, X = a.shape
+    return a.reshape(Z // 2, 2, Y // 2, 2, X // 2, 2).any(axis=(1, 3, 5))
+
+
 def octree_leaves(nb, levels, center, radius):
-    """Leaves (level, i, j, l) of an nb^3 grid refined `levels` times inside a ball, 2:1 balanced."""
-    leaves = {(0, i, j, l) for l in range(nb) for j in range(nb) for i in range(nb)}
+    """Leaves (level, i, j, l) of an nb^3 grid refined `levels` times inside a ball, 2:1 balanced.
 
-    def centre(lf):
-        L, i, j, l = lf
-        h = 1.0 / (nb << L)
-        return np.array([(i + 0.5) * h, (j + 0.5) * h, (l + 0.5) * h])
-
-    def children(lf):
-        L, i, j, l = lf
-        return [(L + 1, 2 * i + a, 2 * j + b, 2 * l + c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
-
+    ref[L] marks the level-L cells that are refined.  A leaf is refined when its centre lies within
+    `radius` of `center` (level by level), then the smallest balanced refinement is taken: a level-L
+    leaf is refined while a refined level-(L+1) cell touches it across a face or an edge.
+    """
     center = np.asarray(center, dtype=np.float64)
-    for L in range(levels):
-        ref = [lf for lf in leaves if lf[0] == L and np.linalg.norm(centre(lf) - center) < radius]
-        for lf in ref:
-            leaves.remove(lf)
-            leaves.update(children(lf))
-    # 2:1 balance across faces and edges
-    Lmax = max(lf[0] for lf in leaves)
-    R = 1 << Lmax
-    while True:
-        lev = np.zeros((nb * R, nb * R, nb * R), dtype=np.int64)
-        for (L, i, j, l) in leaves:
-            s = 1 << (Lmax - L)
-            lev[l * s:(l + 1) * s, j * s:(j + 1) * s, i * s:(i + 1) * s] = L
-        mx = _max_neighbour_level(lev)
-        bad = []
-        for lf in leaves:
-            L, i, j, l = lf
-            s = 1 << (Lmax - L)
-            if mx[l * s:(l + 1) * s, j * s:(j + 1) * s, i * s:(i + 1) * s].max() > L + 1:
-                bad.append(lf)
-        if not bad:
-            break
-        for lf in bad:
-            leaves.remove(lf)
-            leaves.update(children(lf))
-    return np.array(sorted(leaves), dtype=np.int64)
+    exists = [np.ones((nb, nb, nb), dtype=bool)]
+    ref = []
+    for L in range(levels + 1):
+        n = nb << L
+        c = (np.arange(n) + 0.5) / n
+        Zc, Yc, Xc = np.meshgrid(c, c, c, indexing="ij")
+        inside = (Xc - center[0]) ** 2 + (Yc - center[1]) ** 2 + (Zc - center[2]) ** 2 < radius * radius
+        r = exists[L] & inside if L < levels else np.zeros_like(exists[L])
+        ref.append(r)
+        if L < levels:
+            exists.append(np.repeat(np.repeat(np.repeat(r, 2, 0), 2, 1), 2, 2))
+    # balance: fine to coarse, repeated until nothing changes
+    changed = True
+    while changed:
+        changed = False
+        for L in range(levels - 1, -1, -1):
+            need = _children_any(_dilate_faces_edges(ref[L + 1])) & exists[L] & ~ref[L]
+            if need.any():
+                ref[L] |= need
+                changed = True
+                exists[L + 1] = np.repeat(np.repeat(np.repeat(ref[L], 2, 0), 2, 1), 2, 2)
+                # children of newly refined cells exist; deeper levels keep their refinement marks
+                for M in range(L + 1, levels):
+                    ref[M] &= exists[M]
+                    exists[M + 1] = np.repeat(np.repeat(np.repeat(ref[M], 2, 0), 2, 1), 2, 2)
+    out = []
+    for L in range(levels + 1):
+        leaf = exists[L] & ~ref[L]
+        lz, ly, lx = np.nonzero(leaf)
+        out.append(np.stack([np.full(lx.shape, L), lx, ly, lz], axis=1))
+    leaves = np.concatenate(out).astype(np.int64)
+    order = np.lexsort((leaves[:, 3], leaves[:, 2], leaves[:, 1], leaves[:, 0]))
+    return leaves[order]
 
 
 def random_octree(seed, nb=8, max_levels=3):
