@@ -288,6 +288,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   MFX_TRY(prepare_vmult(op));
   MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_diagonal(op, s));
+  // the structured FP64 vmult works in double-float arithmetic on a pre-split metric
+  if (op->structured) MFX_TRY(launch_metric_to_pairs(op, (int64_t)metric_entries, s));
   MFX_CUDA_OP(cudaStreamSynchronize(s));
   *out = op;
   return MFX_OK;

@@ -400,6 +400,22 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
   return MFX_OK;
 }
 
+// FP64 metric -> (hi, lo) float pairs in place (structured operators, after the FP64 diagonal).
+__global__ void metric_to_pairs_kernel(int64_t n, double* __restrict__ m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = m[i];
+    const float h = __double2float_rn(v);
+    const float l = __double2float_rn(v - (double)h);
+    reinterpret_cast<float2*>(m)[i] = make_float2(h, l);
+  }
+}
+
+mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s) {
+  metric_to_pairs_kernel<<<grid_for(entries), 256, 0, s>>>(entries, op->d_metric64);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s) {
   const int64_t work = op->structured ? op->n_dofs : op->n_constrained;
   if (work == 0) return MFX_OK;

@@ -90,7 +90,7 @@ struct mfx_op {
   mfx::OctreeTables tables;
   // device data
   double* d_vertices = nullptr;      // structured: lattice (nx+1)(ny+1)(nz+1) x 3; else cell x 8 x 3
-  double* d_metric64 = nullptr;      // n_cells x 6 x n^3
+  double* d_metric64 = nullptr;      // FP64 metric; structured operators: float pairs after creation
   float* d_metric32 = nullptr;
   double* d_jxw = nullptr;           // n_cells x n^3 (for the right-hand side)
   int32_t* d_cell_dofs = nullptr;    // octree: encoded cell DoFs (n_cells x n^3)
@@ -122,6 +122,7 @@ mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s);
 mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s);
 mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
+mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
 
 int device_sm_count();
 

@@ -1,0 +1,341 @@
+// FP64 structured vmult in double-float arithmetic.
+//
+// GB300 runs FP64 FMAs at 1/62 of the FP32 rate, so the FP64 operator keeps its vectors and the
+// metric in FP64 in HBM but does the arithmetic on pairs of floats (hi + lo, about 48 significant
+// bits): every product of a value with a matrix entry is formed exactly by an FMA-based
+// error-free transformation, sums are accumulated with two-sum, and the pair is renormalised at
+// the end of each contraction.  Values are split into pairs when they are loaded (the 1D
+// matrices at compile time) and joined back to FP64 before they are added to dst.  All
+// arithmetic uses the round-to-nearest intrinsics, which the compiler never fuses, so the
+// error-free transformations stay exact.  The phases are those of brick_vmult_kernel.
+#pragma once
+
+#include "vmult_brick.cuh"
+
+namespace mfx {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_split(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_join(df a) { return (double)a.hi + (double)a.lo; }
+
+// s + t with |s| >= |t| (or s = 0): normalised pair
+__device__ __forceinline__ df df_fast_norm(float s, float t) {
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+// (s, t) = x * c exactly up to the lo*lo term (first term of a sum)
+__device__ __forceinline__ void df_prod(df x, float ch, float cl, float& s, float& t) {
+  s = __fmul_rn(x.hi, ch);
+  float e = __fmaf_rn(x.hi, ch, -s);
+  e = __fmaf_rn(x.hi, cl, e);
+  t = __fmaf_rn(x.lo, ch, e);
+}
+
+// (s, t) += x * c: two-sum of the high parts, error terms into t
+__device__ __forceinline__ void df_prod_acc(df x, float ch, float cl, float& s, float& t) {
+  const float p = __fmul_rn(x.hi, ch);
+  float e = __fmaf_rn(x.hi, ch, -p);
+  e = __fmaf_rn(x.hi, cl, e);
+  e = __fmaf_rn(x.lo, ch, e);
+  const float s2 = __fadd_rn(s, p);
+  const float bv = __fsub_rn(s2, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(p, bv));
+  s = s2;
+  t = __fadd_rn(t, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ df df_dot3(df a0, df b0, df a1, df b1, df a2, df b2) {
+  float s, t;
+  df_prod(b0, a0.hi, a0.lo, s, t);
+  df_prod_acc(b1, a1.hi, a1.lo, s, t);
+  df_prod_acc(b2, a2.hi, a2.lo, s, t);
+  return df_fast_norm(s, t);
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  return df_fast_norm(s, __fadd_rn(err, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_add3(df a, df b, df c) { return df_add(df_add(a, b), c); }
+
+// compile-time split of the 1D matrices
+constexpr float split_hi(double v) { return (float)v; }
+constexpr float split_lo(double v) { return (float)(v - (double)(float)v); }
+
+template <int N, int MAT>
+__device__ __forceinline__ void contract_df(const df (&in)[N], df (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s, t;
+    constexpr int dummy = 0;
+    (void)dummy;
+    df_prod(in[0], split_hi(basis_entry<N, MAT>(i * N)), split_lo(basis_entry<N, MAT>(i * N)), s, t);
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+      df_prod_acc(in[j], split_hi(basis_entry<N, MAT>(i * N + j)), split_lo(basis_entry<N, MAT>(i * N + j)), s, t);
+    out[i] = df_fast_norm(s, t);
+  }
+}
+
+template <int N, int MAT>
+__device__ __forceinline__ void contract_t_df(const df (&in)[N], df (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s, t;
+    df_prod(in[0], split_hi(basis_entry<N, MAT>(i)), split_lo(basis_entry<N, MAT>(i)), s, t);
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+      df_prod_acc(in[j], split_hi(basis_entry<N, MAT>(j * N + i)), split_lo(basis_entry<N, MAT>(j * N + i)), s, t);
+    out[i] = df_fast_norm(s, t);
+  }
+}
+
+template <int N, int CB>
+__global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
+    brick_vmult_df_kernel(const __grid_constant__ BrickArgs<N, double> a, const double* __restrict__ src,
+                          double* __restrict__ dst) {
+  using Real = double;
+  using Sh = BrickShape<N, CB, Real>;
+  constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
+  constexpr int PITCH = Sh::PITCH, SKEW = Sh::SKEW, WMAX = Sh::WMAX;
+  constexpr bool PREFETCH = false;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* tiles = reinterpret_cast<Real*>(smem_raw);
+  df* A = reinterpret_cast<df*>(tiles + Sh::NBUF * Sh::TILE);
+  df* B = A + Sh::CUBES;
+  df* C = B + Sh::CUBES;
+
+  const int t = threadIdx.x;
+  const int c = t % CB;
+  const int r = t / CB;
+  const int f = r % N, s = r / N;
+  const bool line_ok = t < Sh::LINES;
+  // line bases in the cubes
+  const int xa2 = Sh::XSWAP ? s : f, xa3 = Sh::XSWAP ? f : s;
+  const int xbase = c * CELL + xa3 * P2 + xa2 * NP;  // x-line (a2, a3), stride 1
+  const int ybase = c * CELL + s * P2 + f;          // y-line (a1 = f, a3 = s), stride NP
+  const int zbase = c * CELL + s * NP + f;          // z-line (a1 = f, a2 = s), stride P2
+  // z-line (a1 = f, a2 = s) in the tile: point x = c K + f of rows a3 N + s
+  const int zx = c * K + f;
+  const int ztile = s * PITCH + zx + (zx / K) * SKEW;  // + a3 * N * PITCH
+  const int n_batches = (int)a.n_batches;
+
+  // issue the asynchronous copies of batch bb into tile buffer `buf` (Dirichlet points set to 0);
+  // warp w copies tile rows w, w + NWARPS, ...; lanes walk the points of the row
+  constexpr int NWARPS = Sh::THREADS / 32, XITERS = (WMAX + 31) / 32;
+  const int warp = t >> 5, lane = t & 31;
+  auto load_tile = [&](int bb, Real* buf) {
+    const BatchInfo bi = batch_info<CB, K>(a, bb);
+    for (int row = warp; row < N * N; row += NWARPS) {
+      const int a2 = row % N, a3 = row / N;
+      const int rflags = (a2 == 0 ? 1 : 0) | (a2 == K ? 2 : 0) | (a3 == 0 ? 4 : 0) | (a3 == K ? 8 : 0);
+      const bool rbnd = (rflags & bi.eflags) != 0;
+      const Real* g = src + bi.gbase + a.Mx * (a2 + a.My * a3);
+      Real* p = buf + row * PITCH;
+#pragma unroll
+      for (int j = 0; j < XITERS; ++j) {
+        const int x = lane + 32 * j;
+        if (x < bi.Wm) {
+          const bool bnd = rbnd || (x == 0 && bi.xlo) || (x == bi.Wm - 1 && bi.xhi);
+          Real* q = p + x + (x / K) * SKEW;
+          if (bnd)
+            *q = Real(0);
+          else
+            cp_async(q, g + x);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  int buf = 0;
+  if (Sh::NBUF == 2 && (int)blockIdx.x < n_batches) load_tile(blockIdx.x, tiles);
+
+  for (int b = blockIdx.x; b < n_batches; b += gridDim.x) {
+    const BatchInfo bi = batch_info<CB, K>(a, b);
+    const int m = bi.m;
+    const bool act = line_ok && c < m;
+    const Real* Gb = a.metric + (int64_t)b * (6 * N3 * CB) + (xa2 * N + xa3 * N * N) * CB + c;
+    Real* T = tiles + buf * Sh::TILE;
+
+    if constexpr (Sh::NBUF == 2) {
+      // copies of the next batch go into the other buffer; this batch's copies were issued earlier
+      if (b + (int)gridDim.x < n_batches) load_tile(b + gridDim.x, tiles + (buf ^ 1) * Sh::TILE);
+      else cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      load_tile(b, T);
+      cp_async_wait<0>();
+    }
+    // metric of this thread's x-line, consumed four phases later
+    Real G[PREFETCH ? 6 : 1][N];
+    if (PREFETCH && act) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+#pragma unroll
+        for (int q = 0; q < N; ++q) G[e][q] = __ldg(Gb + (e * N3 + q) * CB);
+    }
+    __syncthreads();
+    // 1) S along z: z-lines from the tile into cube A
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = df_split(T[ztile + j * N * PITCH]);
+      contract_df<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
+    }
+    __syncthreads();
+    // 2) S along y
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
+      contract_df<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
+    }
+    __syncthreads();
+    // 3) S along x -> values at Gauss points; D along x kept in registers
+    df g1[N];
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[xbase + j];
+      contract_df<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[xbase + j] = o[j];
+      contract_df<N, MAT_D>(o, g1);
+    }
+    __syncthreads();
+    // 4) D along y -> B, D along z -> C
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
+      contract_df<N, MAT_D>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
+      contract_df<N, MAT_D>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
+    }
+    __syncthreads();
+    // 5) quadrature-point metric on the x-line; D_x^T in registers
+    df t1[N];
+    if (act) {
+      df h1[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        // the metric is stored as float pairs (hi, lo) in place of the FP64 values
+        const float2* Gp = reinterpret_cast<const float2*>(Gb);
+        const float2 g00 = __ldg(Gp + (0 * N3 + q) * CB), g01 = __ldg(Gp + (1 * N3 + q) * CB);
+        const float2 g02 = __ldg(Gp + (2 * N3 + q) * CB), g11 = __ldg(Gp + (3 * N3 + q) * CB);
+        const float2 g12 = __ldg(Gp + (4 * N3 + q) * CB), g22 = __ldg(Gp + (5 * N3 + q) * CB);
+        const df G00{g00.x, g00.y}, G01{g01.x, g01.y}, G02{g02.x, g02.y};
+        const df G11{g11.x, g11.y}, G12{g12.x, g12.y}, G22{g22.x, g22.y};
+        const df u1 = g1[q], u2 = B[xbase + q], u3 = C[xbase + q];
+        h1[q] = df_dot3(G00, u1, G01, u2, G02, u3);
+        B[xbase + q] = df_dot3(G01, u1, G11, u2, G12, u3);
+        C[xbase + q] = df_dot3(G02, u1, G12, u2, G22, u3);
+      }
+      contract_t_df<N, MAT_D>(h1, t1);
+    }
+    __syncthreads();
+    // 6) D_y^T on B, D_z^T on C
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = B[ybase + j * NP];
+      contract_t_df<N, MAT_D>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = C[zbase + j * P2];
+      contract_t_df<N, MAT_D>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
+    }
+    __syncthreads();
+    // 7) sum of the three components, S_x^T -> A
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = df_add3(t1[j], B[xbase + j], C[xbase + j]);
+      contract_t_df<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[xbase + j] = o[j];
+    }
+    __syncthreads();
+    // 8) S_y^T
+    if (act) {
+      df v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
+      contract_t_df<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
+    }
+    __syncthreads();
+    // 9) S_z^T into the output tile (aliases this batch's input tile, consumed in step 1):
+    //    nodes with a1 < K first, then the a1 = K nodes add to the next cell's a1 = 0 node
+    df o9[N];
+    if (act) {
+      df v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
+      contract_t_df<N, MAT_S>(v, o9);
+      if (f < K) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] = df_join(o9[j]);
+      }
+    }
+    __syncthreads();
+    if (act && f == K) {
+      if (c < m - 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] += df_join(o9[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] = df_join(o9[j]);
+      }
+    }
+    __syncthreads();
+    // 10) scatter: coalesced atomic adds, warp per tile row; constrained rows copy src
+    for (int row = warp; row < N * N; row += NWARPS) {
+      const int a2 = row % N, a3 = row / N;
+      const int rflags = (a2 == 0 ? 1 : 0) | (a2 == K ? 2 : 0) | (a3 == 0 ? 4 : 0) | (a3 == K ? 8 : 0);
+      const bool rbnd = (rflags & bi.eflags) != 0;
+      const int g = bi.gbase + a.Mx * (a2 + a.My * a3);
+      const Real* p = T + row * PITCH;
+#pragma unroll
+      for (int j = 0; j < XITERS; ++j) {
+        const int x = lane + 32 * j;
+        if (x < bi.Wm) {
+          const bool bnd = rbnd || (x == 0 && bi.xlo) || (x == bi.Wm - 1 && bi.xhi);
+          if (bnd)
+            dst[g + x] = __ldg(src + g + x);
+          else
+            red_add(dst + g + x, p[x + (x / K) * SKEW]);
+        }
+      }
+    }
+    __syncthreads();
+    buf ^= (Sh::NBUF - 1);
+  }
+  if constexpr (Sh::NBUF == 2) cp_async_wait<0>();
+}
+
+}  // namespace mfx

@@ -9,6 +9,7 @@
 #include "vmult.cuh"
 #include "vmult_brick.cuh"
 #include "vmult_brick_tma.cuh"
+#include "vmult_brick_df.cuh"
 
 namespace mfx {
 
@@ -77,7 +78,13 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
   using Sh = BrickShape<N, CB, Real>;
   static int blocks_per_sm = -1;
   const size_t smem = Sh::SMEM;
-  auto kern = brick_vmult_kernel<N, Real, CB>;
+  // FP64 in double-float arithmetic (same shared memory: a float pair per value)
+  auto kern = [] {
+    if constexpr (std::is_same<Real, double>::value)
+      return brick_vmult_df_kernel<N, CB>;
+    else
+      return brick_vmult_kernel<N, Real, CB>;
+  }();
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
