@@ -32,11 +32,11 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 
 
 # DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
-# profiles/vmult_fp32_tma_q4_48cube.md (48^3 case scaled by cells).  Valid only for the kernel sources it
+# profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case scaled by cells).  Valid only for the kernel sources it
 # was taken from: any change to them makes the figure stale (reported as null).
-TRAFFIC_BYTES = 979.0e6
-TRAFFIC_SOURCES = {"vmult_brick_tma.cuh": "50cedac7d8f2e8a9", "vmult_brick.cuh": "aa71379d66c00ec7",
-                   "vmult.cuh": "d3511f8f3650319c"}
+TRAFFIC_BYTES = 978.5e6
+TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "36f19fc9197e5734", "vmult_brick_tma.cuh": "50cedac7d8f2e8a9",
+                   "vmult_brick.cuh": "bf6bd83f5458fb78", "vmult.cuh": "d3511f8f3650319c"}
 
 
 def measured_traffic(nx, k):
@@ -275,7 +275,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": measured_traffic(nx, kdeg), "peak_kind": peak_kind,
-                     "kernel": "FP32 vmult (boundary_rows_kernel + brick_vmult_tma_kernel), timed together",
+                     "kernel": "FP32 vmult (boundary_rows_kernel + brick_vmult_tma2_kernel), timed together",
                      "algorithmic_bytes": b32},
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": ms_e2e},

@@ -890,7 +890,9 @@ mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
 
 void mfx_batch_destroy(mfx_batch* bt) {
   if (!bt) return;
-  cudaDeviceSynchronize();
+  for (auto& sl : bt->slots)
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+  if (bt->stream) cudaStreamSynchronize(bt->stream);
   if (bt->parent) cudaGraphExecDestroy(bt->parent);
   for (auto& sl : bt->slots) {
     slot_release(sl);
@@ -985,7 +987,9 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
       if (rc != MFX_OK) return rc;
       any_outer = true;
     }
-  if (any_outer) MFX_CUDA_TRY(cudaDeviceSynchronize());
+  if (any_outer)
+    for (auto& sl : bt->slots)
+      if (sl.phase == SLOT_OUTER) MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
   for (auto& sl : bt->slots) {
     if (sl.phase != SLOT_OUTER) continue;
     sl.rr = sl.h_scal[0];
@@ -1007,7 +1011,8 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
   mfx_status rc = rebuild_parent(bt);
   if (rc != MFX_OK) return rc;
   if (bt->parent) {
-    MFX_CUDA_TRY(cudaDeviceSynchronize());  // slot streams (inner starts) before the batch stream
+    for (int i : bt->parent_members)  // slot streams (inner starts) before the batch stream
+      MFX_CUDA_TRY(cudaStreamSynchronize(bt->slots[i].stream));
     MFX_CUDA_TRY(cudaGraphLaunch(bt->parent, bt->stream));
     MFX_CUDA_TRY(cudaStreamSynchronize(bt->stream));
     ++bt->ticks;

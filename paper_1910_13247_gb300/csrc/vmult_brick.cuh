@@ -31,7 +31,7 @@
 namespace mfx {
 
 // cells per batch for each n (= k + 1)
-template <int N> struct BrickCB { static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : N == 8 ? 8 : 4); };
+template <int N> struct BrickCB { static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : 8); };
 
 template <int N, int CB, typename Real>
 struct BrickShape {
@@ -44,7 +44,7 @@ struct BrickShape {
   static constexpr int P2 = N == 2 ? (CB == 16 ? 5 : 4) : N == 3 ? 9 : N == 4 ? 17 : N == 5 ? 25 : N == 6 ? 37
                           : N == 7 ? 49 : N == 8 ? 65 : 81;
   static constexpr int CELL = N == 2 ? (CB == 16 ? 10 : 9) : N == 3 ? (CB == 16 ? 30 : 27)
-                            : N == 4 ? (CB == 8 ? 68 : 70) : N == 5 ? (CB == 8 ? 132 : 126)
+                            : N == 4 ? (CB == 8 ? 68 : 70) : N == 5 ? (CB == 8 ? 132 : CB == 32 ? 125 : 126)
                             : N == 6 ? 222 : N == 7 ? 346 : N == 8 ? (CB == 4 ? 520 : 524) : (CB == 4 ? 744 : 732);
   static constexpr int CUBES = CB * CELL;  // elements per cube array
   // row-major tile: point x of row r at r * PITCH + x + (x / K) * SKEW
@@ -52,7 +52,8 @@ struct BrickShape {
   static constexpr bool F32 = sizeof(Real) == 4;
   static constexpr int SKEW = !F32 ? 0 : N == 4 ? 3 : N == 5 ? 2 : N == 6 ? 1 : N == 8 ? 5 : 0;
   static constexpr int PITCH_MIN = WMAX + (WMAX - 1) / K * SKEW;
-  static constexpr int PITCH = !F32 ? (WMAX | 1) : (N <= 3 ? 33 : N == 9 ? 33 : 97);
+  static constexpr int PITCH_TABLE = N <= 3 ? 33 : 97;  // conflict-free pitches found for the default CB
+  static constexpr int PITCH = !F32 ? (WMAX | 1) : (PITCH_TABLE >= PITCH_MIN ? PITCH_TABLE : (PITCH_MIN | 1));
   static_assert(PITCH >= PITCH_MIN, "tile pitch too small");
   static constexpr int TILE = N * N * PITCH;  // elements per tile buffer
   static constexpr int NBUF = F32 ? 2 : 1;    // input tiles (double-buffered for FP32); output aliases

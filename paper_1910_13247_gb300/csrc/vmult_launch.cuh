@@ -10,6 +10,7 @@
 #include "vmult_brick.cuh"
 #include "vmult_brick_tma.cuh"
 #include "vmult_brick_df.cuh"
+#include "vmult_brick_tma2.cuh"
 
 namespace mfx {
 
@@ -199,13 +200,54 @@ static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, 
 }
 
 template <int N>
+static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  constexpr int CB = BrickCB<N>::value;
+  using Ps = PairShape<N, CB>;
+  using Tm = TmaShape<N, CB>;
+  static int blocks_per_sm = -1;
+  const size_t smem = Ps::SMEM;
+  auto kern = brick_vmult_tma2_kernel<N, CB>;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Ps::THREADS, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  if (op->metric_cb != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
+  TmaArgs<N> a;
+  mfx_status st = encode_1d_map(&a.tsrc, src, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  st = encode_1d_map(&a.tdst, dst, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  a.metric = op->d_metric32;
+  a.nx = op->nx;
+  a.ny = op->ny;
+  a.nz = op->nz;
+  a.nchunk = (op->nx + CB - 1) / CB;
+  a.Mx = op->k * op->nx + 1;
+  a.My = op->k * op->ny + 1;
+  a.Mz = op->k * op->nz + 1;
+  a.n_batches = a.nchunk * op->ny * op->nz;
+  a.err = op->d_err;
+  a.skip = skip;
+  MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
+  const int rows = a.My * a.Mz;
+  boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
+      a.Mx, a.My, a.Mz, src, dst);
+  const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
+  kern<<<grid, Ps::THREADS, smem, s>>>(a);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip) {
   if (prec == MFX_F64) {
     if (op->structured) return run_brick<N, double>(op, (const double*)src, (double*)dst, s, skip);
     return run_vmult<N, double, false>(op, (const double*)src, (double*)dst, s, skip);
   }
-  if (op->structured) return run_brick_tma<N>(op, (const float*)src, (float*)dst, s, skip);
+  if (op->structured) return run_brick_tma2<N>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float, false>(op, (const float*)src, (float*)dst, s, skip);
 }
 

@@ -265,8 +265,8 @@ class Operator:
         check(lib().mfx_rhs(self.handle, _ptr(fq), _ptr(b), _stream()))
         return b
 
-    def distribute(self, x):
-        check(lib().mfx_distribute(self.handle, _ptr(x), _stream()))
+    def distribute(self, x, stream=None):
+        check(lib().mfx_distribute(self.handle, _ptr(x), _stream(stream)))
         return x
 
     def dot(self, a, b, out):

@@ -77,13 +77,17 @@ class Server:
 
     @staticmethod
     def _setup(req):
+        # runs on a set-up thread, on a stream of its own: no device-wide synchronisation, which
+        # would collide with the graph captures of the serving thread
         import torch
-        mesh = mfx.Mesh.octree(req.nb, req.nb, req.nb, req.leaves)
-        op = mfx.Operator(mesh, req.degree)
-        b = torch.tensor(synthetic.gaussian_vector(op.n_dofs, req.seed), device="cuda")
-        op.distribute(b)  # right-hand side on the free DoFs only
-        x = torch.zeros_like(b)
-        torch.cuda.synchronize()
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            mesh = mfx.Mesh.octree(req.nb, req.nb, req.nb, req.leaves)
+            op = mfx.Operator(mesh, req.degree, stream=stream)
+            b = torch.tensor(synthetic.gaussian_vector(op.n_dofs, req.seed), device="cuda")
+            op.distribute(b)  # right-hand side on the free DoFs only
+            x = torch.zeros_like(b)
+        stream.synchronize()
         return op, b, x
 
     def run(self, requests, time_limit=None):
