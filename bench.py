@@ -380,7 +380,11 @@ def batched_measurement(mfx, synthetic, torch, np, n_problems=64, seed=4):
         statuses.add(st["status"])
         dof_iters += st["inner_iterations"] * op.n_dofs
         worst = max(worst, st["rel_residual"])
+    chosen = {}
+    for op, n_, k_ in zip(ops, Ns, ks):
+        chosen.setdefault(f"k{int(k_)}", {})[int(n_)] = op.info()["cells_per_block"]
     return {"problems": n_problems, "total_dofs": total_dofs, "seconds": t_batch, "ticks": ticks,
+            "autotuned_cells_per_block": chosen,
             "dof_iterations_per_s": dof_iters / t_batch, "statuses": sorted(statuses), "max_rel_residual": worst,
             "sequential_seconds": t_seq, "speedup_over_sequential": t_seq / t_batch,
             "sizes": {"N": [int(v) for v in Ns], "k": [int(v) for v in ks]}}

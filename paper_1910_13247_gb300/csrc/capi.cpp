@@ -5,6 +5,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <array>
+#include <map>
+#include <mutex>
 
 #include "mfx_internal.h"
 
@@ -63,6 +66,109 @@ mfx_status prepare_vmult(const mfx_op* op) {
     case 9: return prepare_vmult_n<9>(op);
     default: return set_error(MFX_EUNSUPPORTED, "degree out of range");
   }
+}
+
+int brick_cells_candidates_for_degree(int k, int* out) {
+  switch (k + 1) {
+    case 2: return brick_cells_candidates<2>(out);
+    case 3: return brick_cells_candidates<3>(out);
+    case 4: return brick_cells_candidates<4>(out);
+    case 5: return brick_cells_candidates<5>(out);
+    case 6: return brick_cells_candidates<6>(out);
+    case 7: return brick_cells_candidates<7>(out);
+    case 8: return brick_cells_candidates<8>(out);
+    case 9: return brick_cells_candidates<9>(out);
+    default: return 0;
+  }
+}
+
+// Time the FP32 vmult of a structured operator with the metric laid out for `cb` cells per
+// batch (geometry rebuilt in that layout); returns milliseconds per application.
+static mfx_status time_layout(mfx_op* op, int cb, int coef_kind, const double* par, const double* coef_q,
+                              float* x, float* y, cudaStream_t s, float* ms) {
+  op->metric_cb = cb;
+  op->nchunk = (op->nx + cb - 1) / cb;
+  mfx_status st = launch_geometry(op, coef_kind, par, coef_q, s);
+  if (st != MFX_OK) return st;
+  st = launch_vmult(op, MFX_F32, x, y, s);  // warm-up (first launch sets kernel attributes)
+  if (st != MFX_OK) return st;
+  cudaEvent_t e0, e1;
+  MFX_CUDA_TRY(cudaEventCreate(&e0));
+  MFX_CUDA_TRY(cudaEventCreate(&e1));
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < 3 && st == MFX_OK; ++r) st = launch_vmult(op, MFX_F32, x, y, s);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MFX_OK) return st;
+  if (e != cudaSuccess) return cuda_error(e, "autotune timing");
+  *ms = t / 3;
+  return MFX_OK;
+}
+
+// Autotuner: cells per batch for (degree, mesh size), measured once per process and device.
+static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kind, const double* par,
+                                         const double* coef_q, cudaStream_t s) {
+  int cand[4];
+  const int nc = brick_cells_candidates_for_degree(op->k, cand);
+  if (requested > 0) {
+    for (int i = 0; i < nc; ++i)
+      if (cand[i] == requested) {
+        op->metric_cb = requested;
+        op->nchunk = (op->nx + requested - 1) / requested;
+        return MFX_OK;
+      }
+    return set_error(MFX_EUNSUPPORTED, "cells_per_block not compiled for this degree");
+  }
+  op->metric_cb = cand[0];
+  op->nchunk = (op->nx + cand[0] - 1) / cand[0];
+  if (nc < 2 || !op->has_f32) return MFX_OK;
+  static std::mutex lock;
+  static std::map<std::array<int64_t, 5>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::array<int64_t, 5> key = {op->k, op->nx, op->ny, op->nz, dev};
+  {
+    std::lock_guard<std::mutex> g(lock);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      op->metric_cb = it->second;
+      op->nchunk = (op->nx + it->second - 1) / it->second;
+      return MFX_OK;
+    }
+  }
+  float* x = nullptr;
+  float* y = nullptr;
+  MFX_CUDA_TRY(cudaMalloc(&x, sizeof(float) * op->n_dofs));
+  cudaError_t e = cudaMalloc(&y, sizeof(float) * op->n_dofs);
+  if (e != cudaSuccess) {
+    cudaFree(x);
+    return cuda_error(e, "autotune vectors");
+  }
+  cudaMemsetAsync(x, 0, sizeof(float) * op->n_dofs, s);
+  int best = cand[0];
+  float best_ms = 1e30f;
+  mfx_status st = MFX_OK;
+  for (int i = 0; i < nc && st == MFX_OK; ++i) {
+    float ms = 0;
+    st = time_layout(op, cand[i], coef_kind, par, coef_q, x, y, s, &ms);
+    if (st == MFX_OK && ms < best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(x);
+  cudaFree(y);
+  if (st != MFX_OK) return st;
+  op->metric_cb = best;
+  op->nchunk = (op->nx + best - 1) / best;
+  std::lock_guard<std::mutex> g(lock);
+  cache[key] = best;
+  return MFX_OK;
 }
 
 int brick_cells_for_degree(int k) {
@@ -268,10 +374,17 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   const size_t nq = (size_t)op->n_cells * n3;
   size_t metric_entries = 6 * nq;
   if (op->structured) {
-    // structured meshes: rows of cells in batches of metric_cb, metric interleaved per batch
-    op->metric_cb = brick_cells_for_degree(k);
-    op->nchunk = (op->nx + op->metric_cb - 1) / op->metric_cb;
-    metric_entries = (size_t)op->nchunk * op->ny * op->nz * op->metric_cb * 6 * n3;
+    // structured meshes: rows of cells in batches of metric_cb cells, metric interleaved per batch;
+    // room for the largest layout among the compiled batch sizes (the autotuner may try each)
+    int cand[4];
+    const int nc = brick_cells_candidates_for_degree(k, cand);
+    metric_entries = 0;
+    for (int i = 0; i < nc; ++i) {
+      const size_t nch = (size_t)(op->nx + cand[i] - 1) / cand[i];
+      metric_entries = std::max(metric_entries, nch * op->ny * op->nz * cand[i] * 6 * n3);
+    }
+    op->metric_cb = cand[0];
+    op->nchunk = (op->nx + cand[0] - 1) / cand[0];
   }
   // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
   MFX_TRY(dev_alloc(op, &op->d_metric64, metric_entries));
@@ -286,6 +399,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   MFX_TRY(dev_alloc(op, &op->d_err, 4));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_err, 0, 4 * sizeof(int), s));
   MFX_TRY(prepare_vmult(op));
+  if (op->structured)
+    MFX_TRY(choose_cells_per_batch(op, desc->cells_per_block, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_diagonal(op, s));
   // the structured FP64 vmult works in double-float arithmetic on a pre-split metric
@@ -308,7 +423,7 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   info->degree = op->k;
   info->n_q_1d = op->n;
   info->structured = op->structured ? 1 : 0;
-  info->cells_per_block = 256 / (op->n * op->n);
+  info->cells_per_block = op->structured ? op->metric_cb : 256 / (op->n * op->n);
   return MFX_OK;
 }
 

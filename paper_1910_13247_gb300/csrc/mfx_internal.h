@@ -132,6 +132,9 @@ mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* 
 template <int N>
 int brick_cells_per_batch();
 template <int N>
+int brick_cells_candidates(int* out);
+int brick_cells_candidates_for_degree(int k, int* out);
+template <int N>
 mfx_status prepare_vmult_n(const mfx_op* op);
 mfx_status prepare_vmult(const mfx_op* op);
 int brick_cells_for_degree(int k);

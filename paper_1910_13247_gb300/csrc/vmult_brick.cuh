@@ -31,7 +31,10 @@
 namespace mfx {
 
 // cells per batch for each n (= k + 1)
-template <int N> struct BrickCB { static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : 8); };
+template <int N> struct BrickCB {
+  static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : 8);  // default
+  static constexpr int ALT = (N == 4 || N == 5) ? 8 : 0;          // second compiled choice (0: none)
+};
 
 template <int N, int CB, typename Real>
 struct BrickShape {

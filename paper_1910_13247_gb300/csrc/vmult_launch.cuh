@@ -73,9 +73,8 @@ static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaSt
   return MFX_OK;
 }
 
-template <int N, typename Real>
+template <int N, typename Real, int CB>
 static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
-  constexpr int CB = BrickCB<N>::value;
   using Sh = BrickShape<N, CB, Real>;
   static int blocks_per_sm = -1;
   const size_t smem = Sh::SMEM;
@@ -113,6 +112,18 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
 
 template <int N>
 int brick_cells_per_batch() { return BrickCB<N>::value; }
+
+// Batch sizes (cells per batch) compiled for degree N - 1, default first; the operator picks one
+// by timing (autotuning) or takes the caller's choice.
+template <int N>
+int brick_cells_candidates(int* out) {
+  out[0] = BrickCB<N>::value;
+  if (BrickCB<N>::ALT > 0) {
+    out[1] = BrickCB<N>::ALT;
+    return 2;
+  }
+  return 1;
+}
 
 // dst = src on the Dirichlet (box boundary) DoFs; one warp per lattice row (J, L).
 template <typename Real>
@@ -158,9 +169,8 @@ static mfx_status encode_1d_map(CUtensorMap* map, const void* ptr, int64_t n, in
   return MFX_OK;
 }
 
-template <int N>
+template <int N, int CB>
 static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
-  constexpr int CB = BrickCB<N>::value;
   using Sh = BrickShape<N, CB, float>;
   using Tm = TmaShape<N, CB>;
   static int blocks_per_sm = -1;
@@ -199,9 +209,8 @@ static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, 
   return MFX_OK;
 }
 
-template <int N>
+template <int N, int CB>
 static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
-  constexpr int CB = BrickCB<N>::value;
   using Ps = PairShape<N, CB>;
   using Tm = TmaShape<N, CB>;
   static int blocks_per_sm = -1;
@@ -243,11 +252,19 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip) {
+  constexpr int CB0 = BrickCB<N>::value;
+  constexpr int CB1 = BrickCB<N>::ALT > 0 ? BrickCB<N>::ALT : CB0;
   if (prec == MFX_F64) {
-    if (op->structured) return run_brick<N, double>(op, (const double*)src, (double*)dst, s, skip);
+    if (op->structured) {
+      if (CB1 != CB0 && op->metric_cb == CB1) return run_brick<N, double, CB1>(op, (const double*)src, (double*)dst, s, skip);
+      return run_brick<N, double, CB0>(op, (const double*)src, (double*)dst, s, skip);
+    }
     return run_vmult<N, double, false>(op, (const double*)src, (double*)dst, s, skip);
   }
-  if (op->structured) return run_brick_tma2<N>(op, (const float*)src, (float*)dst, s, skip);
+  if (op->structured) {
+    if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
+    return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
+  }
   return run_vmult<N, float, false>(op, (const float*)src, (float*)dst, s, skip);
 }
 

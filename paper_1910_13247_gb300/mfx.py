@@ -194,7 +194,7 @@ class Operator:
     """The condensed Q_k operator of one mesh (geometry and tables on the device)."""
 
     def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), precisions=3,
-                 coef_qpoint=None, stream=None):
+                 coef_qpoint=None, stream=None, cells_per_block=0):
         d = OpDesc()
         d.degree = degree
         d.n_q_1d = 0
@@ -202,7 +202,7 @@ class Operator:
         d.precisions = precisions
         d.coef_par[0], d.coef_par[1] = coef_par
         d.coef_qpoint = coef_qpoint.data_ptr() if coef_qpoint is not None else None
-        d.cells_per_block = 0
+        d.cells_per_block = cells_per_block
         h = ctypes.c_void_p()
         check(lib().mfx_operator_create(ctypes.byref(h), mesh.handle, ctypes.byref(d), _stream(stream)))
         self.handle = h

@@ -83,6 +83,27 @@ def test_deformed_variable_coefficient_vmult_all_degrees(mfx, k):
     assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
 
 
+@pytest.mark.parametrize("k", [3, 4])
+def test_both_batch_sizes_and_autotuned_choice(mfx, k):
+    """Structured kernels compiled for 8 and 16 cells per batch (metric laid out per choice) give the
+    oracle's result on rows that are not a multiple of either; the autotuner picks one of them."""
+    nx, ny, nz = 13, 3, 2
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 90 + k)
+    ref = K @ x
+    for cb in (8, 16, 0):
+        op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz, verts), k, mfx.COEF_TRIG, (1.0, 0.5),
+                          cells_per_block=cb)
+        assert op.info()["cells_per_block"] in (8, 16)
+        if cb:
+            assert op.info()["cells_per_block"] == cb
+        e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+        assert e2 < 1e-12 and einf < 1e-12, (cb, e2, einf)
+        assert rel_err(run_vmult(op, x, torch.float32), ref)[0] < 1e-5
+
+
 def test_quadrature_points_and_rhs(mfx):
     op, om, par = make_pair(mfx, 3, 4, 2, 3)
     X, _ = fem.quadrature_points(om, 4)
