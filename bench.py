@@ -65,6 +65,21 @@ def bytes_per_vmult(n_dofs, n_cells, k, s):
     return 2 * s * n_dofs + 6 * s * n_cells * (k + 1) ** 3
 
 
+def aggregate_ranks(elapsed_ms, units_per_rank, dist=None, device=None):
+    """Whole-job throughput of replicas: the slowest rank's time, the work of all ranks.
+
+    Returns (max elapsed ms over ranks, total units / that time in units per second)."""
+    import torch
+    world = 1
+    t = float(elapsed_ms)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        v = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return t, world * units_per_rank / (t * 1e-3)
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -226,11 +241,11 @@ def main():
     t_end.record(stream)
     barrier()
     clocks = sampler.stop()
-    total_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    total_ms, units_per_s = aggregate_ranks(t_start.elapsed_time(t_end), N * args.steps, dist, "cuda")
     per_launch = [a.elapsed_time(b) for a, b in ev]
     ms32 = statistics.mean(per_launch)
     ms_per_step = total_ms / args.steps
-    value = world * N / (ms_per_step * 1e-3) / 1e9
+    value = units_per_s / 1e9
 
     hbm, peak_kind = peaks()
     b32 = bytes_per_vmult(N, C, kdeg, 4)

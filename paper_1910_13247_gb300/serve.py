@@ -102,7 +102,7 @@ class Server:
         used = 0
         done = []
         max_active = 0
-        pool = cf.ThreadPoolExecutor(max_workers=2)
+        pool = cf.ThreadPoolExecutor(max_workers=4)
         start = time.perf_counter()
         while pending or queue or active or setting_up:
             now = time.perf_counter() - start

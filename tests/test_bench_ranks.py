@@ -1,0 +1,50 @@
+"""Multi-rank (replica) aggregation of bench.py, on CPU with the gloo backend and two ranks:
+the job time is the slowest rank's and the throughput counts every rank's work."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t, rate = bench.aggregate_ranks(10.0 + 5.0 * rank, 1000.0, dist, "cpu")
+    out[rank] = (t, rate)
+    dist.destroy_process_group()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_two_rank_aggregation_takes_slowest_rank_and_total_work():
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    for rank in (0, 1):
+        t, rate = out[rank]
+        assert t == 15.0
+        assert abs(rate - 2 * 1000.0 / 15e-3) < 1e-6
+
+
+def test_single_process_aggregation():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    t, rate = bench.aggregate_ranks(20.0, 500.0)
+    assert t == 20.0 and abs(rate - 500.0 / 20e-3) < 1e-9
