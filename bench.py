@@ -286,6 +286,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if (nx, kdeg) == (NX, K_DEG) else f"{nx}^3 cells, Q{kdeg} (profiling case)",
                    "n_dofs": N, "n_cells": C, "degree": kdeg, "n_q_1d": kdeg + 1,
+                   "cells_per_block": op.info()["cells_per_block"],
                    "step": "one FP32 vmult", "l2": "inputs larger than L2 (%.2f GB read+written per step)" % (b32 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
