@@ -32,16 +32,16 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 
 
 # DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
-# profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case scaled by cells).  Valid only for the kernel sources it
-# was taken from: any change to them makes the figure stale (reported as null).
-TRAFFIC_BYTES = 978.5e6
+# profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case, 16 cells per batch, scaled by cells).  Valid only for
+# that batch size and the kernel sources it was taken from: anything else reports null.
+TRAFFIC_BYTES = 978.2e6
 TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "36f19fc9197e5734", "vmult_brick_tma.cuh": "50cedac7d8f2e8a9",
-                   "vmult_brick.cuh": "bf6bd83f5458fb78", "vmult.cuh": "d3511f8f3650319c"}
+                   "vmult_brick.cuh": "f053cbb95aed5d25", "vmult.cuh": "d3511f8f3650319c"}
 
 
-def measured_traffic(nx, k):
+def measured_traffic(nx, k, cells_per_block):
     import hashlib
-    if (nx, k) != (NX, K_DEG):
+    if (nx, k, cells_per_block) != (NX, K_DEG, 16):
         return None
     csrc = os.path.join(ROOT, "paper_1910_13247_gb300", "csrc")
     for name, digest in TRAFFIC_SOURCES.items():
@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
+    ap.add_argument("--cells-per-block", type=int, default=0,
+                    help="fix the structured kernel's cells per batch (0: autotuned at operator creation)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -201,7 +203,7 @@ def main():
     nx, kdeg = args.nx, args.degree
     verts = synthetic.deformed_vertices(nx, nx, nx)
     mesh = mfx.Mesh.structured_box(nx, nx, nx, verts)
-    op = mfx.Operator(mesh, kdeg, mfx.COEF_TRIG, (1.0, 0.5))
+    op = mfx.Operator(mesh, kdeg, mfx.COEF_TRIG, (1.0, 0.5), cells_per_block=args.cells_per_block)
     N, C = op.n_dofs, op.n_cells
     x64 = torch.tensor(synthetic.uniform_vector(N, 1), device="cuda")
     x32 = x64.float()
@@ -290,7 +292,7 @@ def main():
                    "step": "one FP32 vmult", "l2": "inputs larger than L2 (%.2f GB read+written per step)" % (b32 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": measured_traffic(nx, kdeg), "peak_kind": peak_kind,
+                     "traffic": measured_traffic(nx, kdeg, op.info()["cells_per_block"]), "peak_kind": peak_kind,
                      "kernel": "FP32 vmult (boundary_rows_kernel + brick_vmult_tma2_kernel), timed together",
                      "algorithmic_bytes": b32},
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,

@@ -230,8 +230,95 @@ __device__ double element_entry(const GeoArgs& g, const double* __restrict__ m64
   return s;
 }
 
-// diag(C^T A C) on free DoFs: sum over cells and local pairs (i, j) sharing a master m of
-// w_im w_jm A_ij; cells without hanging nodes only need j = i.
+// Diagonal of the element matrix of a cell without hanging nodes, by sum factorisation.  With the 1D
+// products M0[q][i] = l_i(x_q)^2, M1[q][i] = l_i(x_q) l_i'(x_q), M2[q][i] = l_i'(x_q)^2, the entry
+// A_ii of node i = (i1, i2, i3) is the sum over the six metric components G_de of
+//   c_de sum_q G_de(q) M_{a1}[q1][i1] M_{a2}[q2][i2] M_{a3}[q3][i3],
+// a_t = [t == d] + [t == e], c_de = 1 for d = e and 2 otherwise (G symmetric): three 1D contractions
+// (over q3, q2, q1) per component instead of n^3 quadrature sums per node.  N^2 threads per cell,
+// one per 1D line; CPB cells per CTA.
+template <int N>
+__global__ void diagonal_sf_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ m64,
+                                   const uint8_t* __restrict__ cell_hanging, double* __restrict__ diag, int cpb) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ double sh[];
+  double* M = sh;  // 3 x N^2
+  const int lc = threadIdx.x / N2;
+  const int r = threadIdx.x - lc * N2;
+  double* X = sh + 3 * N2 + lc * 2 * N3;
+  double* Y = X + N3;
+  for (int t = threadIdx.x; t < N2; t += blockDim.x) {
+    const double s0 = g.S[t], s1 = g.Sd[t];
+    M[t] = s0 * s0;
+    M[N2 + t] = s0 * s1;
+    M[2 * N2 + t] = s1 * s1;
+  }
+  const int64_t cell = (int64_t)blockIdx.x * cpb + lc;
+  const bool ok = lc < cpb && cell < g.n_cells && !(cell_hanging && cell_hanging[cell]);
+  const int64_t base = ok ? metric_offset(g, cell, 0) : 0;
+  const int64_t st = metric_stride(g);
+  const int ra = r % N, rb = r / N;
+  double z[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) z[i] = 0.0;
+  __syncthreads();
+#pragma unroll 1
+  for (int c = 0; c < 6; ++c) {  // components G00, G01, G02, G11, G12, G22
+    const int d = c < 3 ? 0 : (c < 5 ? 1 : 2);
+    const int e = c < 3 ? c : (c < 5 ? c - 2 : 2);
+    const double* T1 = M + ((d == 0) + (e == 0)) * N2;
+    const double* T2 = M + ((d == 1) + (e == 1)) * N2;
+    const double* T3 = M + ((d == 2) + (e == 2)) * N2;
+    // contraction over q3: thread (q1, q2) = (ra, rb)
+    if (ok) {
+      double gq[N];
+#pragma unroll
+      for (int q3 = 0; q3 < N; ++q3) {
+        const int q = ra + N * rb + N2 * q3;
+        gq[q3] = m64[base + c * st + (g.cb == 0 ? q : (int64_t)q * g.cb)];
+      }
+#pragma unroll
+      for (int i3 = 0; i3 < N; ++i3) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q3 = 0; q3 < N; ++q3) acc += gq[q3] * T3[q3 * N + i3];
+        X[ra + N * rb + N2 * i3] = acc;
+      }
+    }
+    __syncthreads();
+    // contraction over q2: thread (q1, i3) = (ra, rb)
+    if (ok) {
+#pragma unroll
+      for (int i2 = 0; i2 < N; ++i2) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q2 = 0; q2 < N; ++q2) acc += X[ra + N * q2 + N2 * rb] * T2[q2 * N + i2];
+        Y[ra + N * i2 + N2 * rb] = acc;
+      }
+    }
+    __syncthreads();
+    // contraction over q1: thread (i2, i3) = (ra, rb)
+    if (ok) {
+      const double cde = d == e ? 1.0 : 2.0;
+#pragma unroll
+      for (int i1 = 0; i1 < N; ++i1) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q1 = 0; q1 < N; ++q1) acc += Y[q1 + N * ra + N2 * rb] * T1[q1 * N + i1];
+        z[i1] += cde * acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (ok) {
+#pragma unroll
+    for (int i1 = 0; i1 < N; ++i1)
+      expand_node(v, cell, i1, ra, rb, [&](int64_t dof, double w) { atomicAdd(diag + dof, w * w * z[i1]); });
+  }
+}
+
+// diag(C^T A C) on free DoFs, cells with hanging nodes: sum over local pairs (i, j) sharing a
+// master m of w_im w_jm A_ij (the element entries by full quadrature).
 __global__ void diagonal_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ m64,
                                 const uint8_t* __restrict__ cell_hanging, double* __restrict__ diag) {
   const int n = g.n, n3 = n * n * n;
@@ -241,12 +328,7 @@ __global__ void diagonal_kernel(const __grid_constant__ GeoArgs g, DofView v, co
     const int64_t cell = idx / n3;
     const int i = (int)(idx - cell * n3);
     const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
-    const bool hang = cell_hanging && cell_hanging[cell];
-    if (!hang) {
-      const double aii = element_entry(g, m64, cell, i, i);
-      expand_node(v, cell, i1, i2, i3, [&](int64_t dof, double w) { atomicAdd(diag + dof, w * w * aii); });
-      continue;
-    }
+    if (!cell_hanging[cell]) continue;  // cells without hanging nodes: diagonal_sf_kernel
     for (int j = 0; j < n3; ++j) {
       const int j1 = j % n, j2 = (j / n) % n, j3 = j / (n * n);
       double aij = 0.0;
@@ -382,6 +464,31 @@ mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_
   return MFX_OK;
 }
 
+template <int N>
+static void run_diagonal_sf(const GeoArgs& g, const DofView& v, const double* m64, const uint8_t* hang, double* d,
+                            cudaStream_t s) {
+  constexpr int cpb = N * N >= 64 ? 1 : 128 / (N * N);  // cells per CTA
+  const int64_t blocks = (g.n_cells + cpb - 1) / cpb;
+  if (blocks == 0) return;
+  const size_t smem = sizeof(double) * (3 * N * N + 2 * cpb * N * N * N);
+  diagonal_sf_kernel<N><<<(unsigned)blocks, cpb * N * N, smem, s>>>(g, v, m64, hang, d, cpb);
+}
+
+static void launch_diagonal_sf(int n, const GeoArgs& g, const DofView& v, const double* m64, const uint8_t* hang,
+                               double* d, cudaStream_t s) {
+  switch (n) {
+    case 2: run_diagonal_sf<2>(g, v, m64, hang, d, s); break;
+    case 3: run_diagonal_sf<3>(g, v, m64, hang, d, s); break;
+    case 4: run_diagonal_sf<4>(g, v, m64, hang, d, s); break;
+    case 5: run_diagonal_sf<5>(g, v, m64, hang, d, s); break;
+    case 6: run_diagonal_sf<6>(g, v, m64, hang, d, s); break;
+    case 7: run_diagonal_sf<7>(g, v, m64, hang, d, s); break;
+    case 8: run_diagonal_sf<8>(g, v, m64, hang, d, s); break;
+    case 9: run_diagonal_sf<9>(g, v, m64, hang, d, s); break;
+    default: break;
+  }
+}
+
 mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
   GeoArgs g = geo_args(op);
   double* tmp = nullptr;
@@ -389,7 +496,9 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(double) * op->n_dofs, s);
   if (e == cudaSuccess) {
     const int64_t work = op->n_cells * op->n * op->n * op->n;
-    diagonal_kernel<<<grid_for(work), 256, 0, s>>>(g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp);
+    if (op->d_cell_hanging)
+      diagonal_kernel<<<grid_for(work), 256, 0, s>>>(g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp);
+    launch_diagonal_sf(op->n, g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp, s);
     diag_finish_kernel<double><<<grid_for(op->n_dofs), 256, 0, s>>>(
         op->n_dofs, op->structured, op->k * op->nx + 1, op->k * op->ny + 1, op->k * op->nz + 1, op->d_cmask, tmp,
         op->d_diag64, op->d_diag32);

@@ -29,6 +29,9 @@ class Request:
         self.leaves = leaves
         self.seed = seed
         self.latency = None
+        self.t_admit = None       # seconds from the start: admitted (set-up begins)
+        self.t_ready = None       # set-up done, solve added to the batch
+        self.setup_s = None       # set-up duration on its worker thread
         self.status = None
         self.n_dofs = None
         self.iterations = None
@@ -80,6 +83,7 @@ class Server:
         # runs on a set-up thread, on a stream of its own: no device-wide synchronisation, which
         # would collide with the graph captures of the serving thread
         import torch
+        t0 = time.perf_counter()
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
             mesh = mfx.Mesh.octree(req.nb, req.nb, req.nb, req.leaves)
@@ -88,6 +92,7 @@ class Server:
             op.distribute(b)  # right-hand side on the free DoFs only
             x = torch.zeros_like(b)
         stream.synchronize()
+        req.setup_s = time.perf_counter() - t0
         return op, b, x
 
     def run(self, requests, time_limit=None):
@@ -119,6 +124,7 @@ class Server:
                     break
                 queue.pop(0)
                 used += est
+                req.t_admit = time.perf_counter() - start
                 setting_up[pool.submit(self._setup, req)] = (req, est)
             for fut in [f for f in setting_up if f.done()]:
                 req, est = setting_up.pop(fut)
@@ -126,6 +132,7 @@ class Server:
                 nbytes = op.info()["bytes_device"] + op.n_dofs * (9 * 8 + 9 * 4 + 16)
                 used += nbytes - est
                 slot = self.batch.add(op, b, x, tol=self.tol, mixed=True)
+                req.t_ready = time.perf_counter() - start
                 active[slot] = (req, op, b, x, nbytes)
                 req.n_dofs = op.n_dofs
             max_active = max(max_active, len(active))
@@ -148,6 +155,11 @@ class Server:
         torch.cuda.synchronize()
         wall = time.perf_counter() - start
         lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+        # where the latency goes: waiting for admission, set-up (host tables, geometry, diagonal),
+        # and the solve itself (from joining the batch to completion)
+        wait = np.array([r.t_admit - r.arrival for r in done]) if done else np.zeros(1)
+        setup = np.array([r.setup_s for r in done]) if done else np.zeros(1)
+        solve = np.array([r.arrival + r.latency - r.t_ready for r in done]) if done else np.zeros(1)
         span = max(r.arrival for r in requests) if requests else 0.0
         return {
             "requests": len(requests), "completed": len(done), "wall_seconds": wall,
@@ -155,6 +167,8 @@ class Server:
             "solves_per_s": len(done) / wall if wall > 0 else 0.0,
             "offered_rate_per_s": len(requests) / span if span > 0 else float("inf"),
             "max_concurrent": max_active, "statuses": sorted({r.status for r in done}),
+            "p50_admission_wait_s": float(np.percentile(wait, 50)), "p50_setup_s": float(np.percentile(setup, 50)),
+            "total_setup_s": float(setup.sum()), "p50_solve_s": float(np.percentile(solve, 50)),
             "dofs_min": int(min(r.n_dofs for r in done)) if done else 0,
             "dofs_max": int(max(r.n_dofs for r in done)) if done else 0,
             "degrees": sorted({r.degree for r in done}),

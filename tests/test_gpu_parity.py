@@ -102,6 +102,10 @@ def test_both_batch_sizes_and_autotuned_choice(mfx, k):
         e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
         assert e2 < 1e-12 and einf < 1e-12, (cb, e2, einf)
         assert rel_err(run_vmult(op, x, torch.float32), ref)[0] < 1e-5
+        d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+        op.diagonal(d)
+        dref = fem.diagonal(K)
+        assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max(), cb
 
 
 def test_quadrature_points_and_rhs(mfx):
@@ -142,6 +146,23 @@ def test_octree_vmult_with_hanging_nodes(mfx, k):
     xs = torch.tensor(x, device=DEV)
     op.distribute(xs)
     assert np.abs(xs.cpu().numpy() - fem.distribute(om, x)).max() < 1e-14
+
+
+@pytest.mark.parametrize("k", [5, 8])
+def test_octree_diagonal_high_degree(mfx, k):
+    """Diagonal on an octree at high degree: cells without hanging nodes take the sum-factorised
+    path (per-cell metric layout), cells with hanging nodes the pairwise one."""
+    leaves = synthetic.octree_leaves(2, 1, np.array([0.3, 0.3, 0.3]), 0.2)
+    verts = synthetic.deformed_vertices(2, 2, 2)
+    m = mfx.Mesh.octree(2, 2, 2, leaves, verts)
+    op = mfx.Operator(m, k, mfx.COEF_TRIG, (1.0, 0.5))
+    om = omesh.octree_mesh(2, 2, 2, k, leaves, verts)
+    assert op.info()["n_hanging"] > 0
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = fem.diagonal(K)
+    assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
 
 
 def test_single_cell_degenerate_meshes(mfx):
