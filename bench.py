@@ -27,6 +27,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX, K_DEG = 64, 4
+# More hardware work queues than the default 8, so that the many streams of the batch engine and the
+# serving loop (one per problem, plus the set-up threads' streams) do not falsely serialise behind each
+# other.  Read when the CUDA context is created, so it is set before torch touches the GPU.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "matrix-free vmult GDoF/s (FP64 vs FP32 mixed) and % HBM peak; solve p50/p99 latency"
 WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2pi y)z, Dirichlet"
 

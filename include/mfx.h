@@ -141,7 +141,24 @@ typedef struct {
  */
 mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc,
                                mfx_stream stream);
+/* Frees the operator after waiting for all work on the device (safe whatever is still queued). */
 void mfx_operator_destroy(mfx_op* op);
+/*
+ * Frees the operator without waiting for the device: its memory (and its solver workspace) is
+ * released in stream order on `stream`.  The caller guarantees that every piece of work that uses
+ * the operator is complete or ordered before `stream`'s current position (for example: a batch slot
+ * that mfx_batch_poll reported done).  No counterpart in the paper: it exists so that a serving
+ * loop can drop finished problems without a device-wide synchronisation.
+ * Errors: MFX_EINVAL (null operator).  The handle is invalid afterwards.
+ */
+mfx_status mfx_operator_release(mfx_op* op, mfx_stream stream);
+/*
+ * Allocates the operator's solver workspace now (nine vectors per stored precision, stream-ordered
+ * device memory) instead of at the first mfx_solve / mfx_batch_add, so that a set-up thread can pay
+ * for it.  No counterpart in the paper.  Synchronises the workspace's own stream.
+ * Errors: MFX_EINVAL (null operator, no FP64 data), MFX_ENOMEM, MFX_ECUDA.
+ */
+mfx_status mfx_solver_prepare(mfx_op* op);
 
 typedef struct {
   int64_t n_dofs, n_cells, n_constrained, n_masters, n_hanging;
@@ -290,7 +307,9 @@ mfx_status mfx_solve(const mfx_op* op, const double* b, double* x, const mfx_sol
 typedef struct mfx_batch mfx_batch;
 mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk);
 void mfx_batch_destroy(mfx_batch* batch);
-/* Add a solve of K x = b (b, x device FP64, caller-owned until released); returns its slot. */
+/* Add a solve of K x = b (b, x device FP64, caller-owned until released); returns its slot.
+ * Queues ||b||^2 and x = 0 on the slot's stream and captures its iteration graph; it does not wait
+ * for the GPU (the solver workspace is allocated here unless mfx_solver_prepare made it). */
 mfx_status mfx_batch_add(mfx_batch* batch, const mfx_op* op, const double* b, double* x,
                          const mfx_solve_params* params, int32_t* slot);
 /* One scheduler tick (synchronising); n_active = slots still running. */

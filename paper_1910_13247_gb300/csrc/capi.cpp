@@ -52,7 +52,8 @@ mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* 
   }
 }
 
-void free_workspace(mfx_op* op);
+void free_workspace(mfx_op* op, cudaStream_t s);
+mfx_status prepare_workspace(mfx_op* op);
 
 mfx_status prepare_vmult(const mfx_op* op) {
   switch (op->n) {
@@ -142,10 +143,10 @@ static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kin
   }
   float* x = nullptr;
   float* y = nullptr;
-  MFX_CUDA_TRY(cudaMalloc(&x, sizeof(float) * op->n_dofs));
-  cudaError_t e = cudaMalloc(&y, sizeof(float) * op->n_dofs);
+  MFX_CUDA_TRY(cudaMallocAsync(&x, sizeof(float) * op->n_dofs, s));
+  cudaError_t e = cudaMallocAsync(&y, sizeof(float) * op->n_dofs, s);
   if (e != cudaSuccess) {
-    cudaFree(x);
+    cudaFreeAsync(x, s);
     return cuda_error(e, "autotune vectors");
   }
   cudaMemsetAsync(x, 0, sizeof(float) * op->n_dofs, s);
@@ -160,9 +161,9 @@ static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kin
       best = cand[i];
     }
   }
+  cudaFreeAsync(x, s);
+  cudaFreeAsync(y, s);
   cudaStreamSynchronize(s);
-  cudaFree(x);
-  cudaFree(y);
   if (st != MFX_OK) return st;
   op->metric_cb = best;
   op->nchunk = (op->nx + best - 1) / best;
@@ -185,11 +186,14 @@ int brick_cells_for_degree(int k) {
   }
 }
 
+// Operator data is allocated in stream order on the creation stream (the operator is complete, and
+// usable from any stream, once mfx_operator_create returns) and freed in stream order: making or
+// dropping an operator never waits for the rest of the device.
 template <typename T>
-static mfx_status dev_alloc(mfx_op* op, T** p, size_t count) {
+static mfx_status dev_alloc(mfx_op* op, T** p, size_t count, cudaStream_t s) {
   *p = nullptr;
   if (count == 0) return MFX_OK;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), s);
   if (e != cudaSuccess) {
     *p = nullptr;
     return set_error(MFX_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
@@ -198,15 +202,36 @@ static mfx_status dev_alloc(mfx_op* op, T** p, size_t count) {
   return MFX_OK;
 }
 
-static void destroy_op(mfx_op* op) {
+// The device's default memory pool keeps up to 16 GiB of freed operator memory for reuse instead of
+// returning it at every synchronisation (the default threshold is 0), once per device and process.
+static void keep_pool_memory() {
+  static std::mutex lock;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> g(lock);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t threshold = (uint64_t)16 << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  done.push_back(dev);
+}
+
+// Frees everything in stream order on `s`; sync = wait for the whole device first (the contract of
+// mfx_operator_destroy) and for the frees after.
+static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sync = true) {
   if (!op) return;
-  free_workspace(op);
+  if (sync) cudaDeviceSynchronize();
+  free_workspace(op, s);
   void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
                   op->d_err};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
+  if (sync) cudaStreamSynchronize(s);
   delete op;
 }
 
@@ -298,6 +323,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (desc->coef_kind == MFX_COEF_QPOINT && !desc->coef_qpoint)
     return set_error(MFX_EINVAL, "MFX_COEF_QPOINT needs coef_qpoint");
   cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_memory();
   mfx_op* op = new (std::nothrow) mfx_op();
   if (!op) return set_error(MFX_ENOMEM, "host allocation failed");
   op->k = k;
@@ -323,9 +349,9 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     }
     op->n_constrained = op->n_dofs - std::max<int64_t>(0, Mx - 2) * std::max<int64_t>(0, My - 2) *
                                          std::max<int64_t>(0, Mz - 2);
-    MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size()));
-    MFX_CUDA_OP(cudaMemcpy(op->d_vertices, m.vertices.data(), m.vertices.size() * sizeof(double),
-                           cudaMemcpyHostToDevice));
+    MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size(), s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, m.vertices.data(), m.vertices.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, s));
   } else {
     MFX_TRY(octree_tables(m, k, &op->tables));
     const OctreeTables& t = op->tables;
@@ -346,30 +372,56 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       enc[i] = r < 0 ? d : -(r + 1);
       if (r >= 0 && t.cptr[r + 1] > t.cptr[r]) cell_hang[i / n3] = 1;
     }
+    // diagonal on cells with hanging nodes: one job per (cell, master of a hanging node of the cell);
+    // the cell's other free nodes keep their own A_ii (flag `simple`)
+    if (std::find(cell_hang.begin(), cell_hang.end(), 1) != cell_hang.end()) {
+      op->hang_simple.assign(enc.size(), 1);
+      std::vector<int32_t> ms;
+      for (int64_t c = 0; c < t.n_cells; ++c) {
+        if (!cell_hang[c]) continue;
+        ms.clear();
+        for (int i = 0; i < n3; ++i) {
+          const int32_t e = enc[c * n3 + i];
+          if (e >= 0) continue;
+          const int32_t r = -e - 1;
+          for (int64_t p = t.cptr[r]; p < t.cptr[r + 1]; ++p) ms.push_back(t.cmaster[p]);
+        }
+        std::sort(ms.begin(), ms.end());
+        ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+        for (int32_t m : ms) {
+          op->hang_job_cell.push_back((int32_t)c);
+          op->hang_job_master.push_back(m);
+        }
+        for (int i = 0; i < n3; ++i) {
+          const int32_t e = enc[c * n3 + i];
+          if (e < 0 || std::binary_search(ms.begin(), ms.end(), e)) op->hang_simple[c * n3 + i] = 0;
+        }
+      }
+    }
     std::vector<uint8_t> mask(t.n_dofs, 0);
     for (int32_t c : t.constrained) mask[c] = 1;
     std::vector<float> w32(t.cweight.begin(), t.cweight.end());
-    MFX_TRY(dev_alloc(op, &op->d_vertices, t.cell_vertices.size()));
-    MFX_TRY(dev_alloc(op, &op->d_cell_dofs, enc.size()));
-    MFX_TRY(dev_alloc(op, &op->d_cmask, mask.size()));
-    MFX_TRY(dev_alloc(op, &op->d_constrained, t.constrained.size()));
-    MFX_TRY(dev_alloc(op, &op->d_cptr, t.cptr.size()));
-    MFX_TRY(dev_alloc(op, &op->d_cmaster, std::max<size_t>(1, t.cmaster.size())));
-    MFX_TRY(dev_alloc(op, &op->d_cweight64, std::max<size_t>(1, t.cweight.size())));
-    MFX_TRY(dev_alloc(op, &op->d_cweight32, std::max<size_t>(1, w32.size())));
-    MFX_TRY(dev_alloc(op, &op->d_cell_hanging, cell_hang.size()));
-    MFX_CUDA_OP(cudaMemcpy(op->d_vertices, t.cell_vertices.data(), t.cell_vertices.size() * 8, cudaMemcpyHostToDevice));
-    MFX_CUDA_OP(cudaMemcpy(op->d_cell_dofs, enc.data(), enc.size() * 4, cudaMemcpyHostToDevice));
-    MFX_CUDA_OP(cudaMemcpy(op->d_cmask, mask.data(), mask.size(), cudaMemcpyHostToDevice));
+    MFX_TRY(dev_alloc(op, &op->d_vertices, t.cell_vertices.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_cell_dofs, enc.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_cmask, mask.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_constrained, t.constrained.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_cptr, t.cptr.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_cmaster, std::max<size_t>(1, t.cmaster.size()), s));
+    MFX_TRY(dev_alloc(op, &op->d_cweight64, std::max<size_t>(1, t.cweight.size()), s));
+    MFX_TRY(dev_alloc(op, &op->d_cweight32, std::max<size_t>(1, w32.size()), s));
+    MFX_TRY(dev_alloc(op, &op->d_cell_hanging, cell_hang.size(), s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, t.cell_vertices.data(), t.cell_vertices.size() * 8, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_cell_dofs, enc.data(), enc.size() * 4, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_cmask, mask.data(), mask.size(), cudaMemcpyHostToDevice, s));
     if (!t.constrained.empty())
-      MFX_CUDA_OP(cudaMemcpy(op->d_constrained, t.constrained.data(), t.constrained.size() * 4, cudaMemcpyHostToDevice));
-    MFX_CUDA_OP(cudaMemcpy(op->d_cptr, t.cptr.data(), t.cptr.size() * 8, cudaMemcpyHostToDevice));
+      MFX_CUDA_OP(cudaMemcpyAsync(op->d_constrained, t.constrained.data(), t.constrained.size() * 4, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_cptr, t.cptr.data(), t.cptr.size() * 8, cudaMemcpyHostToDevice, s));
     if (!t.cmaster.empty()) {
-      MFX_CUDA_OP(cudaMemcpy(op->d_cmaster, t.cmaster.data(), t.cmaster.size() * 4, cudaMemcpyHostToDevice));
-      MFX_CUDA_OP(cudaMemcpy(op->d_cweight64, t.cweight.data(), t.cweight.size() * 8, cudaMemcpyHostToDevice));
-      MFX_CUDA_OP(cudaMemcpy(op->d_cweight32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice));
+      MFX_CUDA_OP(cudaMemcpyAsync(op->d_cmaster, t.cmaster.data(), t.cmaster.size() * 4, cudaMemcpyHostToDevice, s));
+      MFX_CUDA_OP(cudaMemcpyAsync(op->d_cweight64, t.cweight.data(), t.cweight.size() * 8, cudaMemcpyHostToDevice, s));
+      MFX_CUDA_OP(cudaMemcpyAsync(op->d_cweight32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice, s));
     }
-    MFX_CUDA_OP(cudaMemcpy(op->d_cell_hanging, cell_hang.data(), cell_hang.size(), cudaMemcpyHostToDevice));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_cell_hanging, cell_hang.data(), cell_hang.size(), cudaMemcpyHostToDevice, s));
   }
   const size_t nq = (size_t)op->n_cells * n3;
   size_t metric_entries = 6 * nq;
@@ -387,22 +439,25 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     op->nchunk = (op->nx + cand[0] - 1) / cand[0];
   }
   // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
-  MFX_TRY(dev_alloc(op, &op->d_metric64, metric_entries));
-  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, metric_entries));
-  MFX_TRY(dev_alloc(op, &op->d_jxw, nq));
-  MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs)));
-  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs)));
-  MFX_TRY(dev_alloc(op, &op->d_scalars, 64));
-  MFX_TRY(dev_alloc(op, &op->d_partials, 4096));
-  MFX_TRY(dev_alloc(op, &op->d_counter, 16));
+  MFX_TRY(dev_alloc(op, &op->d_metric64, metric_entries, s));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, metric_entries, s));
+  MFX_TRY(dev_alloc(op, &op->d_jxw, nq, s));
+  MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs), s));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs), s));
+  MFX_TRY(dev_alloc(op, &op->d_scalars, 64, s));
+  MFX_TRY(dev_alloc(op, &op->d_partials, 4096, s));
+  MFX_TRY(dev_alloc(op, &op->d_counter, 16, s));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_counter, 0, 16 * sizeof(unsigned int), s));
-  MFX_TRY(dev_alloc(op, &op->d_err, 4));
+  MFX_TRY(dev_alloc(op, &op->d_err, 4, s));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_err, 0, 4 * sizeof(int), s));
   MFX_TRY(prepare_vmult(op));
   if (op->structured)
     MFX_TRY(choose_cells_per_batch(op, desc->cells_per_block, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
   MFX_TRY(launch_diagonal(op, s));
+  std::vector<int32_t>().swap(op->hang_job_cell);  // staged by the copies above: host copies no longer needed
+  std::vector<int32_t>().swap(op->hang_job_master);
+  std::vector<uint8_t>().swap(op->hang_simple);
   // the structured FP64 vmult works in double-float arithmetic on a pre-split metric
   if (op->structured) MFX_TRY(launch_metric_to_pairs(op, (int64_t)metric_entries, s));
   MFX_CUDA_OP(cudaStreamSynchronize(s));
@@ -411,6 +466,18 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
 }
 
 void mfx_operator_destroy(mfx_op* op) { destroy_op(op); }
+
+mfx_status mfx_operator_release(mfx_op* op, mfx_stream stream) {
+  if (!op) return set_error(MFX_EINVAL, "null operator");
+  destroy_op(op, (cudaStream_t)stream, false);
+  return MFX_OK;
+}
+
+mfx_status mfx_solver_prepare(mfx_op* op) {
+  if (!op) return set_error(MFX_EINVAL, "null operator");
+  if (!op->has_f64) return set_error(MFX_EINVAL, "solves need FP64 data");
+  return prepare_workspace(op);
+}
 
 mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   if (!op || !info) return set_error(MFX_EINVAL, "null argument");

@@ -206,40 +206,19 @@ __global__ void rhs_kernel(const __grid_constant__ GeoArgs g, DofView v, const d
   }
 }
 
-// Element entry A_ij = sum_q grad_ref phi_i^T G_q grad_ref phi_j from the stored FP64 metric.
-__device__ double element_entry(const GeoArgs& g, const double* __restrict__ m64, int64_t cell, int i, int j) {
-  const int n = g.n, n3 = n * n * n;
-  const int a1 = i % n, a2 = (i / n) % n, a3 = i / (n * n);
-  const int b1 = j % n, b2 = (j / n) % n, b3 = j / (n * n);
-  const int64_t st = metric_stride(g);
-  double s = 0.0;
-  for (int q = 0; q < n3; ++q) {
-    const double* G = m64 + metric_offset(g, cell, q);
-    const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
-    const double Pi[3] = {g.Sd[q1 * n + a1] * g.S[q2 * n + a2] * g.S[q3 * n + a3],
-                          g.S[q1 * n + a1] * g.Sd[q2 * n + a2] * g.S[q3 * n + a3],
-                          g.S[q1 * n + a1] * g.S[q2 * n + a2] * g.Sd[q3 * n + a3]};
-    const double Pj[3] = {g.Sd[q1 * n + b1] * g.S[q2 * n + b2] * g.S[q3 * n + b3],
-                          g.S[q1 * n + b1] * g.Sd[q2 * n + b2] * g.S[q3 * n + b3],
-                          g.S[q1 * n + b1] * g.S[q2 * n + b2] * g.Sd[q3 * n + b3]};
-    const double G00 = G[0], G01 = G[st], G02 = G[2 * st];
-    const double G11 = G[3 * st], G12 = G[4 * st], G22 = G[5 * st];
-    s += Pi[0] * (G00 * Pj[0] + G01 * Pj[1] + G02 * Pj[2]) + Pi[1] * (G01 * Pj[0] + G11 * Pj[1] + G12 * Pj[2]) +
-         Pi[2] * (G02 * Pj[0] + G12 * Pj[1] + G22 * Pj[2]);
-  }
-  return s;
-}
-
-// Diagonal of the element matrix of a cell without hanging nodes, by sum factorisation.  With the 1D
+// Diagonal of the element matrices by sum factorisation.  With the 1D
 // products M0[q][i] = l_i(x_q)^2, M1[q][i] = l_i(x_q) l_i'(x_q), M2[q][i] = l_i'(x_q)^2, the entry
 // A_ii of node i = (i1, i2, i3) is the sum over the six metric components G_de of
 //   c_de sum_q G_de(q) M_{a1}[q1][i1] M_{a2}[q2][i2] M_{a3}[q3][i3],
 // a_t = [t == d] + [t == e], c_de = 1 for d = e and 2 otherwise (G symmetric): three 1D contractions
 // (over q3, q2, q1) per component instead of n^3 quadrature sums per node.  N^2 threads per cell,
-// one per 1D line; CPB cells per CTA.
+// one per 1D line; CPB cells per CTA.  On a cell with hanging nodes only the nodes flagged in
+// `simple` (free DoFs that no hanging node of the cell depends on) are added here; the other shares
+// come from diagonal_hanging_kernel.
 template <int N>
 __global__ void diagonal_sf_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ m64,
-                                   const uint8_t* __restrict__ cell_hanging, double* __restrict__ diag, int cpb) {
+                                   const uint8_t* __restrict__ cell_hanging, const uint8_t* __restrict__ simple,
+                                   double* __restrict__ diag, int cpb) {
   constexpr int N2 = N * N, N3 = N2 * N;
   extern __shared__ double sh[];
   double* M = sh;  // 3 x N^2
@@ -254,7 +233,8 @@ __global__ void diagonal_sf_kernel(const __grid_constant__ GeoArgs g, DofView v,
     M[2 * N2 + t] = s1 * s1;
   }
   const int64_t cell = (int64_t)blockIdx.x * cpb + lc;
-  const bool ok = lc < cpb && cell < g.n_cells && !(cell_hanging && cell_hanging[cell]);
+  const bool ok = lc < cpb && cell < g.n_cells;
+  const bool hang = ok && cell_hanging && cell_hanging[cell];
   const int64_t base = ok ? metric_offset(g, cell, 0) : 0;
   const int64_t st = metric_stride(g);
   const int ra = r % N, rb = r / N;
@@ -312,39 +292,90 @@ __global__ void diagonal_sf_kernel(const __grid_constant__ GeoArgs g, DofView v,
   }
   if (ok) {
 #pragma unroll
-    for (int i1 = 0; i1 < N; ++i1)
+    for (int i1 = 0; i1 < N; ++i1) {
+      if (hang && !simple[cell * N3 + i1 + N * ra + N2 * rb]) continue;
       expand_node(v, cell, i1, ra, rb, [&](int64_t dof, double w) { atomicAdd(diag + dof, w * w * z[i1]); });
+    }
   }
 }
 
-// diag(C^T A C) on free DoFs, cells with hanging nodes: sum over local pairs (i, j) sharing a
-// master m of w_im w_jm A_ij (the element entries by full quadrature).
-__global__ void diagonal_kernel(const __grid_constant__ GeoArgs g, DofView v, const double* __restrict__ m64,
-                                const uint8_t* __restrict__ cell_hanging, double* __restrict__ diag) {
-  const int n = g.n, n3 = n * n * n;
-  const int64_t total = g.n_cells * n3;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = idx / n3;
-    const int i = (int)(idx - cell * n3);
-    const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
-    if (!cell_hanging[cell]) continue;  // cells without hanging nodes: diagonal_sf_kernel
-    for (int j = 0; j < n3; ++j) {
-      const int j1 = j % n, j2 = (j / n) % n, j3 = j / (n * n);
-      double aij = 0.0;
-      bool have = false;
-      expand_node(v, cell, i1, i2, i3, [&](int64_t mi, double wi) {
-        expand_node(v, cell, j1, j2, j3, [&](int64_t mj, double wj) {
-          if (mi == mj) {
-            if (!have) {
-              aij = element_entry(g, m64, cell, i, j);
-              have = true;
-            }
-            atomicAdd(diag + mi, wi * wj * aij);
-          }
-        });
-      });
+// One 1D sweep of an n^3 array along direction dir (0: x = i1, 1: y = i2, 2: z = i3) with the
+// matrix M[q][i]; thread t owns the line whose other two indices are (t mod N, t / N).
+template <int N>
+__device__ __forceinline__ void sweep3(const double* in, double* out, const double* M, int dir, int t) {
+  constexpr int N2 = N * N;
+  const int a = t % N, b = t / N;
+  const int base = dir == 0 ? N * a + N2 * b : (dir == 1 ? a + N2 * b : a + N * b);
+  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N2);
+  double x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = in[base + i * stride];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc += M[q * N + i] * x[i];
+    out[base + q * stride] = acc;
+  }
+}
+
+// Share of master m in diag(C^T A C) from one cell with hanging nodes: with v the m-th column of the
+// cell's constraint matrix (v_i = 1 where node i is the free DoF m, the weight of m where node i is
+// hanging, else 0), the share is v^T A_cell v = sum_q grad v(q)^T G_q grad v(q).  The reference
+// gradient at the Gauss points takes eight sum-factorisation sweeps in three phases:
+//   S_z v, D_z v  ->  S_y S_z v, D_y S_z v, S_y D_z v  ->  D_x S_y S_z v, S_x D_y S_z v, S_x S_y D_z v.
+// One CTA of N^2 threads (one per 1D line) per (cell, master) job.
+template <int N>
+__global__ void diagonal_hanging_kernel(const __grid_constant__ GeoArgs g, DofView dv, const double* __restrict__ m64,
+                                        const int32_t* __restrict__ job_cell, const int32_t* __restrict__ job_master,
+                                        double* __restrict__ diag) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  __shared__ double S[N2], Sd[N2], red[N2];
+  __shared__ double v[N3], A[N3], B[N3], C[N3], D[N3], E[N3];
+  const int t = threadIdx.x;
+  const int64_t cell = job_cell[blockIdx.x];
+  const int32_t m = job_master[blockIdx.x];
+  S[t] = g.S[t];
+  Sd[t] = g.Sd[t];
+  for (int i = t; i < N3; i += N2) {
+    const int32_t e = dv.cell_dofs[cell * N3 + i];
+    double w = 0.0;
+    if (e >= 0) {
+      w = e == m ? 1.0 : 0.0;
+    } else {
+      const int32_t row = -e - 1;
+      for (int64_t p = dv.cptr[row]; p < dv.cptr[row + 1]; ++p)
+        if (dv.cmaster[p] == m) w += dv.cweight[p];
     }
+    v[i] = w;
+  }
+  __syncthreads();
+  sweep3<N>(v, A, S, 2, t);   // A = S_z v
+  sweep3<N>(v, B, Sd, 2, t);  // B = D_z v
+  __syncthreads();
+  sweep3<N>(A, C, S, 1, t);   // C = S_y S_z v
+  sweep3<N>(A, D, Sd, 1, t);  // D = D_y S_z v
+  sweep3<N>(B, E, S, 1, t);   // E = S_y D_z v
+  __syncthreads();
+  sweep3<N>(C, v, Sd, 0, t);  // grad_x -> v
+  sweep3<N>(D, A, S, 0, t);   // grad_y -> A
+  sweep3<N>(E, B, S, 0, t);   // grad_z -> B
+  __syncthreads();
+  const int64_t base = metric_offset(g, cell, 0), st = metric_stride(g);
+  const int64_t qs = g.cb == 0 ? 1 : g.cb;
+  double acc = 0.0;
+  for (int q = t; q < N3; q += N2) {
+    const double* G = m64 + base + q * qs;
+    const double u1 = v[q], u2 = A[q], u3 = B[q];
+    acc += u1 * (G[0] * u1 + 2.0 * (G[st] * u2 + G[2 * st] * u3)) + u2 * (G[3 * st] * u2 + 2.0 * G[4 * st] * u3) +
+           u3 * G[5 * st] * u3;
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < N2; ++w) s += red[w];
+    atomicAdd(diag + m, s);
   }
 }
 
@@ -465,26 +496,29 @@ mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_
 }
 
 template <int N>
-static void run_diagonal_sf(const GeoArgs& g, const DofView& v, const double* m64, const uint8_t* hang, double* d,
-                            cudaStream_t s) {
+static void run_diagonal_sf(const GeoArgs& g, const DofView& v, const double* m64, const uint8_t* hang,
+                            const uint8_t* simple, const int32_t* job_cell, const int32_t* job_master, int64_t n_jobs,
+                            double* d, cudaStream_t s) {
   constexpr int cpb = N * N >= 64 ? 1 : 128 / (N * N);  // cells per CTA
   const int64_t blocks = (g.n_cells + cpb - 1) / cpb;
   if (blocks == 0) return;
   const size_t smem = sizeof(double) * (3 * N * N + 2 * cpb * N * N * N);
-  diagonal_sf_kernel<N><<<(unsigned)blocks, cpb * N * N, smem, s>>>(g, v, m64, hang, d, cpb);
+  diagonal_sf_kernel<N><<<(unsigned)blocks, cpb * N * N, smem, s>>>(g, v, m64, hang, simple, d, cpb);
+  if (n_jobs > 0) diagonal_hanging_kernel<N><<<(unsigned)n_jobs, N * N, 0, s>>>(g, v, m64, job_cell, job_master, d);
 }
 
 static void launch_diagonal_sf(int n, const GeoArgs& g, const DofView& v, const double* m64, const uint8_t* hang,
-                               double* d, cudaStream_t s) {
+                               const uint8_t* simple, const int32_t* jc, const int32_t* jm, int64_t nj, double* d,
+                               cudaStream_t s) {
   switch (n) {
-    case 2: run_diagonal_sf<2>(g, v, m64, hang, d, s); break;
-    case 3: run_diagonal_sf<3>(g, v, m64, hang, d, s); break;
-    case 4: run_diagonal_sf<4>(g, v, m64, hang, d, s); break;
-    case 5: run_diagonal_sf<5>(g, v, m64, hang, d, s); break;
-    case 6: run_diagonal_sf<6>(g, v, m64, hang, d, s); break;
-    case 7: run_diagonal_sf<7>(g, v, m64, hang, d, s); break;
-    case 8: run_diagonal_sf<8>(g, v, m64, hang, d, s); break;
-    case 9: run_diagonal_sf<9>(g, v, m64, hang, d, s); break;
+    case 2: run_diagonal_sf<2>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 3: run_diagonal_sf<3>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 4: run_diagonal_sf<4>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 5: run_diagonal_sf<5>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 6: run_diagonal_sf<6>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 7: run_diagonal_sf<7>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 8: run_diagonal_sf<8>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
+    case 9: run_diagonal_sf<9>(g, v, m64, hang, simple, jc, jm, nj, d, s); break;
     default: break;
   }
 }
@@ -492,19 +526,32 @@ static void launch_diagonal_sf(int n, const GeoArgs& g, const DofView& v, const 
 mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
   GeoArgs g = geo_args(op);
   double* tmp = nullptr;
+  uint8_t* simple = nullptr;
+  int32_t* jobs = nullptr;
+  const int64_t nj = (int64_t)op->hang_job_cell.size();
   MFX_CUDA_TRY(cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(1, op->n_dofs), s));
   cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(double) * op->n_dofs, s);
+  if (e == cudaSuccess && op->d_cell_hanging && !op->hang_simple.empty()) {
+    e = cudaMallocAsync((void**)&simple, op->hang_simple.size(), s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(simple, op->hang_simple.data(), op->hang_simple.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nj > 0) e = cudaMallocAsync((void**)&jobs, sizeof(int32_t) * 2 * nj, s);
+    if (e == cudaSuccess && nj > 0)
+      e = cudaMemcpyAsync(jobs, op->hang_job_cell.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nj > 0)
+      e = cudaMemcpyAsync(jobs + nj, op->hang_job_master.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) {
-    const int64_t work = op->n_cells * op->n * op->n * op->n;
-    if (op->d_cell_hanging)
-      diagonal_kernel<<<grid_for(work), 256, 0, s>>>(g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp);
-    launch_diagonal_sf(op->n, g, dof_view(op), op->d_metric64, op->d_cell_hanging, tmp, s);
+    launch_diagonal_sf(op->n, g, dof_view(op), op->d_metric64, simple ? op->d_cell_hanging : nullptr, simple, jobs,
+                       jobs ? jobs + nj : nullptr, jobs ? nj : 0, tmp, s);
     diag_finish_kernel<double><<<grid_for(op->n_dofs), 256, 0, s>>>(
         op->n_dofs, op->structured, op->k * op->nx + 1, op->k * op->ny + 1, op->k * op->nz + 1, op->d_cmask, tmp,
         op->d_diag64, op->d_diag32);
     e = cudaGetLastError();
   }
   cudaFreeAsync(tmp, s);
+  if (simple) cudaFreeAsync(simple, s);
+  if (jobs) cudaFreeAsync(jobs, s);
   if (e != cudaSuccess) return cuda_error(e, "diagonal");
   return MFX_OK;
 }

@@ -101,6 +101,10 @@ struct mfx_op {
   double* d_cweight64 = nullptr;
   float* d_cweight32 = nullptr;
   uint8_t* d_cell_hanging = nullptr; // octree: 1 if a cell touches a hanging node
+  // diagonal set-up on cells with hanging nodes (host; cleared once the diagonal is built):
+  // one quadratic form v^T A_cell v per (cell, master) pair, v = the master's column of C on the cell
+  std::vector<int32_t> hang_job_cell, hang_job_master;
+  std::vector<uint8_t> hang_simple;  // n_cells x n^3: 1 if the node's A_ii is its DoF's whole share
   double* d_diag64 = nullptr;
   float* d_diag32 = nullptr;
   // solver workspace (allocated at create)

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "mfx_internal.h"
@@ -325,6 +326,33 @@ struct SolveWorkspace {
 
 static SolveWorkspace* workspace(mfx_op* op) { return reinterpret_cast<SolveWorkspace*>(op->d_work); }
 
+// Pinned host blocks for the solver status words, cut from slabs that live as long as the process:
+// taking and returning a block needs no CUDA call (cudaFreeHost would synchronise the device).
+static constexpr size_t kPinBlock = (sizeof(SolveState) + 255) / 256 * 256;
+static std::mutex g_pin_lock;
+static std::vector<void*> g_pin_free;
+
+static SolveState* pinned_status_get() {
+  std::lock_guard<std::mutex> g(g_pin_lock);
+  if (g_pin_free.empty()) {
+    constexpr int kPerSlab = 32;
+    void* slab = nullptr;
+    if (cudaMallocHost(&slab, kPinBlock * kPerSlab) != cudaSuccess) return nullptr;
+    for (int i = kPerSlab - 1; i >= 0; --i) g_pin_free.push_back((char*)slab + i * kPinBlock);
+  }
+  void* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return (SolveState*)p;
+}
+
+static void pinned_status_put(SolveState* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pin_lock);
+  g_pin_free.push_back(p);
+}
+
+// Solver workspace: one stream-ordered device allocation (no device-wide synchronisation when it
+// is made or freed), a pinned status block and a stream of its own.
 static mfx_status ensure_workspace(mfx_op* op) {
   if (op->d_work) return MFX_OK;
   auto* ws = new SolveWorkspace();
@@ -334,14 +362,23 @@ static mfx_status ensure_workspace(mfx_op* op) {
   size_t total = al(sizeof(SolveState)) + al(64 * sizeof(double));
   if (op->has_f64) total += 9 * al(n64);
   if (op->has_f32) total += 9 * al(n32) + 2 * al(n64);
-  cudaError_t e = cudaMalloc(&ws->base, total);
+  cudaError_t e = cudaStreamCreateWithFlags(&ws->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    delete ws;
+    return cuda_error(e, "solver stream");
+  }
+  cudaStream_t s = ws->stream;
+  e = cudaMallocAsync(&ws->base, total, s);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
     delete ws;
     return set_error(MFX_ENOMEM, "solver workspace allocation failed");
   }
-  e = cudaMallocHost((void**)&ws->h_st, sizeof(SolveState));
-  if (e != cudaSuccess) {
-    cudaFree(ws->base);
+  ws->h_st = pinned_status_get();
+  if (!ws->h_st) {
+    cudaFreeAsync(ws->base, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
     delete ws;
     return set_error(MFX_ENOMEM, "pinned status allocation failed");
   }
@@ -373,8 +410,6 @@ static mfx_status ensure_workspace(mfx_op* op) {
   ws->bytes = total;
   op->d_work = ws;
   op->work_bytes = total;
-  MFX_CUDA_TRY(cudaStreamCreateWithFlags(&ws->stream, cudaStreamNonBlocking));
-  cudaStream_t s = ws->stream;
   // inverse diagonals
   if (op->has_f64) reciprocal_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, op->d_diag64, ws->w64.dinv);
   if (op->has_f32) reciprocal_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, op->d_diag32, ws->w32.dinv);
@@ -393,16 +428,19 @@ static mfx_status ensure_workspace(mfx_op* op) {
   return MFX_OK;
 }
 
-void free_workspace(mfx_op* op) {
+// Frees the workspace in stream order on `s` (0: its own stream, after its pending work).
+void free_workspace(mfx_op* op, cudaStream_t s) {
   auto* ws = workspace(op);
   if (!ws) return;
-  if (ws->stream) cudaStreamSynchronize(ws->stream);
-  cudaFree(ws->base);
-  cudaFreeHost(ws->h_st);
-  if (ws->stream) cudaStreamDestroy(ws->stream);
+  cudaFreeAsync(ws->base, s ? s : ws->stream);
+  pinned_status_put(ws->h_st);
+  cudaStreamDestroy(ws->stream);  // returns at once; resources go when its work is done
   delete ws;
   op->d_work = nullptr;
+  op->work_bytes = 0;
 }
+
+mfx_status prepare_workspace(mfx_op* op) { return ensure_workspace(op); }
 
 template <typename Real>
 static Work<Real>& work_of(SolveWorkspace* ws);
@@ -737,6 +775,7 @@ struct BatchSlot {
   cudaEvent_t event = nullptr;     // completion of the slot's last launched work
   bool busy = false;               // work in flight (asynchronous stepping)
   bool residual_pending = false;   // OUTER: residual launched, norm not read yet
+  bool bb_pending = true;          // (b, b) copied to h_scal[1] by the slot's stream, not read yet
   double* h_scal = nullptr;     // pinned: (r, r), (b, b)
 };
 
@@ -762,6 +801,33 @@ static void slot_release(BatchSlot& sl) {
   sl.residual_pending = false;
   sl.op = nullptr;
   sl.phase = SLOT_FREE;
+}
+
+// (b, b) of a slot, once the slot's stream has passed the copy queued by mfx_batch_add.
+static void slot_read_bb(BatchSlot& sl) {
+  if (!sl.bb_pending) return;
+  sl.bb = sl.h_scal[1];
+  sl.bb_pending = false;
+}
+
+// Decision after the FP64 residual of an OUTER slot: done, or start the next inner solve.
+static mfx_status slot_outer_decide(BatchSlot& sl, bool* start_inner) {
+  slot_read_bb(sl);
+  sl.rr = sl.h_scal[0];
+  *start_inner = false;
+  if (!std::isfinite(sl.rr) || !std::isfinite(sl.bb)) {
+    sl.phase = SLOT_DONE;
+    sl.status = MFX_BREAKDOWN;
+  } else if (sl.rr <= sl.p.tol * sl.p.tol * sl.bb) {
+    sl.phase = SLOT_DONE;
+    sl.status = MFX_OK;
+  } else if (sl.outer >= sl.p.max_it) {
+    sl.phase = SLOT_DONE;
+    sl.status = MFX_NOT_CONVERGED;
+  } else {
+    *start_inner = true;
+  }
+  return MFX_OK;
 }
 
 // Capture one chunk of inner PCG iterations of the slot's operator.
@@ -947,23 +1013,18 @@ mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, dou
     sl.hi = p.cheb_hi > 0 ? p.cheb_hi : 1.2 * ws->lambda_max[pi];
     sl.lo = p.cheb_hi > 0 ? p.cheb_lo : sl.hi / 20.0;
   }
-  // ||b||^2 and x = 0
+  // ||b||^2 (read by the host at the slot's first decision) and x = 0; nothing here waits for the GPU
   launch_dot(op, MFX_F64, op->n_dofs, b, b, ws->scal + 1, sl.stream);
   MFX_CUDA_TRY(cudaMemcpyAsync(sl.h_scal + 1, ws->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
   MFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * op->n_dofs, sl.stream));
-  MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
-  sl.bb = sl.h_scal[1];
+  sl.bb = 0.0;
+  sl.bb_pending = true;
   rc = mixed ? capture_chunk<float>(sl, bt->chunk) : capture_chunk<double>(sl, bt->chunk);
   if (rc != MFX_OK) {
     slot_release(sl);
     return rc;
   }
-  if (!std::isfinite(sl.bb)) {
-    sl.phase = SLOT_DONE;
-    sl.status = MFX_BREAKDOWN;
-  } else if (sl.bb == 0.0) {
-    sl.phase = SLOT_DONE;
-  } else if (mixed) {
+  if (mixed) {
     sl.phase = SLOT_OUTER;
   } else {
     rc = slot_start_inner(sl);
@@ -992,17 +1053,9 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
       if (sl.phase == SLOT_OUTER) MFX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
   for (auto& sl : bt->slots) {
     if (sl.phase != SLOT_OUTER) continue;
-    sl.rr = sl.h_scal[0];
-    if (!std::isfinite(sl.rr)) {
-      sl.phase = SLOT_DONE;
-      sl.status = MFX_BREAKDOWN;
-    } else if (sl.rr <= sl.p.tol * sl.p.tol * sl.bb) {
-      sl.phase = SLOT_DONE;
-      sl.status = MFX_OK;
-    } else if (sl.outer >= sl.p.max_it) {
-      sl.phase = SLOT_DONE;
-      sl.status = MFX_NOT_CONVERGED;
-    } else {
+    bool start = false;
+    slot_outer_decide(sl, &start);
+    if (start) {
       mfx_status rc = slot_start_inner(sl);
       if (rc != MFX_OK) return rc;
     }
@@ -1024,6 +1077,7 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
       SolveWorkspace* ws = workspace(sl.op);
       const SolveState& h = *ws->h_st;
       if (h.done) {
+        slot_read_bb(sl);
         sl.inner_total += h.it;
         if (h.status == MFX_BREAKDOWN) {
           sl.phase = SLOT_DONE;
@@ -1070,17 +1124,9 @@ mfx_status mfx_batch_advance(mfx_batch* bt, int32_t* n_active) {
         sl.residual_pending = true;
       } else {
         sl.residual_pending = false;
-        sl.rr = sl.h_scal[0];
-        if (!std::isfinite(sl.rr)) {
-          sl.phase = SLOT_DONE;
-          sl.status = MFX_BREAKDOWN;
-        } else if (sl.rr <= sl.p.tol * sl.p.tol * sl.bb) {
-          sl.phase = SLOT_DONE;
-          sl.status = MFX_OK;
-        } else if (sl.outer >= sl.p.max_it) {
-          sl.phase = SLOT_DONE;
-          sl.status = MFX_NOT_CONVERGED;
-        } else {
+        bool start = false;
+        slot_outer_decide(sl, &start);
+        if (start) {
           rc = slot_start_inner(sl);
           if (rc != MFX_OK) return rc;
           MFX_CUDA_TRY(cudaGraphLaunch(sl.exec, sl.stream));
@@ -1092,6 +1138,7 @@ mfx_status mfx_batch_advance(mfx_batch* bt, int32_t* n_active) {
       if (!h.done) {
         MFX_CUDA_TRY(cudaGraphLaunch(sl.exec, sl.stream));
       } else {
+        slot_read_bb(sl);
         sl.inner_total += h.it;
         if (h.status == MFX_BREAKDOWN) {
           sl.phase = SLOT_DONE;

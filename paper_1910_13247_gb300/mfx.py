@@ -79,6 +79,8 @@ def lib():
         "mfx_mesh_tables": (S, [_VP, S, _VP, _VP, _VP, _VP, _VP]),
         "mfx_operator_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), _VP]),
         "mfx_operator_destroy": (None, [_VP]),
+        "mfx_operator_release": (S, [_VP, _VP]),
+        "mfx_solver_prepare": (S, [_VP]),
         "mfx_operator_info": (S, [_VP, ctypes.POINTER(OpInfo)]),
         "mfx_get_tables": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "mfx_vmult": (S, [_VP, S, _VP, _VP, _VP]),
@@ -213,6 +215,19 @@ class Operator:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.mfx_operator_destroy(self.handle)
             self.handle = None
+
+    def release(self, stream=None):
+        """Free the operator in stream order on `stream`, without a device-wide wait; every use of the
+        operator must already be complete or ordered before that stream (mfx_operator_release)."""
+        if getattr(self, "handle", None):
+            h, self.handle = self.handle, None
+            check(lib().mfx_operator_release(h, _stream(stream)))
+
+    def prepare_solver(self):
+        """Allocate the solver workspace now rather than at the first solve (mfx_solver_prepare)."""
+        check(lib().mfx_solver_prepare(self.handle))
+        self._info = self.info()
+        return self
 
     def info(self):
         i = OpInfo()

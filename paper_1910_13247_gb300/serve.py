@@ -88,8 +88,10 @@ class Server:
         with torch.cuda.stream(stream):
             mesh = mfx.Mesh.octree(req.nb, req.nb, req.nb, req.leaves)
             op = mfx.Operator(mesh, req.degree, stream=stream)
-            b = torch.tensor(synthetic.gaussian_vector(op.n_dofs, req.seed), device="cuda")
-            op.distribute(b)  # right-hand side on the free DoFs only
+            op.prepare_solver()  # workspace here, not in the serving thread's batch.add
+            b = torch.from_numpy(synthetic.gaussian_vector(op.n_dofs, req.seed)).pin_memory().to(
+                "cuda", non_blocking=True)
+            op.distribute(b, stream=stream)  # right-hand side on the free DoFs only
             x = torch.zeros_like(b)
         stream.synchronize()
         req.setup_s = time.perf_counter() - t0
@@ -148,6 +150,7 @@ class Server:
                         req.iterations = st["inner_iterations"]
                         req.result = x
                         self.batch.release(slot)
+                        op.release()  # its slot reported done: free in stream order, no device-wide wait
                         used -= nbytes
                         done.append(req)
             time.sleep(0.0002)
