@@ -328,7 +328,6 @@ def main():
 
 def solve_measurements(mfx, synthetic, torch, np):
     """Latency of the 8^3 Q2 Poisson Jacobi-PCG solve (p50/p99 over repeated solves)."""
-    from oracle import fem, mesh as omesh  # noqa: F401  (forcing values only via the library's q-points)
     out = {}
     m = mfx.Mesh.structured_box(8, 8, 8)
     op = mfx.Operator(m, 2, mfx.COEF_CONSTANT, (1.0, 0.0))

@@ -328,6 +328,99 @@ mfx_status mfx_batch_poll(mfx_batch* batch, int32_t slot, int32_t* done, mfx_sol
 /* Free a slot (its operator and vectors can then be reused or destroyed). */
 mfx_status mfx_batch_release(mfx_batch* batch, int32_t slot);
 
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A solve server: a native runtime that admits Poisson solves as they
+ * arrive, builds their operators on set-up threads, runs them together in
+ * one batch with independent stepping (mfx_batch_advance) on a scheduler
+ * thread, and keeps each finished solve's operator and solution on the
+ * device until the caller retires it.  Admission: requests wait in a queue
+ * and are admitted (policy order) while fewer than max_slots are being set
+ * up or solved and the estimated device bytes of all admitted, unretired
+ * requests stay within budget_bytes; one request is always admitted when
+ * nothing else is, so a request larger than the budget still runs, alone.
+ * No counterpart in the paper: this is the serving workload's runtime.
+ * All calls are thread-safe; none of them waits for the GPU except
+ * mfx_server_result_copy and mfx_server_destroy.
+ */
+typedef struct mfx_server mfx_server;
+enum { MFX_ADMIT_FIFO = 0,            /* arrival order                               */
+       MFX_ADMIT_SMALLEST_FIRST = 1 }; /* smallest estimated size first             */
+typedef struct {
+  int64_t budget_bytes;   /* device bytes for admitted requests (estimate, then exact)     */
+  int32_t max_slots;      /* requests in set-up or solving at once (1..4096)                */
+  int32_t chunk;          /* inner iterations per scheduler step of a solve (0: 16)         */
+  int32_t setup_threads;  /* host threads building operators (0: 4)                        */
+  int32_t policy;         /* MFX_ADMIT_*                                                    */
+  int32_t reserved[2];
+} mfx_server_config;
+
+/*
+ * Right-hand side callback, run on a set-up thread once the operator exists:
+ * fill b (host, n_dofs doubles, the operator's DoF numbering).  The server
+ * copies it to the device and applies mfx_distribute (constrained entries).
+ */
+typedef void (*mfx_rhs_fn)(const mfx_op* op, double* b, int64_t n_dofs, void* user);
+
+typedef struct {
+  /* mesh: either an existing mesh (caller-owned, alive until the request is
+     retired) or an octree description (copied at submission; the mesh is
+     built on a set-up thread). */
+  const mfx_mesh* mesh;
+  int32_t nx, ny, nz, reserved0;   /* octree: coarse cells per direction        */
+  const int32_t* leaves;           /* octree: n_leaves x 4 (level, i, j, k)      */
+  int64_t n_leaves;
+  const double* coarse_vertices;   /* octree: NULL = unit cube (copied)          */
+  mfx_op_desc desc;                /* degree, coefficient, precisions (need both for mixed) */
+  mfx_solve_params params;         /* tol, mixed, preconditioner, ...            */
+  mfx_rhs_fn rhs;                  /* NULL: b = 1 on every DoF before distribute */
+  void* user;
+  int64_t est_bytes;               /* 0: estimated from cells and degree         */
+} mfx_request;
+
+enum { MFX_REQ_QUEUED = 0, MFX_REQ_SETUP = 1, MFX_REQ_RUNNING = 2, MFX_REQ_DONE = 3,
+       MFX_REQ_CANCELLED = 4, MFX_REQ_FAILED = 5 };
+
+typedef struct {
+  int32_t state;                   /* MFX_REQ_*                                  */
+  int32_t error;                   /* failed: the mfx_status of the failing call */
+  int64_t n_dofs;
+  int64_t bytes;                   /* device bytes held (estimate until set up)  */
+  double t_submit, t_admit, t_ready, t_done;  /* seconds since the server was created (-1: not yet) */
+  double setup_seconds;            /* set-up thread time (mesh, operator, workspace, rhs) */
+  mfx_solve_stats stats;           /* final solve statistics (state DONE)        */
+} mfx_request_info;
+
+typedef struct {
+  int64_t submitted, queued, in_setup, running, done, cancelled, failed, retired;
+  int64_t bytes_in_use;            /* admitted, not yet retired                  */
+  int32_t max_concurrent;          /* most solves running at once so far         */
+  int32_t reserved;
+  double now;                      /* seconds since creation                     */
+} mfx_server_stats;
+
+/* Errors: MFX_EINVAL (bad config), MFX_ENOMEM, MFX_ECUDA. */
+mfx_status mfx_server_create(mfx_server** out, const mfx_server_config* config);
+/* Cancels what is queued, waits for running and set-up work, frees everything. */
+void mfx_server_destroy(mfx_server* server);
+/* Queue a request; ticket identifies it.  Errors: MFX_EINVAL (no mesh, bad description). */
+mfx_status mfx_server_submit(mfx_server* server, const mfx_request* request, int64_t* ticket);
+/* Current state and times of a request.  Errors: MFX_EINVAL (unknown or retired ticket). */
+mfx_status mfx_server_poll(mfx_server* server, int64_t ticket, mfx_request_info* info);
+/* Cancel: a queued request is dropped at once; one in set-up or running is stopped at the
+ * scheduler's next step (state MFX_REQ_CANCELLED).  Finished requests are left as they are. */
+mfx_status mfx_server_cancel(mfx_server* server, int64_t ticket);
+/* Copy the solution of a DONE request to host memory (n = n_dofs doubles).  Errors: MFX_EINVAL
+ * (unknown ticket, wrong n), MFX_EBUSY (not done). */
+mfx_status mfx_server_result_copy(mfx_server* server, int64_t ticket, double* x_host, int64_t n);
+/* The operator of a DONE request (valid until retired), e.g. to apply it to the solution. */
+mfx_status mfx_server_operator(mfx_server* server, int64_t ticket, const mfx_op** op);
+/* Free a finished (done, cancelled or failed) request's device data and forget the ticket.
+ * Errors: MFX_EINVAL (unknown ticket), MFX_EBUSY (still queued, in set-up or running). */
+mfx_status mfx_server_retire(mfx_server* server, int64_t ticket);
+mfx_status mfx_server_stats_get(mfx_server* server, mfx_server_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,38 @@ class SolveStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("setup_threads", ctypes.c_int32), ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+RHS_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p)
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("leaves", ctypes.c_void_p), ("n_leaves", ctypes.c_int64),
+                ("coarse_vertices", ctypes.c_void_p), ("desc", OpDesc), ("params", SolveParams),
+                ("rhs", RHS_FN), ("user", ctypes.c_void_p), ("est_bytes", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
+                ("bytes", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_ready", ctypes.c_double), ("t_done", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+                ("stats", SolveStats)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_setup", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("done", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("retired", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("max_concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32), ("now", ctypes.c_double)]
+
+
+ADMIT_FIFO, ADMIT_SMALLEST_FIRST = 0, 1
+REQ_QUEUED, REQ_SETUP, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(6)
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -101,6 +133,15 @@ def lib():
         "mfx_batch_advance": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_poll": (S, [_VP, S, ctypes.POINTER(S), ctypes.POINTER(SolveStats)]),
         "mfx_batch_release": (S, [_VP, S]),
+        "mfx_server_create": (S, [ctypes.POINTER(_VP), ctypes.POINTER(ServerConfig)]),
+        "mfx_server_destroy": (None, [_VP]),
+        "mfx_server_submit": (S, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+        "mfx_server_poll": (S, [_VP, ctypes.c_int64, ctypes.POINTER(RequestInfo)]),
+        "mfx_server_cancel": (S, [_VP, ctypes.c_int64]),
+        "mfx_server_result_copy": (S, [_VP, ctypes.c_int64, _VP, ctypes.c_int64]),
+        "mfx_server_operator": (S, [_VP, ctypes.c_int64, ctypes.POINTER(_VP)]),
+        "mfx_server_retire": (S, [_VP, ctypes.c_int64]),
+        "mfx_server_stats_get": (S, [_VP, ctypes.POINTER(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -369,3 +410,81 @@ class Batch:
         while self.step() > 0 and ticks < max_ticks:
             ticks += 1
         return ticks
+
+
+class Server:
+    """Native solve server (mfx_server_*): admission by memory budget, operator set-up on library threads,
+    a scheduler thread stepping every running solve.  Requests carry an octree description (or a Mesh) and
+    an optional right-hand side function rhs(n_dofs) -> array of n_dofs values (called on a set-up thread)."""
+
+    def __init__(self, budget_bytes=64 << 30, max_slots=32, chunk=16, setup_threads=4, policy=ADMIT_FIFO):
+        c = ServerConfig()
+        c.budget_bytes, c.max_slots, c.chunk, c.setup_threads, c.policy = budget_bytes, max_slots, chunk, \
+            setup_threads, policy
+        h = ctypes.c_void_p()
+        check(lib().mfx_server_create(ctypes.byref(h), ctypes.byref(c)))
+        self.handle = h
+        self._keep = {}  # ticket -> objects the library may still use (mesh, callback)
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfx_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, degree, leaves=None, n_coarse=None, mesh=None, rhs=None, tol=1e-10, mixed=True,
+               coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), est_bytes=0, **params):
+        r = Request()
+        keep = []
+        if mesh is not None:
+            r.mesh = mesh.handle
+            keep.append(mesh)
+        else:
+            lv = np.ascontiguousarray(leaves, dtype=np.int32)
+            nx, ny, nz = n_coarse if isinstance(n_coarse, (tuple, list)) else (n_coarse,) * 3
+            r.nx, r.ny, r.nz = nx, ny, nz
+            r.leaves = lv.ctypes.data_as(_VP)
+            r.n_leaves = lv.shape[0]
+            keep.append(lv)  # copied by the library at submission; kept only for the call
+        r.desc.degree, r.desc.coef_kind, r.desc.precisions = degree, coef_kind, 3
+        r.desc.coef_par[0], r.desc.coef_par[1] = coef_par
+        r.params = make_params(tol=tol, mixed=mixed, **params)
+        if rhs is not None:
+            def fill(_op, b, n, _user):
+                np.ctypeslib.as_array(b, shape=(n,))[:] = rhs(n)
+            cb = RHS_FN(fill)
+            r.rhs = cb
+            keep.append(cb)
+        r.est_bytes = est_bytes
+        t = ctypes.c_int64()
+        check(lib().mfx_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket):
+        i = RequestInfo()
+        check(lib().mfx_server_poll(self.handle, ticket, ctypes.byref(i)))
+        d = {f: getattr(i, f) for f, _ in i._fields_ if f != "stats"}
+        d["stats"] = i.stats.as_dict()
+        return d
+
+    def cancel(self, ticket):
+        check(lib().mfx_server_cancel(self.handle, ticket))
+
+    def result(self, ticket):
+        n = self.poll(ticket)["n_dofs"]
+        x = np.empty(n, dtype=np.float64)
+        check(lib().mfx_server_result_copy(self.handle, ticket, x.ctypes.data_as(_VP), n))
+        return x
+
+    def retire(self, ticket):
+        check(lib().mfx_server_retire(self.handle, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        st = ServerStats()
+        check(lib().mfx_server_stats_get(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
