@@ -58,7 +58,13 @@ typedef enum { MFX_F64 = 0, MFX_F32 = 1 } mfx_prec;
 
 enum { MFX_COEF_CONSTANT = 0, /* a = par[0]                                   */
        MFX_COEF_TRIG = 1,     /* a = par[0] + par[1] sin(2 pi x) cos(2 pi y) z */
-       MFX_COEF_QPOINT = 2 }; /* a given at every quadrature point             */
+       MFX_COEF_QPOINT = 2,   /* a given at every quadrature point             */
+       MFX_COEF_FUNCTION = 3 }; /* a(x) from a host function at set-up         */
+
+/* A scalar function of a physical point, evaluated on the host in FP64. */
+typedef double (*mfx_point_fn)(const double x[3], void* user);
+/* A map of physical points, evaluated on the host in FP64. */
+typedef void (*mfx_map_fn)(const double in[3], double out[3], void* user);
 
 enum { MFX_PRECOND_JACOBI = 0, MFX_PRECOND_CHEBYSHEV = 1 };
 
@@ -103,6 +109,30 @@ mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_
 void mfx_mesh_destroy(mfx_mesh* mesh);
 
 /*
+ * Boundary conditions: bit 2d of `faces` (d = 0 x, 1 y, 2 z) makes the box face at coordinate 0
+ * a homogeneous Dirichlet face (u = 0), bit 2d + 1 the face at the far end; the other faces are
+ * natural (Neumann, zero flux) boundaries of the weak form.  Default 0x3F (all six faces).  The
+ * constrained set (and with it the tables, the identity rows of the operator and the diagonal)
+ * follows the mask; operators built earlier keep theirs.  A DoF on several faces is Dirichlet if
+ * any of them is.  With no Dirichlet face the operator is singular (constants are in its kernel).
+ * Errors: MFX_EINVAL (null mesh, faces > 0x3F).
+ */
+enum { MFX_FACE_X0 = 1, MFX_FACE_X1 = 2, MFX_FACE_Y0 = 4, MFX_FACE_Y1 = 8, MFX_FACE_Z0 = 16,
+       MFX_FACE_Z1 = 32, MFX_FACES_ALL = 63 };
+mfx_status mfx_mesh_set_dirichlet(mfx_mesh* mesh, uint32_t faces);
+mfx_status mfx_mesh_get_dirichlet(const mfx_mesh* mesh, uint32_t* faces);
+
+/*
+ * Move the mesh: every vertex v of the vertex lattice (structured) or of the
+ * coarse lattice (octree) becomes phi(v), evaluated on the host in FP64
+ * (the geometry is given by the moved vertices and the trilinear map of each
+ * cell, Sec. 3.4).  Octree leaf vertices follow from the moved coarse cells'
+ * trilinear maps, so leaves stay conforming.  Operators built earlier keep
+ * their geometry.  Errors: MFX_EINVAL (null mesh or map).
+ */
+mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user);
+
+/*
  * Host-only (no GPU needed): sizes of the DoF and constraint tables of the
  * mesh at degree k (numbering and constraint rules as described above).
  * Any output pointer may be NULL.
@@ -128,6 +158,9 @@ typedef struct {
                                 q = q1 + n_q (q2 + n_q q3); read during create  */
   int32_t cells_per_block;   /* 0 = autotuned default                             */
   int32_t reserved;
+  mfx_point_fn coef_fn;      /* MFX_COEF_FUNCTION: a(x), called once per quadrature
+                                point during create (on the calling thread)      */
+  void* coef_user;
 } mfx_op_desc;
 
 /*
@@ -206,6 +239,13 @@ mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream
  * fq: device, n_cells x n_q^3 doubles; b: device, n_dofs doubles.
  */
 mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream);
+/*
+ * The same load vector for f given as a host function: f is evaluated on the
+ * host at the physical quadrature points (as returned by
+ * mfx_quadrature_points), then integrated as mfx_rhs does.  Synchronises the
+ * stream.  Errors: MFX_EINVAL, MFX_ENOMEM, MFX_ECUDA.
+ */
+mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double* b, mfx_stream stream);
 
 /*
  * Fill constrained entries of x (device, FP64) from the free ones: hanging

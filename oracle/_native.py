@@ -20,7 +20,7 @@ def lib():
         _lib.or_cell_rhs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
                                      ctypes.c_int, _D, ctypes.c_int, _D, _D]
         _lib.or_cell_qpoints.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]
-        _lib.or_l2_error_sq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]
+        _lib.or_l2_error_sq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, ctypes.c_int]
         _lib.or_l2_error_sq.restype = ctypes.c_double
         _lib.or_csr_spmv.argtypes = [ctypes.c_int64, _L, _L, _D, _D, _D]
     return _lib

@@ -11,7 +11,10 @@ Structured mesh (nx x ny x nz cells):
     cell vertex v = a + 2 b + 4 c for corner (a, b, c);
   * global DoF = I + Mx (J + My L) on the (k nx + 1) x (k ny + 1) x (k nz + 1)
     lattice of GLL nodes; local DoF = i1 + n (i2 + n i3), n = k + 1;
-  * Dirichlet: every DoF on the boundary of the box is constrained to 0.
+  * Dirichlet: every DoF on a Dirichlet face of the box is constrained to 0;
+    by default all six faces, else the faces of the bit mask `dirichlet`
+    (bit 2d: the face at coordinate 0 in direction d, bit 2d + 1: the far
+    face); the other faces are natural boundaries of the weak form.
 
 Octree mesh (leaves (level, i, j, l) over an nx x ny x nz coarse grid):
   * leaves must tile the coarse box and be 2:1 balanced across faces and
@@ -65,7 +68,7 @@ def unit_vertices(nx, ny, nz):
     return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
 
 
-def structured_mesh(nx, ny, nz, k, vertices=None):
+def structured_mesh(nx, ny, nz, k, vertices=None, dirichlet=0x3F):
     """Structured box mesh of nx*ny*nz cells with degree-k lexicographic DoFs."""
     if vertices is None:
         vertices = unit_vertices(nx, ny, nz)
@@ -92,7 +95,9 @@ def structured_mesh(nx, ny, nz, k, vertices=None):
     I = np.arange(N) % Mx
     J = (np.arange(N) // Mx) % My
     L = np.arange(N) // (Mx * My)
-    bnd = (I == 0) | (I == Mx - 1) | (J == 0) | (J == My - 1) | (L == 0) | (L == Mz - 1)
+    f = [bool(dirichlet >> b & 1) for b in range(6)]
+    bnd = ((I == 0) & f[0]) | ((I == Mx - 1) & f[1]) | ((J == 0) & f[2]) | ((J == My - 1) & f[3]) | \
+          ((L == 0) & f[4]) | ((L == Mz - 1) & f[5])
     constrained = np.nonzero(bnd)[0].astype(np.int64)
     cptr = np.zeros(len(constrained) + 1, dtype=np.int64)
     return Mesh(cv, cd, N, constrained, cptr, np.zeros(0, np.int64), np.zeros(0), k)
@@ -153,8 +158,9 @@ def _check_balance(owner, levels):
             raise MeshError("mesh is not 2:1 balanced across faces and edges")
 
 
-def octree_mesh(nx, ny, nz, k, leaves, coarse_vertices=None):
+def octree_mesh(nx, ny, nz, k, leaves, coarse_vertices=None, dirichlet=0x3F):
     """Octree mesh from leaves (level, i, j, l), with DoF tables and constraints."""
+    faces = int(dirichlet)  # Dirichlet face mask (the name is reused below for the Dirichlet DoF set)
     leaves = [tuple(int(v) for v in lf) for lf in np.asarray(leaves).reshape(-1, 4)]
     if not leaves:
         raise MeshError("no leaves")
@@ -238,9 +244,11 @@ def octree_mesh(nx, ny, nz, k, leaves, coarse_vertices=None):
     N = len(dof_of)
 
     def on_boundary(key):
+        # on a Dirichlet face: a rational position at 0 or at the far end of the box
         for d in range(3):
             kd = key[d]
-            if kd[0] == 0 and (kd[1] == 0 or kd[1] == ext[d]):
+            if kd[0] == 0 and ((kd[1] == 0 and faces >> (2 * d) & 1) or
+                               (kd[1] == ext[d] and faces >> (2 * d + 1) & 1)):
                 return True
         return False
 

@@ -248,7 +248,7 @@ int or_cell_qpoints(int ncell, int nq, const double* xq, const double* wq, const
  * cell's nodal values.
  */
 double or_l2_error_sq(int ncell, int k, int nq, const double* nodes, const double* xq,
-                      const double* wq, const double* verts, const double* ucell) {
+                      const double* wq, const double* verts, const double* ucell, int exact) {
   int n = k + 1, nd = n * n * n, NQ = nq * nq * nq;
   double total = 0.0;
 #pragma omp parallel for reduction(+ : total) schedule(dynamic)
@@ -262,7 +262,9 @@ double or_l2_error_sq(int ncell, int k, int nq, const double* nodes, const doubl
         shape(k, nodes, i, xi, &v, g);
         uh += ucell[(size_t)c * nd + i] * v;
       }
-      double u = sin(PI * d.x[0]) * sin(PI * d.x[1]) * sin(PI * d.x[2]);
+      /* exact solution: 0 -> sin(pi x) sin(pi y) sin(pi z) (u = 0 on every face),
+         1 -> sin(pi x) (u = 0 on the x faces, zero normal derivative on the others) */
+      double u = exact == 1 ? sin(PI * d.x[0]) : sin(PI * d.x[0]) * sin(PI * d.x[1]) * sin(PI * d.x[2]);
       total += (uh - u) * (uh - u) * d.JxW;
     }
   }

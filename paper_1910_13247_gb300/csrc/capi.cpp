@@ -219,6 +219,41 @@ static void keep_pool_memory() {
   done.push_back(dev);
 }
 
+// Values of a host function at the operator's physical quadrature points (cell-major, q fastest, as
+// mfx_quadrature_points lays them out), returned in a stream-ordered device array of n_cells n_q^3.
+static mfx_status host_point_values(const mfx_op* op, mfx_point_fn f, void* user, double** out, cudaStream_t s) {
+  const int64_t nq = op->n_cells * (int64_t)op->n * op->n * op->n;
+  double* d = nullptr;
+  *out = nullptr;
+  if (cudaMallocAsync((void**)&d, sizeof(double) * 3 * std::max<int64_t>(1, nq), s) != cudaSuccess)
+    return set_error(MFX_ENOMEM, "quadrature point buffer");
+  std::vector<double> x((size_t)(3 * nq));
+  mfx_status st = launch_qpoints(op, d, s);
+  cudaError_t e = cudaSuccess;
+  if (st == MFX_OK) e = cudaMemcpyAsync(x.data(), d, sizeof(double) * 3 * nq, cudaMemcpyDeviceToHost, s);
+  if (st == MFX_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (st != MFX_OK || e != cudaSuccess) {
+    cudaFreeAsync(d, s);
+    return st != MFX_OK ? st : cuda_error(e, "quadrature points");
+  }
+  std::vector<double> v((size_t)nq);
+  for (int64_t i = 0; i < nq; ++i) v[i] = f(&x[3 * i], user);
+  e = cudaMemcpyAsync(d, v.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // v is a local buffer
+  if (e != cudaSuccess) {
+    cudaFreeAsync(d, s);
+    return cuda_error(e, "point values upload");
+  }
+  *out = d;
+  return MFX_OK;
+}
+
+// Lattice points of a structured mesh on no Dirichlet face.
+static int64_t free_lattice_points(uint32_t dmask, int64_t Mx, int64_t My, int64_t Mz) {
+  auto cnt = [](int64_t M, bool lo, bool hi) { return std::max<int64_t>(0, M - (lo ? 1 : 0) - (hi ? 1 : 0)); };
+  return cnt(Mx, dmask & 1u, dmask & 2u) * cnt(My, dmask & 4u, dmask & 8u) * cnt(Mz, dmask & 16u, dmask & 32u);
+}
+
 // Frees everything in stream order on `s`; sync = wait for the whole device first (the contract of
 // mfx_operator_destroy) and for the frees after.
 static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sync = true) {
@@ -311,6 +346,18 @@ mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_
 
 void mfx_mesh_destroy(mfx_mesh* mesh) { delete mesh; }
 
+mfx_status mfx_mesh_set_dirichlet(mfx_mesh* mesh, uint32_t faces) {
+  if (!mesh || faces > kAllFaces) return set_error(MFX_EINVAL, "mfx_mesh_set_dirichlet: null mesh or faces > 0x3F");
+  mesh->m.dirichlet = faces;
+  return MFX_OK;
+}
+
+mfx_status mfx_mesh_get_dirichlet(const mfx_mesh* mesh, uint32_t* faces) {
+  if (!mesh || !faces) return set_error(MFX_EINVAL, "null argument");
+  *faces = mesh->m.dirichlet;
+  return MFX_OK;
+}
+
 mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) {
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "null argument");
   *out = nullptr;
@@ -318,10 +365,12 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (k < 1 || k > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
   if (desc->n_q_1d != 0 && desc->n_q_1d != k + 1)
     return set_error(MFX_EUNSUPPORTED, "only n_q_1d = k + 1 is implemented");
-  if (desc->coef_kind < MFX_COEF_CONSTANT || desc->coef_kind > MFX_COEF_QPOINT)
+  if (desc->coef_kind < MFX_COEF_CONSTANT || desc->coef_kind > MFX_COEF_FUNCTION)
     return set_error(MFX_EINVAL, "unknown coefficient kind");
   if (desc->coef_kind == MFX_COEF_QPOINT && !desc->coef_qpoint)
     return set_error(MFX_EINVAL, "MFX_COEF_QPOINT needs coef_qpoint");
+  if (desc->coef_kind == MFX_COEF_FUNCTION && !desc->coef_fn)
+    return set_error(MFX_EINVAL, "MFX_COEF_FUNCTION needs coef_fn");
   cudaStream_t s = (cudaStream_t)stream;
   keep_pool_memory();
   mfx_op* op = new (std::nothrow) mfx_op();
@@ -338,6 +387,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   op->ny = m.ny;
   op->nz = m.nz;
   op->structured = m.structured;
+  op->dirichlet = m.dirichlet;
   const int n = op->n, n3 = n * n * n;
   if (m.structured) {
     op->n_cells = (int64_t)m.nx * m.ny * m.nz;
@@ -347,8 +397,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       destroy_op(op);
       return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
     }
-    op->n_constrained = op->n_dofs - std::max<int64_t>(0, Mx - 2) * std::max<int64_t>(0, My - 2) *
-                                         std::max<int64_t>(0, Mz - 2);
+    op->n_constrained = op->n_dofs - free_lattice_points(m.dirichlet, Mx, My, Mz);
     MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size(), s));
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, m.vertices.data(), m.vertices.size() * sizeof(double),
                                 cudaMemcpyHostToDevice, s));
@@ -451,9 +500,21 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   MFX_TRY(dev_alloc(op, &op->d_err, 4, s));
   MFX_CUDA_OP(cudaMemsetAsync(op->d_err, 0, 4 * sizeof(int), s));
   MFX_TRY(prepare_vmult(op));
-  if (op->structured)
-    MFX_TRY(choose_cells_per_batch(op, desc->cells_per_block, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
-  MFX_TRY(launch_geometry(op, desc->coef_kind, desc->coef_par, desc->coef_qpoint, s));
+  // a(x) from a host function: evaluated once at the physical quadrature points, then used as a
+  // per-quadrature-point coefficient
+  int coef_kind = desc->coef_kind;
+  const double* coef_q = desc->coef_qpoint;
+  double* coef_tmp = nullptr;
+  if (coef_kind == MFX_COEF_FUNCTION) {
+    MFX_TRY(host_point_values(op, desc->coef_fn, desc->coef_user, &coef_tmp, s));
+    coef_kind = MFX_COEF_QPOINT;
+    coef_q = coef_tmp;
+  }
+  mfx_status geo_st = MFX_OK;
+  if (op->structured) geo_st = choose_cells_per_batch(op, desc->cells_per_block, coef_kind, desc->coef_par, coef_q, s);
+  if (geo_st == MFX_OK) geo_st = launch_geometry(op, coef_kind, desc->coef_par, coef_q, s);
+  if (coef_tmp) cudaFreeAsync(coef_tmp, s);
+  MFX_TRY(geo_st);
   MFX_TRY(launch_diagonal(op, s));
   std::vector<int32_t>().swap(op->hang_job_cell);  // staged by the copies above: host copies no longer needed
   std::vector<int32_t>().swap(op->hang_job_master);
@@ -494,8 +555,8 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   return MFX_OK;
 }
 
-static void structured_tables(int nx, int ny, int nz, int k, int32_t* cell_dofs, int32_t* constrained,
-                              int64_t* cptr) {
+static void structured_tables(int nx, int ny, int nz, int k, uint32_t dmask, int32_t* cell_dofs,
+                              int32_t* constrained, int64_t* cptr) {
   const int n = k + 1, n3 = n * n * n;
   const int64_t Mx = (int64_t)k * nx + 1, My = (int64_t)k * ny + 1, Mz = (int64_t)k * nz + 1;
   const int64_t C = (int64_t)nx * ny * nz;
@@ -513,7 +574,7 @@ static void structured_tables(int nx, int ny, int nz, int k, int32_t* cell_dofs,
   for (int64_t L = 0; L < Mz; ++L)
     for (int64_t J = 0; J < My; ++J)
       for (int64_t I = 0; I < Mx; ++I)
-        if (I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1) {
+        if (on_dirichlet(dmask, I, J, L, Mx, My, Mz)) {
           if (constrained) constrained[t] = (int32_t)(I + Mx * (J + My * L));
           if (cptr) cptr[t] = 0;
           ++t;
@@ -540,7 +601,7 @@ mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n
     const int64_t k = degree, Mx = k * m.nx + 1, My = k * m.ny + 1, Mz = k * m.nz + 1;
     C = (int64_t)m.nx * m.ny * m.nz;
     N = Mx * My * Mz;
-    NC = N - (Mx - 2) * (My - 2) * (Mz - 2);
+    NC = N - free_lattice_points(m.dirichlet, Mx, My, Mz);
     NM = 0;
   } else {
     OctreeTables t;
@@ -564,7 +625,7 @@ mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_d
   if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
   const Mesh& m = mesh->m;
   if (m.structured) {
-    structured_tables(m.nx, m.ny, m.nz, degree, cell_dofs, constrained, cptr);
+    structured_tables(m.nx, m.ny, m.nz, degree, m.dirichlet, cell_dofs, constrained, cptr);
     return MFX_OK;
   }
   OctreeTables t;
@@ -578,7 +639,7 @@ mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constra
                           int32_t* cmaster, double* cweight) {
   if (!op) return set_error(MFX_EINVAL, "null operator");
   if (op->structured) {
-    structured_tables(op->nx, op->ny, op->nz, op->k, cell_dofs, constrained, cptr);
+    structured_tables(op->nx, op->ny, op->nz, op->k, op->dirichlet, cell_dofs, constrained, cptr);
     return MFX_OK;
   }
   copy_tables(op->tables, cell_dofs, constrained, cptr, cmaster, cweight);
@@ -622,6 +683,32 @@ mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream
 mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream) {
   if (!op || !fq || !b) return set_error(MFX_EINVAL, "mfx_rhs: null argument");
   return launch_rhs(op, fq, b, (cudaStream_t)stream);
+}
+
+mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double* b, mfx_stream stream) {
+  if (!op || !f || !b) return set_error(MFX_EINVAL, "mfx_rhs_function: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* fq = nullptr;
+  mfx_status st = host_point_values(op, f, user, &fq, s);
+  if (st != MFX_OK) return st;
+  st = launch_rhs(op, fq, b, s);
+  cudaFreeAsync(fq, s);
+  if (st == MFX_OK) MFX_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user) {
+  if (!mesh || !phi) return set_error(MFX_EINVAL, "mfx_mesh_transform: null argument");
+  std::vector<double>& v = mesh->m.vertices;
+  for (size_t i = 0; i + 2 < v.size(); i += 3) {
+    const double in[3] = {v[i], v[i + 1], v[i + 2]};
+    double out[3] = {in[0], in[1], in[2]};
+    phi(in, out, user);
+    v[i] = out[0];
+    v[i + 1] = out[1];
+    v[i + 2] = out[2];
+  }
+  return MFX_OK;
 }
 
 mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream) {

@@ -159,6 +159,7 @@ __global__ void qpoints_kernel(const __grid_constant__ GeoArgs g, double* __rest
 // Global DoF of local node (i1, i2, i3) and its constraint class.
 struct DofView {
   bool structured;
+  uint32_t dmask;  // structured: Dirichlet faces
   int nx, ny, k, Mx, My, Mz, n;
   const int32_t* cell_dofs;
   const int64_t* cptr;
@@ -174,7 +175,7 @@ __device__ __forceinline__ void expand_node(const DofView& v, int64_t cell, int 
     const int64_t rest = cell / v.nx;
     const int cy = (int)(rest % v.ny), cz = (int)(rest / v.ny);
     const int I = cx * v.k + i1, J = cy * v.k + i2, L = cz * v.k + i3;
-    if (I == 0 || I == v.Mx - 1 || J == 0 || J == v.My - 1 || L == 0 || L == v.Mz - 1) return;
+    if (on_dirichlet(v.dmask, I, J, L, v.Mx, v.My, v.Mz)) return;
     f((int64_t)I + (int64_t)v.Mx * (J + (int64_t)v.My * L), 1.0);
   } else {
     const int32_t e = v.cell_dofs[cell * v.n * v.n * v.n + (i3 * v.n + i2) * v.n + i1];
@@ -380,14 +381,14 @@ __global__ void diagonal_hanging_kernel(const __grid_constant__ GeoArgs g, DofVi
 }
 
 template <typename Real>
-__global__ void diag_finish_kernel(int64_t n_dofs, bool structured, int Mx, int My, int Mz,
+__global__ void diag_finish_kernel(int64_t n_dofs, bool structured, uint32_t dmask, int Mx, int My, int Mz,
                                    const uint8_t* __restrict__ cmask, const double* __restrict__ d,
                                    double* __restrict__ d64, float* __restrict__ d32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dofs; i += (int64_t)gridDim.x * blockDim.x) {
     bool c;
     if (structured) {
       const int64_t I = i % Mx, rest = i / Mx, J = rest % My, L = rest / My;
-      c = I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1;
+      c = on_dirichlet(dmask, I, J, L, Mx, My, Mz);
     } else {
       c = cmask[i] != 0;
     }
@@ -397,7 +398,8 @@ __global__ void diag_finish_kernel(int64_t n_dofs, bool structured, int Mx, int 
   }
 }
 
-__global__ void distribute_kernel(int64_t n_dofs, bool structured, int Mx, int My, int Mz, int64_t n_constrained,
+__global__ void distribute_kernel(int64_t n_dofs, bool structured, uint32_t dmask, int Mx, int My, int Mz,
+                                  int64_t n_constrained,
                                   const int32_t* __restrict__ constrained, const int64_t* __restrict__ cptr,
                                   const int32_t* __restrict__ cmaster, const double* __restrict__ cweight,
                                   double* __restrict__ x) {
@@ -405,7 +407,7 @@ __global__ void distribute_kernel(int64_t n_dofs, bool structured, int Mx, int M
   if (structured) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dofs; i += stride) {
       const int64_t I = i % Mx, rest = i / Mx, J = rest % My, L = rest / My;
-      if (I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || L == 0 || L == Mz - 1) x[i] = 0.0;
+      if (on_dirichlet(dmask, I, J, L, Mx, My, Mz)) x[i] = 0.0;
     }
     return;
   }
@@ -447,6 +449,7 @@ static GeoArgs geo_args(const mfx_op* op) {
 static DofView dof_view(const mfx_op* op) {
   DofView v;
   v.structured = op->structured;
+  v.dmask = op->dirichlet;
   v.nx = op->nx;
   v.ny = op->ny;
   v.k = op->k;
@@ -545,7 +548,7 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
     launch_diagonal_sf(op->n, g, dof_view(op), op->d_metric64, simple ? op->d_cell_hanging : nullptr, simple, jobs,
                        jobs ? jobs + nj : nullptr, jobs ? nj : 0, tmp, s);
     diag_finish_kernel<double><<<grid_for(op->n_dofs), 256, 0, s>>>(
-        op->n_dofs, op->structured, op->k * op->nx + 1, op->k * op->ny + 1, op->k * op->nz + 1, op->d_cmask, tmp,
+        op->n_dofs, op->structured, op->dirichlet, op->k * op->nx + 1, op->k * op->ny + 1, op->k * op->nz + 1, op->d_cmask, tmp,
         op->d_diag64, op->d_diag32);
     e = cudaGetLastError();
   }
@@ -575,7 +578,7 @@ mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s) {
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s) {
   const int64_t work = op->structured ? op->n_dofs : op->n_constrained;
   if (work == 0) return MFX_OK;
-  distribute_kernel<<<grid_for(work), 256, 0, s>>>(op->n_dofs, op->structured, op->k * op->nx + 1,
+  distribute_kernel<<<grid_for(work), 256, 0, s>>>(op->n_dofs, op->structured, op->dirichlet, op->k * op->nx + 1,
                                                    op->k * op->ny + 1, op->k * op->nz + 1, op->n_constrained,
                                                    op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, x);
   MFX_CUDA_TRY(cudaGetLastError());

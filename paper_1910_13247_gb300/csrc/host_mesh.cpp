@@ -297,7 +297,8 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   for (int64_t d = 0; d < N; ++d)
     for (int e = 0; e < 3; ++e) {
       const uint32_t dk = keys_by_dof[d].d[e];
-      if (!irrational(dk) && (dk == 0 || dk == ext[e])) dirichlet[d] = 1;
+      if (!irrational(dk) && ((dk == 0 && (m.dirichlet >> (2 * e) & 1u)) || (dk == ext[e] && (m.dirichlet >> (2 * e + 1) & 1u))))
+        dirichlet[d] = 1;
     }
   // hanging constraints
   std::map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;

@@ -43,8 +43,18 @@ struct BasisTables {
 void make_basis(int k, BasisTables* t);
 
 // ----------------------------------------------------------------- mesh
+// Faces of the box with homogeneous Dirichlet conditions: bit 2d (d = 0 x, 1 y, 2 z) is the face at
+// coordinate 0, bit 2d + 1 the face at the far end; the other faces are natural (Neumann) boundaries.
+constexpr uint32_t kAllFaces = 0x3F;
+__host__ __device__ inline bool on_dirichlet(uint32_t mask, int64_t I, int64_t J, int64_t L, int64_t Mx, int64_t My,
+                                             int64_t Mz) {
+  return ((mask & 1u) && I == 0) || ((mask & 2u) && I == Mx - 1) || ((mask & 4u) && J == 0) ||
+         ((mask & 8u) && J == My - 1) || ((mask & 16u) && L == 0) || ((mask & 32u) && L == Mz - 1);
+}
+
 struct Mesh {
   bool structured = true;
+  uint32_t dirichlet = kAllFaces;     // Dirichlet faces (bit mask above)
   int nx = 0, ny = 0, nz = 0;
   std::vector<double> vertices;       // structured lattice or coarse lattice
   std::vector<int32_t> leaves;        // octree: sorted leaves, 4 per leaf
@@ -80,6 +90,7 @@ struct mfx_op {
   int k = 0, n = 0;
   int64_t n_cells = 0, n_dofs = 0, n_constrained = 0, n_masters = 0, n_hanging = 0;
   bool structured = true;
+  uint32_t dirichlet = mfx::kAllFaces;    // Dirichlet faces of the box
   int nx = 0, ny = 0, nz = 0;             // structured cells per direction
   int cells_per_block = 0;
   int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)

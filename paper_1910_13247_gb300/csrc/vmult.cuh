@@ -33,9 +33,6 @@ template <int N, typename Real>
 struct VmultArgs {
   const Real* metric;  // [cell][6][N^3]
   int64_t n_cells;
-  // structured meshes
-  int nx, ny, nz, k, Mx, My, Mz;
-  // table meshes
   const int32_t* cell_dofs;  // >= 0 free DoF, < 0: -(row + 1) into the constraint rows
   const int64_t* cptr;
   const int32_t* cmaster;
@@ -90,71 +87,44 @@ __device__ __forceinline__ void contract_t(const Real (&in)[N], Real (&out)[N]) 
   }
 }
 
-// x-line gather of cell `cell` at (i2, i3) with constraint resolution.
-template <int N, typename Real, bool STRUCT>
+// x-line gather of cell `cell` at (i2, i3) through the cell's index table, with constraint
+// resolution (hanging: weighted masters; Dirichlet: no masters, value 0).
+template <int N, typename Real>
 __device__ __forceinline__ void gather_xline(const VmultArgs<N, Real>& a, const Real* __restrict__ src,
                                              int64_t cell, int i2, int i3, Real (&v)[N]) {
-  if constexpr (STRUCT) {
-    const int cx = (int)(cell % a.nx);
-    const int64_t rest = cell / a.nx;
-    const int cy = (int)(rest % a.ny), cz = (int)(rest / a.ny);
-    const int J = cy * a.k + i2, L = cz * a.k + i3, I0 = cx * a.k;
-    const bool plane_bnd = (J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1);
-    const Real* row = src + (int64_t)a.Mx * (J + (int64_t)a.My * L) + I0;
+  const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
 #pragma unroll
-    for (int i1 = 0; i1 < N; ++i1) {
-      const int I = I0 + i1;
-      const bool bnd = plane_bnd | (I == 0) | (I == a.Mx - 1);
-      v[i1] = bnd ? Real(0) : __ldg(row + i1);
-    }
-  } else {
-    const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
-#pragma unroll
-    for (int i1 = 0; i1 < N; ++i1) {
-      const int32_t e = __ldg(cd + i1);
-      if (e >= 0) {
-        v[i1] = __ldg(src + e);
-      } else {
-        const int32_t row = -e - 1;
-        Real s = Real(0);
-        for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) s += a.cweight[p] * __ldg(src + a.cmaster[p]);
-        v[i1] = s;
-      }
+  for (int i1 = 0; i1 < N; ++i1) {
+    const int32_t e = __ldg(cd + i1);
+    if (e >= 0) {
+      v[i1] = __ldg(src + e);
+    } else {
+      const int32_t row = -e - 1;
+      Real s = Real(0);
+      for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) s += a.cweight[p] * __ldg(src + a.cmaster[p]);
+      v[i1] = s;
     }
   }
 }
 
-template <int N, typename Real, bool STRUCT>
+// x-line scatter: the transpose of the gather (atomics into the free DoFs).
+template <int N, typename Real>
 __device__ __forceinline__ void scatter_xline(const VmultArgs<N, Real>& a, Real* __restrict__ dst, int64_t cell,
                                               int i2, int i3, const Real (&v)[N]) {
-  if constexpr (STRUCT) {
-    const int cx = (int)(cell % a.nx);
-    const int64_t rest = cell / a.nx;
-    const int cy = (int)(rest % a.ny), cz = (int)(rest / a.ny);
-    const int J = cy * a.k + i2, L = cz * a.k + i3, I0 = cx * a.k;
-    if ((J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1)) return;
-    Real* row = dst + (int64_t)a.Mx * (J + (int64_t)a.My * L) + I0;
+  const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
 #pragma unroll
-    for (int i1 = 0; i1 < N; ++i1) {
-      const int I = I0 + i1;
-      if ((I != 0) & (I != a.Mx - 1)) atomicAdd(row + i1, v[i1]);
-    }
-  } else {
-    const int32_t* cd = a.cell_dofs + cell * (N * N * N) + (i3 * N + i2) * N;
-#pragma unroll
-    for (int i1 = 0; i1 < N; ++i1) {
-      const int32_t e = __ldg(cd + i1);
-      if (e >= 0) {
-        atomicAdd(dst + e, v[i1]);
-      } else {
-        const int32_t row = -e - 1;
-        for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) atomicAdd(dst + a.cmaster[p], a.cweight[p] * v[i1]);
-      }
+  for (int i1 = 0; i1 < N; ++i1) {
+    const int32_t e = __ldg(cd + i1);
+    if (e >= 0) {
+      atomicAdd(dst + e, v[i1]);
+    } else {
+      const int32_t row = -e - 1;
+      for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) atomicAdd(dst + a.cmaster[p], a.cweight[p] * v[i1]);
     }
   }
 }
 
-template <int N, typename Real, bool STRUCT>
+template <int N, typename Real>
 __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ VmultArgs<N, Real> a,
                                                     const Real* __restrict__ src, Real* __restrict__ dst) {
   using Sh = VmultShape<N>;
@@ -183,7 +153,7 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
     // 1) gather + S along x: x-line (i2 = ra, i3 = rb)
     if (act) {
       Real v[N], o[N];
-      gather_xline<N, Real, STRUCT>(a, src, cell, ra, rb, v);
+      gather_xline<N, Real>(a, src, cell, ra, rb, v);
       contract<N, Real, MAT_S>(v, o);
       Real* p = B0 + (rb * N + ra) * NP;
 #pragma unroll
@@ -302,30 +272,20 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = p[j];
       contract_t<N, Real, MAT_S>(v, o);
-      scatter_xline<N, Real, STRUCT>(a, dst, cell, ra, rb, o);
+      scatter_xline<N, Real>(a, dst, cell, ra, rb, o);
     }
     __syncthreads();
   }
 }
 
 // dst = src on constrained rows, 0 elsewhere (identity rows of the condensed operator).
-template <int N, typename Real, bool STRUCT>
+template <int N, typename Real>
 __global__ void vmult_prologue(const __grid_constant__ VmultArgs<N, Real> a, const Real* __restrict__ src,
                                Real* __restrict__ dst) {
   if (a.skip && *a.skip) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_dofs; i += stride) {
-    bool c;
-    if constexpr (STRUCT) {
-      const int64_t I = i % a.Mx;
-      const int64_t rest = i / a.Mx;
-      const int64_t J = rest % a.My, L = rest / a.My;
-      c = (I == 0) | (I == a.Mx - 1) | (J == 0) | (J == a.My - 1) | (L == 0) | (L == a.Mz - 1);
-    } else {
-      c = a.cmask[i] != 0;
-    }
-    dst[i] = c ? src[i] : Real(0);
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_dofs; i += stride)
+    dst[i] = a.cmask[i] != 0 ? src[i] : Real(0);
 }
 
 }  // namespace mfx

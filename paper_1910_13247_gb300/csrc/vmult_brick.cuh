@@ -70,6 +70,7 @@ struct BrickArgs {
   int Mx, My, Mz;
   int64_t n_batches;
   const int32_t* skip;
+  uint32_t dmask;  // Dirichlet faces
 };
 
 template <typename Real>
@@ -94,9 +95,11 @@ __device__ __forceinline__ BatchInfo batch_info(const Args& a, int b) {
   bi.m = min(CB, a.nx - bi.cx0);
   bi.Wm = bi.m * K + 1;
   bi.gbase = bi.cx0 * K + a.Mx * (cy * K + a.My * (cz * K));
-  bi.xlo = bi.cx0 == 0;
-  bi.xhi = bi.cx0 + bi.m == a.nx;
-  bi.eflags = (cy == 0 ? 1 : 0) | (cy == a.ny - 1 ? 2 : 0) | (cz == 0 ? 4 : 0) | (cz == a.nz - 1 ? 8 : 0);
+  const uint32_t f = a.dmask;
+  bi.xlo = bi.cx0 == 0 && (f & 1u);
+  bi.xhi = bi.cx0 + bi.m == a.nx && (f & 2u);
+  bi.eflags = (cy == 0 && (f & 4u) ? 1 : 0) | (cy == a.ny - 1 && (f & 8u) ? 2 : 0) | (cz == 0 && (f & 16u) ? 4 : 0) |
+              (cz == a.nz - 1 && (f & 32u) ? 8 : 0);
   return bi;
 }
 

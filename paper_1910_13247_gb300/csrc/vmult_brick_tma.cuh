@@ -43,6 +43,7 @@ struct TmaArgs {
   int n_batches;
   int* err;               // set to 1 if a bounded wait ran out
   const int32_t* skip;
+  uint32_t dmask;         // Dirichlet faces
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -30,13 +30,6 @@ template <int N, typename Real>
 static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
   a->metric = std::is_same<Real, double>::value ? (const Real*)op->d_metric64 : (const Real*)op->d_metric32;
   a->n_cells = op->n_cells;
-  a->nx = op->nx;
-  a->ny = op->ny;
-  a->nz = op->nz;
-  a->k = op->k;
-  a->Mx = op->k * op->nx + 1;
-  a->My = op->k * op->ny + 1;
-  a->Mz = op->k * op->nz + 1;
   a->cell_dofs = op->d_cell_dofs;
   a->cptr = op->d_cptr;
   a->cmaster = op->d_cmaster;
@@ -45,12 +38,12 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
   a->n_dofs = op->n_dofs;
 }
 
-template <int N, typename Real, bool STRUCT>
+template <int N, typename Real>
 static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
   const size_t smem = 3 * (size_t)Sh::CB * Sh::CELL * sizeof(Real);
-  auto kern = vmult_kernel<N, Real, STRUCT>;
+  auto kern = vmult_kernel<N, Real>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -63,7 +56,7 @@ static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaSt
   const int sms = device_sm_count();
   int pb = (int)std::min<int64_t>((op->n_dofs + 255) / 256, (int64_t)sms * 8);
   if (pb < 1) pb = 1;
-  vmult_prologue<N, Real, STRUCT><<<pb, 256, 0, s>>>(a, src, dst);
+  vmult_prologue<N, Real><<<pb, 256, 0, s>>>(a, src, dst);
   const int64_t nbatch = (op->n_cells + Sh::CB - 1) / Sh::CB;
   if (nbatch > 0) {
     const int grid = (int)std::min<int64_t>(nbatch, (int64_t)sms * blocks_per_sm);
@@ -103,6 +96,7 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
   a.Mz = op->k * op->nz + 1;
   a.n_batches = (int64_t)a.nchunk * op->ny * op->nz;
   a.skip = skip;
+  a.dmask = op->dirichlet;
   MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(Real) * op->n_dofs, s));
   const int grid = (int)std::min<int64_t>(a.n_batches, (int64_t)device_sm_count() * blocks_per_sm);
   kern<<<grid, Sh::THREADS, smem, s>>>(a, src, dst);
@@ -125,20 +119,22 @@ int brick_cells_candidates(int* out) {
   return 1;
 }
 
-// dst = src on the Dirichlet (box boundary) DoFs; one warp per lattice row (J, L).
+// dst = src on the Dirichlet DoFs (faces in dmask); one warp per lattice row (J, L).
 template <typename Real>
-__global__ void boundary_rows_kernel(int Mx, int My, int Mz, const Real* __restrict__ src, Real* __restrict__ dst) {
+__global__ void boundary_rows_kernel(int Mx, int My, int Mz, uint32_t dmask, const Real* __restrict__ src,
+                                     Real* __restrict__ dst) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int rows = My * Mz;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
     const int J = row % My, L = row / My;
     const int64_t base = (int64_t)Mx * row;
-    if (J == 0 || J == My - 1 || L == 0 || L == Mz - 1) {
+    if (((dmask & 4u) && J == 0) || ((dmask & 8u) && J == My - 1) || ((dmask & 16u) && L == 0) ||
+        ((dmask & 32u) && L == Mz - 1)) {
       for (int I = lane; I < Mx; I += 32) dst[base + I] = src[base + I];
     } else if (lane == 0) {
-      dst[base] = src[base];
-      dst[base + Mx - 1] = src[base + Mx - 1];
+      if (dmask & 1u) dst[base] = src[base];
+      if (dmask & 2u) dst[base + Mx - 1] = src[base + Mx - 1];
     }
   }
 }
@@ -199,10 +195,11 @@ static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, 
   a.n_batches = a.nchunk * op->ny * op->nz;
   a.err = op->d_err;
   a.skip = skip;
+  a.dmask = op->dirichlet;
   MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
   const int rows = a.My * a.Mz;
   boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
-      a.Mx, a.My, a.Mz, src, dst);
+      a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
   kern<<<grid, Sh::THREADS, smem, s>>>(a);
   MFX_CUDA_TRY(cudaGetLastError());
@@ -239,10 +236,11 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
   a.n_batches = a.nchunk * op->ny * op->nz;
   a.err = op->d_err;
   a.skip = skip;
+  a.dmask = op->dirichlet;
   MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
   const int rows = a.My * a.Mz;
   boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
-      a.Mx, a.My, a.Mz, src, dst);
+      a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
   kern<<<grid, Ps::THREADS, smem, s>>>(a);
   MFX_CUDA_TRY(cudaGetLastError());
@@ -259,13 +257,13 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
       if (CB1 != CB0 && op->metric_cb == CB1) return run_brick<N, double, CB1>(op, (const double*)src, (double*)dst, s, skip);
       return run_brick<N, double, CB0>(op, (const double*)src, (double*)dst, s, skip);
     }
-    return run_vmult<N, double, false>(op, (const double*)src, (double*)dst, s, skip);
+    return run_vmult<N, double>(op, (const double*)src, (double*)dst, s, skip);
   }
   if (op->structured) {
     if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
     return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
-  return run_vmult<N, float, false>(op, (const float*)src, (float*)dst, s, skip);
+  return run_vmult<N, float>(op, (const float*)src, (float*)dst, s, skip);
 }
 
 }  // namespace mfx

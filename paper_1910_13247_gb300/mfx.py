@@ -13,10 +13,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmfx.so")
 
 F64, F32 = 0, 1
-COEF_CONSTANT, COEF_TRIG, COEF_QPOINT = 0, 1, 2
+COEF_CONSTANT, COEF_TRIG, COEF_QPOINT, COEF_FUNCTION = 0, 1, 2, 3
 PRECOND_JACOBI, PRECOND_CHEBYSHEV = 0, 1
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, EMESH, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 NOT_CONVERGED, BREAKDOWN = 1, 2
+FACE_X0, FACE_X1, FACE_Y0, FACE_Y1, FACE_Z0, FACE_Z1, FACES_ALL = 1, 2, 4, 8, 16, 32, 63
 
 
 class MfxError(RuntimeError):
@@ -25,11 +26,20 @@ class MfxError(RuntimeError):
         self.code = code
 
 
+POINT_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+MAP_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
+def point_fn(f):
+    """Wrap f(x, y, z) -> float as an mfx_point_fn (keep the result alive while the library may call it)."""
+    return POINT_FN(lambda x, _user: float(f(x[0], x[1], x[2])))
+
+
 class OpDesc(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("coef_kind", ctypes.c_int32),
                 ("precisions", ctypes.c_int32), ("coef_par", ctypes.c_double * 2),
                 ("coef_qpoint", ctypes.c_void_p), ("cells_per_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("coef_fn", POINT_FN), ("coef_user", ctypes.c_void_p)]
 
 
 class OpInfo(ctypes.Structure):
@@ -107,6 +117,10 @@ def lib():
         "mfx_mesh_create_structured": (S, [ctypes.POINTER(_VP), S, S, S, _VP]),
         "mfx_mesh_create_octree": (S, [ctypes.POINTER(_VP), S, S, S, _VP, _VP, ctypes.c_int64]),
         "mfx_mesh_destroy": (None, [_VP]),
+        "mfx_mesh_transform": (S, [_VP, MAP_FN, _VP]),
+        "mfx_mesh_set_dirichlet": (S, [_VP, ctypes.c_uint32]),
+        "mfx_mesh_get_dirichlet": (S, [_VP, ctypes.POINTER(ctypes.c_uint32)]),
+        "mfx_rhs_function": (S, [_VP, POINT_FN, _VP, _VP, _VP]),
         "mfx_mesh_table_sizes": (S, [_VP, S, _VP, _VP, _VP, _VP]),
         "mfx_mesh_tables": (S, [_VP, S, _VP, _VP, _VP, _VP, _VP]),
         "mfx_operator_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), _VP]),
@@ -191,7 +205,7 @@ class Mesh:
         self.structured = structured
 
     @classmethod
-    def structured_box(cls, nx, ny, nz, vertices=None):
+    def structured_box(cls, nx, ny, nz, vertices=None, dirichlet=FACES_ALL):
         h = ctypes.c_void_p()
         v = None
         if vertices is not None:
@@ -199,22 +213,39 @@ class Mesh:
             assert v.size == 3 * (nx + 1) * (ny + 1) * (nz + 1)
         check(lib().mfx_mesh_create_structured(ctypes.byref(h), nx, ny, nz,
                                                v.ctypes.data_as(_VP) if v is not None else None))
-        return cls(h, True)
+        return cls(h, True).set_dirichlet(dirichlet)
 
     @classmethod
-    def octree(cls, nx, ny, nz, leaves, coarse_vertices=None):
+    def octree(cls, nx, ny, nz, leaves, coarse_vertices=None, dirichlet=FACES_ALL):
         h = ctypes.c_void_p()
         lv = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 4)
         v = None if coarse_vertices is None else np.ascontiguousarray(coarse_vertices, dtype=np.float64)
         check(lib().mfx_mesh_create_octree(ctypes.byref(h), nx, ny, nz,
                                            v.ctypes.data_as(_VP) if v is not None else None,
                                            lv.ctypes.data_as(_VP), lv.shape[0]))
-        return cls(h, False)
+        return cls(h, False).set_dirichlet(dirichlet)
+
+    def set_dirichlet(self, faces):
+        """Dirichlet faces as a bit mask (FACE_X0 | FACE_X1 | ...); the others are natural boundaries."""
+        check(lib().mfx_mesh_set_dirichlet(self.handle, faces))
+        return self
+
+    def dirichlet(self):
+        f = ctypes.c_uint32()
+        check(lib().mfx_mesh_get_dirichlet(self.handle, ctypes.byref(f)))
+        return f.value
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.mfx_mesh_destroy(self.handle)
             self.handle = None
+
+    def transform(self, phi):
+        """Move every (coarse) vertex v to phi(x, y, z) -> (x', y', z'), on the host (mfx_mesh_transform)."""
+        def call(inp, out, _user):
+            out[0], out[1], out[2] = phi(inp[0], inp[1], inp[2])
+        check(lib().mfx_mesh_transform(self.handle, MAP_FN(call), None))
+        return self
 
     def tables(self, degree):
         """DoF and constraint tables at degree k, computed on the host (no GPU needed)."""
@@ -237,8 +268,11 @@ class Operator:
     """The condensed Q_k operator of one mesh (geometry and tables on the device)."""
 
     def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), precisions=3,
-                 coef_qpoint=None, stream=None, cells_per_block=0):
+                 coef_qpoint=None, stream=None, cells_per_block=0, coef_fn=None):
         d = OpDesc()
+        if coef_fn is not None:  # a(x, y, z) on the host at every quadrature point
+            coef_kind = COEF_FUNCTION
+            d.coef_fn = point_fn(coef_fn)
         d.degree = degree
         d.n_q_1d = 0
         d.coef_kind = coef_kind
@@ -319,6 +353,11 @@ class Operator:
 
     def rhs(self, fq, b):
         check(lib().mfx_rhs(self.handle, _ptr(fq), _ptr(b), _stream()))
+        return b
+
+    def rhs_function(self, f, b):
+        """Load vector of a host function f(x, y, z), evaluated at the quadrature points (mfx_rhs_function)."""
+        check(lib().mfx_rhs_function(self.handle, point_fn(f), None, _ptr(b), _stream()))
         return b
 
     def distribute(self, x, stream=None):

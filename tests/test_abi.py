@@ -107,3 +107,30 @@ def test_bad_degree_rejected():
     with pytest.raises(mfx.MfxError) as e:
         m.tables(9)
     assert e.value.code == mfx.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("faces", [0, 0b000011, 0b110100, 0b101010])
+def test_tables_with_dirichlet_face_masks_bit_exact(faces):
+    """Dirichlet on a subset of the box faces: the constrained set and the hanging constraints (masters
+    on natural faces kept, masters on Dirichlet faces dropped) match the oracle bit for bit."""
+    T = mfx.Mesh.structured_box(4, 3, 2, dirichlet=faces).tables(2)
+    om = omesh.structured_mesh(4, 3, 2, 2, dirichlet=faces)
+    assert np.array_equal(T["constrained"], om.constrained) and np.array_equal(T["cell_dofs"], om.cell_dofs)
+    # closed form: lattice points on no Dirichlet face
+    Mx, My, Mz = 9, 7, 5
+    free = 1
+    for M, b in ((Mx, 0), (My, 2), (Mz, 4)):
+        free *= M - (faces >> b & 1) - (faces >> (b + 1) & 1)
+    assert len(T["constrained"]) == Mx * My * Mz - free
+    # the refined ball touches the x = 0 and y = 0 faces of the box
+    leaves = synthetic.octree_leaves(3, 2, np.array([0.15, 0.2, 0.5]), 0.3)
+    for k in (1, 3):
+        T = mfx.Mesh.octree(3, 3, 3, leaves, dirichlet=faces).tables(k)
+        om = omesh.octree_mesh(3, 3, 3, k, leaves, dirichlet=faces)
+        assert T["n_dofs"] == om.n_dofs
+        assert np.array_equal(T["constrained"], om.constrained)
+        assert np.array_equal(T["cptr"], om.cptr)
+        assert np.array_equal(T["cmaster"], om.cmaster)
+        assert np.array_equal(T["cweight"], om.cweight)
+    with pytest.raises(mfx.MfxError):
+        mfx.Mesh.structured_box(2, 2, 2, dirichlet=64)

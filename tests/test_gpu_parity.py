@@ -299,3 +299,93 @@ def test_solver_statuses(mfx):
     z = torch.zeros_like(bd)
     st = op.solve(z, x, tol=1e-10)
     assert st["status"] == 0 and torch.count_nonzero(x).item() == 0
+
+
+def test_mesh_transform_coefficient_and_rhs_functions(mfx):
+    """Geometry by a host map of the vertices (mfx_mesh_transform), the coefficient as a host function
+    (MFX_COEF_FUNCTION) and the load vector of a host function (mfx_rhs_function) give the operator and
+    right-hand side of the same problem set up from vertex arrays and closed-form kinds."""
+    import math
+
+    def phi(x, y, z):
+        d = 0.05 * math.sin(math.pi * x) * math.sin(math.pi * y) * math.sin(math.pi * z)
+        return x + d, y + d, z + d
+
+    def coef(x, y, z):
+        return 1.0 + 0.5 * math.sin(2 * math.pi * x) * math.cos(2 * math.pi * y) * z
+
+    nx, ny, nz, k = 4, 3, 3, 3
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 33)
+    ref = K @ x
+    op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz).transform(phi), k, coef_fn=coef)
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    # octree: the coarse lattice moves, leaves follow
+    leaves = synthetic.octree_leaves(3, 1, np.array([0.4, 0.5, 0.5]), 0.3)
+    oo = omesh.octree_mesh(3, 3, 3, 2, leaves, synthetic.deformed_vertices(3, 3, 3))
+    Ko = fem.assemble(oo, 3, fem.COEF_TRIG, (1.0, 0.5))
+    xo = synthetic.uniform_vector(oo.n_dofs, 34)
+    opo = mfx.Operator(mfx.Mesh.octree(3, 3, 3, leaves).transform(phi), 2, coef_fn=coef)
+    e2, einf = rel_err(run_vmult(opo, xo, torch.float64), Ko @ xo)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+
+    # load vector of f(x) = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) against the oracle's
+    def f(x, y, z):
+        return 3 * math.pi ** 2 * math.sin(math.pi * x) * math.sin(math.pi * y) * math.sin(math.pi * z)
+
+    b = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.rhs_function(f, b)
+    Xq, _ = fem.quadrature_points(om, k + 1)
+    fq = np.array([f(*p) for p in Xq.reshape(-1, 3)]).reshape(op.n_cells, (k + 1) ** 3)
+    e2, einf = rel_err(b.cpu().numpy(), fem.rhs(om, k + 1, fq=fq))
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+
+
+@pytest.mark.parametrize("faces", [0, 0b000011, 0b110100, 0b011001])
+def test_dirichlet_face_masks(mfx, faces):
+    """Dirichlet on a subset of the faces (natural boundaries elsewhere): FP64 / FP32 vmult of both
+    structured batch layouts and of an octree with hanging nodes, the diagonal and (with at least one
+    Dirichlet face) a PCG solve, against the oracle's operator built with the same mask."""
+    nx, ny, nz, k = 13, 3, 2, 3  # rows not a multiple of either batch size
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts, dirichlet=faces)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 50)
+    ref = K @ x
+    dref = fem.diagonal(K)
+    for cb in (8, 16):
+        op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz, verts, dirichlet=faces), k, mfx.COEF_TRIG, (1.0, 0.5),
+                          cells_per_block=cb)
+        assert op.info()["n_constrained"] == len(om.constrained)
+        e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+        assert e2 < 1e-12 and einf < 1e-12, (cb, e2, einf)
+        assert rel_err(run_vmult(op, x, torch.float32), ref)[0] < 1e-5
+        d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+        op.diagonal(d)
+        assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max(), cb
+    if faces:
+        b = synthetic.uniform_vector(om.n_dofs, 51)
+        b[om.constrained] = 0.0
+        bd = torch.tensor(b, device=DEV)
+        xs = torch.zeros_like(bd)
+        st = op.solve(bd, xs, tol=1e-10)
+        assert st["status"] == 0
+        assert np.linalg.norm(b - K @ xs.cpu().numpy()) <= 1.0001e-10 * np.linalg.norm(b)
+    # octree: the refined ball touches the x = 0 and y = 0 faces
+    leaves = synthetic.octree_leaves(3, 1, np.array([0.15, 0.2, 0.5]), 0.3)
+    ov = synthetic.deformed_vertices(3, 3, 3)
+    oo = omesh.octree_mesh(3, 3, 3, 2, leaves, ov, dirichlet=faces)
+    Ko = fem.assemble(oo, 3, fem.COEF_TRIG, (1.0, 0.5))
+    xo = synthetic.uniform_vector(oo.n_dofs, 52)
+    opo = mfx.Operator(mfx.Mesh.octree(3, 3, 3, leaves, ov, dirichlet=faces), 2, mfx.COEF_TRIG, (1.0, 0.5))
+    e2, einf = rel_err(run_vmult(opo, xo, torch.float64), Ko @ xo)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    d = torch.empty(opo.n_dofs, dtype=torch.float64, device=DEV)
+    opo.diagonal(d)
+    assert np.abs(d.cpu().numpy() - fem.diagonal(Ko)).max() < 1e-12 * np.abs(fem.diagonal(Ko)).max()
+    xs = torch.tensor(xo, device=DEV)
+    opo.distribute(xs)
+    assert np.abs(xs.cpu().numpy() - fem.distribute(oo, xo)).max() < 1e-14

@@ -302,3 +302,40 @@ def test_defect_correction_reaches_fp64_solution():
     assert np.linalg.norm(b - K @ res.x) <= 1e-10 * np.linalg.norm(b)
     xd = spla.spsolve(K.tocsc(), b)
     assert np.linalg.norm(res.x - xd) < 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("kind", ["structured", "octree"])
+def test_pure_neumann_operator_annihilates_constants(kind):
+    """With no Dirichlet face the weak Laplacian of a constant vanishes for any geometry and coefficient:
+    C^T A C applied to the constant free vector is zero (hanging interpolation reproduces constants)."""
+    if kind == "structured":
+        m = mesh.structured_mesh(3, 3, 2, 2, synthetic.deformed_vertices(3, 3, 2), dirichlet=0)
+        assert len(m.constrained) == 0
+    else:
+        leaves = synthetic.octree_leaves(3, 1, np.array([0.3, 0.4, 0.5]), 0.3)
+        m = mesh.octree_mesh(3, 3, 3, 2, leaves, synthetic.deformed_vertices(3, 3, 3), dirichlet=0)
+        assert len(m.constrained) > 0 and all(m.cptr[1:] > m.cptr[:-1])  # hanging rows only
+    K = fem.assemble(m, 3, fem.COEF_TRIG, (1.0, 0.5))
+    v = np.ones(m.n_dofs)
+    v[m.constrained] = 0.0
+    r = K @ v
+    assert np.abs(r).max() < 1e-12 * abs(K).max()
+    assert abs(K - K.T).max() < 1e-14 * abs(K).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_mixed_boundary_manufactured_convergence(k):
+    """Dirichlet on the x faces only, natural boundaries elsewhere: u = sin(pi x) solves -lap u = pi^2 sin(pi x)
+    with zero normal derivative on the y and z faces (the deformation keeps every face of the box in
+    place), so the L2 error falls at the optimal rate k + 1."""
+    sizes = (2, 4, 8) if k < 3 else (2, 4, 6)
+    errs = []
+    for nx in sizes:
+        m = mesh.structured_mesh(nx, nx, nx, k, synthetic.deformed_vertices(nx, nx, nx), dirichlet=0b11)
+        X, _ = fem.quadrature_points(m, k + 1)
+        fq = np.pi ** 2 * np.sin(np.pi * X[..., 0])
+        K = fem.assemble(m, k + 1)
+        x = spla.spsolve(K.tocsc(), fem.rhs(m, k + 1, fq=fq))
+        errs.append(fem.l2_error(m, x, exact="sinx"))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(sizes[i + 1] / sizes[i]) for i in range(len(errs) - 1)]
+    assert rates[-1] > k + 1 - 0.35, (errs, rates)
