@@ -298,7 +298,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": measured_traffic(nx, kdeg, op.info()["cells_per_block"]), "peak_kind": peak_kind,
-                     "kernel": "FP32 vmult (boundary_rows_kernel + brick_vmult_tma2_kernel), timed together",
+                     "kernel": "FP32 vmult (init_rows_kernel + brick_vmult_tma2_kernel), timed together",
                      "algorithmic_bytes": b32},
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": ms_e2e},

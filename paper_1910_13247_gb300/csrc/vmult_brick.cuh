@@ -33,7 +33,7 @@ namespace mfx {
 // cells per batch for each n (= k + 1)
 template <int N> struct BrickCB {
   static constexpr int value = N == 2 ? 32 : (N <= 7 ? 16 : 8);  // default
-  static constexpr int ALT = (N == 4 || N == 5) ? 8 : 0;          // second compiled choice (0: none)
+  static constexpr int ALT = (N == 4 || N == 5) ? 8 : N == 3 ? 32 : 0;  // second compiled choice (0: none)
 };
 
 template <int N, int CB, typename Real>
@@ -85,12 +85,34 @@ struct BatchInfo {
   bool xlo, xhi;
 };
 
-template <int CB, int K, typename Args>
-__device__ __forceinline__ BatchInfo batch_info(const Args& a, int b) {
-  BatchInfo bi;
-  const int chunk = b % a.nchunk;
+// Position of batch b: chunk of its row of cells, and the row (cy, cz).
+struct BatchPos {
+  int chunk, cy, cz;
+};
+
+template <typename Args>
+__device__ __forceinline__ BatchPos batch_pos(const Args& a, int b) {
   const int row = b / a.nchunk;
-  const int cy = row % a.ny, cz = row / a.ny;
+  return BatchPos{b - row * a.nchunk, row % a.ny, row / a.ny};
+}
+
+// Advance a position by the grid size (a.step_* = the grid size split as chunk, y, z), with carries
+// instead of the divisions of batch_pos.
+template <typename Args>
+__device__ __forceinline__ void batch_advance(BatchPos& p, const Args& a) {
+  p.chunk += a.step_chunk;
+  const int c1 = p.chunk >= a.nchunk ? 1 : 0;
+  p.chunk -= c1 * a.nchunk;
+  p.cy += a.step_y + c1;
+  const int c2 = p.cy >= a.ny ? 1 : 0;
+  p.cy -= c2 * a.ny;
+  p.cz += a.step_z + c2;
+}
+
+template <int CB, int K, typename Args>
+__device__ __forceinline__ BatchInfo batch_info_at(const Args& a, const BatchPos& p) {
+  BatchInfo bi;
+  const int chunk = p.chunk, cy = p.cy, cz = p.cz;
   bi.cx0 = chunk * CB;
   bi.m = min(CB, a.nx - bi.cx0);
   bi.Wm = bi.m * K + 1;
@@ -101,6 +123,11 @@ __device__ __forceinline__ BatchInfo batch_info(const Args& a, int b) {
   bi.eflags = (cy == 0 && (f & 4u) ? 1 : 0) | (cy == a.ny - 1 && (f & 8u) ? 2 : 0) | (cz == 0 && (f & 16u) ? 4 : 0) |
               (cz == a.nz - 1 && (f & 32u) ? 8 : 0);
   return bi;
+}
+
+template <int CB, int K, typename Args>
+__device__ __forceinline__ BatchInfo batch_info(const Args& a, int b) {
+  return batch_info_at<CB, K>(a, batch_pos(a, b));
 }
 
 template <typename Real>

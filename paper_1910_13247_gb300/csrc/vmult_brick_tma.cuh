@@ -44,6 +44,7 @@ struct TmaArgs {
   int* err;               // set to 1 if a bounded wait ran out
   const int32_t* skip;
   uint32_t dmask;         // Dirichlet faces
+  int step_chunk, step_y, step_z;  // the grid size as (chunk, y, z) steps of batch positions
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -96,9 +96,10 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   fence_proxy_async();
   __syncthreads();
 
-  // TMA warp: copies of batch bb into input tile buffer `buf`, lane l issues rows l, l + 32, ...
-  auto issue_loads = [&](int bb, int buf) {
-    const BatchInfo bi = batch_info<CB, K>(a, bb);
+  // TMA warp: copies of the batch at position pb into input tile buffer `buf`, lane l issues rows
+  // l, l + 32, ...
+  auto issue_loads = [&](const BatchPos& pb, int buf) {
+    const BatchInfo bi = batch_info_at<CB, K>(a, pb);
     fence_proxy_async();
     if (lane == 0) mbar_arrive_expect_tx(&bars[buf], ROWS * BOX * 4);
     __syncwarp();
@@ -112,11 +113,13 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
 
   int it = 0;
   bool failed = false, next_issued = false;
-  if (tma_warp && (int)blockIdx.x < a.n_batches) issue_loads(blockIdx.x, 0);
+  BatchPos pos = batch_pos(a, blockIdx.x), next = pos;
+  batch_advance(next, a);
+  if (tma_warp && (int)blockIdx.x < a.n_batches) issue_loads(pos, 0);
 
   for (int b = blockIdx.x; b < a.n_batches; b += gridDim.x, ++it) {
     const int buf = it & 1;
-    const BatchInfo bi = batch_info<CB, K>(a, b);
+    const BatchInfo bi = batch_info_at<CB, K>(a, pos);
     const int m = bi.m;
     const bool act = line_ok && 2 * c < m;       // first cell of the pair valid
     const bool act1 = line_ok && 2 * c + 1 < m;  // second cell valid
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
     const bool zlo = (bi.eflags & 4) != 0, zhi = (bi.eflags & 8) != 0;
 
     next_issued = b + (int)gridDim.x < a.n_batches;
-    if (tma_warp && next_issued) issue_loads(b + gridDim.x, buf ^ 1);
+    if (tma_warp && next_issued) issue_loads(next, buf ^ 1);
     float2 G[PREFETCH ? 6 : 1][N];
     if (PREFETCH && act) {
 #pragma unroll
@@ -324,6 +327,8 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
       }
       bulk_commit();
     }
+    pos = next;
+    batch_advance(next, a);
   }
   if (tma_warp) bulk_wait_all();
   if (failed) {

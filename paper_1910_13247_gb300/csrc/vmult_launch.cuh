@@ -119,25 +119,36 @@ int brick_cells_candidates(int* out) {
   return 1;
 }
 
-// dst = src on the Dirichlet DoFs (faces in dmask); one warp per lattice row (J, L).
+// Initial dst of the reduce-add kernels, in one pass: src on the Dirichlet DoFs (faces in dmask, the
+// identity rows of the operator), 0 elsewhere.  One warp per lattice row (J, L).
 template <typename Real>
-__global__ void boundary_rows_kernel(int Mx, int My, int Mz, uint32_t dmask, const Real* __restrict__ src,
-                                     Real* __restrict__ dst) {
+__global__ void init_rows_kernel(int Mx, int My, int Mz, uint32_t dmask, const Real* __restrict__ src,
+                                 Real* __restrict__ dst) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int rows = My * Mz;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
     const int J = row % My, L = row / My;
     const int64_t base = (int64_t)Mx * row;
-    if (((dmask & 4u) && J == 0) || ((dmask & 8u) && J == My - 1) || ((dmask & 16u) && L == 0) ||
-        ((dmask & 32u) && L == Mz - 1)) {
-      for (int I = lane; I < Mx; I += 32) dst[base + I] = src[base + I];
-    } else if (lane == 0) {
-      if (dmask & 1u) dst[base] = src[base];
-      if (dmask & 2u) dst[base + Mx - 1] = src[base + Mx - 1];
+    const bool whole = ((dmask & 4u) && J == 0) || ((dmask & 8u) && J == My - 1) || ((dmask & 16u) && L == 0) ||
+                       ((dmask & 32u) && L == Mz - 1);
+    for (int I = lane; I < Mx; I += 32) {
+      const bool d = whole || ((dmask & 1u) && I == 0) || ((dmask & 2u) && I == Mx - 1);
+      dst[base + I] = d ? src[base + I] : Real(0);
     }
   }
 }
+
+// The grid size as a step of batch positions (chunk, y, z) for batch_advance.
+template <int N>
+static void set_batch_steps(TmaArgs<N>* a, int grid) {
+  const int row = grid / a->nchunk;
+  a->step_chunk = grid - row * a->nchunk;
+  a->step_y = row % a->ny;
+  a->step_z = row / a->ny;
+}
+
+static int init_rows_grid(int rows) { return std::max(1, std::min((rows + 7) / 8, device_sm_count() * 16)); }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -196,11 +207,10 @@ static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, 
   a.err = op->d_err;
   a.skip = skip;
   a.dmask = op->dirichlet;
-  MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
   const int rows = a.My * a.Mz;
-  boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
-      a.Mx, a.My, a.Mz, a.dmask, src, dst);
+  init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
+  set_batch_steps(&a, grid);
   kern<<<grid, Sh::THREADS, smem, s>>>(a);
   MFX_CUDA_TRY(cudaGetLastError());
   return MFX_OK;
@@ -237,11 +247,10 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
   a.err = op->d_err;
   a.skip = skip;
   a.dmask = op->dirichlet;
-  MFX_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(float) * op->n_dofs, s));
   const int rows = a.My * a.Mz;
-  boundary_rows_kernel<float><<<std::max(1, std::min((rows + 7) / 8, device_sm_count() * 8)), 256, 0, s>>>(
-      a.Mx, a.My, a.Mz, a.dmask, src, dst);
+  init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
+  set_batch_steps(&a, grid);
   kern<<<grid, Ps::THREADS, smem, s>>>(a);
   MFX_CUDA_TRY(cudaGetLastError());
   return MFX_OK;
