@@ -39,9 +39,9 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 # DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
 # profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case, 16 cells per batch, scaled by cells).  Valid only for
 # that batch size and the kernel sources it was taken from: anything else reports null.
-TRAFFIC_BYTES = 978.2e6
-TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "36f19fc9197e5734", "vmult_brick_tma.cuh": "50cedac7d8f2e8a9",
-                   "vmult_brick.cuh": "f053cbb95aed5d25", "vmult.cuh": "d3511f8f3650319c"}
+TRAFFIC_BYTES = 979.3e6
+TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "6216e946f456fec0", "vmult_brick_tma.cuh": "8333bd9d80bf4ab6",
+                   "vmult_brick.cuh": "bbb92b0ed289ae99", "vmult.cuh": "681d7f586882a616"}
 
 
 def measured_traffic(nx, k, cells_per_block):

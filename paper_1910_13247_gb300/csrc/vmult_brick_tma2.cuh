@@ -113,8 +113,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
 
   int it = 0;
   bool failed = false, next_issued = false;
-  BatchPos pos = batch_pos(a, blockIdx.x), next = pos;
-  batch_advance(next, a);
+  BatchPos pos = batch_pos(a, blockIdx.x);
   if (tma_warp && (int)blockIdx.x < a.n_batches) issue_loads(pos, 0);
 
   for (int b = blockIdx.x; b < a.n_batches; b += gridDim.x, ++it) {
@@ -136,7 +135,11 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
     const bool zlo = (bi.eflags & 4) != 0, zhi = (bi.eflags & 8) != 0;
 
     next_issued = b + (int)gridDim.x < a.n_batches;
-    if (tma_warp && next_issued) issue_loads(next, buf ^ 1);
+    if (tma_warp && next_issued) {
+      BatchPos next = pos;
+      batch_advance(next, a);
+      issue_loads(next, buf ^ 1);
+    }
     float2 G[PREFETCH ? 6 : 1][N];
     if (PREFETCH && act) {
 #pragma unroll
@@ -327,8 +330,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
       }
       bulk_commit();
     }
-    pos = next;
-    batch_advance(next, a);
+    batch_advance(pos, a);
   }
   if (tma_warp) bulk_wait_all();
   if (failed) {
