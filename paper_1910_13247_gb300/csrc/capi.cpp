@@ -172,6 +172,20 @@ static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kin
   return MFX_OK;
 }
 
+int octree_pair_cells_for_degree(int k) {
+  switch (k + 1) {
+    case 2: return octree_pair_cells<2>();
+    case 3: return octree_pair_cells<3>();
+    case 4: return octree_pair_cells<4>();
+    case 5: return octree_pair_cells<5>();
+    case 6: return octree_pair_cells<6>();
+    case 7: return octree_pair_cells<7>();
+    case 8: return octree_pair_cells<8>();
+    case 9: return octree_pair_cells<9>();
+    default: return 0;
+  }
+}
+
 int brick_cells_for_degree(int k) {
   switch (k + 1) {
     case 2: return brick_cells_per_batch<2>();
@@ -488,8 +502,18 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     op->nchunk = (op->nx + cand[0] - 1) / cand[0];
   }
   // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
+  size_t metric32_entries = metric_entries;
+  if (!op->structured) {
+    // octree FP32 metric in runs of the paired kernel's batch size (the last run padded)
+    // (0: the per-cell kernel's [cell][6][q] layout)
+    op->metric_cb32 = octree_pair_cells_for_degree(k);
+    if (op->metric_cb32 > 0) {
+      const size_t nb = (size_t)(op->n_cells + op->metric_cb32 - 1) / op->metric_cb32;
+      metric32_entries = nb * op->metric_cb32 * 6 * n3;
+    }
+  }
   MFX_TRY(dev_alloc(op, &op->d_metric64, metric_entries, s));
-  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, metric_entries, s));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_metric32, metric32_entries, s));
   MFX_TRY(dev_alloc(op, &op->d_jxw, nq, s));
   MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs), s));
   if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs), s));
@@ -551,7 +575,7 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   info->degree = op->k;
   info->n_q_1d = op->n;
   info->structured = op->structured ? 1 : 0;
-  info->cells_per_block = op->structured ? op->metric_cb : 256 / (op->n * op->n);
+  info->cells_per_block = op->structured ? op->metric_cb : (op->metric_cb32 > 0 ? op->metric_cb32 : 256 / (op->n * op->n));
   return MFX_OK;
 }
 

@@ -26,23 +26,34 @@ struct GeoArgs {
   double par0, par1;
   const double* coef_q;
   int cb, nchunk;  // metric layout: cb = 0 -> [cell][6][q]; else [batch][6][q][cb] (structured rows)
+  int cb32;        // FP32 copy: as cb (structured); octree: 0, or [cell / cb32][6][q][cb32] (runs of cells)
 };
 
-// Offset of metric entry (cell, 0, q); entry e is at offset + e * metric_stride(g).
-__device__ __forceinline__ int64_t metric_offset(const GeoArgs& g, int64_t cell, int q) {
+// Offset of metric entry (cell, 0, q) in the layout of batch size cb; entry e is at
+// offset + e * metric_stride_cb(g, cb).
+__device__ __forceinline__ int64_t metric_offset_cb(const GeoArgs& g, int64_t cell, int q, int cb) {
   const int n3 = g.n * g.n * g.n;
-  if (g.cb == 0) return cell * 6 * n3 + q;
+  if (cb == 0) return cell * 6 * n3 + q;
+  if (!g.structured) {
+    const int64_t batch = cell / cb;
+    return (batch * 6 * n3 + q) * cb + (cell - batch * cb);
+  }
   const int cx = (int)(cell % g.nx);
   const int64_t rest = cell / g.nx;
   const int cy = (int)(rest % g.ny), cz = (int)(rest / g.ny);
-  const int chunk = cx / g.cb, c = cx - chunk * g.cb;
+  const int chunk = cx / cb, c = cx - chunk * cb;
   const int64_t batch = chunk + (int64_t)g.nchunk * (cy + (int64_t)g.ny * cz);
-  return (batch * 6 * n3 + q) * g.cb + c;
+  return (batch * 6 * n3 + q) * cb + c;
 }
-__device__ __forceinline__ int64_t metric_stride(const GeoArgs& g) {
+__device__ __forceinline__ int64_t metric_stride_cb(const GeoArgs& g, int cb) {
   const int n3 = g.n * g.n * g.n;
-  return g.cb == 0 ? (int64_t)n3 : (int64_t)n3 * g.cb;
+  return cb == 0 ? (int64_t)n3 : (int64_t)n3 * cb;
 }
+// The FP64 metric's layout.
+__device__ __forceinline__ int64_t metric_offset(const GeoArgs& g, int64_t cell, int q) {
+  return metric_offset_cb(g, cell, q, g.cb);
+}
+__device__ __forceinline__ int64_t metric_stride(const GeoArgs& g) { return metric_stride_cb(g, g.cb); }
 
 __device__ __forceinline__ void cell_vertices(const GeoArgs& g, int64_t cell, double V[8][3]) {
   if (g.structured) {
@@ -132,9 +143,10 @@ __global__ void geometry_kernel(const __grid_constant__ GeoArgs g, double* __res
       G[e] = f * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
     }
     const int64_t base = metric_offset(g, cell, q), st = metric_stride(g);
+    const int64_t base32 = metric_offset_cb(g, cell, q, g.cb32), st32 = metric_stride_cb(g, g.cb32);
     for (int e = 0; e < 6; ++e) {
       if (m64) m64[base + e * st] = G[e];
-      if (m32) m32[base + e * st] = (float)G[e];
+      if (m32) m32[base32 + e * st32] = (float)G[e];
     }
     if (jxw) jxw[idx] = dx;
   }
@@ -443,6 +455,7 @@ static GeoArgs geo_args(const mfx_op* op) {
   g.coef_q = nullptr;
   g.cb = op->metric_cb;
   g.nchunk = op->nchunk;
+  g.cb32 = op->structured ? op->metric_cb : op->metric_cb32;
   return g;
 }
 

@@ -95,6 +95,7 @@ struct mfx_op {
   int cells_per_block = 0;
   int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)
   int nchunk = 0;                     // structured: batches per row of cells
+  int metric_cb32 = 0;                // octree FP32 metric: 0 [cell][6][q]; > 0 [cell / cb][6][q][cb]
   bool has_f64 = false, has_f32 = false;
   mfx::BasisTables basis;
   // host tables (octree) or empty (structured)
@@ -146,6 +147,9 @@ mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* 
                         const int32_t* skip = nullptr);
 template <int N>
 int brick_cells_per_batch();
+// FP32 octree metric layout: cells per run for the paired kernel, 0 for the per-cell kernel.
+template <int N>
+int octree_pair_cells();
 template <int N>
 int brick_cells_candidates(int* out);
 int brick_cells_candidates_for_degree(int k, int* out);
@@ -153,6 +157,7 @@ template <int N>
 mfx_status prepare_vmult_n(const mfx_op* op);
 mfx_status prepare_vmult(const mfx_op* op);
 int brick_cells_for_degree(int k);
+int octree_pair_cells_for_degree(int k);
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip);

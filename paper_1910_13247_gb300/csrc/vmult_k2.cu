@@ -7,6 +7,7 @@ namespace mfx {
 template mfx_status launch_vmult_n<3>(const mfx_op*, mfx_prec, const void*, void*, cudaStream_t,
                                            const int32_t*);
 template int brick_cells_per_batch<3>();
+template int octree_pair_cells<3>();
 template mfx_status prepare_vmult_n<3>(const mfx_op*);
 template int brick_cells_candidates<3>(int*);
 }  // namespace mfx

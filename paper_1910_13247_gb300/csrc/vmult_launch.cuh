@@ -11,6 +11,7 @@
 #include "vmult_brick_tma.cuh"
 #include "vmult_brick_df.cuh"
 #include "vmult_brick_tma2.cuh"
+#include "vmult_octree2.cuh"
 
 namespace mfx {
 
@@ -106,6 +107,9 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
 
 template <int N>
 int brick_cells_per_batch() { return BrickCB<N>::value; }
+
+template <int N>
+int octree_pair_cells() { return OctreePairFor<N>::value ? BrickCB<N>::value : 0; }
 
 // Batch sizes (cells per batch) compiled for degree N - 1, default first; the operator picks one
 // by timing (autotuning) or takes the caller's choice.
@@ -256,6 +260,45 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
   return MFX_OK;
 }
 
+template <int N, int CB>
+static mfx_status run_octree_pair(const mfx_op* op, const float* src, float* dst, cudaStream_t s,
+                                  const int32_t* skip) {
+  using Ps = PairShape<N, CB>;
+  using Os = OctreePairShape<N, CB>;
+  static int blocks_per_sm = -1;
+  const size_t smem = Os::SMEM;
+  auto kern = octree_vmult_pair_kernel<N, CB>;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Ps::THREADS, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  if (op->metric_cb32 != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
+  VmultArgs<N, float> pa;
+  fill_vmult_args<N, float>(op, &pa);
+  pa.skip = skip;
+  const int sms = device_sm_count();
+  int pb = (int)std::min<int64_t>((op->n_dofs + 255) / 256, (int64_t)sms * 8);
+  if (pb < 1) pb = 1;
+  vmult_prologue<N, float><<<pb, 256, 0, s>>>(pa, src, dst);
+  OctreePairArgs<N> a;
+  a.metric = op->d_metric32;
+  a.cell_dofs = op->d_cell_dofs;
+  a.cptr = op->d_cptr;
+  a.cmaster = op->d_cmaster;
+  a.cweight = op->d_cweight32;
+  a.n_cells = op->n_cells;
+  a.n_batches = (int)((op->n_cells + CB - 1) / CB);
+  a.skip = skip;
+  if (a.n_batches > 0) {
+    const int grid = std::min(a.n_batches, sms * blocks_per_sm);
+    kern<<<grid, Ps::THREADS, smem, s>>>(a, src, dst);
+  }
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
 template <int N>
 mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                           const int32_t* skip) {
@@ -272,6 +315,7 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
     return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
+  if constexpr (OctreePairFor<N>::value) return run_octree_pair<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float>(op, (const float*)src, (float*)dst, s, skip);
 }
 

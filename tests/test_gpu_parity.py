@@ -153,8 +153,8 @@ def test_octree_vmult_with_hanging_nodes(mfx, k):
 
 @pytest.mark.parametrize("k", [5, 8])
 def test_octree_diagonal_high_degree(mfx, k):
-    """Diagonal on an octree at high degree: cells without hanging nodes take the sum-factorised
-    path (per-cell metric layout), cells with hanging nodes the pairwise one."""
+    """Diagonal and vmult on an octree at high degree: the diagonal's sum-factorised paths (cells with
+    and without hanging nodes) and both FP32 octree kernels."""
     leaves = synthetic.octree_leaves(2, 1, np.array([0.3, 0.3, 0.3]), 0.2)
     verts = synthetic.deformed_vertices(2, 2, 2)
     m = mfx.Mesh.octree(2, 2, 2, leaves, verts)
@@ -166,6 +166,12 @@ def test_octree_diagonal_high_degree(mfx, k):
     op.diagonal(d)
     dref = fem.diagonal(K)
     assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
+    # vmult at high degree (k = 8: the paired octree kernel in FP32; k = 5: the per-cell kernel)
+    x = synthetic.uniform_vector(om.n_dofs, 40 + k)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    assert rel_err(run_vmult(op, x, torch.float32), ref)[0] < 1e-5
 
 
 def test_single_cell_degenerate_meshes(mfx):
