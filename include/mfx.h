@@ -219,6 +219,18 @@ mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constra
  * Errors: MFX_EINVAL (null, precision not built), MFX_ECUDA (launch).
  */
 mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, mfx_stream stream);
+/*
+ * dst[i] = K src[i] for `count` vectors in HOST memory (pinned for full speed; pageable works,
+ * with staged copies).  The vectors go through a three-stage pipeline on the library's own streams:
+ * the upload of vector i + 1, the vmult of vector i and the download of vector i - 1 overlap, with
+ * double-buffered device staging (allocated stream-ordered per call).  The call waits for the
+ * work already queued on `stream` before it starts and returns once every result is in host
+ * memory.  src[i], dst[i]: n_dofs entries of the precision; no dst[i] may alias a src[j].
+ * No counterpart in the paper: this is the host-buffer path of the operator.
+ * Errors: MFX_EINVAL (null, count < 0, precision not built), MFX_ENOMEM, MFX_ECUDA.
+ */
+mfx_status mfx_vmult_host(const mfx_op* op, mfx_prec prec, int32_t count, const void* const* src,
+                          void* const* dst, mfx_stream stream);
 
 /*
  * Synchronise the stream and report device-side failures of this operator's

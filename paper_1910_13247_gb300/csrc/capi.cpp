@@ -678,6 +678,68 @@ mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst
   return launch_vmult(op, prec, src, dst, (cudaStream_t)stream);
 }
 
+mfx_status mfx_vmult_host(const mfx_op* op, mfx_prec prec, int32_t count, const void* const* src, void* const* dst,
+                          mfx_stream stream) {
+  if (!op || count < 0 || (count > 0 && (!src || !dst))) return set_error(MFX_EINVAL, "mfx_vmult_host: bad argument");
+  if ((prec == MFX_F64 && !op->has_f64) || (prec == MFX_F32 && !op->has_f32) || (prec != MFX_F64 && prec != MFX_F32))
+    return set_error(MFX_EINVAL, "mfx_vmult_host: precision not built for this operator");
+  if (count == 0) return MFX_OK;
+  for (int32_t i = 0; i < count; ++i)
+    if (!src[i] || !dst[i]) return set_error(MFX_EINVAL, "mfx_vmult_host: null vector");
+  const size_t bytes = (size_t)op->n_dofs * (prec == MFX_F64 ? sizeof(double) : sizeof(float));
+  // stages: upload (h2d), operator (cmp), download (d2h); buffers b = i mod 2
+  cudaStream_t h2d = nullptr, cmp = nullptr, d2h = nullptr;
+  cudaEvent_t ev[7] = {};
+  void* buf[4] = {};  // in0, in1, out0, out1
+  mfx_status st = MFX_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cmp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  // ev[0]: the caller's queued work; ev[1 + b]: input b uploaded; ev[3 + b]: vmult on buffers b done;
+  // ev[5 + b]: output b downloaded
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h2d, ev[0], 0);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMallocAsync(&buf[i], bytes, h2d);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[5], h2d);  // buffers exist before any stage uses them
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cmp, ev[5], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, ev[5], 0);
+  for (int32_t i = 0; i < count && e == cudaSuccess && st == MFX_OK; ++i) {
+    const int b = i & 1;
+    // upload i once the vmult of i - 2 has finished reading in[b]
+    if (i >= 2) e = cudaStreamWaitEvent(h2d, ev[3 + b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf[b], src[i], bytes, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + b], h2d);
+    // vmult i once its input is in and the download of i - 2 has read out[b]
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cmp, ev[1 + b], 0);
+    if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(cmp, ev[5 + b], 0);
+    if (e == cudaSuccess) st = launch_vmult(op, prec, buf[b], buf[2 + b], cmp);
+    if (e == cudaSuccess && st == MFX_OK) e = cudaEventRecord(ev[3 + b], cmp);
+    // download i
+    if (e == cudaSuccess && st == MFX_OK) e = cudaStreamWaitEvent(d2h, ev[3 + b], 0);
+    if (e == cudaSuccess && st == MFX_OK) e = cudaMemcpyAsync(dst[i], buf[2 + b], bytes, cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess && st == MFX_OK) e = cudaEventRecord(ev[5 + b], d2h);
+  }
+  // free the staging after every stage is done, then wait for the results
+  if (h2d && cmp && d2h) {
+    cudaEvent_t done_cmp = ev[3], done_d2h = ev[5];
+    if (cudaEventRecord(done_cmp, cmp) == cudaSuccess) cudaStreamWaitEvent(d2h, done_cmp, 0);
+    if (cudaEventRecord(done_d2h, h2d) == cudaSuccess) cudaStreamWaitEvent(d2h, done_d2h, 0);
+    for (int i = 0; i < 4; ++i)
+      if (buf[i]) cudaFreeAsync(buf[i], d2h);
+    const cudaError_t es = cudaStreamSynchronize(d2h);
+    if (e == cudaSuccess) e = es;
+  }
+  for (int i = 0; i < 7; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (h2d) cudaStreamDestroy(h2d);
+  if (cmp) cudaStreamDestroy(cmp);
+  if (d2h) cudaStreamDestroy(d2h);
+  if (st != MFX_OK) return st;
+  if (e != cudaSuccess) return cuda_error(e, "mfx_vmult_host");
+  return MFX_OK;
+}
+
 mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream) {
   if (!op) return set_error(MFX_EINVAL, "null operator");
   int h = 0;

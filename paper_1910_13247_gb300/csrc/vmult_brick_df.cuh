@@ -7,7 +7,9 @@
 // the end of each contraction.  Values are split into pairs when they are loaded (the 1D
 // matrices at compile time) and joined back to FP64 before they are added to dst.  All
 // arithmetic uses the round-to-nearest intrinsics, which the compiler never fuses, so the
-// error-free transformations stay exact.  The phases are those of brick_vmult_kernel.
+// error-free transformations stay exact.  The phases are those of the FP32 brick-row kernel
+// (vmult_brick_tma2.cuh), with the tile rows moved by 8-byte cp.async copies and the output tile
+// added to dst with coalesced FP64 atomics; Dirichlet rows get dst = src inside the kernel.
 #pragma once
 
 #include "vmult_brick.cuh"

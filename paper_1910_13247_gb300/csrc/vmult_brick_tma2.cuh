@@ -1,6 +1,12 @@
 // FP32 brick-row vmult on pairs of cells with packed FP32 arithmetic.
 //
-// Same batches, TMA tile traffic and phases as brick_vmult_tma_kernel, but every thread owns the
+// Per batch of CB cells of one row: the batch's n^2 lattice rows are copied into a shared-memory tile
+// by TMA one batch ahead (vmult_brick_tma.cuh); forward contractions S_z (z-lines read straight from
+// the tile, Dirichlet points as 0), S_y, S_x, then D_x (registers), D_y, D_z; h = G_q grad at every
+// Gauss point with G prefetched into registers; transposed contractions summed over the components,
+// S_x^T, S_y^T, and S_z^T into an output tile (nodes shared by neighbouring cells in two passes),
+// which is added to dst by TMA reduce-adds (dst holds src on Dirichlet rows and 0 elsewhere before
+// the launch).  Every thread owns the
 // same line of two neighbouring cells (2c, 2c + 1) of the batch, held as a float pair: each
 // contraction is a chain of packed FMAs (two FMAs per instruction, Blackwell FFMA2), shared-memory
 // accesses move 8 bytes, and the per-line index and control work is shared by two cells.  The

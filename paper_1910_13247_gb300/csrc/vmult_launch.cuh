@@ -73,12 +73,8 @@ static mfx_status run_brick(const mfx_op* op, const Real* src, Real* dst, cudaSt
   static int blocks_per_sm = -1;
   const size_t smem = Sh::SMEM;
   // FP64 in double-float arithmetic (same shared memory: a float pair per value)
-  auto kern = [] {
-    if constexpr (std::is_same<Real, double>::value)
-      return brick_vmult_df_kernel<N, CB>;
-    else
-      return brick_vmult_kernel<N, Real, CB>;
-  }();
+  static_assert(std::is_same<Real, double>::value, "the FP32 structured path is run_brick_tma2");
+  auto kern = brick_vmult_df_kernel<N, CB>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -177,46 +173,6 @@ static mfx_status encode_1d_map(CUtensorMap* map, const void* ptr, int64_t n, in
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(MFX_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-  return MFX_OK;
-}
-
-template <int N, int CB>
-static mfx_status run_brick_tma(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
-  using Sh = BrickShape<N, CB, float>;
-  using Tm = TmaShape<N, CB>;
-  static int blocks_per_sm = -1;
-  const size_t smem = (size_t)(4 * Tm::TILE + 3 * Sh::CUBES + 1) * sizeof(float) + 2 * sizeof(uint64_t);
-  auto kern = brick_vmult_tma_kernel<N, CB>;
-  if (blocks_per_sm < 0) {
-    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int b = 0;
-    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Sh::THREADS, smem));
-    blocks_per_sm = b > 0 ? b : 1;
-  }
-  if (op->metric_cb != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
-  TmaArgs<N> a;
-  mfx_status st = encode_1d_map(&a.tsrc, src, op->n_dofs, Tm::BOX);
-  if (st != MFX_OK) return st;
-  st = encode_1d_map(&a.tdst, dst, op->n_dofs, Tm::BOX);
-  if (st != MFX_OK) return st;
-  a.metric = op->d_metric32;
-  a.nx = op->nx;
-  a.ny = op->ny;
-  a.nz = op->nz;
-  a.nchunk = (op->nx + CB - 1) / CB;
-  a.Mx = op->k * op->nx + 1;
-  a.My = op->k * op->ny + 1;
-  a.Mz = op->k * op->nz + 1;
-  a.n_batches = a.nchunk * op->ny * op->nz;
-  a.err = op->d_err;
-  a.skip = skip;
-  a.dmask = op->dirichlet;
-  const int rows = a.My * a.Mz;
-  init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
-  const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
-  set_batch_steps(&a, grid);
-  kern<<<grid, Sh::THREADS, smem, s>>>(a);
-  MFX_CUDA_TRY(cudaGetLastError());
   return MFX_OK;
 }
 

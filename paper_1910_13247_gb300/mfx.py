@@ -130,6 +130,7 @@ def lib():
         "mfx_operator_info": (S, [_VP, ctypes.POINTER(OpInfo)]),
         "mfx_get_tables": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "mfx_vmult": (S, [_VP, S, _VP, _VP, _VP]),
+        "mfx_vmult_host": (S, [_VP, S, S, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
         "mfx_diagonal": (S, [_VP, S, _VP, _VP]),
         "mfx_device_check": (S, [_VP, _VP]),
         "mfx_quadrature_points": (S, [_VP, _VP, _VP]),
@@ -335,6 +336,19 @@ class Operator:
         assert src.numel() == self.n_dofs and dst.numel() == self.n_dofs
         check(lib().mfx_vmult(self.handle, _prec_of(src), _ptr(src), _ptr(dst), _stream(stream)))
         return dst
+
+    def vmult_host(self, srcs, dsts, stream=None):
+        """dst[i] = K src[i] for host vectors (CPU tensors, pinned for full speed), pipelined through the
+        device (mfx_vmult_host); returns when every result is in host memory."""
+        assert len(srcs) == len(dsts) and len(srcs) > 0
+        dt = srcs[0].dtype
+        for t in list(srcs) + list(dsts):
+            assert (not t.is_cuda) and t.dtype == dt and t.is_contiguous() and t.numel() == self.n_dofs
+        n = len(srcs)
+        sp = (_VP * n)(*[t.data_ptr() for t in srcs])
+        dp = (_VP * n)(*[t.data_ptr() for t in dsts])
+        check(lib().mfx_vmult_host(self.handle, _prec_of(srcs[0]), n, sp, dp, _stream(stream)))
+        return dsts
 
     def device_check(self):
         """Synchronise and raise if a bounded device wait of this operator ran out."""

@@ -398,3 +398,26 @@ def test_dirichlet_face_masks(mfx, faces):
     xs = torch.tensor(xo, device=DEV)
     opo.distribute(xs)
     assert np.abs(xs.cpu().numpy() - fem.distribute(oo, xo)).max() < 1e-14
+
+
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_vmult_on_host_vectors(mfx, count):
+    """mfx_vmult_host: the pipelined host-buffer path gives, for every vector, the oracle's product
+    (FP64 within 1e-12, FP32 within 1e-5), on a structured and an octree operator."""
+    nx, ny, nz, k = 5, 4, 3, 3
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz, verts), k, mfx.COEF_TRIG, (1.0, 0.5))
+    leaves = synthetic.octree_leaves(3, 1, np.array([0.5, 0.5, 0.5]), 0.3)
+    oo = omesh.octree_mesh(3, 3, 3, 2, leaves)
+    Ko = fem.assemble(oo, 3)
+    opo = mfx.Operator(mfx.Mesh.octree(3, 3, 3, leaves), 2)
+    for o, KK, n in ((op, K, om.n_dofs), (opo, Ko, oo.n_dofs)):
+        xs = [synthetic.uniform_vector(n, 60 + i) for i in range(count)]
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            src = [torch.tensor(x, dtype=dt).pin_memory() for x in xs]
+            dst = [torch.full((n,), float("nan"), dtype=dt).pin_memory() for _ in xs]
+            o.vmult_host(src, dst)
+            for x, y in zip(xs, dst):
+                assert rel_err(y.double().numpy(), KK @ x)[0] < tol
