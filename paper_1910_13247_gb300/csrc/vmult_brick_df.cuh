@@ -101,6 +101,89 @@ __device__ __forceinline__ void contract_t_df(const df (&in)[N], df (&out)[N]) {
   }
 }
 
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// Entry (q, j) of M (T = false) or of M^T (T = true).
+template <int N, int MAT, bool T>
+__device__ __forceinline__ constexpr double mat_entry(int q, int j) {
+  return T ? basis_entry<N, MAT>(j * N + q) : basis_entry<N, MAT>(q * N + j);
+}
+
+// out = M in (T = false) or M^T in (T = true) in even-odd form.  S and D are reflection symmetric,
+// M[n-1-q][n-1-j] = sigma M[q][j] with sigma = +1 for S (symmetric Gauss and Gauss-Lobatto points)
+// and -1 for D (the derivative changes sign), and so is M^T.  With e_j = in_j + in_{n-1-j} and
+// o_j = in_j - in_{n-1-j} (j < n/2), the half sums A_q = (out_q + sigma out_{n-1-q}) / 2 and
+// B_q = (out_q - sigma out_{n-1-q}) / 2 are contractions of half length with the coefficients
+// (M[q][j] +- M[q][n-1-j]) / 2 (plus the middle column for odd n in A), and
+// out_q = A_q + B_q, out_{n-1-q} = sigma (A_q - B_q); the middle row of odd n is a half-length
+// contraction of e (sigma = +1) or o (sigma = -1).  About a quarter fewer double-float operations
+// than the direct form at n = 5.
+template <int N, int MAT, bool T>
+__device__ __forceinline__ void contract_df_eo(const df (&in)[N], df (&out)[N]) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N % 2) == 1;
+  constexpr bool SYM = MAT == MAT_S;
+  df e[H > 0 ? H : 1], o[H > 0 ? H : 1];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = df_add(in[j], in[N - 1 - j]);
+    o[j] = df_add(in[j], df_neg(in[N - 1 - j]));
+  }
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    float s, t;
+    df A, B;
+    {
+      constexpr int j0 = 0;
+      const double c0 = 0.5 * (mat_entry<N, MAT, T>(q, j0) + mat_entry<N, MAT, T>(q, N - 1 - j0));
+      df_prod(e[0], split_hi(c0), split_lo(c0), s, t);
+#pragma unroll
+      for (int j = 1; j < H; ++j) {
+        const double c = 0.5 * (mat_entry<N, MAT, T>(q, j) + mat_entry<N, MAT, T>(q, N - 1 - j));
+        df_prod_acc(e[j], split_hi(c), split_lo(c), s, t);
+      }
+      if constexpr (ODD) {
+        const double c = mat_entry<N, MAT, T>(q, H);
+        df_prod_acc(in[H], split_hi(c), split_lo(c), s, t);
+      }
+      A = df_fast_norm(s, t);
+    }
+    {
+      const double c0 = 0.5 * (mat_entry<N, MAT, T>(q, 0) - mat_entry<N, MAT, T>(q, N - 1));
+      df_prod(o[0], split_hi(c0), split_lo(c0), s, t);
+#pragma unroll
+      for (int j = 1; j < H; ++j) {
+        const double c = 0.5 * (mat_entry<N, MAT, T>(q, j) - mat_entry<N, MAT, T>(q, N - 1 - j));
+        df_prod_acc(o[j], split_hi(c), split_lo(c), s, t);
+      }
+      B = df_fast_norm(s, t);
+    }
+    out[q] = df_add(A, B);
+    out[N - 1 - q] = SYM ? df_add(A, df_neg(B)) : df_add(B, df_neg(A));
+  }
+  if constexpr (ODD) {
+    float s, t;
+    if constexpr (SYM) {
+      const double cm = mat_entry<N, MAT, T>(H, H);
+      df_prod(in[H], split_hi(cm), split_lo(cm), s, t);
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const double c = mat_entry<N, MAT, T>(H, j);
+        df_prod_acc(e[j], split_hi(c), split_lo(c), s, t);
+      }
+    } else {
+      const double c0 = mat_entry<N, MAT, T>(H, 0);
+      df_prod(o[0], split_hi(c0), split_lo(c0), s, t);
+#pragma unroll
+      for (int j = 1; j < H; ++j) {
+        const double c = mat_entry<N, MAT, T>(H, j);
+        df_prod_acc(o[j], split_hi(c), split_lo(c), s, t);
+      }
+    }
+    out[H] = df_fast_norm(s, t);
+  }
+}
+
 template <int N, int CB>
 __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
     brick_vmult_df_kernel(const __grid_constant__ BrickArgs<N, double> a, const double* __restrict__ src,
@@ -193,7 +276,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = df_split(T[ztile + j * N * PITCH]);
-      contract_df<N, MAT_S>(v, o);
+      contract_df_eo<N, MAT_S, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
     }
@@ -203,7 +286,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
-      contract_df<N, MAT_S>(v, o);
+      contract_df_eo<N, MAT_S, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
     }
@@ -214,10 +297,10 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[xbase + j];
-      contract_df<N, MAT_S>(v, o);
+      contract_df_eo<N, MAT_S, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[xbase + j] = o[j];
-      contract_df<N, MAT_D>(o, g1);
+      contract_df_eo<N, MAT_D, false>(o, g1);
     }
     __syncthreads();
     // 4) D along y -> B, D along z -> C
@@ -225,12 +308,12 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
-      contract_df<N, MAT_D>(v, o);
+      contract_df_eo<N, MAT_D, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
-      contract_df<N, MAT_D>(v, o);
+      contract_df_eo<N, MAT_D, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
     }
@@ -253,7 +336,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
         B[xbase + q] = df_dot3(G01, u1, G11, u2, G12, u3);
         C[xbase + q] = df_dot3(G02, u1, G12, u2, G22, u3);
       }
-      contract_t_df<N, MAT_D>(h1, t1);
+      contract_df_eo<N, MAT_D, true>(h1, t1);
     }
     __syncthreads();
     // 6) D_y^T on B, D_z^T on C
@@ -261,12 +344,12 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = B[ybase + j * NP];
-      contract_t_df<N, MAT_D>(v, o);
+      contract_df_eo<N, MAT_D, true>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = C[zbase + j * P2];
-      contract_t_df<N, MAT_D>(v, o);
+      contract_df_eo<N, MAT_D, true>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
     }
@@ -276,7 +359,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = df_add3(t1[j], B[xbase + j], C[xbase + j]);
-      contract_t_df<N, MAT_S>(v, o);
+      contract_df_eo<N, MAT_S, true>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[xbase + j] = o[j];
     }
@@ -286,7 +369,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
-      contract_t_df<N, MAT_S>(v, o);
+      contract_df_eo<N, MAT_S, true>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
     }
@@ -298,7 +381,7 @@ __global__ void __launch_bounds__(BrickShape<N, CB, double>::THREADS, 1)
       df v[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[zbase + j * P2];
-      contract_t_df<N, MAT_S>(v, o9);
+      contract_df_eo<N, MAT_S, true>(v, o9);
       if (f < K) {
 #pragma unroll
         for (int j = 0; j < N; ++j) T[ztile + j * N * PITCH] = df_join(o9[j]);
