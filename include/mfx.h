@@ -327,6 +327,7 @@ typedef struct {
   double rel_residual;   /* final ||b - Kx|| / ||b|| in FP64                        */
   double lambda_max;     /* eigenvalue estimate used for Chebyshev (0 if none)     */
   double cheb_lo, cheb_hi;
+  double seconds;        /* wall time of the call (mfx_solve, mfx_mg_solve)         */
 } mfx_solve_stats;
 
 /* Fill params with the defaults listed above. */
@@ -379,6 +380,52 @@ mfx_status mfx_batch_advance(mfx_batch* batch, int32_t* n_active);
 mfx_status mfx_batch_poll(mfx_batch* batch, int32_t slot, int32_t* done, mfx_solve_stats* stats);
 /* Free a slot (its operator and vectors can then be reused or destroyed). */
 mfx_status mfx_batch_release(mfx_batch* batch, int32_t slot);
+
+/* ---------------------------------------------------------------- multigrid */
+
+/*
+ * Geometric multigrid (the paper's large-scale solver: conjugate gradients
+ * preconditioned by a multigrid V-cycle with Chebyshev smoothing and
+ * matrix-free level transfers, Sec. 3.5 and Sec. 6.1), for structured meshes.
+ * Levels: the given mesh and coarser ones with half the cells per direction,
+ * while all three counts are even and at least 4 (or up to max_levels); a
+ * coarser level's vertices are every other vertex of the finer lattice; every
+ * level has the operator of `desc` (same degree, coefficient kind, Dirichlet
+ * faces).  Prolongation interpolates the coarse Q_k function at the fine
+ * nodes (sum-factorised per coarse cell), restriction is its transpose.  The
+ * V-cycle for K_l x = b: x = S(b); x += P V_{l-1}(P^T (b - K x));
+ * x += S(b - K x), with S the Chebyshev(degree) polynomial in D^-1 K on
+ * [hi / range, hi], hi = 1.2 x the Lanczos estimate of each level; the
+ * coarsest level is solved exactly (dense inverse of its free block).  The
+ * cycle is a symmetric linear operator (identity on constrained rows).
+ * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (octree mesh, MFX_COEF_QPOINT, a
+ * coarsest level above 8192 free DoFs), MFX_ENOMEM, MFX_ECUDA.
+ */
+typedef struct mfx_mg mfx_mg;
+typedef struct {
+  int32_t max_levels;       /* 0: as many as the halving rule allows                 */
+  int32_t smoother_degree;  /* Chebyshev degree of each smoothing step (default 6)   */
+  double smoothing_range;   /* lo = hi / range (default 20)                         */
+  int32_t lanczos_steps;    /* steps of the eigenvalue estimate per level (15)       */
+  int32_t reserved;
+} mfx_mg_params;
+void mfx_mg_params_default(mfx_mg_params* params);
+mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* desc, const mfx_mg_params* params,
+                         mfx_stream stream);
+void mfx_mg_destroy(mfx_mg* mg);
+/* Number of levels and free DoFs of the coarsest level. */
+mfx_status mfx_mg_info(const mfx_mg* mg, int32_t* n_levels, int32_t* coarse_free_dofs);
+/* The operator of a level (0 = coarsest, n_levels - 1 = the given mesh); owned by the hierarchy. */
+const mfx_op* mfx_mg_operator(const mfx_mg* mg, int32_t level);
+/* Chebyshev interval of a level's smoother (levels >= 1); set replaces the Lanczos-based one. */
+mfx_status mfx_mg_get_bounds(const mfx_mg* mg, int32_t level, double* lo, double* hi);
+mfx_status mfx_mg_set_bounds(mfx_mg* mg, int32_t level, double lo, double hi);
+/* z = V(r) on the finest level (device vectors of its precision, not aliased); asynchronous. */
+mfx_status mfx_mg_vcycle(mfx_mg* mg, mfx_prec prec, const void* r, void* z, mfx_stream stream);
+/* mfx_solve on the finest operator with the V-cycle as preconditioner (params.precond is ignored;
+ * mixed = 1: FP32 PCG with the FP32 V-cycle inside FP64 defect correction). */
+mfx_status mfx_mg_solve(mfx_mg* mg, const double* b, double* x, const mfx_solve_params* params,
+                        mfx_solve_stats* stats, mfx_stream stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -472,20 +472,45 @@ static mfx_status cheb_apply(const mfx_op* op, Work<Real>& w, const Real* r, Rea
   return MFX_OK;
 }
 
+}  // namespace mfx
+
+struct mfx_mg;
+
+namespace mfx {
+
+// Preconditioner of a PCG: Jacobi (fused into the CG update), Chebyshev(degree) in D^-1 K on
+// [lo, hi], or the multigrid V-cycle of `mg` (mg.cuh).
+struct Precond {
+  int kind = 0;  // 0 Jacobi, 1 Chebyshev, 2 multigrid
+  int degree = 0;
+  double lo = 0.0, hi = 0.0;
+  mfx_mg* mg = nullptr;
+};
+
+template <typename Real>
+mfx_status mg_vcycle(mfx_mg* mg, const Real* r, Real* z, const int32_t* skip, cudaStream_t s);
+
+template <typename Real>
+static mfx_status precond_apply(const mfx_op* op, Work<Real>& w, const Precond& pc, const Real* r, Real* z,
+                                const int32_t* skip, cudaStream_t s) {
+  if (pc.kind == 1) return cheb_apply<Real>(op, w, r, z, pc.degree, pc.lo, pc.hi, skip, s);
+  return mg_vcycle<Real>(pc.mg, r, z, skip, s);
+}
+
 // One PCG iteration (all kernels no-op once done).
 template <typename Real>
-static mfx_status pcg_iteration(const mfx_op* op, SolveWorkspace* ws, Work<Real>& w, bool cheb, int degree,
-                                double lo, double hi, cudaStream_t s) {
+static mfx_status pcg_iteration(const mfx_op* op, SolveWorkspace* ws, Work<Real>& w, const Precond& pc, cudaStream_t s) {
   const int64_t n = op->n_dofs;
   const int g = reduction_blocks(n);
   const int32_t* done = &ws->st->done;
+  const bool jacobi = pc.kind == 0;
   mfx_status rc = launch_vmult(op, prec_of<Real>(), w.p, w.q, s, done);
   if (rc != MFX_OK) return rc;
   cg_pq_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.p, w.q, ws->st, op->d_partials, op->d_counter);
-  cg_update_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.x, w.r, w.p, w.q, w.dinv, !cheb, ws->st, op->d_partials,
+  cg_update_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.x, w.r, w.p, w.q, w.dinv, jacobi, ws->st, op->d_partials,
                                                    op->d_counter);
-  if (cheb) {
-    rc = cheb_apply<Real>(op, w, w.r, w.z, degree, lo, hi, done, s);
+  if (!jacobi) {
+    rc = precond_apply<Real>(op, w, pc, w.r, w.z, done, s);
     if (rc != MFX_OK) return rc;
     cg_rz_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.r, w.z, ws->st, op->d_partials, op->d_counter);
     cg_p_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, w.p, w.r, w.dinv, w.z, ws->st);
@@ -498,20 +523,21 @@ static mfx_status pcg_iteration(const mfx_op* op, SolveWorkspace* ws, Work<Real>
 
 // Solve K x = b in precision Real (b, x in w.b, w.x).  Returns the final state in ws->h_st.
 template <typename Real>
-static mfx_status pcg_run(const mfx_op* op, SolveWorkspace* ws, bool cheb, int degree, double lo, double hi,
-                          double tol, int max_it, int check_every, bool record, cudaStream_t s) {
+static mfx_status pcg_run(const mfx_op* op, SolveWorkspace* ws, const Precond& pc, double tol, int max_it,
+                          int check_every, bool record, cudaStream_t s) {
   Work<Real>& w = work_of<Real>(ws);
   const int64_t n = op->n_dofs;
   const int g = reduction_blocks(n);
+  const bool jacobi = pc.kind == 0;
   SolveState init{};
   init.tol2 = tol * tol;
   init.max_it = max_it;
   init.record = record ? 1 : 0;
   MFX_CUDA_TRY(cudaMemcpyAsync(ws->st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-  cg_init_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.b, w.x, w.r, w.p, w.dinv, !cheb, ws->st, op->d_partials,
+  cg_init_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.b, w.x, w.r, w.p, w.dinv, jacobi, ws->st, op->d_partials,
                                                  op->d_counter);
-  if (cheb) {
-    mfx_status rc = cheb_apply<Real>(op, w, w.r, w.p, degree, lo, hi, &ws->st->done, s);
+  if (!jacobi) {
+    mfx_status rc = precond_apply<Real>(op, w, pc, w.r, w.p, &ws->st->done, s);
     if (rc != MFX_OK) return rc;
     // rz = (r, z) with z = p
     dot_kernel<Real><<<g, kRedThreads, 0, s>>>(n, w.r, w.p, &ws->st->rz, op->d_partials, op->d_counter);
@@ -522,7 +548,7 @@ static mfx_status pcg_run(const mfx_op* op, SolveWorkspace* ws, bool cheb, int d
   cudaGraphExec_t exec = nullptr;
   MFX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   mfx_status rc = MFX_OK;
-  for (int i = 0; i < check_every && rc == MFX_OK; ++i) rc = pcg_iteration<Real>(op, ws, w, cheb, degree, lo, hi, s);
+  for (int i = 0; i < check_every && rc == MFX_OK; ++i) rc = pcg_iteration<Real>(op, ws, w, pc, s);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (rc != MFX_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -586,7 +612,7 @@ static mfx_status estimate_lambda(const mfx_op* op, SolveWorkspace* ws, const do
   steps = std::max(2, std::min(steps, kMaxLanczos - 1));
   convert_kernel<Real><<<vec_grid(n), 256, 0, s>>>(n, start, w.b);
   // constrained rows do not belong to D^-1 K on the free space: zero them
-  mfx_status rc = pcg_run<Real>(op, ws, false, 0, 0.0, 0.0, 0.0, steps, steps, true, s);
+  mfx_status rc = pcg_run<Real>(op, ws, Precond{}, 0.0, steps, steps, true, s);
   if (rc != MFX_OK) return rc;
   const SolveState& h = *ws->h_st;
   const int m = std::min(h.it, steps);
@@ -599,6 +625,121 @@ static mfx_status estimate_lambda(const mfx_op* op, SolveWorkspace* ws, const do
   *lam = tridiag_lambda_max(a, b);
   return MFX_OK;
 }
+
+}  // namespace mfx
+
+extern "C" void mfx_solve_params_default(mfx_solve_params* p);
+
+namespace mfx {
+
+// PCG (Jacobi or Chebyshev-Jacobi, or the V-cycle of mg when mg is not null) in FP64, or FP64
+// defect correction around the FP32 PCG (mixed).
+mfx_status solve_impl(mfx_op* op, const double* b, double* x, const mfx_solve_params* params, mfx_mg* mg,
+                      mfx_solve_stats* stats, mfx_stream stream) {
+  if (!op || !b || !x || !stats) return set_error(MFX_EINVAL, "mfx_solve: null argument");
+  const auto t_start = std::chrono::steady_clock::now();
+  mfx_solve_params p;
+  mfx_solve_params_default(&p);
+  if (params) p = *params;
+  if (!(p.tol >= 0.0) || p.max_it < 1 || p.cheb_degree < 1 || (p.precond != MFX_PRECOND_JACOBI && p.precond != MFX_PRECOND_CHEBYSHEV))
+    return set_error(MFX_EINVAL, "mfx_solve: bad parameters");
+  const bool mixed = p.mixed != 0;
+  if (mixed && !(op->has_f32 && op->has_f64))
+    return set_error(MFX_EINVAL, "mfx_solve: mixed precision needs FP64 and FP32 data");
+  if (!mixed && !op->has_f64) return set_error(MFX_EINVAL, "mfx_solve: FP64 data not built");
+  mfx_status rc = ensure_workspace(op);
+  if (rc != MFX_OK) return rc;
+  auto* ws = workspace(op);
+  // order after the caller's work, then run on the solver stream (capturable)
+  MFX_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t s = ws->stream;
+  const int64_t n = op->n_dofs;
+  const int g = reduction_blocks(n);
+  const bool cheb = !mg && p.precond == MFX_PRECOND_CHEBYSHEV;
+  const int check = p.check_every > 0 ? p.check_every : 8;
+  *stats = mfx_solve_stats{};
+  const int pi = mixed ? 1 : 0;
+  double lo = p.cheb_lo, hi = p.cheb_hi;
+  if (cheb && !(hi > 0.0)) {
+    if (ws->lambda_max[pi] == 0.0 || p.lanczos_start) {
+      double lam = 0.0;
+      const double* start = p.lanczos_start ? p.lanczos_start : b;
+      rc = mixed ? estimate_lambda<float>(op, ws, start, p.lanczos_steps, s, &lam)
+                 : estimate_lambda<double>(op, ws, start, p.lanczos_steps, s, &lam);
+      if (rc != MFX_OK) return rc;
+      ws->lambda_max[pi] = lam;
+    }
+    stats->lambda_max = ws->lambda_max[pi];
+    hi = 1.2 * ws->lambda_max[pi];
+    lo = hi / 20.0;
+  }
+  stats->cheb_lo = lo;
+  stats->cheb_hi = hi;
+  Precond pc;
+  pc.kind = mg ? 2 : (cheb ? 1 : 0);
+  pc.degree = p.cheb_degree;
+  pc.lo = lo;
+  pc.hi = hi;
+  pc.mg = mg;
+  if (!mixed) {
+    MFX_CUDA_TRY(cudaMemcpyAsync(ws->w64.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    rc = pcg_run<double>(op, ws, pc, p.tol, p.max_it, check, false, s);
+    if (rc != MFX_OK) return rc;
+    stats->iterations = ws->h_st->it;
+    stats->status = ws->h_st->status;
+    MFX_CUDA_TRY(cudaMemcpyAsync(x, ws->w64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    MFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    double* rr = ws->scal;      // (r, r)
+    double* bb = ws->scal + 1;  // (b, b)
+    double h[2];
+    launch_dot(op, MFX_F64, n, b, b, bb, s);
+    stats->status = MFX_NOT_CONVERGED;
+    int inner_total = 0;
+    for (int outer = 0; outer <= p.max_it; ++outer) {
+      rc = launch_vmult(op, MFX_F64, x, ws->y64, s);
+      if (rc != MFX_OK) return rc;
+      residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64, ws->r64, rr, op->d_partials, op->d_counter);
+      MFX_CUDA_TRY(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MFX_CUDA_TRY(cudaStreamSynchronize(s));
+      stats->iterations = outer;
+      if (!std::isfinite(h[0])) {
+        stats->status = MFX_BREAKDOWN;
+        break;
+      }
+      if (h[0] <= p.tol * p.tol * h[1]) {
+        stats->status = MFX_OK;
+        break;
+      }
+      if (outer == p.max_it) break;
+      scale_to_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, ws->r64, rr, ws->w32.b);
+      rc = pcg_run<float>(op, ws, pc, p.inner_tol, p.inner_max_it, check, false, s);
+      if (rc != MFX_OK) return rc;
+      inner_total += ws->h_st->it;
+      if (ws->h_st->status == MFX_BREAKDOWN) {
+        stats->status = MFX_BREAKDOWN;
+        break;
+      }
+      add_scaled_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, ws->w32.x, rr);
+    }
+    stats->inner_iterations = inner_total;
+  }
+  // true FP64 residual of the result
+  rc = launch_vmult(op, MFX_F64, x, ws->y64 ? ws->y64 : ws->w64.q, s);
+  if (rc != MFX_OK) return rc;
+  double* rr = ws->scal + 2;
+  double* bb = ws->scal + 3;
+  residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64 ? ws->y64 : ws->w64.q, ws->r64 ? ws->r64 : ws->w64.t, rr,
+                                            op->d_partials, op->d_counter);
+  launch_dot(op, MFX_F64, n, b, b, bb, s);
+  double h[2];
+  MFX_CUDA_TRY(cudaMemcpyAsync(h, rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MFX_CUDA_TRY(cudaStreamSynchronize(s));
+  stats->rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return MFX_OK;
+}
+
 
 }  // namespace mfx
 
@@ -647,101 +788,7 @@ mfx_status mfx_chebyshev(const mfx_op* op_c, mfx_prec prec, const void* r, void*
 
 mfx_status mfx_solve(const mfx_op* op_c, const double* b, double* x, const mfx_solve_params* params,
                      mfx_solve_stats* stats, mfx_stream stream) {
-  mfx_op* op = const_cast<mfx_op*>(op_c);
-  if (!op || !b || !x || !stats) return set_error(MFX_EINVAL, "mfx_solve: null argument");
-  mfx_solve_params p;
-  mfx_solve_params_default(&p);
-  if (params) p = *params;
-  if (!(p.tol >= 0.0) || p.max_it < 1 || p.cheb_degree < 1 || (p.precond != MFX_PRECOND_JACOBI && p.precond != MFX_PRECOND_CHEBYSHEV))
-    return set_error(MFX_EINVAL, "mfx_solve: bad parameters");
-  const bool mixed = p.mixed != 0;
-  if (mixed && !(op->has_f32 && op->has_f64))
-    return set_error(MFX_EINVAL, "mfx_solve: mixed precision needs FP64 and FP32 data");
-  if (!mixed && !op->has_f64) return set_error(MFX_EINVAL, "mfx_solve: FP64 data not built");
-  mfx_status rc = ensure_workspace(op);
-  if (rc != MFX_OK) return rc;
-  auto* ws = workspace(op);
-  // order after the caller's work, then run on the solver stream (capturable)
-  MFX_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-  cudaStream_t s = ws->stream;
-  const int64_t n = op->n_dofs;
-  const int g = reduction_blocks(n);
-  const bool cheb = p.precond == MFX_PRECOND_CHEBYSHEV;
-  const int check = p.check_every > 0 ? p.check_every : 8;
-  *stats = mfx_solve_stats{};
-  const int pi = mixed ? 1 : 0;
-  double lo = p.cheb_lo, hi = p.cheb_hi;
-  if (cheb && !(hi > 0.0)) {
-    if (ws->lambda_max[pi] == 0.0 || p.lanczos_start) {
-      double lam = 0.0;
-      const double* start = p.lanczos_start ? p.lanczos_start : b;
-      rc = mixed ? estimate_lambda<float>(op, ws, start, p.lanczos_steps, s, &lam)
-                 : estimate_lambda<double>(op, ws, start, p.lanczos_steps, s, &lam);
-      if (rc != MFX_OK) return rc;
-      ws->lambda_max[pi] = lam;
-    }
-    stats->lambda_max = ws->lambda_max[pi];
-    hi = 1.2 * ws->lambda_max[pi];
-    lo = hi / 20.0;
-  }
-  stats->cheb_lo = lo;
-  stats->cheb_hi = hi;
-  if (!mixed) {
-    MFX_CUDA_TRY(cudaMemcpyAsync(ws->w64.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    rc = pcg_run<double>(op, ws, cheb, p.cheb_degree, lo, hi, p.tol, p.max_it, check, false, s);
-    if (rc != MFX_OK) return rc;
-    stats->iterations = ws->h_st->it;
-    stats->status = ws->h_st->status;
-    MFX_CUDA_TRY(cudaMemcpyAsync(x, ws->w64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  } else {
-    MFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-    double* rr = ws->scal;      // (r, r)
-    double* bb = ws->scal + 1;  // (b, b)
-    double h[2];
-    launch_dot(op, MFX_F64, n, b, b, bb, s);
-    stats->status = MFX_NOT_CONVERGED;
-    int inner_total = 0;
-    for (int outer = 0; outer <= p.max_it; ++outer) {
-      rc = launch_vmult(op, MFX_F64, x, ws->y64, s);
-      if (rc != MFX_OK) return rc;
-      residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64, ws->r64, rr, op->d_partials, op->d_counter);
-      MFX_CUDA_TRY(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      MFX_CUDA_TRY(cudaStreamSynchronize(s));
-      stats->iterations = outer;
-      if (!std::isfinite(h[0])) {
-        stats->status = MFX_BREAKDOWN;
-        break;
-      }
-      if (h[0] <= p.tol * p.tol * h[1]) {
-        stats->status = MFX_OK;
-        break;
-      }
-      if (outer == p.max_it) break;
-      scale_to_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, ws->r64, rr, ws->w32.b);
-      rc = pcg_run<float>(op, ws, cheb, p.cheb_degree, lo, hi, p.inner_tol, p.inner_max_it, check, false, s);
-      if (rc != MFX_OK) return rc;
-      inner_total += ws->h_st->it;
-      if (ws->h_st->status == MFX_BREAKDOWN) {
-        stats->status = MFX_BREAKDOWN;
-        break;
-      }
-      add_scaled_f32_kernel<<<vec_grid(n), 256, 0, s>>>(n, x, ws->w32.x, rr);
-    }
-    stats->inner_iterations = inner_total;
-  }
-  // true FP64 residual of the result
-  rc = launch_vmult(op, MFX_F64, x, ws->y64 ? ws->y64 : ws->w64.q, s);
-  if (rc != MFX_OK) return rc;
-  double* rr = ws->scal + 2;
-  double* bb = ws->scal + 3;
-  residual_kernel<<<g, kRedThreads, 0, s>>>(n, b, ws->y64 ? ws->y64 : ws->w64.q, ws->r64 ? ws->r64 : ws->w64.t, rr,
-                                            op->d_partials, op->d_counter);
-  launch_dot(op, MFX_F64, n, b, b, bb, s);
-  double h[2];
-  MFX_CUDA_TRY(cudaMemcpyAsync(h, rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MFX_CUDA_TRY(cudaStreamSynchronize(s));
-  stats->rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
-  return MFX_OK;
+  return solve_impl(const_cast<mfx_op*>(op_c), b, x, params, nullptr, stats, stream);
 }
 
 }  // extern "C"
@@ -839,7 +886,8 @@ static mfx_status capture_chunk(BatchSlot& sl, int chunk) {
   MFX_CUDA_TRY(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
   mfx_status rc = MFX_OK;
   for (int i = 0; i < chunk && rc == MFX_OK; ++i)
-    rc = pcg_iteration<Real>(sl.op, ws, w, sl.cheb, sl.p.cheb_degree, sl.lo, sl.hi, sl.stream);
+    rc = pcg_iteration<Real>(sl.op, ws, w, Precond{sl.cheb ? 1 : 0, sl.p.cheb_degree, sl.lo, sl.hi, nullptr},
+                             sl.stream);
   cudaMemcpyAsync(ws->h_st, ws->st, sizeof(SolveState), cudaMemcpyDeviceToHost, sl.stream);
   cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
   if (rc != MFX_OK) {
@@ -1203,3 +1251,5 @@ mfx_status mfx_batch_release(mfx_batch* bt, int32_t slot) {
 }
 
 }  // extern "C"
+
+#include "mg.cuh"

@@ -60,10 +60,16 @@ class SolveParams(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("lambda_max", ctypes.c_double),
-                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double)]
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [("max_levels", ctypes.c_int32), ("smoother_degree", ctypes.c_int32),
+                ("smoothing_range", ctypes.c_double), ("lanczos_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -148,6 +154,15 @@ def lib():
         "mfx_batch_advance": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_poll": (S, [_VP, S, ctypes.POINTER(S), ctypes.POINTER(SolveStats)]),
         "mfx_batch_release": (S, [_VP, S]),
+        "mfx_mg_params_default": (None, [ctypes.POINTER(MgParams)]),
+        "mfx_mg_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), ctypes.POINTER(MgParams), _VP]),
+        "mfx_mg_destroy": (None, [_VP]),
+        "mfx_mg_info": (S, [_VP, ctypes.POINTER(S), ctypes.POINTER(S)]),
+        "mfx_mg_operator": (_VP, [_VP, S]),
+        "mfx_mg_get_bounds": (S, [_VP, S, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "mfx_mg_set_bounds": (S, [_VP, S, ctypes.c_double, ctypes.c_double]),
+        "mfx_mg_vcycle": (S, [_VP, S, _VP, _VP, _VP]),
+        "mfx_mg_solve": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
         "mfx_server_create": (S, [ctypes.POINTER(_VP), ctypes.POINTER(ServerConfig)]),
         "mfx_server_destroy": (None, [_VP]),
         "mfx_server_submit": (S, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
@@ -541,3 +556,85 @@ class Server:
         st = ServerStats()
         check(lib().mfx_server_stats_get(self.handle, ctypes.byref(st)))
         return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
+class Multigrid:
+    """Geometric multigrid hierarchy of a structured mesh (mfx_mg_*): level operators, transfers,
+    Chebyshev smoothers, exact coarse solve; V-cycle application and MG-preconditioned solves."""
+
+    def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), max_levels=0,
+                 smoother_degree=6, smoothing_range=20.0, lanczos_steps=15, stream=None):
+        d = OpDesc()
+        d.degree, d.n_q_1d, d.coef_kind, d.precisions = degree, 0, coef_kind, 3
+        d.coef_par[0], d.coef_par[1] = coef_par
+        p = MgParams()
+        lib().mfx_mg_params_default(ctypes.byref(p))
+        p.max_levels, p.smoother_degree, p.smoothing_range, p.lanczos_steps = max_levels, smoother_degree, \
+            smoothing_range, lanczos_steps
+        h = ctypes.c_void_p()
+        check(lib().mfx_mg_create(ctypes.byref(h), mesh.handle, ctypes.byref(d), ctypes.byref(p), _stream(stream)))
+        self.handle = h
+        self.degree = degree
+        nl, nf = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().mfx_mg_info(h, ctypes.byref(nl), ctypes.byref(nf)))
+        self.n_levels, self.coarse_free_dofs = nl.value, nf.value
+
+    @property
+    def fine(self):
+        """The finest level's operator (a view that keeps the hierarchy alive)."""
+        return self.operator(self.n_levels - 1)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfx_mg_destroy(self.handle)
+            self.handle = None
+
+    def operator(self, level):
+        """Non-owning view of a level's operator (0 = coarsest)."""
+        h = lib().mfx_mg_operator(self.handle, level)
+        if not h:
+            raise MfxError(EINVAL, "bad level")
+        h = ctypes.c_void_p(h)
+        i = OpInfo()
+        check(lib().mfx_operator_info(h, ctypes.byref(i)))
+        return _OpView(h, self.degree, {f: getattr(i, f) for f, _ in i._fields_}, self)
+
+    def bounds(self, level):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        check(lib().mfx_mg_get_bounds(self.handle, level, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    def set_bounds(self, level, lo, hi):
+        check(lib().mfx_mg_set_bounds(self.handle, level, lo, hi))
+
+    def vcycle(self, r, z, stream=None):
+        check(lib().mfx_mg_vcycle(self.handle, _prec_of(r), _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def solve(self, b, x, tol=1e-10, max_it=1000, mixed=False, inner_tol=1e-4, check_every=0, inner_max_it=1000):
+        p = make_params(tol=tol, max_it=max_it, mixed=mixed, inner_tol=inner_tol, check_every=check_every,
+                        inner_max_it=inner_max_it)
+        st = SolveStats()
+        check(lib().mfx_mg_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st), _stream()))
+        return st.as_dict()
+
+
+class _OpView(Operator):
+    """An operator owned by something else (a multigrid level): same methods, never destroyed here."""
+
+    def __init__(self, handle, degree, info, owner):
+        self._handle = handle
+        self.degree = degree
+        self._info = info
+        self._owner = owner  # keeps the hierarchy alive
+
+    @property
+    def handle(self):
+        return self._handle
+
+    @handle.setter
+    def handle(self, v):
+        pass
+
+    def __del__(self):
+        pass
