@@ -71,3 +71,27 @@ def test_mg_pcg_matches_oracle_iterations_and_residual(mfx, mixed):
             its.append(st["iterations"])
     if its:
         assert max(its) <= 12 and its[1] <= its[0] + 2, its
+
+
+def test_mg_options_and_errors(mfx):
+    verts = synthetic.deformed_vertices(8, 8, 8)
+    mesh = mfx.Mesh.structured_box(8, 8, 8, verts)
+    g = mfx.Multigrid(mesh, 2, mfx.COEF_TRIG, (1.0, 0.5), max_levels=2)
+    assert g.n_levels == 2
+    lo, hi = g.bounds(1)
+    g.set_bounds(1, lo / 2, hi)
+    assert g.bounds(1) == (lo / 2, hi)
+    # the cycle with the new interval equals the oracle's with the same interval
+    meshes, sizes = omg.level_meshes(8, 8, 8, 2, verts, max_levels=2)
+    h = omg.Hierarchy(meshes, sizes, 2, fem.COEF_TRIG, (1.0, 0.5), degree=6, bounds=[(1.0, 2.0), (lo / 2, hi)])
+    r = synthetic.uniform_vector(meshes[-1].n_dofs, 90)
+    z = torch.empty(meshes[-1].n_dofs, dtype=torch.float64, device=DEV)
+    g.vcycle(torch.tensor(r, device=DEV), z)
+    ref = h.vcycle(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) < 1e-10 * np.linalg.norm(ref)
+    with pytest.raises(mfx.MfxError):
+        g.set_bounds(0, 1.0, 2.0)  # the coarsest level has no smoother
+    leaves = synthetic.octree_leaves(2, 1, np.array([0.5, 0.5, 0.5]), 0.3)
+    with pytest.raises(mfx.MfxError) as e:
+        mfx.Multigrid(mfx.Mesh.octree(2, 2, 2, leaves), 2)
+    assert e.value.code == mfx.EUNSUPPORTED
