@@ -17,7 +17,10 @@ cycle out with assembled matrices, in this reading (the paper fixes none of thes
     x += P V_{l-1}(P^T r); post-smoothing x += S(b - K x); on the coarsest level V_0 = K_0^-1 on the
     free DoFs (direct solve);
   * as a preconditioner of the condensed operator (identity on constrained rows, decoupled from the
-    free ones) the cycle runs on the free DoFs and returns the residual itself on constrained rows.
+    free ones) the cycle runs on the free DoFs and returns the residual itself on constrained rows;
+  * optionally a discontinuous (SIPG, oracle/dg.py) level on top of the finest continuous one, on the
+    same mesh and degree, reached by the injection of the continuous space (its transpose restricts),
+    as in the paper's benchmark hierarchy.
 
 Both smoothing steps use the same symmetric polynomial and the coarse solve is exact, so the cycle is
 a symmetric linear operator.
@@ -89,16 +92,24 @@ class Hierarchy:
     """Assembled levels: condensed K, inverse diagonal, Chebyshev interval, prolongation from below."""
 
     def __init__(self, meshes, sizes, k, coef_kind=fem.COEF_CONSTANT, coef_par=(1.0, 0.0), degree=6,
-                 bounds=None, smoothing_range=20.0, lanczos_steps=15):
-        self.meshes, self.k, self.degree = meshes, k, degree
+                 bounds=None, smoothing_range=20.0, lanczos_steps=15, dg_top=None):
+        """dg_top = (K_dg, P): a discontinuous level above the finest continuous one, reached by the
+        injection P of the continuous space (the paper's hierarchy switches from SIPG to the
+        continuous space of the same degree on the same mesh before it coarsens)."""
+        self.meshes, self.k, self.degree = list(meshes), k, degree
         self.K = [fem.assemble(m, k + 1, coef_kind, coef_par) for m in meshes]
-        self.dinv = [1.0 / fem.diagonal(K) for K in self.K]
         self.free = []
         for m in meshes:
             f = np.ones(m.n_dofs, dtype=bool)
             f[m.constrained] = False
             self.free.append(f)
         self.P = [None] + [prolongation(meshes[l - 1], meshes[l], sizes[l - 1], k) for l in range(1, len(meshes))]
+        if dg_top is not None:
+            self.K.append(dg_top[0].tocsr())
+            self.P.append(dg_top[1].tocsr())
+            self.free.append(np.ones(dg_top[0].shape[0], dtype=bool))
+            self.meshes.append(None)
+        self.dinv = [1.0 / fem.diagonal(K) for K in self.K]
         self.bounds = []
         for l, (K, dinv) in enumerate(zip(self.K, self.dinv)):
             if bounds is not None:
@@ -128,7 +139,7 @@ class Hierarchy:
     def vcycle(self, r):
         """Preconditioner of the finest condensed operator: the cycle on the free DoFs, identity on
         the constrained ones."""
-        L = len(self.meshes) - 1
+        L = len(self.K) - 1
         b = np.where(self.free[L], r, 0.0)
         z = self.cycle(L, b)
         return np.where(self.free[L], z, r)
