@@ -157,11 +157,25 @@ typedef struct {
   const double* coef_qpoint; /* MFX_COEF_QPOINT: device, n_cells x n_q^3 doubles,
                                 q = q1 + n_q (q2 + n_q q3); read during create  */
   int32_t cells_per_block;   /* 0 = autotuned default                             */
-  int32_t reserved;
+  int32_t discretization;    /* MFX_CONTINUOUS (0) or MFX_SIPG (1)                 */
   mfx_point_fn coef_fn;      /* MFX_COEF_FUNCTION: a(x), called once per quadrature
                                 point during create (on the calling thread)      */
   void* coef_user;
+  double dg_penalty;         /* MFX_SIPG: eta of the penalty (0 means 1)            */
 } mfx_op_desc;
+
+/*
+ * MFX_SIPG: the symmetric interior penalty DG Laplacian of the paper's multigrid benchmark
+ * (Sec. 6.1) on a structured mesh of uniform, axis-aligned cells (the lattice must be
+ * x_i = x_0 + i h per direction, else MFX_EUNSUPPORTED) with a constant coefficient a = par[0]:
+ * discontinuous Q_k on Gauss-Lobatto nodes, DoFs cell-major (n_cells x (k+1)^3, cell c's node
+ * i1 + n (i2 + n i3) at c n^3 + ...), interior faces -{d_n u}[v] - [u]{d_n v} + sigma [u][v] with
+ * sigma = eta (k+1)^2 / h, homogeneous Dirichlet data imposed weakly on the mesh's Dirichlet faces
+ * (sigma = 2 eta (k+1)^2 / h there), the other faces natural.  There are no constrained DoFs.
+ * vmult, diagonal, dot, Chebyshev, solve and batches work as for the continuous operator;
+ * quadrature points, right-hand sides and tables are MFX_EUNSUPPORTED.
+ */
+enum { MFX_CONTINUOUS = 0, MFX_SIPG = 1 };
 
 /*
  * Build the operator: DoF tables and constraints on the host, then the
@@ -197,6 +211,8 @@ typedef struct {
   int64_t n_dofs, n_cells, n_constrained, n_masters, n_hanging;
   int64_t bytes_device; /* device memory owned by the operator */
   int32_t degree, n_q_1d, structured, cells_per_block;
+  int32_t discretization;  /* MFX_CONTINUOUS or MFX_SIPG */
+  int32_t reserved;
 } mfx_op_info;
 
 mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info);
@@ -398,8 +414,15 @@ mfx_status mfx_batch_release(mfx_batch* batch, int32_t slot);
  * [hi / range, hi], hi = 1.2 x the Lanczos estimate of each level; the
  * coarsest level is solved exactly (dense inverse of its free block).  The
  * cycle is a symmetric linear operator (identity on constrained rows).
+ * desc->discretization = MFX_SIPG: the hierarchy of the paper's DG benchmark
+ * (Sec. 6.1): the SIPG operator of the mesh on top, then the continuous
+ * operators of the same degree on the same mesh and the coarsened ones; the
+ * top transfer is the injection of the continuous space (the continuous
+ * value at each DG node, Dirichlet nodes 0) and its transpose.  n_levels
+ * counts the SIPG level.
  * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (octree mesh, MFX_COEF_QPOINT, a
- * coarsest level above 8192 free DoFs), MFX_ENOMEM, MFX_ECUDA.
+ * coarsest level above 8192 free DoFs, SIPG on a non-uniform lattice or with
+ * a variable coefficient), MFX_ENOMEM, MFX_ECUDA.
  */
 typedef struct mfx_mg mfx_mg;
 typedef struct {

@@ -39,6 +39,7 @@ int device_sm_count() {
 
 mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                         const int32_t* skip) {
+  if (op->dg) return launch_dg_vmult(op, prec, src, dst, s, skip);
   switch (op->n) {
     case 2: return launch_vmult_n<2>(op, prec, src, dst, s, skip);
     case 3: return launch_vmult_n<3>(op, prec, src, dst, s, skip);
@@ -372,6 +373,70 @@ mfx_status mfx_mesh_get_dirichlet(const mfx_mesh* mesh, uint32_t* faces) {
   return MFX_OK;
 }
 
+// SIPG operator (Sec. 6.1 benchmark): a structured mesh whose lattice is x_0 + (i h_x, j h_y, l h_z), a
+// constant coefficient; n_cells x (k+1)^3 cell-major DoFs, no constraints, no stored geometry.
+static mfx_status create_sipg(mfx_op** out, const Mesh& m, const mfx_op_desc* desc, cudaStream_t s) {
+  if (!m.structured) return set_error(MFX_EUNSUPPORTED, "SIPG needs a structured mesh");
+  if (desc->coef_kind != MFX_COEF_CONSTANT) return set_error(MFX_EUNSUPPORTED, "SIPG takes a constant coefficient");
+  if (!(desc->coef_par[0] > 0.0)) return set_error(MFX_EINVAL, "SIPG coefficient must be positive");
+  const double eta = desc->dg_penalty == 0.0 ? 1.0 : desc->dg_penalty;
+  if (!(eta > 0.0)) return set_error(MFX_EINVAL, "SIPG penalty must be positive");
+  const int nv[3] = {m.nx + 1, m.ny + 1, m.nz + 1};
+  const double* v = m.vertices.data();
+  auto vert = [&](int64_t i, int64_t j, int64_t l, int d) { return v[3 * (i + nv[0] * (j + nv[1] * l)) + d]; };
+  double h[3];
+  h[0] = (vert(m.nx, 0, 0, 0) - vert(0, 0, 0, 0)) / m.nx;
+  h[1] = (vert(0, m.ny, 0, 1) - vert(0, 0, 0, 1)) / m.ny;
+  h[2] = (vert(0, 0, m.nz, 2) - vert(0, 0, 0, 2)) / m.nz;
+  if (!(h[0] > 0.0 && h[1] > 0.0 && h[2] > 0.0)) return set_error(MFX_EUNSUPPORTED, "SIPG needs a positively oriented lattice");
+  const double tol = 1e-10 * std::max({h[0] * m.nx, h[1] * m.ny, h[2] * m.nz});
+  for (int64_t l = 0; l < nv[2]; ++l)
+    for (int64_t j = 0; j < nv[1]; ++j)
+      for (int64_t i = 0; i < nv[0]; ++i) {
+        const double want[3] = {vert(0, 0, 0, 0) + i * h[0], vert(0, 0, 0, 1) + j * h[1], vert(0, 0, 0, 2) + l * h[2]};
+        for (int d = 0; d < 3; ++d)
+          if (std::abs(vert(i, j, l, d) - want[d]) > tol)
+            return set_error(MFX_EUNSUPPORTED, "SIPG needs a uniform axis-aligned lattice");
+      }
+  const int k = desc->degree;
+  keep_pool_memory();
+  mfx_op* op = new (std::nothrow) mfx_op();
+  if (!op) return set_error(MFX_ENOMEM, "host allocation failed");
+  op->k = k;
+  op->n = k + 1;
+  make_basis(k, &op->basis);
+  const int prec = desc->precisions ? desc->precisions : 3;
+  op->has_f64 = (prec & 1) != 0;
+  op->has_f32 = (prec & 2) != 0;
+  op->nx = m.nx;
+  op->ny = m.ny;
+  op->nz = m.nz;
+  op->structured = true;
+  op->dg = true;
+  op->dirichlet = m.dirichlet;
+  for (int d = 0; d < 3; ++d) op->dg_h[d] = h[d];
+  op->dg_penalty = eta;
+  op->dg_coef = desc->coef_par[0];
+  op->n_cells = (int64_t)m.nx * m.ny * m.nz;
+  op->n_dofs = op->n_cells * op->n * op->n * op->n;
+  if (op->n_dofs >= ((int64_t)1 << 31)) {
+    destroy_op(op);
+    return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
+  }
+  MFX_TRY(dev_alloc(op, &op->d_diag64, std::max<int64_t>(1, op->n_dofs), s));
+  if (op->has_f32) MFX_TRY(dev_alloc(op, &op->d_diag32, std::max<int64_t>(1, op->n_dofs), s));
+  MFX_TRY(dev_alloc(op, &op->d_scalars, 64, s));
+  MFX_TRY(dev_alloc(op, &op->d_partials, 4096, s));
+  MFX_TRY(dev_alloc(op, &op->d_counter, 16, s));
+  MFX_CUDA_OP(cudaMemsetAsync(op->d_counter, 0, 16 * sizeof(unsigned int), s));
+  MFX_TRY(dev_alloc(op, &op->d_err, 4, s));
+  MFX_CUDA_OP(cudaMemsetAsync(op->d_err, 0, 4 * sizeof(int), s));
+  MFX_TRY(launch_dg_diagonal(op, s));
+  MFX_CUDA_OP(cudaStreamSynchronize(s));
+  *out = op;
+  return MFX_OK;
+}
+
 mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) {
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "null argument");
   *out = nullptr;
@@ -385,6 +450,9 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     return set_error(MFX_EINVAL, "MFX_COEF_QPOINT needs coef_qpoint");
   if (desc->coef_kind == MFX_COEF_FUNCTION && !desc->coef_fn)
     return set_error(MFX_EINVAL, "MFX_COEF_FUNCTION needs coef_fn");
+  if (desc->discretization != MFX_CONTINUOUS && desc->discretization != MFX_SIPG)
+    return set_error(MFX_EINVAL, "unknown discretization");
+  if (desc->discretization == MFX_SIPG) return create_sipg(out, mesh->m, desc, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   keep_pool_memory();
   mfx_op* op = new (std::nothrow) mfx_op();
@@ -576,6 +644,9 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   info->n_q_1d = op->n;
   info->structured = op->structured ? 1 : 0;
   info->cells_per_block = op->structured ? op->metric_cb : (op->metric_cb32 > 0 ? op->metric_cb32 : 256 / (op->n * op->n));
+  info->discretization = op->dg ? MFX_SIPG : MFX_CONTINUOUS;
+  if (op->dg) info->cells_per_block = std::max(1, 128 / (op->n * op->n));
+  info->reserved = 0;
   return MFX_OK;
 }
 
@@ -662,6 +733,12 @@ mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_d
 mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
                           int32_t* cmaster, double* cweight) {
   if (!op) return set_error(MFX_EINVAL, "null operator");
+  if (op->dg) {  // cell-major DoFs, nothing constrained
+    if (cell_dofs)
+      for (int64_t i = 0; i < op->n_dofs; ++i) cell_dofs[i] = (int32_t)i;
+    if (cptr) cptr[0] = 0;
+    return MFX_OK;
+  }
   if (op->structured) {
     structured_tables(op->nx, op->ny, op->nz, op->k, op->dirichlet, cell_dofs, constrained, cptr);
     return MFX_OK;
@@ -763,16 +840,19 @@ mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream 
 
 mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream) {
   if (!op || !xq) return set_error(MFX_EINVAL, "mfx_quadrature_points: null argument");
+  if (op->dg) return set_error(MFX_EUNSUPPORTED, "quadrature points of an SIPG operator");
   return launch_qpoints(op, xq, (cudaStream_t)stream);
 }
 
 mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream) {
   if (!op || !fq || !b) return set_error(MFX_EINVAL, "mfx_rhs: null argument");
+  if (op->dg) return set_error(MFX_EUNSUPPORTED, "right-hand side of an SIPG operator");
   return launch_rhs(op, fq, b, (cudaStream_t)stream);
 }
 
 mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double* b, mfx_stream stream) {
   if (!op || !f || !b) return set_error(MFX_EINVAL, "mfx_rhs_function: null argument");
+  if (op->dg) return set_error(MFX_EUNSUPPORTED, "right-hand side of an SIPG operator");
   cudaStream_t s = (cudaStream_t)stream;
   double* fq = nullptr;
   mfx_status st = host_point_values(op, f, user, &fq, s);
@@ -799,6 +879,7 @@ mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user) {
 
 mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream) {
   if (!op || !x) return set_error(MFX_EINVAL, "mfx_distribute: null argument");
+  if (op->dg) return MFX_OK;  // no constrained DoFs
   return launch_distribute(op, x, (cudaStream_t)stream);
 }
 

@@ -91,6 +91,8 @@ struct mfx_op {
   int64_t n_cells = 0, n_dofs = 0, n_constrained = 0, n_masters = 0, n_hanging = 0;
   bool structured = true;
   uint32_t dirichlet = mfx::kAllFaces;    // Dirichlet faces of the box
+  bool dg = false;                        // SIPG operator (cell-major DoFs, no constraints)
+  double dg_h[3] = {0, 0, 0}, dg_penalty = 1.0, dg_coef = 1.0;
   int nx = 0, ny = 0, nz = 0;             // structured cells per direction
   int cells_per_block = 0;
   int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)
@@ -139,6 +141,10 @@ mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_
 mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
 mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
+// SIPG operator (dg.cu).
+mfx_status launch_dg_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
+                           const int32_t* skip);
+mfx_status launch_dg_diagonal(mfx_op* op, cudaStream_t s);
 
 int device_sm_count();
 

@@ -12,6 +12,12 @@
 // exactly with the inverse of its free-DoF block, formed once at set-up from operator applications to
 // unit vectors and inverted on the host (Cholesky), then applied as a dense matrix-vector product.  All
 // of a cycle is a fixed sequence of kernels on one stream, so it is captured with the PCG iterations.
+//
+// With an SIPG operator on top (the paper's DG benchmark hierarchy, Sec. 6.1), the top level is the
+// discontinuous space on the finest mesh, reached from the continuous space of the same degree on the
+// same mesh by injection (each DG node takes the continuous value at its lattice point, Dirichlet
+// points 0); restriction is its transpose, a gather of the up to eight DG nodes on each lattice point.
+// The DG level's vectors are flat (n_dofs x 1 x 1, nothing constrained).
 #pragma once
 
 #include <array>
@@ -26,6 +32,7 @@ struct MgLevel {
   mfx_op* op = nullptr;
   int nx = 0, ny = 0, nz = 0, Mx = 0, My = 0, Mz = 0;
   uint32_t dmask = 0;
+  bool dg = false;            // SIPG level (top of the hierarchy; flat vectors, no Dirichlet DoFs)
   double lo = 0.0, hi = 0.0;  // Chebyshev interval of the smoother
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *c64 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *c32 = nullptr;
@@ -177,6 +184,62 @@ __global__ void mg_restrict_kernel(const __grid_constant__ XferArgs a, const Rea
   }
 }
 
+// Injection of the continuous level c into the DG level f on the same cells: xf[c n^3 + i] += xc at the
+// lattice point of cell c's node i (nothing for Dirichlet points).  One thread per DG DoF.
+template <typename Real>
+__global__ void mg_inject_kernel(const __grid_constant__ XferArgs a, int n, const Real* __restrict__ xc,
+                                 Real* __restrict__ xf, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int k = n - 1, n3 = n * n * n;
+  const int64_t total = (int64_t)a.nxc * a.nyc * a.nzc * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int i = (int)(idx - cell * n3);
+    const int64_t I = (cell % a.nxc) * k + i % n;
+    const int64_t J = ((cell / a.nxc) % a.nyc) * k + (i / n) % n;
+    const int64_t L = (cell / ((int64_t)a.nxc * a.nyc)) * k + i / (n * n);
+    if (!on_dirichlet(a.dmask_c, I, J, L, a.Mxc, a.Myc, a.Mzc)) xf[idx] += xc[I + a.Mxc * (J + (int64_t)a.Myc * L)];
+  }
+}
+
+// Transpose of the injection: xc[p] += sum of xf over the DG nodes at lattice point p (free p only).
+// Along one direction a lattice index I is node I mod k of cell I / k, or, where I is a multiple of k,
+// node k of cell I / k - 1 and node 0 of cell I / k (those that exist).  One thread per lattice point.
+template <typename Real>
+__global__ void mg_inject_t_kernel(const __grid_constant__ XferArgs a, int n, const Real* __restrict__ xf,
+                                   Real* __restrict__ xc, const int32_t* skip) {
+  if (skip && *skip) return;
+  const int k = n - 1, n3 = n * n * n;
+  const int64_t total = (int64_t)a.Mxc * a.Myc * a.Mzc;
+  const int nc[3] = {a.nxc, a.nyc, a.nzc};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = p % a.Mxc, rest = p / a.Mxc, J = rest % a.Myc, L = rest / a.Myc;
+    if (on_dirichlet(a.dmask_c, I, J, L, a.Mxc, a.Myc, a.Mzc)) continue;
+    const int64_t lat[3] = {I, J, L};
+    int cnt[3], cc[3][2], ci[3][2];
+    for (int d = 0; d < 3; ++d) {
+      const int c = (int)(lat[d] / k), r = (int)(lat[d] - (int64_t)c * k);
+      cnt[d] = 0;
+      if (r == 0 && c > 0) {
+        cc[d][cnt[d]] = c - 1;
+        ci[d][cnt[d]++] = k;
+      }
+      if (c < nc[d]) {
+        cc[d][cnt[d]] = c;
+        ci[d][cnt[d]++] = r;
+      }
+    }
+    Real s = Real(0);
+    for (int c3 = 0; c3 < cnt[2]; ++c3)
+      for (int c2 = 0; c2 < cnt[1]; ++c2)
+        for (int c1 = 0; c1 < cnt[0]; ++c1) {
+          const int64_t cell = cc[0][c1] + (int64_t)nc[0] * (cc[1][c2] + (int64_t)nc[1] * cc[2][c3]);
+          s += xf[cell * n3 + ci[0][c1] + n * (ci[1][c2] + n * ci[2][c3])];
+        }
+    xc[p] += s;
+  }
+}
+
 // out = (in1 - in2) on free DoFs (in2 may be null: out = in1), 0 on Dirichlet DoFs.
 template <typename Real>
 __global__ void mg_masked_diff_kernel(int Mx, int My, int Mz, uint32_t dmask, const Real* __restrict__ in1,
@@ -260,6 +323,16 @@ template <typename Real>
 static mfx_status mg_transfer(mfx_mg* mg, int l, bool prolong, const Real* in, Real* out, const int32_t* skip,
                               cudaStream_t s) {
   const XferArgs& a = mg->xfer[l];
+  if (mg->levels[l].dg) {
+    const int n = mg->k + 1;
+    const int64_t work = prolong ? mg->levels[l].op->n_dofs : (int64_t)a.Mxc * a.Myc * a.Mzc;
+    if (prolong)
+      mg_inject_kernel<Real><<<vec_grid(work), 256, 0, s>>>(a, n, in, out, skip);
+    else
+      mg_inject_t_kernel<Real><<<vec_grid(work), 256, 0, s>>>(a, n, in, out, skip);
+    MFX_CUDA_TRY(cudaGetLastError());
+    return MFX_OK;
+  }
   const unsigned cells = (unsigned)((int64_t)a.nxc * a.nyc * a.nzc);
   const int F = 2 * mg->k + 1;
   const int threads = std::min(256, std::max(32, (F * F + 31) / 32 * 32));
@@ -414,6 +487,11 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
   if (!fm.structured) return set_error(MFX_EUNSUPPORTED, "multigrid levels need a structured mesh");
   if (desc->coef_kind == MFX_COEF_QPOINT)
     return set_error(MFX_EUNSUPPORTED, "multigrid: per-quadrature-point coefficients exist on one level only");
+  const bool dg_top = desc->discretization == MFX_SIPG;
+  if (dg_top && desc->coef_kind != MFX_COEF_CONSTANT)
+    return set_error(MFX_EUNSUPPORTED, "SIPG takes a constant coefficient");
+  mfx_op_desc cg_desc = *desc;  // the continuous levels
+  cg_desc.discretization = MFX_CONTINUOUS;
   mfx_mg_params p;
   mfx_mg_params_default(&p);
   if (params) p = *params;
@@ -429,7 +507,8 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
   mg->k = desc->degree;
   mg->degree = p.smoother_degree;
   mg->has_f32 = (desc->precisions == 0 || (desc->precisions & 2));
-  const int nl = (int)sizes.size();
+  const int ncg = (int)sizes.size();
+  const int nl = ncg + (dg_top ? 1 : 0);
   mg->levels.resize(nl);
   mg->xfer.resize(nl);
   cudaStream_t s = (cudaStream_t)stream;
@@ -441,12 +520,12 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
   MFX_CUDA_TRY(cudaStreamSynchronize(s));
   // meshes: the finest is a copy of the caller's; each coarser one takes every other vertex
   std::vector<double> verts = fm.vertices;
-  for (int l = nl - 1; l >= 0; --l) {
+  for (int l = ncg - 1; l >= 0; --l) {
     MgLevel& L = mg->levels[l];
     L.nx = sizes[l][0];
     L.ny = sizes[l][1];
     L.nz = sizes[l][2];
-    if (l < nl - 1) {
+    if (l < ncg - 1) {
       const int fx = sizes[l + 1][0], fy = sizes[l + 1][1];
       std::vector<double> c((size_t)3 * (L.nx + 1) * (L.ny + 1) * (L.nz + 1));
       for (int kz = 0; kz <= L.nz; ++kz)
@@ -460,7 +539,7 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
     mfx_status st = mfx_mesh_create_structured(&L.mesh, L.nx, L.ny, L.nz, verts.data());
     if (st != MFX_OK) return fail(st);
     L.mesh->m.dirichlet = fm.dirichlet;
-    st = mfx_operator_create(&L.op, L.mesh, desc, (mfx_stream)mg->stream);
+    st = mfx_operator_create(&L.op, L.mesh, &cg_desc, (mfx_stream)mg->stream);
     if (st != MFX_OK) return fail(st);
     st = ensure_workspace(L.op);
     if (st != MFX_OK) return fail(st);
@@ -468,6 +547,20 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
     L.My = mg->k * L.ny + 1;
     L.Mz = mg->k * L.nz + 1;
     L.dmask = fm.dirichlet;
+  }
+  if (dg_top) {  // the SIPG operator of the caller's mesh
+    MgLevel& L = mg->levels[ncg];
+    L.dg = true;
+    L.nx = fm.nx;
+    L.ny = fm.ny;
+    L.nz = fm.nz;
+    mfx_status st = mfx_operator_create(&L.op, mesh, desc, (mfx_stream)mg->stream);
+    if (st != MFX_OK) return fail(st);
+    st = ensure_workspace(L.op);
+    if (st != MFX_OK) return fail(st);
+    L.Mx = (int)L.op->n_dofs;
+    L.My = L.Mz = 1;
+    L.dmask = 0;
   }
   // level vectors
   size_t total = 0;
@@ -510,6 +603,7 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
     a.Mzf = Fl.Mz;
     a.dmask_c = C.dmask;
     a.dmask_f = Fl.dmask;
+    if (Fl.dg) continue;  // injection: no interpolation table
     for (int i = 0; i < F; ++i) {
       const double pos = i <= K ? gll[i] / 2.0 : (1.0 + gll[i - K]) / 2.0;
       for (int j = 0; j < N; ++j) {

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libmfx.so")
 
 F64, F32 = 0, 1
 COEF_CONSTANT, COEF_TRIG, COEF_QPOINT, COEF_FUNCTION = 0, 1, 2, 3
+CONTINUOUS, SIPG = 0, 1  # discretization of an operator (mfx_op_desc.discretization)
 PRECOND_JACOBI, PRECOND_CHEBYSHEV = 0, 1
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, EMESH, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 NOT_CONVERGED, BREAKDOWN = 1, 2
@@ -39,14 +40,16 @@ class OpDesc(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("coef_kind", ctypes.c_int32),
                 ("precisions", ctypes.c_int32), ("coef_par", ctypes.c_double * 2),
                 ("coef_qpoint", ctypes.c_void_p), ("cells_per_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("coef_fn", POINT_FN), ("coef_user", ctypes.c_void_p)]
+                ("discretization", ctypes.c_int32), ("coef_fn", POINT_FN), ("coef_user", ctypes.c_void_p),
+                ("dg_penalty", ctypes.c_double)]
 
 
 class OpInfo(ctypes.Structure):
     _fields_ = [("n_dofs", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_constrained", ctypes.c_int64),
                 ("n_masters", ctypes.c_int64), ("n_hanging", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
                 ("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("structured", ctypes.c_int32),
-                ("cells_per_block", ctypes.c_int32)]
+                ("cells_per_block", ctypes.c_int32), ("discretization", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):
@@ -284,7 +287,10 @@ class Operator:
     """The condensed Q_k operator of one mesh (geometry and tables on the device)."""
 
     def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), precisions=3,
-                 coef_qpoint=None, stream=None, cells_per_block=0, coef_fn=None):
+                 coef_qpoint=None, stream=None, cells_per_block=0, coef_fn=None, discretization=CONTINUOUS,
+                 dg_penalty=1.0):
+        """discretization=SIPG: the symmetric interior penalty DG operator (uniform box, constant
+        coefficient coef_par[0], penalty eta = dg_penalty, cell-major DoFs)."""
         d = OpDesc()
         if coef_fn is not None:  # a(x, y, z) on the host at every quadrature point
             coef_kind = COEF_FUNCTION
@@ -296,6 +302,8 @@ class Operator:
         d.coef_par[0], d.coef_par[1] = coef_par
         d.coef_qpoint = coef_qpoint.data_ptr() if coef_qpoint is not None else None
         d.cells_per_block = cells_per_block
+        d.discretization = discretization
+        d.dg_penalty = dg_penalty
         h = ctypes.c_void_p()
         check(lib().mfx_operator_create(ctypes.byref(h), mesh.handle, ctypes.byref(d), _stream(stream)))
         self.handle = h
@@ -563,9 +571,12 @@ class Multigrid:
     Chebyshev smoothers, exact coarse solve; V-cycle application and MG-preconditioned solves."""
 
     def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), max_levels=0,
-                 smoother_degree=6, smoothing_range=20.0, lanczos_steps=15, stream=None):
+                 smoother_degree=6, smoothing_range=20.0, lanczos_steps=15, stream=None, discretization=CONTINUOUS,
+                 dg_penalty=1.0):
+        """discretization=SIPG: the SIPG operator on top of the continuous hierarchy of the same mesh."""
         d = OpDesc()
         d.degree, d.n_q_1d, d.coef_kind, d.precisions = degree, 0, coef_kind, 3
+        d.discretization, d.dg_penalty = discretization, dg_penalty
         d.coef_par[0], d.coef_par[1] = coef_par
         p = MgParams()
         lib().mfx_mg_params_default(ctypes.byref(p))

@@ -1,0 +1,177 @@
+"""SIPG operator (discretization = SIPG): vmult and diagonal equal the oracle's assembled SIPG matrix
+(oracle/dg.py) element by element, FP64 within 1e-12 and FP32 within 1e-5 (relative to the largest
+entry), for every compiled degree, anisotropic cells and every kind of face mask; PCG on the DG operator
+solves its system; the multigrid hierarchy with the SIPG level on top equals the oracle's cycle."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import dg as odg, fem, mg as omg
+from paper_1910_13247_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mfx():
+    from paper_1910_13247_gb300 import build, mfx as m
+    build.build()
+    m.lib()
+    return m
+
+
+def box(dims, lengths):
+    return synthetic.lattice_vertices(*dims) * np.asarray(lengths)[None, :]
+
+
+def sipg(mfx, dims, k, lengths=(1.0, 1.0, 1.0), faces=0x3F, eta=1.0, coef=1.0, precisions=3):
+    mesh = mfx.Mesh.structured_box(*dims, box(dims, lengths), dirichlet=faces)
+    return mfx.Operator(mesh, k, mfx.COEF_CONSTANT, (coef, 0.0), precisions=precisions, discretization=mfx.SIPG,
+                        dg_penalty=eta)
+
+
+def apply(op, x, dtype):
+    src = torch.tensor(x, device=DEV, dtype=dtype)
+    dst = torch.empty_like(src)
+    op.vmult(src, dst)
+    return dst.cpu().double().numpy()
+
+
+CASES = [
+    ((3, 2, 4), 1, (1.0, 1.0, 1.0), 0x3F, 1.0, 1.0),
+    ((3, 3, 2), 2, (1.0, 0.7, 1.3), 0x3F, 1.5, 0.8),
+    ((2, 3, 2), 3, (1.0, 1.0, 1.0), 0b010110, 1.0, 1.0),
+    ((3, 2, 2), 4, (2.0, 1.0, 1.0), 0, 2.0, 1.0),
+    ((2, 2, 3), 5, (1.0, 1.0, 1.0), 0b101001, 1.0, 3.0),
+    ((2, 2, 2), 6, (1.0, 0.5, 1.0), 0x3F, 1.0, 1.0),
+    ((2, 1, 2), 7, (1.0, 1.0, 1.0), 0b001100, 1.0, 1.0),
+    ((2, 2, 1), 8, (1.0, 1.0, 0.5), 0b100001, 1.0, 1.0),
+]
+
+
+@pytest.mark.parametrize("dims,k,lengths,faces,eta,coef", CASES)
+def test_sipg_vmult_and_diagonal_equal_the_oracle(mfx, dims, k, lengths, faces, eta, coef):
+    K = odg.dg_operator(*dims, k, lengths, faces, eta=eta, coef=coef)
+    op = sipg(mfx, dims, k, lengths, faces, eta, coef)
+    info = op.info()
+    assert op.n_dofs == K.shape[0] and info["discretization"] == mfx.SIPG and info["n_constrained"] == 0
+    x = synthetic.uniform_vector(op.n_dofs, 300 + k)
+    ref = K @ x
+    scale = np.abs(ref).max()
+    y = apply(op, x, torch.float64)
+    assert np.abs(y - ref).max() <= 1e-12 * scale, np.abs(y - ref).max() / scale
+    y32 = apply(op, x, torch.float32)
+    assert np.abs(y32 - ref).max() <= 1e-5 * scale, np.abs(y32 - ref).max() / scale
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = K.diagonal()
+    assert np.abs(d.cpu().numpy() - dref).max() <= 1e-12 * np.abs(dref).max()
+    d32 = torch.empty(op.n_dofs, dtype=torch.float32, device=DEV)
+    op.diagonal(d32)
+    assert np.abs(d32.cpu().double().numpy() - dref).max() <= 1e-6 * np.abs(dref).max()
+    # cell-major DoFs, nothing constrained
+    t = op.tables()
+    assert np.array_equal(t["cell_dofs"].ravel(), np.arange(op.n_dofs)) and t["constrained"].size == 0
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_sipg_many_cells_span_several_blocks_and_a_ragged_tail(mfx, k):
+    """More cells than one CTA batch and than one wave of the grid, with a partial last batch."""
+    dims = (7, 5, 3)
+    K = odg.dg_operator(*dims, k, (1.0, 1.2, 0.9), 0b011011)
+    op = sipg(mfx, dims, k, (1.0, 1.2, 0.9), 0b011011)
+    x = synthetic.uniform_vector(op.n_dofs, 41)
+    ref = K @ x
+    y = apply(op, x, torch.float64)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_sipg_pure_neumann_kernel_is_the_constants(mfx):
+    """Without Dirichlet faces the SIPG form vanishes on constants (no jumps, no gradients)."""
+    op = sipg(mfx, (3, 3, 3), 3, faces=0)
+    one = np.ones(op.n_dofs)
+    y = apply(op, one, torch.float64)
+    x = synthetic.uniform_vector(op.n_dofs, 5)
+    assert np.abs(y).max() <= 1e-12 * np.abs(apply(op, x, torch.float64)).max()
+
+
+def test_sipg_pcg_solves_the_system(mfx):
+    dims, k = (4, 4, 4), 2
+    K = odg.dg_operator(*dims, k)
+    op = sipg(mfx, dims, k)
+    b = synthetic.uniform_vector(op.n_dofs, 9)
+    x = torch.zeros(op.n_dofs, dtype=torch.float64, device=DEV)
+    st = op.solve(torch.tensor(b, device=DEV), x, tol=1e-10, precond=mfx.PRECOND_CHEBYSHEV, cheb_degree=4)
+    assert st["status"] == 0
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(b - K @ xs) <= 1.0001e-10 * np.linalg.norm(b)
+    ref = spla.spsolve(K.tocsc(), b)
+    assert np.linalg.norm(xs - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_sipg_rejects_what_it_does_not_cover(mfx):
+    v = synthetic.deformed_vertices(3, 3, 3)
+    mesh = mfx.Mesh.structured_box(3, 3, 3, v)
+    with pytest.raises(mfx.MfxError) as e:
+        mfx.Operator(mesh, 2, discretization=mfx.SIPG)
+    assert e.value.code == mfx.EUNSUPPORTED
+    mesh = mfx.Mesh.structured_box(3, 3, 3, box((3, 3, 3), (1, 1, 1)))
+    with pytest.raises(mfx.MfxError) as e:
+        mfx.Operator(mesh, 2, mfx.COEF_TRIG, (1.0, 0.5), discretization=mfx.SIPG)
+    assert e.value.code == mfx.EUNSUPPORTED
+    op = mfx.Operator(mesh, 2, discretization=mfx.SIPG)
+    b = torch.zeros(op.n_dofs, dtype=torch.float64, device=DEV)
+    with pytest.raises(mfx.MfxError) as e:
+        op.rhs_function(lambda x, y, z: 1.0, b)
+    assert e.value.code == mfx.EUNSUPPORTED
+    op.distribute(b)  # nothing constrained: a no-op
+
+
+def dg_hierarchy(mfx, n, k, faces, degree=4, lengths=(1.0, 1.0, 1.0)):
+    verts = box((n, n, n), lengths)
+    mesh = mfx.Mesh.structured_box(n, n, n, verts, dirichlet=faces)
+    g = mfx.Multigrid(mesh, k, mfx.COEF_CONSTANT, (1.0, 0.0), smoother_degree=degree, discretization=mfx.SIPG)
+    meshes, sizes = omg.level_meshes(n, n, n, k, verts, dirichlet=faces)
+    assert g.n_levels == len(meshes) + 1
+    Kdg = odg.dg_operator(n, n, n, k, lengths, faces)
+    P = odg.injection(meshes[-1], k)
+    bounds = [(1.0, 2.0)] + [g.bounds(l) for l in range(1, g.n_levels)]
+    h = omg.Hierarchy(meshes, sizes, k, fem.COEF_CONSTANT, (1.0, 0.0), degree=degree, bounds=bounds,
+                      dg_top=(Kdg, P))
+    # the library's Lanczos interval of the SIPG level agrees with the oracle's own estimate
+    h2 = omg.Hierarchy(meshes[-1:], sizes[-1:], k, fem.COEF_CONSTANT, (1.0, 0.0), degree=degree, dg_top=(Kdg, P))
+    lo, hi = g.bounds(g.n_levels - 1)
+    assert abs(hi - h2.bounds[-1][1]) < 1e-6 * hi
+    return g, h, Kdg
+
+
+@pytest.mark.parametrize("n,k,faces", [(8, 2, 0x3F), (4, 3, 0x3F), (8, 1, 0b001111), (4, 4, 0x3F)])
+def test_sipg_multigrid_vcycle_equals_the_oracle_cycle(mfx, n, k, faces):
+    g, h, Kdg = dg_hierarchy(mfx, n, k, faces)
+    assert g.fine.info()["discretization"] == mfx.SIPG
+    r = synthetic.uniform_vector(Kdg.shape[0], 90 + k)
+    ref = h.vcycle(r)
+    z = torch.empty(Kdg.shape[0], dtype=torch.float64, device=DEV)
+    g.vcycle(torch.tensor(r, device=DEV), z)
+    zz = z.cpu().numpy()
+    assert np.linalg.norm(zz - ref) < 1e-10 * np.linalg.norm(ref), np.linalg.norm(zz - ref) / np.linalg.norm(ref)
+    z32 = torch.empty(Kdg.shape[0], dtype=torch.float32, device=DEV)
+    g.vcycle(torch.tensor(r, device=DEV).float(), z32)
+    assert np.linalg.norm(z32.cpu().double().numpy() - ref) < 1e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_sipg_multigrid_pcg_matches_the_oracle(mfx, mixed):
+    g, h, Kdg = dg_hierarchy(mfx, 8, 2, 0x3F)
+    b = synthetic.uniform_vector(Kdg.shape[0], 95)
+    x = torch.zeros(Kdg.shape[0], dtype=torch.float64, device=DEV)
+    st = g.solve(torch.tensor(b, device=DEV), x, tol=1e-10, mixed=mixed)
+    assert st["status"] == 0
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(b - Kdg @ xs) <= 1.0001e-10 * np.linalg.norm(b)
+    if not mixed:
+        ref = fem.pcg(lambda v: Kdg @ v, b, h.vcycle, tol=1e-10)
+        assert abs(st["iterations"] - ref.iterations) <= 1, (st["iterations"], ref.iterations)
+        assert st["iterations"] <= 15
