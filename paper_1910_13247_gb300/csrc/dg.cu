@@ -10,15 +10,28 @@
 // sigma_F = eta (k+1)^2 / h on interior faces and 2 eta (k+1)^2 / h on Dirichlet faces (h the cell
 // size normal to the face), (k+1)-point Gauss quadrature on cells and faces.
 //
-// Element-centric: a CTA takes CB cells, one thread per line of a cell, and computes each cell's
-// output row block on its own, so dst is written once per entry, without atomics:
-//   * cell term in Kronecker form, c_x (K1 (x) M1 (x) M1) + c_y (M1 (x) K1 (x) M1) + c_z (M1 (x) M1 (x) K1)
-//     with the exact 1D stiffness / mass matrices K1, M1 of the nodal basis (n-point Gauss is exact
-//     for them) and c_d = a V / h_d^2: eight 1D sweeps in shared memory;
-//   * the six faces in turn: traces (value and normal derivative at the face nodes) of the cell and
-//     of the neighbour across the face, interpolated to the face Gauss points, the face integrand, and
-//     its transpose back onto the cell's face nodes (value test functions) and onto every node of each
-//     normal line (normal-derivative test functions).
+// On a uniform Cartesian mesh with a constant coefficient the operator is a sum of Kronecker products,
+//   A = a sum_d  L_d (x) (h_e M1) (x) (h_f M1)      (e, f the other two directions),
+// with M1 the exact 1D mass matrix of the nodal basis on [0, 1] (n-point Gauss is exact for it) and L_d
+// the 1D SIPG matrix along direction d: per cell K1 / h_d (K1 the 1D stiffness on [0, 1]) plus, at each
+// cell end, rank-two face terms in the end value and end derivative of the cell's own line and of the
+// neighbour's line across that end.  With GLL nodes the end value is the end node, so for a line x of a
+// cell (l_j the 1D basis, d0_j = l_j'(0), d1_j = l_j'(1), K = n - 1, f = 1/2 at interior ends, 1 at
+// Dirichlet ends, 0 at natural ends, sigma the end's penalty, w the neighbour's line):
+//   lower end:  (L x)_i += f (delta_i0 g0 + d0_i x_0 / h) + sigma delta_i0 x_0,   g0 = sum_j d0_j x_j / h
+//      interior also:  += delta_i0 gw / 2 - d0_i w_K / (2h) - sigma delta_i0 w_K, gw = sum_j d1_j w_j / h
+//   upper end:  (L x)_i += -f (delta_iK g1 + d1_i x_K / h) + sigma delta_iK x_K,  g1 = sum_j d1_j x_j / h
+//      interior also:  += -delta_iK gw / 2 + d1_i w_0 / (2h) - sigma delta_iK w_0, gw = sum_j d0_j w_j / h
+// (the SIPG face integrals of one direction; their tangential factors are the tangential mass matrices).
+//
+// Element-centric: a CTA takes CB cells (one contiguous chunk of DoFs, staged in shared memory by
+// coalesced loads), one thread per line of a cell, and writes each cell's output block once, without
+// atomics.  Per cell, with the tangential masses shared between directions:
+//   P = L_x u, Q = L_y u, R = L_z u          (1D SIPG sweeps; the neighbours' lines from global memory)
+//   T1 = M_y P, T2 = M_x Q, T3 = M_x R
+//   y = M_z (T1 + T2) + M_y T3               (eight sweeps, three barriers per batch of cells)
+// The 1D tables are compile-time-indexed kernel parameters in the kernel's own precision, so the
+// contractions read them as constant-bank operands.
 #include <algorithm>
 
 #include "mfx_internal.h"
@@ -32,25 +45,45 @@ struct DgArgs {
   int64_t n_cells;
   double h[3];
   double coef, sig_int[3], sig_bnd[3];
+  double scale[3];  // a h_e h_f: the factor of direction d's term
   uint32_t dmask;
-  // 1D tables (n <= 9): S[q][i] = l_i(x_q), K1, M1 (n x n), endpoint values / derivatives
-  double S[kMaxN * kMaxN], K1[kMaxN * kMaxN], M1[kMaxN * kMaxN], wq[kMaxN];
-  double d0[kMaxN], d1[kMaxN];  // l_i'(0), l_i'(1)
+  // 1D tables (n <= 9): K1, M1 (n x n, row-major), end derivatives l_i'(0), l_i'(1)
+  double K1[kMaxN * kMaxN], M1[kMaxN * kMaxN], d0[kMaxN], d1[kMaxN];
+  float K1f[kMaxN * kMaxN], M1f[kMaxN * kMaxN], d0f[kMaxN], d1f[kMaxN];
   const int32_t* skip;
 };
 
 template <typename Real>
-__device__ __forceinline__ Real tab(const double* t, int i) {
-  return (Real)t[i];
+struct DgTab;
+template <>
+struct DgTab<double> {
+  static __device__ __forceinline__ const double* K1(const DgArgs& a) { return a.K1; }
+  static __device__ __forceinline__ const double* M1(const DgArgs& a) { return a.M1; }
+  static __device__ __forceinline__ const double* d0(const DgArgs& a) { return a.d0; }
+  static __device__ __forceinline__ const double* d1(const DgArgs& a) { return a.d1; }
+};
+template <>
+struct DgTab<float> {
+  static __device__ __forceinline__ const float* K1(const DgArgs& a) { return a.K1f; }
+  static __device__ __forceinline__ const float* M1(const DgArgs& a) { return a.M1f; }
+  static __device__ __forceinline__ const float* d0(const DgArgs& a) { return a.d0f; }
+  static __device__ __forceinline__ const float* d1(const DgArgs& a) { return a.d1f; }
+};
+
+// Line `line` (0 .. n^2 - 1) of an n^3 block along direction dir: first element and stride.
+template <int N>
+__device__ __forceinline__ void dg_line(int dir, int line, int* base, int* stride) {
+  constexpr int N2 = N * N;
+  const int p = line % N, q = line / N;
+  *base = dir == 0 ? N * p + N2 * q : (dir == 1 ? p + N2 * q : p + N * q);
+  *stride = dir == 0 ? 1 : (dir == 1 ? N : N2);
 }
 
-// out = M along direction dir (0: i1, 1: i2, 2: i3) of an n^3 cube; thread owns line `line`
+// out = M along direction dir on one line (M a compile-time-indexed 1D table)
 template <int N, typename Real>
-__device__ __forceinline__ void dg_sweep(const Real* in, Real* out, const double* M, int dir, int line) {
-  constexpr int N2 = N * N;
-  const int a = line % N, b = line / N;
-  const int base = dir == 0 ? N * a + N2 * b : (dir == 1 ? a + N2 * b : a + N * b);
-  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N2);
+__device__ __forceinline__ void dg_sweep(const Real* in, Real* out, const Real* M, int dir, int line) {
+  int base, stride;
+  dg_line<N>(dir, line, &base, &stride);
   Real x[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) x[i] = in[base + i * stride];
@@ -58,155 +91,150 @@ __device__ __forceinline__ void dg_sweep(const Real* in, Real* out, const double
   for (int i = 0; i < N; ++i) {
     Real s = Real(0);
 #pragma unroll
-    for (int j = 0; j < N; ++j) s += tab<Real>(M, i * N + j) * x[j];
+    for (int j = 0; j < N; ++j) s += M[i * N + j] * x[j];
     out[base + i * stride] = s;
   }
+}
+
+// The 1D SIPG operator along direction d on one line of cell `cell` (own data u in shared memory, the
+// neighbours' lines read from src), times a h_e h_f.
+template <int N, typename Real>
+__device__ __forceinline__ void dg_line_sipg(const DgArgs& a, const Real* __restrict__ u, Real* __restrict__ out,
+                                             const Real* __restrict__ src, int64_t cell, const int* cidx, int d,
+                                             int line) {
+  constexpr int N3 = N * N * N, K = N - 1;
+  const Real* K1 = DgTab<Real>::K1(a);
+  const Real* d0 = DgTab<Real>::d0(a);
+  const Real* d1 = DgTab<Real>::d1(a);
+  int base, stride;
+  dg_line<N>(d, line, &base, &stride);
+  const int dims[3] = {a.nx, a.ny, a.nz};
+  const Real hinv = Real(1.0 / a.h[d]);
+  Real x[N], y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = u[base + i * stride];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Real s = Real(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) s += K1[i * N + j] * x[j];
+    y[i] = s * hinv;
+  }
+  const bool lo_nb = cidx[d] > 0, hi_nb = cidx[d] + 1 < dims[d];
+  const bool lo_dir = !lo_nb && ((a.dmask >> (2 * d)) & 1u), hi_dir = !hi_nb && ((a.dmask >> (2 * d + 1)) & 1u);
+  const int64_t step = d == 0 ? 1 : (d == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny);
+  const Real sig_i = Real(a.sig_int[d]), sig_b = Real(a.sig_bnd[d]);
+  if (lo_nb || lo_dir) {  // lower end
+    const Real f = lo_nb ? Real(0.5) : Real(1.0);
+    const Real sg = lo_nb ? sig_i : sig_b;
+    Real g0 = Real(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) g0 += d0[j] * x[j];
+    const Real fx0 = f * x[0] * hinv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] += d0[i] * fx0;
+    y[0] += f * g0 * hinv + sg * x[0];
+    if (lo_nb) {
+      const Real* w = src + (cell - step) * N3 + base;
+      Real wv[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
+      Real gw = Real(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) gw += d1[j] * wv[j];
+      const Real wKh = Real(0.5) * wv[K] * hinv;
+#pragma unroll
+      for (int i = 0; i < N; ++i) y[i] -= d0[i] * wKh;
+      y[0] += Real(0.5) * gw * hinv - sig_i * wv[K];
+    }
+  }
+  if (hi_nb || hi_dir) {  // upper end
+    const Real f = hi_nb ? Real(0.5) : Real(1.0);
+    const Real sg = hi_nb ? sig_i : sig_b;
+    Real g1 = Real(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) g1 += d1[j] * x[j];
+    const Real fxK = f * x[K] * hinv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] -= d1[i] * fxK;
+    y[K] += sg * x[K] - f * g1 * hinv;
+    if (hi_nb) {
+      const Real* w = src + (cell + step) * N3 + base;
+      Real wv[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
+      Real gw = Real(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) gw += d0[j] * wv[j];
+      const Real w0h = Real(0.5) * wv[0] * hinv;
+#pragma unroll
+      for (int i = 0; i < N; ++i) y[i] += d1[i] * w0h;
+      y[K] -= Real(0.5) * gw * hinv + sig_i * wv[0];
+    }
+  }
+  const Real sc = Real(a.scale[d]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = sc * y[i];
 }
 
 template <int N, typename Real>
 __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ DgArgs a, const Real* __restrict__ src,
                                                         Real* __restrict__ dst) {
-  constexpr int N2 = N * N, N3 = N2 * N, K = N - 1;
+  constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int CB = 128 / N2 > 0 ? 128 / N2 : 1;
+  constexpr int CH = CB * N3;  // DoFs of one batch of cells
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sh = reinterpret_cast<Real*>(smem_raw);
+  Real* U = reinterpret_cast<Real*>(smem_raw);  // u, then T1
+  Real* P = U + CH;                             // P, then M_z (T1 + T2)
+  Real* Q = P + CH;                             // Q, then M_y T3
+  Real* R = Q + CH;
+  Real* T2 = R + CH;
+  Real* T3 = T2 + CH;
   const int cl = threadIdx.x / N2;
   const int r = threadIdx.x - cl * N2;
   const bool lane_ok = cl < CB;
-  // per cell: u, y, T1, T2, B1 (n^3 each) and the face buffers (4 traces + 2 integrands, n^2 each)
-  Real* u = sh + (size_t)(lane_ok ? cl : 0) * (5 * N3 + 6 * N2);
-  Real* y = u + N3;
-  Real* T1 = y + N3;
-  Real* T2 = T1 + N3;
-  Real* B1 = T2 + N3;
-  Real* fb = B1 + N3;  // ov, od, nv, nd, fval, fder
+  const Real* M1 = DgTab<Real>::M1(a);
+  const int64_t total = a.n_cells * N3;
   const int64_t nbatch = (a.n_cells + CB - 1) / CB;
   for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+    const int64_t first = bt * CB * (int64_t)N3;
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) U[i] = first + i < total ? src[first + i] : Real(0);
+    __syncthreads();
     const int64_t cell = bt * CB + cl;
     const bool act = lane_ok && cell < a.n_cells;
-    const int cx = act ? (int)(cell % a.nx) : 0;
-    const int64_t rest = act ? cell / a.nx : 0;
-    const int cy = (int)(rest % a.ny), cz = (int)(rest / a.ny);
-    const int cidx[3] = {cx, cy, cz};
-    const int dims[3] = {a.nx, a.ny, a.nz};
-    if (act)
-      for (int i = r; i < N3; i += N2) u[i] = src[cell * N3 + i];
-    __syncthreads();
-    // ---- cell term
-    const double vol = a.h[0] * a.h[1] * a.h[2];
-    const Real cxf = (Real)(a.coef * vol / (a.h[0] * a.h[0]));
-    const Real cyf = (Real)(a.coef * vol / (a.h[1] * a.h[1]));
-    const Real czf = (Real)(a.coef * vol / (a.h[2] * a.h[2]));
-    if (act) dg_sweep<N, Real>(u, T1, a.K1, 0, r);   // K1_x u
-    if (act) dg_sweep<N, Real>(u, B1, a.M1, 0, r);   // M1_x u
-    __syncthreads();
-    if (act) dg_sweep<N, Real>(T1, T2, a.M1, 1, r);  // M1_y K1_x u
-    __syncthreads();
-    if (act) dg_sweep<N, Real>(T2, T1, a.M1, 2, r);  // M1_z M1_y K1_x u
-    __syncthreads();
-    if (act)
-      for (int i = r; i < N3; i += N2) y[i] = cxf * T1[i];
-    if (act) dg_sweep<N, Real>(B1, T2, a.K1, 1, r);  // K1_y M1_x u
-    __syncthreads();
-    if (act) dg_sweep<N, Real>(T2, T1, a.M1, 2, r);  // M1_z K1_y M1_x u
-    __syncthreads();
-    if (act)
-      for (int i = r; i < N3; i += N2) y[i] += cyf * T1[i];
-    if (act) dg_sweep<N, Real>(B1, T2, a.M1, 1, r);  // M1_y M1_x u
-    __syncthreads();
-    if (act) dg_sweep<N, Real>(T2, T1, a.K1, 2, r);  // K1_z M1_y M1_x u
-    __syncthreads();
-    if (act)
-      for (int i = r; i < N3; i += N2) y[i] += czf * T1[i];
-    __syncthreads();
-    // ---- faces
-    for (int d = 0; d < 3; ++d) {
-      const int e = d == 0 ? 1 : 0, f = d == 2 ? 1 : 2;  // tangential directions (e < f)
-      const int st[3] = {1, N, N2};
-      const double hd = a.h[d];
-      const double area = a.h[e] * a.h[f];
-      for (int s = 0; s < 2; ++s) {
-        const bool has_nb = s == 1 ? cidx[d] + 1 < dims[d] : cidx[d] > 0;
-        const bool dir_face = !has_nb && ((a.dmask >> (2 * d + s)) & 1u);
-        // uniform across the CTA's cells only by accident: every thread runs the same sequence of
-        // barriers and masks its work
-        const int ta = r % N, tb = r / N;  // face node (a, b) = (i_e, i_f)
-        const int fbase = ta * st[e] + tb * st[f];
-        const double* dl = s == 1 ? a.d1 : a.d0;   // own normal derivative at xi_d = s
-        const double* dn = s == 1 ? a.d0 : a.d1;   // neighbour's at xi_d = 1 - s
-        if (act && (has_nb || dir_face)) {
-          Real od = Real(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) od += tab<Real>(dl, j) * u[fbase + j * st[d]];
-          fb[0 * N2 + r] = u[fbase + (s * K) * st[d]];
-          fb[1 * N2 + r] = od / (Real)hd;
-          Real nv = Real(0), nd = Real(0);
-          if (has_nb) {
-            const int64_t ncell = cell + (s == 1 ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny));
-            const Real* un = src + ncell * N3;
-#pragma unroll
-            for (int j = 0; j < N; ++j) nd += tab<Real>(dn, j) * un[fbase + j * st[d]];
-            nv = un[fbase + ((1 - s) * K) * st[d]];
-          }
-          fb[2 * N2 + r] = nv;
-          fb[3 * N2 + r] = nd / (Real)hd;
-        }
-        __syncthreads();
-        // integrand at the face Gauss point (qa, qb) = (ta, tb)
-        if (act && (has_nb || dir_face)) {
-          Real tr[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            Real acc = Real(0);
-            for (int j = 0; j < N; ++j) {
-              const Real sa = tab<Real>(a.S, ta * N + j);
-              for (int l = 0; l < N; ++l) acc += sa * tab<Real>(a.S, tb * N + l) * fb[c * N2 + j + N * l];
-            }
-            tr[c] = acc;
-          }
-          const Real w = (Real)(a.coef * area) * tab<Real>(a.wq, ta) * tab<Real>(a.wq, tb);
-          Real fval, fder;
-          if (has_nb) {
-            const Real sig = (Real)a.sig_int[d];
-            // own side "-" when the face is the cell's upper face (s = 1)
-            const Real Um = s == 1 ? tr[0] : tr[2], Up = s == 1 ? tr[2] : tr[0];
-            const Real Dm = s == 1 ? tr[1] : tr[3], Dp = s == 1 ? tr[3] : tr[1];
-            const Real J = Um - Up, A = Real(0.5) * (Dm + Dp);
-            fval = (s == 1 ? (-A + sig * J) : (A - sig * J)) * w;
-            fder = Real(-0.5) * J * w;
-          } else {
-            const Real sig = (Real)a.sig_bnd[d];
-            const Real dnu = s == 1 ? tr[1] : -tr[1];   // outward normal derivative
-            fval = (-dnu + sig * tr[0]) * w;
-            fder = (s == 1 ? -tr[0] : tr[0]) * w;       // coefficient of d_{+d} v
-          }
-          fb[4 * N2 + r] = fval;
-          fb[5 * N2 + r] = fder;
-        }
-        __syncthreads();
-        // transpose back onto face node (ta, tb) and its normal line
-        if (act && (has_nb || dir_face)) {
-          Real gv = Real(0), gd = Real(0);
-          for (int qa = 0; qa < N; ++qa) {
-            const Real sa = tab<Real>(a.S, qa * N + ta);
-            for (int qb = 0; qb < N; ++qb) {
-              const Real sab = sa * tab<Real>(a.S, qb * N + tb);
-              gv += sab * fb[4 * N2 + qa + N * qb];
-              gd += sab * fb[5 * N2 + qa + N * qb];
-            }
-          }
-          y[fbase + (s * K) * st[d]] += gv;
-          const Real gdh = gd / (Real)hd;
-#pragma unroll
-          for (int j = 0; j < N; ++j) y[fbase + j * st[d]] += tab<Real>(dl, j) * gdh;
-        }
-        __syncthreads();
-      }
+    const int off = (lane_ok ? cl : 0) * N3;
+    if (act) {
+      const int cidx[3] = {(int)(cell % a.nx), (int)((cell / a.nx) % a.ny), (int)(cell / ((int64_t)a.nx * a.ny))};
+      dg_line_sipg<N, Real>(a, U + off, P + off, src, cell, cidx, 0, r);
+      dg_line_sipg<N, Real>(a, U + off, Q + off, src, cell, cidx, 1, r);
+      dg_line_sipg<N, Real>(a, U + off, R + off, src, cell, cidx, 2, r);
     }
-    if (act)
-      for (int i = r; i < N3; i += N2) dst[cell * N3 + i] = y[i];
     __syncthreads();
+    if (act) {
+      dg_sweep<N, Real>(P + off, U + off, M1, 1, r);   // T1 = M_y P
+      dg_sweep<N, Real>(Q + off, T2 + off, M1, 0, r);  // T2 = M_x Q
+      dg_sweep<N, Real>(R + off, T3 + off, M1, 0, r);  // T3 = M_x R
+    }
+    __syncthreads();
+    if (act) {
+      int base, stride;
+      dg_line<N>(2, r, &base, &stride);
+      Real x[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = U[off + base + i * stride] + T2[off + base + i * stride];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        Real s = Real(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s += M1[i * N + j] * x[j];
+        P[off + base + i * stride] = s;                  // M_z (T1 + T2)
+      }
+      dg_sweep<N, Real>(T3 + off, Q + off, M1, 1, r);  // M_y T3
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < CH; i += blockDim.x)
+      if (first + i < total) dst[first + i] = P[i] + Q[i];
   }
 }
 
@@ -264,11 +292,12 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
     a.sig_int[d] = op->dg_penalty * n * n / op->dg_h[d];
     a.sig_bnd[d] = op->dg_penalty * n * n * 2.0 / op->dg_h[d];
   }
+  a.scale[0] = op->dg_coef * op->dg_h[1] * op->dg_h[2];
+  a.scale[1] = op->dg_coef * op->dg_h[0] * op->dg_h[2];
+  a.scale[2] = op->dg_coef * op->dg_h[0] * op->dg_h[1];
   a.coef = op->dg_coef;
   a.dmask = op->dirichlet;
   const BasisTables& b = op->basis;
-  for (int q = 0; q < n; ++q) a.wq[q] = b.wq[q];
-  for (int i = 0; i < n * n; ++i) a.S[i] = b.S[i];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       double k1 = 0.0, m1 = 0.0;
@@ -278,10 +307,14 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
       }
       a.K1[i * n + j] = k1;
       a.M1[i * n + j] = m1;
+      a.K1f[i * n + j] = (float)k1;
+      a.M1f[i * n + j] = (float)m1;
     }
   for (int i = 0; i < n; ++i) {
     a.d0[i] = lagrange_derivative(n, b.gll, i, 0.0);
     a.d1[i] = lagrange_derivative(n, b.gll, i, 1.0);
+    a.d0f[i] = (float)a.d0[i];
+    a.d1f[i] = (float)a.d1[i];
   }
   a.skip = skip;
   return a;
@@ -291,7 +324,7 @@ template <int N, typename Real>
 static mfx_status run_dg(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int CB = 128 / N2 > 0 ? 128 / N2 : 1;
-  const size_t smem = (size_t)CB * (5 * N3 + 6 * N2) * sizeof(Real);
+  const size_t smem = (size_t)6 * CB * N3 * sizeof(Real);
   auto kern = dg_vmult_kernel<N, Real>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
