@@ -181,6 +181,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96^3 Q3 mixed-precision solve")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched solve")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-sipg", action="store_true", help="skip the SIPG DG vmult and multigrid solve")
+    ap.add_argument("--sipg-dims", type=int, nargs=3, default=[128, 64, 64],
+                    help="cells of the SIPG hyper-rectangle (profiling on smaller cases)")
+    ap.add_argument("--sipg-vmult-only", action="store_true", help="SIPG: time the vmult only, no multigrid solve")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
@@ -322,6 +326,9 @@ def main():
             line["batched"] = batched_measurement(mfx, synthetic, torch, np)
         if not args.no_serve:
             line["serving"] = serving_measurement(args.serve_requests)
+        if not args.no_sipg:
+            line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims),
+                                            solve=not args.sipg_vmult_only)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -468,6 +475,63 @@ def mixed_solve_measurement(mfx, synthetic, torch, np):
     out["mg_levels"] = g.n_levels
     out["mg_setup_seconds"] = setup
     out["speedup_mg_mixed_over_cheb_mixed"] = out["mixed"]["seconds"] / out["mg_mixed"]["seconds"]
+    return out
+
+
+def sipg_measurement(mfx, synthetic, torch, np, dims=(128, 64, 64), k=4, solve=True):
+    """The paper's multigrid benchmark discretisation: SIPG of degree 4 on the hyper-rectangle
+    [0, 2] x [0, 1] x [0, 1] (128 x 64 x 64 cells, 65.5M DoFs, homogeneous Dirichlet data on every face).
+    FP32 and FP64 vmult of the DG operator (device-resident vectors larger than L2), then PCG with the
+    V-cycle of the DG -> continuous -> coarser hierarchy (Chebyshev(6) smoothing, exact coarse solve on
+    4 x 2 x 2 cells), FP64 and mixed (FP32 V-cycle inside FP64 defect correction), to 1e-10."""
+    lengths = (2.0, 1.0, 1.0)
+    verts = synthetic.lattice_vertices(*dims) * np.asarray(lengths)[None, :]
+    mesh = mfx.Mesh.structured_box(*dims, verts)
+    op = mfx.Operator(mesh, k, discretization=mfx.SIPG)
+    n = op.n_dofs
+    hbm, peak_kind = peaks()
+    out = {"workload": "SIPG Q%d, %dx%dx%d cells of [0,2]x[0,1]x[0,1]" % ((k,) + tuple(dims)), "n_dofs": n}
+    stream = torch.cuda.current_stream()
+    for name, dt, nbytes in (("vmult_fp32", torch.float32, 8), ("vmult_fp64", torch.float64, 16)):
+        x = torch.tensor(synthetic.uniform_vector(n, 61), device="cuda", dtype=dt)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.vmult(x, y)
+        reps = 30 if dt == torch.float32 else 8
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            op.vmult(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes * n / (ms * 1e-3) / 1e9
+        out[name] = {"gdofs": n / (ms * 1e-3) / 1e9, "ms": ms, "algorithmic_bytes": nbytes * n,
+                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm, "peak_kind": peak_kind}
+        del x, y
+    del op
+    if not solve:
+        return out
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = mfx.Multigrid(mesh, k, smoother_degree=6, discretization=mfx.SIPG)
+    torch.cuda.synchronize()
+    out["mg_levels"] = g.n_levels
+    out["mg_setup_seconds"] = time.perf_counter() - t0
+    b = torch.tensor(synthetic.gaussian_vector(n, 62), device="cuda")
+    for name, mixed in (("mg_fp64", False), ("mg_mixed", True)):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.solve(b, x, tol=1e-10, mixed=mixed, inner_tol=1e-4)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "status": st["status"], "iterations": st["iterations"],
+                     "inner_iterations": st["inner_iterations"], "rel_residual": st["rel_residual"]}
+        if not mixed:
+            # residual reduction per MG-preconditioned CG iteration
+            out[name]["convergence_rate"] = st["rel_residual"] ** (1.0 / max(1, st["iterations"]))
     return out
 
 

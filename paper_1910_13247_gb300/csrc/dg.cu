@@ -43,7 +43,7 @@ int device_sm_count();
 struct DgArgs {
   int nx, ny, nz;
   int64_t n_cells;
-  double h[3];
+  double h[3], hinv[3];
   double coef, sig_int[3], sig_bnd[3];
   double scale[3];  // a h_e h_f: the factor of direction d's term
   uint32_t dmask;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void dg_line_sipg(const DgArgs& a, const Real* __rest
   int base, stride;
   dg_line<N>(d, line, &base, &stride);
   const int dims[3] = {a.nx, a.ny, a.nz};
-  const Real hinv = Real(1.0 / a.h[d]);
+  const Real hinv = Real(a.hinv[d]);
   Real x[N], y[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) x[i] = u[base + i * stride];
@@ -121,56 +121,52 @@ __device__ __forceinline__ void dg_line_sipg(const DgArgs& a, const Real* __rest
     y[i] = s * hinv;
   }
   const bool lo_nb = cidx[d] > 0, hi_nb = cidx[d] + 1 < dims[d];
-  const bool lo_dir = !lo_nb && ((a.dmask >> (2 * d)) & 1u), hi_dir = !hi_nb && ((a.dmask >> (2 * d + 1)) & 1u);
   const int64_t step = d == 0 ? 1 : (d == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny);
-  const Real sig_i = Real(a.sig_int[d]), sig_b = Real(a.sig_bnd[d]);
-  if (lo_nb || lo_dir) {  // lower end
-    const Real f = lo_nb ? Real(0.5) : Real(1.0);
-    const Real sg = lo_nb ? sig_i : sig_b;
-    Real g0 = Real(0);
+  // at an interior end the own and the neighbour's rank-one terms share the vector d0 (d1): one update
+  // with the jump of the end values
+  if (lo_nb) {
+    const Real* w = src + (cell - step) * N3 + base;
+    Real wv[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) g0 += d0[j] * x[j];
-    const Real fx0 = f * x[0] * hinv;
+    for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
+    Real g = Real(0);
 #pragma unroll
-    for (int i = 0; i < N; ++i) y[i] += d0[i] * fx0;
-    y[0] += f * g0 * hinv + sg * x[0];
-    if (lo_nb) {
-      const Real* w = src + (cell - step) * N3 + base;
-      Real wv[N];
+    for (int j = 0; j < N; ++j) g += d0[j] * x[j] + d1[j] * wv[j];
+    const Real jmp = x[0] - wv[K];
+    const Real t = Real(0.5) * jmp * hinv;
 #pragma unroll
-      for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
-      Real gw = Real(0);
+    for (int i = 0; i < N; ++i) y[i] += d0[i] * t;
+    y[0] += Real(0.5) * g * hinv + Real(a.sig_int[d]) * jmp;
+  } else if ((a.dmask >> (2 * d)) & 1u) {
+    Real g = Real(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) gw += d1[j] * wv[j];
-      const Real wKh = Real(0.5) * wv[K] * hinv;
+    for (int j = 0; j < N; ++j) g += d0[j] * x[j];
+    const Real t = x[0] * hinv;
 #pragma unroll
-      for (int i = 0; i < N; ++i) y[i] -= d0[i] * wKh;
-      y[0] += Real(0.5) * gw * hinv - sig_i * wv[K];
-    }
+    for (int i = 0; i < N; ++i) y[i] += d0[i] * t;
+    y[0] += g * hinv + Real(a.sig_bnd[d]) * x[0];
   }
-  if (hi_nb || hi_dir) {  // upper end
-    const Real f = hi_nb ? Real(0.5) : Real(1.0);
-    const Real sg = hi_nb ? sig_i : sig_b;
-    Real g1 = Real(0);
+  if (hi_nb) {
+    const Real* w = src + (cell + step) * N3 + base;
+    Real wv[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) g1 += d1[j] * x[j];
-    const Real fxK = f * x[K] * hinv;
+    for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
+    Real g = Real(0);
 #pragma unroll
-    for (int i = 0; i < N; ++i) y[i] -= d1[i] * fxK;
-    y[K] += sg * x[K] - f * g1 * hinv;
-    if (hi_nb) {
-      const Real* w = src + (cell + step) * N3 + base;
-      Real wv[N];
+    for (int j = 0; j < N; ++j) g += d1[j] * x[j] + d0[j] * wv[j];
+    const Real jmp = x[K] - wv[0];
+    const Real t = Real(0.5) * jmp * hinv;
 #pragma unroll
-      for (int j = 0; j < N; ++j) wv[j] = w[j * stride];
-      Real gw = Real(0);
+    for (int i = 0; i < N; ++i) y[i] -= d1[i] * t;
+    y[K] += Real(a.sig_int[d]) * jmp - Real(0.5) * g * hinv;
+  } else if ((a.dmask >> (2 * d + 1)) & 1u) {
+    Real g = Real(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) gw += d0[j] * wv[j];
-      const Real w0h = Real(0.5) * wv[0] * hinv;
+    for (int j = 0; j < N; ++j) g += d1[j] * x[j];
+    const Real t = x[K] * hinv;
 #pragma unroll
-      for (int i = 0; i < N; ++i) y[i] += d1[i] * w0h;
-      y[K] -= Real(0.5) * gw * hinv + sig_i * wv[0];
-    }
+    for (int i = 0; i < N; ++i) y[i] -= d1[i] * t;
+    y[K] += Real(a.sig_bnd[d]) * x[K] - g * hinv;
   }
   const Real sc = Real(a.scale[d]);
 #pragma unroll
@@ -199,13 +195,21 @@ __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ D
   const int64_t nbatch = (a.n_cells + CB - 1) / CB;
   for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
     const int64_t first = bt * CB * (int64_t)N3;
-    for (int i = threadIdx.x; i < CH; i += blockDim.x) U[i] = first + i < total ? src[first + i] : Real(0);
+    const bool full = first + CH <= total;
+    if (full) {
+#pragma unroll 4
+      for (int i = threadIdx.x; i < CH; i += 128) U[i] = src[first + i];
+    } else {
+      for (int i = threadIdx.x; i < CH; i += 128) U[i] = first + i < total ? src[first + i] : Real(0);
+    }
     __syncthreads();
     const int64_t cell = bt * CB + cl;
     const bool act = lane_ok && cell < a.n_cells;
     const int off = (lane_ok ? cl : 0) * N3;
     if (act) {
-      const int cidx[3] = {(int)(cell % a.nx), (int)((cell / a.nx) % a.ny), (int)(cell / ((int64_t)a.nx * a.ny))};
+      // fewer than 2^31 cells (fewer than 2^31 DoFs): 32-bit coordinates
+      const unsigned c32 = (unsigned)cell, q = c32 / (unsigned)a.nx, cz = q / (unsigned)a.ny;
+      const int cidx[3] = {(int)(c32 - q * (unsigned)a.nx), (int)(q - cz * (unsigned)a.ny), (int)cz};
       dg_line_sipg<N, Real>(a, U + off, P + off, src, cell, cidx, 0, r);
       dg_line_sipg<N, Real>(a, U + off, Q + off, src, cell, cidx, 1, r);
       dg_line_sipg<N, Real>(a, U + off, R + off, src, cell, cidx, 2, r);
@@ -233,8 +237,13 @@ __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ D
       dg_sweep<N, Real>(T3 + off, Q + off, M1, 1, r);  // M_y T3
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < CH; i += blockDim.x)
-      if (first + i < total) dst[first + i] = P[i] + Q[i];
+    if (full) {
+#pragma unroll 4
+      for (int i = threadIdx.x; i < CH; i += 128) dst[first + i] = P[i] + Q[i];
+    } else {
+      for (int i = threadIdx.x; i < CH; i += 128)
+        if (first + i < total) dst[first + i] = P[i] + Q[i];
+    }
   }
 }
 
@@ -289,6 +298,7 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
   a.n_cells = op->n_cells;
   for (int d = 0; d < 3; ++d) {
     a.h[d] = op->dg_h[d];
+    a.hinv[d] = 1.0 / op->dg_h[d];
     a.sig_int[d] = op->dg_penalty * n * n / op->dg_h[d];
     a.sig_bnd[d] = op->dg_penalty * n * n * 2.0 / op->dg_h[d];
   }
