@@ -185,6 +185,7 @@ def main():
     ap.add_argument("--sipg-dims", type=int, nargs=3, default=[128, 64, 64],
                     help="cells of the SIPG hyper-rectangle (profiling on smaller cases)")
     ap.add_argument("--sipg-vmult-only", action="store_true", help="SIPG: time the vmult only, no multigrid solve")
+    ap.add_argument("--sipg-degree", type=int, default=4, help="SIPG polynomial degree (the paper's benchmark: 4)")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
@@ -327,7 +328,7 @@ def main():
         if not args.no_serve:
             line["serving"] = serving_measurement(args.serve_requests)
         if not args.no_sipg:
-            line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims),
+            line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims), k=args.sipg_degree,
                                             solve=not args.sipg_vmult_only)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
