@@ -69,7 +69,11 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   constexpr int PP = CB / 2;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
   constexpr int PITCH = Tm::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
-  constexpr bool PREFETCH = N <= 5;  // 6 N float pairs per thread, loaded one phase group ahead
+  constexpr bool PREFETCH = N <= 5;  // 6 N float pairs per thread, loaded ahead of their use
+  // k <= 2: the next batch's metric is requested right after the current one is used (spreads the
+  // metric stream over the whole batch: Q2 on 128^3 50 -> 56 % of HBM); k = 3, 4: at the start of the
+  // batch, which measured faster there (Q4 on 64^3 0.2894 against 0.296 ms)
+  constexpr bool XPREF = PREFETCH && N <= 3;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* in_tiles = reinterpret_cast<float*>(smem_raw);  // 2 x TILE
@@ -121,6 +125,18 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   bool failed = false, next_issued = false;
   BatchPos pos = batch_pos(a, blockIdx.x);
   if (tma_warp && (int)blockIdx.x < a.n_batches) issue_loads(pos, 0);
+  // metric of the batch in registers (XPREF: requested during the previous batch, right after that
+  // batch's own metric was used); entries of pairs outside a partial batch lie inside the padded
+  // layout and are unused
+  const float2* Gthread = reinterpret_cast<const float2*>(a.metric + (xa2 * N + xa3 * N * N) * CB + 2 * c);
+  float2 G[PREFETCH ? 6 : 1][N];
+  if (XPREF && line_ok && (int)blockIdx.x < a.n_batches) {
+    const float2* G0 = Gthread + (int64_t)blockIdx.x * (6 * N3 * CB) / 2;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+#pragma unroll
+      for (int q = 0; q < N; ++q) G[e][q] = __ldg(G0 + (e * N3 + q) * PP);
+  }
 
   for (int b = blockIdx.x; b < a.n_batches; b += gridDim.x, ++it) {
     const int buf = it & 1;
@@ -146,12 +162,12 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
       batch_advance(next, a);
       issue_loads(next, buf ^ 1);
     }
-    float2 G[PREFETCH ? 6 : 1][N];
-    if (PREFETCH && act) {
+    if (PREFETCH && !XPREF && act) {
+      const float2* G0 = Gthread + (int64_t)b * (6 * N3 * CB) / 2;
 #pragma unroll
       for (int e = 0; e < 6; ++e)
 #pragma unroll
-        for (int q = 0; q < N; ++q) G[e][q] = __ldg(Gb + (e * N3 + q) * PP);
+        for (int q = 0; q < N; ++q) G[e][q] = __ldg(G0 + (e * N3 + q) * PP);
     }
     const bool ok = mbar_wait(&bars[buf], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
@@ -231,6 +247,13 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
         C[xbase + q] = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
       }
       contract2_t<N, MAT_D>(h1, t1);
+    }
+    if (XPREF && line_ok && b + (int)gridDim.x < a.n_batches) {  // the next batch's metric
+      const float2* Gn = Gthread + (int64_t)(b + gridDim.x) * (6 * N3 * CB) / 2;
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+#pragma unroll
+        for (int q = 0; q < N; ++q) G[e][q] = __ldg(Gn + (e * N3 + q) * PP);
     }
     __syncthreads();
     // 6) D_y^T on B, D_z^T on C
