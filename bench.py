@@ -130,7 +130,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds=12.0, sub=12):
+def cpu_baseline(seconds=12.0, sub=12, one_core=True):
     """The FP64 oracle (assembled CSR SpMV, OpenMP) on a sub-mesh of the same workload."""
     import numpy as np
     from oracle import fem, mesh
@@ -150,7 +150,17 @@ def cpu_baseline(seconds=12.0, sub=12):
         reps += 1
     dt = (time.perf_counter() - t0) / reps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if one_core and cores > 1:
+        # the same SpMV on one core (a fresh process: the OpenMP team size is fixed at start)
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        code = ("import json, bench; print(json.dumps(bench.cpu_baseline(seconds=%r, sub=%d, one_core=False)))"
+                % (max(2.0, seconds / 4), sub))
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+        one = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 and r.stdout.strip() else None
+    else:
+        one = None
     return {"value": om.n_dofs / dt / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "one_core_value": one["value"] if one else None,
             "sample": f"FP64 CSR SpMV of the oracle-assembled operator on a {sub}^3-cell sub-mesh of the same "
                       f"workload ({om.n_dofs} DoFs, {K.nnz} nonzeros), {reps} SpMVs over {seconds:.0f} s; "
                       f"assembly ({t_asm:.1f} s) excluded"}
@@ -256,6 +266,7 @@ def main():
     total_ms, units_per_s = aggregate_ranks(t_start.elapsed_time(t_end), N * args.steps, dist, "cuda")
     per_launch = [a.elapsed_time(b) for a, b in ev]
     ms32 = statistics.mean(per_launch)
+    q32 = statistics.quantiles(per_launch, n=10) if len(per_launch) >= 10 else [ms32] * 9
     ms_per_step = total_ms / args.steps
     value = units_per_s / 1e9
 
@@ -266,13 +277,15 @@ def main():
 
     # FP64 vmult (ALU-bound on GB300: reported with its own roofline)
     reps64 = max(10, min(200, args.steps // 10))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps64):
+    ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps64)]
+    for i in range(reps64):
+        ev64[i][0].record(stream)
         op.vmult(x64, y64)
-    e1.record(stream)
+        ev64[i][1].record(stream)
     torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1) / reps64
+    per64 = [a.elapsed_time(b) for a, b in ev64]
+    ms64 = statistics.mean(per64)
+    q64 = statistics.quantiles(per64, n=10) if len(per64) >= 10 else [ms64] * 9
 
     # end to end through the C-ABI with host buffers (mfx_vmult_host): every step uploads its input from
     # pinned host memory, applies the operator and downloads the result; the library pipelines the
@@ -307,14 +320,19 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": measured_traffic(nx, kdeg, op.info()["cells_per_block"]), "peak_kind": peak_kind,
                      "kernel": "FP32 vmult (init_rows_kernel + brick_vmult_tma2_kernel), timed together",
-                     "algorithmic_bytes": b32},
+                     "algorithmic_bytes": b32,
+                     # secondary model: coefficient per q-point and vertices instead of the stored metric
+                     "algorithmic_bytes_minimal": 2 * 4 * N + 4 * C * (kdeg + 1) ** 3 + 24 * C},
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": ms_e2e, "steps": n_e2e,
                 "call": "mfx_vmult_host (pinned host vectors, upload / vmult / download pipelined)"},
         "gpu_launches": 2 * args.steps,
         "fp64": {"gdofs": N / (ms64 * 1e-3) / 1e9, "ms": ms64, "algorithmic_bytes": b64,
-                 "hbm_frac": b64 / (ms64 * 1e-3) / 1e9 / hbm},
+                 "hbm_frac": b64 / (ms64 * 1e-3) / 1e9 / hbm,
+                 "launch_ms": {"median": statistics.median(per64), "p10": q64[0], "p90": q64[-1], "reps": reps64}},
         "fp32_ms_per_launch": ms32,
+        "fp32_launch_ms": {"median": statistics.median(per_launch), "p10": q32[0], "p90": q32[-1],
+                           "reps": len(per_launch)},
     }
     if clocks:
         line["clocks"] = clocks
@@ -361,6 +379,22 @@ def solve_measurements(mfx, synthetic, torch, np):
     lat = sorted(lat[3:])
     out["poisson_8x8x8_q2_jacobi_pcg"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                            "iterations": its, "rel_residual": st["rel_residual"], "runs": len(lat)}
+    # the 8^3 Q2 operator fits in L2: its vmult is reported as latency
+    stream = torch.cuda.current_stream()
+    for name, dt in (("vmult_8x8x8_q2_fp64_us", torch.float64), ("vmult_8x8x8_q2_fp32_us", torch.float32)):
+        xs = torch.tensor(synthetic.uniform_vector(op.n_dofs, 1), device="cuda", dtype=dt)
+        ys = torch.empty_like(xs)
+        for _ in range(10):
+            op.vmult(xs, ys)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+        for e0, e1 in evs:
+            e0.record(stream)
+            op.vmult(xs, ys)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        out[name] = {"median": us[len(us) // 2], "p10": us[len(us) // 10], "p90": us[(9 * len(us)) // 10],
+                     "reps": len(us)}
     return out
 
 
