@@ -175,3 +175,53 @@ def test_sipg_multigrid_pcg_matches_the_oracle(mfx, mixed):
         ref = fem.pcg(lambda v: Kdg @ v, b, h.vcycle, tol=1e-10)
         assert abs(st["iterations"] - ref.iterations) <= 1, (st["iterations"], ref.iterations)
         assert st["iterations"] <= 15
+
+
+def test_sipg_full_size_sampled_rows(mfx):
+    """The benchmark's SIPG workload at full size (p = 4, 128 x 64 x 64 cells of [0,2] x [0,1] x [0,1],
+    65.5M DoFs) in the benchmark's launch configuration: the rows of sampled cells against the oracle.
+    A cell's rows involve only the cell and its face neighbours, so the oracle's matrix of the sub-box of
+    the cell and its neighbours (same cell size; the box's own faces where the sub-box touches them)
+    gives them exactly; corner, edge, face and interior cells are sampled."""
+    dims, k, lengths, faces = (128, 64, 64), 4, (2.0, 1.0, 1.0), 0x3F
+    n3 = (k + 1) ** 3
+    op = sipg(mfx, dims, k, lengths, faces)
+    n = op.n_dofs
+    gen = torch.Generator(device=DEV).manual_seed(71)
+    x = torch.rand(n, generator=gen, dtype=torch.float64, device=DEV) * 2 - 1
+    y = torch.empty_like(x)
+    op.vmult(x, y)
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    op.vmult(x32, y32)
+    h = [lengths[d] / dims[d] for d in range(3)]
+    samples = [(0, 0, 0), (127, 63, 63), (0, 31, 63), (64, 0, 17), (5, 63, 40), (77, 12, 0), (100, 50, 33),
+               (1, 1, 1)]
+    for c in samples:
+        lo = [max(0, c[d] - 1) for d in range(3)]
+        hi = [min(dims[d] - 1, c[d] + 1) for d in range(3)]
+        sd = [hi[d] - lo[d] + 1 for d in range(3)]
+        mask = 0
+        for d in range(3):
+            if lo[d] > 0 or (faces >> (2 * d)) & 1:
+                mask |= 1 << (2 * d)
+            if hi[d] < dims[d] - 1 or (faces >> (2 * d + 1)) & 1:
+                mask |= 1 << (2 * d + 1)
+        Ks = odg.dg_operator(*sd, k, tuple(sd[d] * h[d] for d in range(3)), mask).tocsr()
+        gidx = []
+        for bz in range(sd[2]):
+            for by in range(sd[1]):
+                for bx in range(sd[0]):
+                    gc = (lo[0] + bx) + dims[0] * ((lo[1] + by) + dims[1] * (lo[2] + bz))
+                    gidx.append(gc * n3 + np.arange(n3))
+        gidx = np.concatenate(gidx)
+        xs = x[torch.tensor(gidx, device=DEV)].cpu().numpy()
+        lc = (c[0] - lo[0]) + sd[0] * ((c[1] - lo[1]) + sd[1] * (c[2] - lo[2]))
+        rows = lc * n3 + np.arange(n3)
+        ref = Ks[rows] @ xs
+        gc = c[0] + dims[0] * (c[1] + dims[1] * c[2])
+        got = y[gc * n3:(gc + 1) * n3].cpu().numpy()
+        got32 = y32[gc * n3:(gc + 1) * n3].cpu().double().numpy()
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale, (c, np.abs(got - ref).max() / scale)
+        assert np.abs(got32 - ref).max() <= 1e-5 * scale, (c, np.abs(got32 - ref).max() / scale)
