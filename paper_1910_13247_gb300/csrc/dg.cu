@@ -34,6 +34,8 @@
 // contractions read them as constant-bank operands.
 #include <algorithm>
 
+#include "basis_tables.h"
+#include "df.cuh"
 #include "mfx_internal.h"
 
 namespace mfx {
@@ -50,6 +52,9 @@ struct DgArgs {
   // 1D tables (n <= 9): K1, M1 (n x n, row-major), end derivatives l_i'(0), l_i'(1)
   double K1[kMaxN * kMaxN], M1[kMaxN * kMaxN], d0[kMaxN], d1[kMaxN];
   float K1f[kMaxN * kMaxN], M1f[kMaxN * kMaxN], d0f[kMaxN], d1f[kMaxN];
+  // the FP64 kernel's runtime scalars as float pairs: per direction 1/h, 1/(2h), sigma interior,
+  // sigma Dirichlet, a h_e h_f
+  float dfs[3][5][2];
   const int32_t* skip;
 };
 
@@ -247,6 +252,184 @@ __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ D
   }
 }
 
+// FP64 data in double-float arithmetic (the native FP64 kernel runs at the FP64 FMA rate, 1/62 of the
+// FP32 rate on GB300): the same phases, with values split into float pairs when loaded and joined back
+// to FP64 when stored, the 1D tables split at compile time, and the per-direction scalars split on the
+// host.
+template <int N, int W>  // W: 0 K1, 1 M1, 2 d0, 3 d1
+__device__ __forceinline__ constexpr double dg_tab(int i) {
+  return W == 0 ? DgConst<N>::K1(i) : W == 1 ? DgConst<N>::M1(i) : W == 2 ? DgConst<N>::d0(i) : DgConst<N>::d1(i);
+}
+
+// y_i = sum_j T[i][j] x_j (T = K1 or M1)
+template <int N, int W>
+__device__ __forceinline__ void dg_contract_df(const df (&x)[N], df (&y)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s, t;
+    df_prod(x[0], split_hi(dg_tab<N, W>(i * N)), split_lo(dg_tab<N, W>(i * N)), s, t);
+#pragma unroll
+    for (int j = 1; j < N; ++j) df_prod_acc(x[j], split_hi(dg_tab<N, W>(i * N + j)), split_lo(dg_tab<N, W>(i * N + j)), s, t);
+    y[i] = df_fast_norm(s, t);
+  }
+}
+
+// sum_j v_j x_j + sum_j w_j z_j (v, w = d0 or d1)
+template <int N, int V, int W>
+__device__ __forceinline__ df dg_dot2_df(const df (&x)[N], const df (&z)[N]) {
+  float s, t;
+  df_prod(x[0], split_hi(dg_tab<N, V>(0)), split_lo(dg_tab<N, V>(0)), s, t);
+#pragma unroll
+  for (int j = 1; j < N; ++j) df_prod_acc(x[j], split_hi(dg_tab<N, V>(j)), split_lo(dg_tab<N, V>(j)), s, t);
+#pragma unroll
+  for (int j = 0; j < N; ++j) df_prod_acc(z[j], split_hi(dg_tab<N, W>(j)), split_lo(dg_tab<N, W>(j)), s, t);
+  return df_fast_norm(s, t);
+}
+template <int N, int V>
+__device__ __forceinline__ df dg_dot_df(const df (&x)[N]) {
+  float s, t;
+  df_prod(x[0], split_hi(dg_tab<N, V>(0)), split_lo(dg_tab<N, V>(0)), s, t);
+#pragma unroll
+  for (int j = 1; j < N; ++j) df_prod_acc(x[j], split_hi(dg_tab<N, V>(j)), split_lo(dg_tab<N, V>(j)), s, t);
+  return df_fast_norm(s, t);
+}
+
+// x * c and acc + x * c with c = (ch, cl)
+__device__ __forceinline__ df df_mul_c(df x, float ch, float cl) {
+  float s, t;
+  df_prod(x, ch, cl, s, t);
+  return df_fast_norm(s, t);
+}
+__device__ __forceinline__ df df_fma_c(df x, float ch, float cl, df acc) {
+  float s = acc.hi, t = acc.lo;
+  df_prod_acc(x, ch, cl, s, t);
+  return df_fast_norm(s, t);
+}
+
+template <int N>
+__device__ __forceinline__ void dg_sweep_df(const df* in, df* out, int dir, int line) {
+  int base, stride;
+  dg_line<N>(dir, line, &base, &stride);
+  df x[N], y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = in[base + i * stride];
+  dg_contract_df<N, 1>(x, y);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = y[i];
+}
+
+template <int N>
+__device__ __forceinline__ void dg_line_sipg_df(const DgArgs& a, const df* __restrict__ u, df* __restrict__ out,
+                                                const double* __restrict__ src, int64_t cell, const int* cidx,
+                                                int d, int line) {
+  constexpr int N3 = N * N * N, K = N - 1;
+  int base, stride;
+  dg_line<N>(d, line, &base, &stride);
+  const int dims[3] = {a.nx, a.ny, a.nz};
+  const float(*c)[2] = a.dfs[d];  // 0: 1/h, 1: 1/(2h), 2: sigma interior, 3: sigma Dirichlet, 4: scale
+  df x[N], y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = u[base + i * stride];
+  dg_contract_df<N, 0>(x, y);
+#pragma unroll
+  for (int i = 0; i < N; ++i) y[i] = df_mul_c(y[i], c[0][0], c[0][1]);
+  const bool lo_nb = cidx[d] > 0, hi_nb = cidx[d] + 1 < dims[d];
+  const int64_t step = d == 0 ? 1 : (d == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny);
+  if (lo_nb) {
+    df wv[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) wv[j] = df_split(src[(cell - step) * N3 + base + j * stride]);
+    const df g = dg_dot2_df<N, 2, 3>(x, wv);
+    const df jmp = df_add(x[0], df_neg(wv[K]));
+    const df t = df_mul_c(jmp, c[1][0], c[1][1]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = df_fma_c(t, split_hi(dg_tab<N, 2>(i)), split_lo(dg_tab<N, 2>(i)), y[i]);
+    y[0] = df_fma_c(jmp, c[2][0], c[2][1], df_fma_c(g, c[1][0], c[1][1], y[0]));
+  } else if ((a.dmask >> (2 * d)) & 1u) {
+    const df g = dg_dot_df<N, 2>(x);
+    const df t = df_mul_c(x[0], c[0][0], c[0][1]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = df_fma_c(t, split_hi(dg_tab<N, 2>(i)), split_lo(dg_tab<N, 2>(i)), y[i]);
+    y[0] = df_fma_c(x[0], c[3][0], c[3][1], df_fma_c(g, c[0][0], c[0][1], y[0]));
+  }
+  if (hi_nb) {
+    df wv[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) wv[j] = df_split(src[(cell + step) * N3 + base + j * stride]);
+    const df g = dg_dot2_df<N, 3, 2>(x, wv);
+    const df jmp = df_add(x[K], df_neg(wv[0]));
+    const df t = df_neg(df_mul_c(jmp, c[1][0], c[1][1]));
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = df_fma_c(t, split_hi(dg_tab<N, 3>(i)), split_lo(dg_tab<N, 3>(i)), y[i]);
+    y[K] = df_fma_c(jmp, c[2][0], c[2][1], df_fma_c(df_neg(g), c[1][0], c[1][1], y[K]));
+  } else if ((a.dmask >> (2 * d + 1)) & 1u) {
+    const df g = dg_dot_df<N, 3>(x);
+    const df t = df_neg(df_mul_c(x[K], c[0][0], c[0][1]));
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = df_fma_c(t, split_hi(dg_tab<N, 3>(i)), split_lo(dg_tab<N, 3>(i)), y[i]);
+    y[K] = df_fma_c(x[K], c[3][0], c[3][1], df_fma_c(df_neg(g), c[0][0], c[0][1], y[K]));
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = df_mul_c(y[i], c[4][0], c[4][1]);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) dg_vmult_df_kernel(const __grid_constant__ DgArgs a,
+                                                           const double* __restrict__ src, double* __restrict__ dst) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int CB = 128 / N2 > 0 ? 128 / N2 : 1;
+  constexpr int CH = CB * N3;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df* U = reinterpret_cast<df*>(smem_raw);
+  df* P = U + CH;
+  df* Q = P + CH;
+  df* R = Q + CH;
+  df* T2 = R + CH;
+  df* T3 = T2 + CH;
+  const int cl = threadIdx.x / N2;
+  const int r = threadIdx.x - cl * N2;
+  const bool lane_ok = cl < CB;
+  const int64_t total = a.n_cells * N3;
+  const int64_t nbatch = (a.n_cells + CB - 1) / CB;
+  for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+    const int64_t first = bt * CB * (int64_t)N3;
+    for (int i = threadIdx.x; i < CH; i += 128) U[i] = df_split(first + i < total ? src[first + i] : 0.0);
+    __syncthreads();
+    const int64_t cell = bt * CB + cl;
+    const bool act = lane_ok && cell < a.n_cells;
+    const int off = (lane_ok ? cl : 0) * N3;
+    if (act) {
+      const unsigned c32 = (unsigned)cell, q = c32 / (unsigned)a.nx, cz = q / (unsigned)a.ny;
+      const int cidx[3] = {(int)(c32 - q * (unsigned)a.nx), (int)(q - cz * (unsigned)a.ny), (int)cz};
+      dg_line_sipg_df<N>(a, U + off, P + off, src, cell, cidx, 0, r);
+      dg_line_sipg_df<N>(a, U + off, Q + off, src, cell, cidx, 1, r);
+      dg_line_sipg_df<N>(a, U + off, R + off, src, cell, cidx, 2, r);
+    }
+    __syncthreads();
+    if (act) {
+      dg_sweep_df<N>(P + off, U + off, 1, r);
+      dg_sweep_df<N>(Q + off, T2 + off, 0, r);
+      dg_sweep_df<N>(R + off, T3 + off, 0, r);
+    }
+    __syncthreads();
+    if (act) {
+      int base, stride;
+      dg_line<N>(2, r, &base, &stride);
+      df x[N], y[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = df_add(U[off + base + i * stride], T2[off + base + i * stride]);
+      dg_contract_df<N, 1>(x, y);
+#pragma unroll
+      for (int i = 0; i < N; ++i) P[off + base + i * stride] = y[i];
+      dg_sweep_df<N>(T3 + off, Q + off, 1, r);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < CH; i += 128)
+      if (first + i < total) dst[first + i] = df_join(df_add(P[i], Q[i]));
+  }
+}
+
 // Diagonal: cell term c_x K1_ii M1_jj M1_ll + ... plus, on each face with a term, the self-coupling
 // of the face nodes: sum_q w (-+ phi d phi + sigma phi^2) (separable in the 1D mass diagonal).
 __global__ void dg_diagonal_kernel(const __grid_constant__ DgArgs a, int n, double* __restrict__ d64,
@@ -307,6 +490,13 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
   a.scale[2] = op->dg_coef * op->dg_h[0] * op->dg_h[1];
   a.coef = op->dg_coef;
   a.dmask = op->dirichlet;
+  for (int d = 0; d < 3; ++d) {
+    const double v[5] = {a.hinv[d], 0.5 * a.hinv[d], a.sig_int[d], a.sig_bnd[d], a.scale[d]};
+    for (int e = 0; e < 5; ++e) {
+      a.dfs[d][e][0] = (float)v[e];
+      a.dfs[d][e][1] = (float)(v[e] - (double)(float)v[e]);
+    }
+  }
   const BasisTables& b = op->basis;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
@@ -351,6 +541,27 @@ static mfx_status run_dg(const mfx_op* op, const Real* src, Real* dst, cudaStrea
   return MFX_OK;
 }
 
+template <int N>
+static mfx_status run_dg_df(const mfx_op* op, const double* src, double* dst, cudaStream_t s, const int32_t* skip) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int CB = 128 / N2 > 0 ? 128 / N2 : 1;
+  const size_t smem = (size_t)6 * CB * N3 * sizeof(df);
+  auto kern = dg_vmult_df_kernel<N>;
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  const DgArgs a = dg_args(op, skip);
+  const int64_t nbatch = (op->n_cells + CB - 1) / CB;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nbatch, (int64_t)device_sm_count() * blocks_per_sm));
+  kern<<<grid, 128, smem, s>>>(a, src, dst);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
 template <typename Real>
 static mfx_status dg_dispatch(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   switch (op->n) {
@@ -368,7 +579,21 @@ static mfx_status dg_dispatch(const mfx_op* op, const Real* src, Real* dst, cuda
 
 mfx_status launch_dg_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                            const int32_t* skip) {
-  if (prec == MFX_F64) return dg_dispatch<double>(op, (const double*)src, (double*)dst, s, skip);
+  if (prec == MFX_F64) {
+    const double* x = (const double*)src;
+    double* y = (double*)dst;
+    switch (op->n) {
+      case 2: return run_dg_df<2>(op, x, y, s, skip);
+      case 3: return run_dg_df<3>(op, x, y, s, skip);
+      case 4: return run_dg_df<4>(op, x, y, s, skip);
+      case 5: return run_dg_df<5>(op, x, y, s, skip);
+      case 6: return run_dg_df<6>(op, x, y, s, skip);
+      case 7: return run_dg_df<7>(op, x, y, s, skip);
+      case 8: return run_dg_df<8>(op, x, y, s, skip);
+      case 9: return run_dg_df<9>(op, x, y, s, skip);
+      default: return set_error(MFX_EUNSUPPORTED, "degree out of range");
+    }
+  }
   return dg_dispatch<float>(op, (const float*)src, (float*)dst, s, skip);
 }
 
