@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   // metric stream over the whole batch: Q2 on 128^3 50 -> 56 % of HBM); k = 3, 4: at the start of the
   // batch, which measured faster there (Q4 on 64^3 0.2894 against 0.296 ms)
   constexpr bool XPREF = PREFETCH && N <= 3;
+  // L2 prefetch of the metric one batch ahead for k >= 3 (k = 8: 0.949 -> 0.863 ms on 40^3, Q3 on 86^3
+  // 0.310 -> 0.304, Q4 on 64^3 0.2892 -> 0.2872); at k <= 2 it measured slower (Q2 on 128^3 0.391 -> 0.412)
+  constexpr int MDIST = N >= 4 ? 1 : 0;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* in_tiles = reinterpret_cast<float*>(smem_raw);  // 2 x TILE
@@ -161,6 +164,20 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
       BatchPos next = pos;
       batch_advance(next, a);
       issue_loads(next, buf ^ 1);
+    }
+    // the metric of this CTA's batch MDIST batches ahead is brought into L2 by the TMA engine, so the
+    // register loads of that batch hit L2 and the HBM stream of the metric, which is most of the bytes,
+    // overlaps the batches in between without holding registers
+    if (MDIST > 0 && tma_warp && lane < 3) {
+      const int bn = b + MDIST * (int)gridDim.x;
+      if (bn < a.n_batches) {
+        constexpr unsigned BYTES = 6u * N3 * CB * 4u;  // one batch of the metric, contiguous
+        constexpr unsigned CHUNK = (BYTES / 3 + 15u) & ~15u;
+        const unsigned off = lane * CHUNK;
+        if (off < BYTES)
+          prefetch_l2_bulk(reinterpret_cast<const char*>(a.metric + (int64_t)bn * (6 * N3 * CB)) + off,
+                           off + CHUNK <= BYTES ? CHUNK : BYTES - off);
+      }
     }
     if (PREFETCH && !XPREF && act) {
       const float2* G0 = Gthread + (int64_t)b * (6 * N3 * CB) / 2;
