@@ -518,7 +518,7 @@ def sipg_measurement(mfx, synthetic, torch, np, dims=(128, 64, 64), k=4, solve=T
     [0, 2] x [0, 1] x [0, 1] (128 x 64 x 64 cells, 65.5M DoFs, homogeneous Dirichlet data on every face).
     FP32 and FP64 vmult of the DG operator (device-resident vectors larger than L2), then PCG with the
     V-cycle of the DG -> continuous -> coarser hierarchy (Chebyshev(6) smoothing, exact coarse solve on
-    4 x 2 x 2 cells), FP64 and mixed (FP32 V-cycle inside FP64 defect correction), to 1e-10."""
+    2 x 1 x 1 cells as in the paper), FP64 and mixed (FP32 V-cycle inside FP64 defect correction), to 1e-10."""
     lengths = (2.0, 1.0, 1.0)
     verts = synthetic.lattice_vertices(*dims) * np.asarray(lengths)[None, :]
     mesh = mfx.Mesh.structured_box(*dims, verts)

@@ -404,7 +404,8 @@ mfx_status mfx_batch_release(mfx_batch* batch, int32_t slot);
  * preconditioned by a multigrid V-cycle with Chebyshev smoothing and
  * matrix-free level transfers, Sec. 3.5 and Sec. 6.1), for structured meshes.
  * Levels: the given mesh and coarser ones with half the cells per direction,
- * while all three counts are even and at least 4 (or up to max_levels); a
+ * while all three counts are even (or up to max_levels; a 2:1:1 box of
+ * 2^(l+1) x 2^l x 2^l cells ends on the paper's 2 x 1 x 1 coarse mesh); a
  * coarser level's vertices are every other vertex of the finer lattice; every
  * level has the operator of `desc` (same degree, coefficient kind, Dirichlet
  * faces).  Prolongation interpolates the coarse Q_k function at the fine

@@ -41,10 +41,11 @@ def coarsen_vertices(vertices, nx, ny, nz):
 
 
 def level_sizes(nx, ny, nz, max_levels=0):
-    """Cells per direction of every level, coarse to fine: halve while all three are even and at
-    least 4 (so the coarsest level keeps two cells per direction), up to max_levels levels."""
+    """Cells per direction of every level, coarse to fine: halve while all three counts are even (a
+    2:1:1 box of 2^(l+1) x 2^l x 2^l cells ends on 2 x 1 x 1 cells, the coarse mesh of the paper's
+    benchmark, Sec. 6.1), up to max_levels levels."""
     sizes = [(nx, ny, nz)]
-    while all(s % 2 == 0 and s >= 4 for s in sizes[0]) and (max_levels <= 0 or len(sizes) < max_levels):
+    while all(s % 2 == 0 for s in sizes[0]) and (max_levels <= 0 or len(sizes) < max_levels):
         sizes.insert(0, tuple(s // 2 for s in sizes[0]))
     return sizes
 

@@ -497,10 +497,11 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
   if (params) p = *params;
   if (p.smoother_degree < 1 || !(p.smoothing_range > 1.0) || p.lanczos_steps < 2 || p.max_levels < 0)
     return set_error(MFX_EINVAL, "mfx_mg_create: bad parameters");
-  // level sizes: halve while all three are even and >= 4
+  // level sizes: halve while all three counts are even (a 2:1:1 box of 2^(l+1) x 2^l x 2^l cells ends on
+  // 2 x 1 x 1 cells, the coarse mesh of the paper's benchmark, Sec. 6.1)
   std::vector<std::array<int, 3>> sizes = {{fm.nx, fm.ny, fm.nz}};
-  while (sizes.front()[0] % 2 == 0 && sizes.front()[1] % 2 == 0 && sizes.front()[2] % 2 == 0 && sizes.front()[0] >= 4 &&
-         sizes.front()[1] >= 4 && sizes.front()[2] >= 4 && (p.max_levels == 0 || (int)sizes.size() < p.max_levels))
+  while (sizes.front()[0] % 2 == 0 && sizes.front()[1] % 2 == 0 && sizes.front()[2] % 2 == 0 &&
+         (p.max_levels == 0 || (int)sizes.size() < p.max_levels))
     sizes.insert(sizes.begin(), {sizes.front()[0] / 2, sizes.front()[1] / 2, sizes.front()[2] / 2});
   auto* mg = new (std::nothrow) mfx_mg();
   if (!mg) return set_error(MFX_ENOMEM, "host allocation failed");

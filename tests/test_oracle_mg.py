@@ -45,7 +45,8 @@ def test_prolongation_reproduces_tensor_polynomials(k):
 
 def test_level_sizes_and_coarse_vertices():
     assert mg.level_sizes(96, 96, 96) == [(3, 3, 3), (6, 6, 6), (12, 12, 12), (24, 24, 24), (48, 48, 48), (96, 96, 96)]
-    assert mg.level_sizes(64, 64, 64)[0] == (2, 2, 2) and len(mg.level_sizes(64, 64, 64)) == 6
+    assert mg.level_sizes(64, 64, 64)[0] == (1, 1, 1) and len(mg.level_sizes(64, 64, 64)) == 7
+    assert mg.level_sizes(128, 64, 64)[0] == (2, 1, 1) and len(mg.level_sizes(128, 64, 64)) == 7
     assert mg.level_sizes(8, 8, 6) == [(4, 4, 3), (8, 8, 6)]
     assert mg.level_sizes(16, 16, 16, max_levels=2) == [(8, 8, 8), (16, 16, 16)]
     v = synthetic.deformed_vertices(4, 4, 4)
@@ -68,7 +69,7 @@ def test_single_level_cycle_is_the_exact_inverse():
 
 def test_vcycle_is_symmetric_and_positive():
     h = _hier(8, 2)
-    assert len(h.meshes) == 3
+    assert len(h.meshes) == 4
     n = h.meshes[-1].n_dofs
     x, y = synthetic.uniform_vector(n, 4), synthetic.uniform_vector(n, 5)
     vx, vy = h.vcycle(x), h.vcycle(y)
