@@ -24,8 +24,8 @@ struct PairShape {
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int CUBES = (CB / 2) * BrickShape<N, CB, float>::CELL;  // float2 elements per cube
   // resident CTAs per SM the register budget is sized for (fewer for the larger degrees)
-  static constexpr int MIN_BLOCKS = N <= 4 ? (512 / THREADS > 0 ? 512 / THREADS : 1)
-                                            : (768 / THREADS > 0 ? 768 / THREADS : 1);
+  static constexpr int MIN_BLOCKS = (N == 2 || N == 4) ? (512 / THREADS > 0 ? 512 / THREADS : 1)
+                                                      : (768 / THREADS > 0 ? 768 / THREADS : 1);
   static constexpr size_t SMEM =
       (size_t)4 * TmaShape<N, CB>::TILE * sizeof(float) + 3 * (size_t)CUBES * sizeof(float2) + 2 * sizeof(uint64_t);
 };
@@ -69,17 +69,17 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   constexpr int PP = CB / 2;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
   constexpr int PITCH = Tm::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
-  // k <= 3: the metric of a thread's x-line in registers (6 N float pairs), loaded ahead of its use.
-  // k = 4: loaded where it is used, from L2 (the TMA engine prefetches each batch's metric one batch
-  // ahead, below), which frees the registers of a third CTA per SM: 0.2871 -> 0.2708 ms on 64^3
-  constexpr bool PREFETCH = N <= 4;
-  // k <= 2: the next batch's metric is requested right after the current one is used (spreads the
-  // metric stream over the whole batch: Q2 on 128^3 50 -> 56 % of HBM); k = 3, 4: at the start of the
-  // batch, which measured faster there (Q4 on 64^3 0.2894 against 0.296 ms)
+  // k = 1, 3: the metric of a thread's x-line in registers (6 N float pairs), loaded ahead of its use.
+  // k = 2, 4: loaded where it is used, from L2 (the TMA engine prefetches each batch's metric one batch
+  // ahead, below), which frees registers for more CTAs per SM: Q4 on 64^3 0.2871 -> 0.2708 ms, Q2 on
+  // 128^3 0.3903 -> 0.3814 ms (Q3 measured slower that way: 0.304 -> 0.314 ms)
+  constexpr bool PREFETCH = N == 2 || N == 4;
+  // k = 1: the next batch's metric is requested right after the current one is used (spreads the
+  // metric stream over the whole batch); k = 3: at the start of the batch
   constexpr bool XPREF = PREFETCH && N <= 3;
-  // L2 prefetch of the metric one batch ahead for k >= 3 (k = 8: 0.949 -> 0.863 ms on 40^3, Q3 on 86^3
-  // 0.310 -> 0.304, Q4 on 64^3 0.2892 -> 0.2872); at k <= 2 it measured slower (Q2 on 128^3 0.391 -> 0.412)
-  constexpr int MDIST = N >= 4 ? 1 : 0;
+  // L2 prefetch of the metric one batch ahead for k >= 2 (k = 8: 0.949 -> 0.863 ms on 40^3, Q3 on 86^3
+  // 0.310 -> 0.304); with the register prefetch of k = 1 it measured slower
+  constexpr int MDIST = N >= 3 ? 1 : 0;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* in_tiles = reinterpret_cast<float*>(smem_raw);  // 2 x TILE
