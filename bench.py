@@ -401,11 +401,18 @@ def solve_measurements(mfx, synthetic, torch, np):
 def serving_measurement(n_requests, rate=200.0, seed=5):
     """Poisson arrivals (200/s) of octree Poisson solves, degree 1..8, sizes log-uniform in 1e3..1e7 DoFs
     (clamped by the mesh generator), tol 1e-10, continuous batching under a 64 GB device-memory budget."""
-    from paper_1910_13247_gb300 import serve
+    from paper_1910_13247_gb300 import mfx, serve
     reqs = serve.make_requests(n_requests, rate=rate, seed=seed)
     server = serve.Server(budget_bytes=64 << 30, max_slots=32, chunk=16)
     out = server.run(reqs, time_limit=240.0)
     out["budget_bytes"] = 64 << 30
+    out["policy"] = "fifo"
+    # the same stream admitted smallest-first (estimated device bytes): small requests stop queueing
+    # behind large ones while the offered load exceeds capacity
+    small = serve.Server(budget_bytes=64 << 30, max_slots=32, chunk=16, policy=mfx.ADMIT_SMALLEST_FIRST)
+    alt = small.run(serve.make_requests(n_requests, rate=rate, seed=seed), time_limit=240.0)
+    out["smallest_first"] = {key: alt[key] for key in ("p50_latency_s", "p99_latency_s", "solves_per_s", "wall_seconds",
+                                                        "completed") if key in alt}
     return out
 
 
