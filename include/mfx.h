@@ -172,8 +172,9 @@ typedef struct {
  * i1 + n (i2 + n i3) at c n^3 + ...), interior faces -{d_n u}[v] - [u]{d_n v} + sigma [u][v] with
  * sigma = eta (k+1)^2 / h, homogeneous Dirichlet data imposed weakly on the mesh's Dirichlet faces
  * (sigma = 2 eta (k+1)^2 / h there), the other faces natural.  There are no constrained DoFs.
- * vmult, diagonal, dot, Chebyshev, solve and batches work as for the continuous operator;
- * quadrature points, right-hand sides and tables are MFX_EUNSUPPORTED.
+ * vmult, diagonal, dot, Chebyshev, solve, batches, quadrature points and right-hand sides
+ * (mfx_rhs, mfx_rhs_function: b_i = integral of f phi_i over phi_i's cell) work as for the
+ * continuous operator; mfx_get_tables returns the identity cell-to-DoF map and no constraints.
  */
 enum { MFX_CONTINUOUS = 0, MFX_SIPG = 1 };
 

@@ -414,7 +414,10 @@ static mfx_status create_sipg(mfx_op** out, const Mesh& m, const mfx_op_desc* de
   op->structured = true;
   op->dg = true;
   op->dirichlet = m.dirichlet;
-  for (int d = 0; d < 3; ++d) op->dg_h[d] = h[d];
+  for (int d = 0; d < 3; ++d) {
+    op->dg_h[d] = h[d];
+    op->dg_origin[d] = vert(0, 0, 0, d);
+  }
   op->dg_penalty = eta;
   op->dg_coef = desc->coef_par[0];
   op->n_cells = (int64_t)m.nx * m.ny * m.nz;
@@ -840,19 +843,16 @@ mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream 
 
 mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream) {
   if (!op || !xq) return set_error(MFX_EINVAL, "mfx_quadrature_points: null argument");
-  if (op->dg) return set_error(MFX_EUNSUPPORTED, "quadrature points of an SIPG operator");
   return launch_qpoints(op, xq, (cudaStream_t)stream);
 }
 
 mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream stream) {
   if (!op || !fq || !b) return set_error(MFX_EINVAL, "mfx_rhs: null argument");
-  if (op->dg) return set_error(MFX_EUNSUPPORTED, "right-hand side of an SIPG operator");
   return launch_rhs(op, fq, b, (cudaStream_t)stream);
 }
 
 mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double* b, mfx_stream stream) {
   if (!op || !f || !b) return set_error(MFX_EINVAL, "mfx_rhs_function: null argument");
-  if (op->dg) return set_error(MFX_EUNSUPPORTED, "right-hand side of an SIPG operator");
   cudaStream_t s = (cudaStream_t)stream;
   double* fq = nullptr;
   mfx_status st = host_point_values(op, f, user, &fq, s);

@@ -55,6 +55,9 @@ struct DgArgs {
   // the FP64 kernel's runtime scalars as float pairs: per direction 1/h, 1/(2h), sigma interior,
   // sigma Dirichlet, a h_e h_f
   float dfs[3][5][2];
+  // quadrature points and right-hand sides: the box's first vertex, Gauss points and weights on [0, 1],
+  // S[q][i] = l_i(x_q)
+  double origin[3], xq[kMaxN], wq[kMaxN], S[kMaxN * kMaxN];
   const int32_t* skip;
 };
 
@@ -472,6 +475,40 @@ __global__ void dg_diagonal_kernel(const __grid_constant__ DgArgs a, int n, doub
   }
 }
 
+// Physical quadrature points: x = origin + (cell index + x_q) h per direction, [cell][q][3].
+__global__ void dg_qpoints_kernel(const __grid_constant__ DgArgs a, int n, double* __restrict__ out) {
+  const int n3 = n * n * n;
+  const int64_t total = a.n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int q = (int)(idx - cell * n3);
+    const int qq[3] = {q % n, (q / n) % n, q / (n * n)};
+    const int64_t c[3] = {cell % a.nx, (cell / a.nx) % a.ny, cell / ((int64_t)a.nx * a.ny)};
+    for (int d = 0; d < 3; ++d) out[3 * idx + d] = a.origin[d] + ((double)c[d] + a.xq[qq[d]]) * a.h[d];
+  }
+}
+
+// Load vector of f given at the quadrature points: b_i = sum_q w_q |K| f(x_q) phi_i(x_q), each DoF in its
+// own cell (no accumulation across cells).
+__global__ void dg_rhs_kernel(const __grid_constant__ DgArgs a, int n, const double* __restrict__ fq,
+                              double* __restrict__ b) {
+  const int n3 = n * n * n;
+  const int64_t total = a.n_cells * n3;
+  const double vol = a.h[0] * a.h[1] * a.h[2];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int i = (int)(idx - cell * n3);
+    const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+    double s = 0.0;
+    for (int q = 0; q < n3; ++q) {
+      const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
+      const double w = a.wq[q1] * a.wq[q2] * a.wq[q3];
+      s += w * a.S[q1 * n + i1] * a.S[q2 * n + i2] * a.S[q3 * n + i3] * fq[cell * n3 + q];
+    }
+    b[idx] = s * vol;
+  }
+}
+
 static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
   DgArgs a{};
   const int n = op->n;
@@ -516,6 +553,12 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
     a.d0f[i] = (float)a.d0[i];
     a.d1f[i] = (float)a.d1[i];
   }
+  for (int d = 0; d < 3; ++d) a.origin[d] = op->dg_origin[d];
+  for (int q = 0; q < n; ++q) {
+    a.xq[q] = b.xq[q];
+    a.wq[q] = b.wq[q];
+  }
+  for (int i = 0; i < n * n; ++i) a.S[i] = b.S[i];
   a.skip = skip;
   return a;
 }
@@ -595,6 +638,24 @@ mfx_status launch_dg_vmult(const mfx_op* op, mfx_prec prec, const void* src, voi
     }
   }
   return dg_dispatch<float>(op, (const float*)src, (float*)dst, s, skip);
+}
+
+mfx_status launch_dg_qpoints(const mfx_op* op, double* xq, cudaStream_t s) {
+  const DgArgs a = dg_args(op, nullptr);
+  const int64_t total = op->n_dofs;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count() * 16));
+  dg_qpoints_kernel<<<grid, 256, 0, s>>>(a, op->n, xq);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+mfx_status launch_dg_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s) {
+  const DgArgs a = dg_args(op, nullptr);
+  const int64_t total = op->n_dofs;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count() * 16));
+  dg_rhs_kernel<<<grid, 256, 0, s>>>(a, op->n, fq, b);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
 }
 
 mfx_status launch_dg_diagonal(mfx_op* op, cudaStream_t s) {

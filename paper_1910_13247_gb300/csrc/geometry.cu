@@ -495,6 +495,7 @@ mfx_status launch_geometry(mfx_op* op, int coef_kind, const double* par, const d
 }
 
 mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s) {
+  if (op->dg) return launch_dg_qpoints(op, xq, s);
   GeoArgs g = geo_args(op);
   const int64_t work = op->n_cells * op->n * op->n * op->n;
   qpoints_kernel<<<grid_for(work), 256, 0, s>>>(g, xq);
@@ -503,6 +504,7 @@ mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s) {
 }
 
 mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s) {
+  if (op->dg) return launch_dg_rhs(op, fq, b, s);
   GeoArgs g = geo_args(op);
   MFX_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * op->n_dofs, s));
   const int64_t work = op->n_cells * op->n * op->n * op->n;

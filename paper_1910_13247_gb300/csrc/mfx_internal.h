@@ -92,7 +92,7 @@ struct mfx_op {
   bool structured = true;
   uint32_t dirichlet = mfx::kAllFaces;    // Dirichlet faces of the box
   bool dg = false;                        // SIPG operator (cell-major DoFs, no constraints)
-  double dg_h[3] = {0, 0, 0}, dg_penalty = 1.0, dg_coef = 1.0;
+  double dg_h[3] = {0, 0, 0}, dg_penalty = 1.0, dg_coef = 1.0, dg_origin[3] = {0, 0, 0};
   int nx = 0, ny = 0, nz = 0;             // structured cells per direction
   int cells_per_block = 0;
   int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)
@@ -145,6 +145,8 @@ mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
 mfx_status launch_dg_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                            const int32_t* skip);
 mfx_status launch_dg_diagonal(mfx_op* op, cudaStream_t s);
+mfx_status launch_dg_qpoints(const mfx_op* op, double* xq, cudaStream_t s);
+mfx_status launch_dg_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s);
 
 int device_sm_count();
 
