@@ -259,3 +259,44 @@ def test_sipg_full_size_sampled_rows(mfx):
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 1e-12 * scale, (c, np.abs(got - ref).max() / scale)
         assert np.abs(got32 - ref).max() <= 1e-5 * scale, (c, np.abs(got32 - ref).max() / scale)
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_sipg_problems_in_a_batch_equal_their_standalone_solves(mfx, mixed):
+    """SIPG operators share one batch with a continuous one: every result equals its own mfx_solve
+    (both stop at a 1e-10 relative residual) and meets the residual bound of the oracle's matrix."""
+    probs = []
+    for dims, k in (((3, 2, 2), 2), ((2, 2, 2), 3)):
+        op = sipg(mfx, dims, k)
+        probs.append((op, odg.dg_operator(*dims, k), None))
+    verts = synthetic.deformed_vertices(4, 4, 4)
+    cg = mfx.Operator(mfx.Mesh.structured_box(4, 4, 4, verts), 2, mfx.COEF_TRIG, (1.0, 0.5))
+    from oracle import mesh as omesh
+    om = omesh.structured_mesh(4, 4, 4, 2, verts)
+    probs.append((cg, fem.assemble(om, 3, fem.COEF_TRIG, (1.0, 0.5)), om))
+    bs, alone = [], []
+    for i, (op, K, om) in enumerate(probs):
+        b = synthetic.uniform_vector(op.n_dofs, 80 + i)
+        if om is not None:
+            b[om.constrained] = 0.0
+        bd = torch.tensor(b, device=DEV)
+        x = torch.zeros_like(bd)
+        st = op.solve(bd, x, tol=1e-10, mixed=mixed)
+        assert st["status"] == 0
+        bs.append(bd)
+        alone.append(x.cpu().numpy())
+    batch = mfx.Batch(4, chunk=4)
+    xs, slots = [], []
+    for (op, K, om), bd in zip(probs, bs):
+        x = torch.full_like(bd, float("nan"))
+        slots.append(batch.add(op, bd, x, tol=1e-10, mixed=mixed))
+        xs.append(x)
+    assert batch.run() > 0
+    for (op, K, om), slot, bd, x, xa in zip(probs, slots, bs, xs, alone):
+        done, st = batch.poll(slot)
+        assert done and st["status"] == 0, st
+        xb = x.cpu().numpy()
+        b = bd.cpu().numpy()
+        assert np.linalg.norm(b - K @ xb) <= 1.0001e-10 * np.linalg.norm(b)
+        assert np.linalg.norm(xb - xa) <= 1e-8 * np.linalg.norm(xa)
+        batch.release(slot)
