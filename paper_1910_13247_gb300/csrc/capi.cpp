@@ -486,6 +486,19 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size(), s));
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, m.vertices.data(), m.vertices.size() * sizeof(double),
                                 cudaMemcpyHostToDevice, s));
+    if (k >= 6 && op->has_f32) {
+      // from k = 6 on the per-cell kernels beat the row-batch kernel for the FP32 vmult (k = 6 / 7 / 8
+      // on 48^3 / 32^3 / 32^3 cells: 59.9 / 66.2 / 47.8 against 52.6 / 38.1 / 37.5 GDoF/s): index table
+      // of the lattice (Dirichlet points as constraint rows without masters), FP32 metric per cell
+      op->percell32 = true;
+      MFX_TRY(dev_alloc(op, &op->d_cell_dofs, (size_t)op->n_cells * n3, s));
+      MFX_TRY(dev_alloc(op, &op->d_cmask, (size_t)op->n_dofs, s));
+      MFX_TRY(dev_alloc(op, &op->d_cptr, 2, s));
+      MFX_TRY(dev_alloc(op, &op->d_cmaster, 1, s));
+      MFX_TRY(dev_alloc(op, &op->d_cweight64, 1, s));
+      MFX_TRY(dev_alloc(op, &op->d_cweight32, 1, s));
+      MFX_TRY(launch_structured_index_tables(op, s));
+    }
   } else {
     MFX_TRY(octree_tables(m, k, &op->tables));
     const OctreeTables& t = op->tables;
@@ -574,8 +587,9 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   }
   // the FP64 metric is always built (geometry and diagonal are FP64); the FP32 copy on request
   size_t metric32_entries = metric_entries;
-  if (!op->structured) {
-    // octree FP32 metric in runs of the paired kernel's batch size (the last run padded)
+  if (!op->structured || op->percell32) {
+    // octree (and per-cell structured) FP32 metric in runs of the paired kernel's batch size (the last
+    // run padded)
     // (0: the per-cell kernel's [cell][6][q] layout)
     op->metric_cb32 = octree_pair_cells_for_degree(k);
     if (op->metric_cb32 > 0) {

@@ -27,6 +27,7 @@ struct GeoArgs {
   const double* coef_q;
   int cb, nchunk;  // metric layout: cb = 0 -> [cell][6][q]; else [batch][6][q][cb] (structured rows)
   int cb32;        // FP32 copy: as cb (structured); octree: 0, or [cell / cb32][6][q][cb32] (runs of cells)
+  bool runs32;     // FP32 copy of a structured mesh in the octree layouts (per cell, or runs of cb32 cells)
 };
 
 // Offset of metric entry (cell, 0, q) in the layout of batch size cb; entry e is at
@@ -143,7 +144,14 @@ __global__ void geometry_kernel(const __grid_constant__ GeoArgs g, double* __res
       G[e] = f * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
     }
     const int64_t base = metric_offset(g, cell, q), st = metric_stride(g);
-    const int64_t base32 = metric_offset_cb(g, cell, q, g.cb32), st32 = metric_stride_cb(g, g.cb32);
+    int64_t base32;
+    if (g.runs32 && g.cb32 > 0) {  // runs of cb32 consecutive cells
+      const int64_t batch = cell / g.cb32;
+      base32 = (batch * 6 * (int64_t)g.n * g.n * g.n + q) * g.cb32 + (cell - batch * g.cb32);
+    } else {
+      base32 = metric_offset_cb(g, cell, q, g.cb32);
+    }
+    const int64_t st32 = metric_stride_cb(g, g.cb32);
     for (int e = 0; e < 6; ++e) {
       if (m64) m64[base + e * st] = G[e];
       if (m32) m32[base32 + e * st32] = (float)G[e];
@@ -455,8 +463,44 @@ static GeoArgs geo_args(const mfx_op* op) {
   g.coef_q = nullptr;
   g.cb = op->metric_cb;
   g.nchunk = op->nchunk;
-  g.cb32 = op->structured ? op->metric_cb : op->metric_cb32;
+  g.cb32 = op->structured && !op->percell32 ? op->metric_cb : op->metric_cb32;
+  g.runs32 = op->percell32;
   return g;
+}
+
+// Index tables of a structured mesh for the per-cell kernels: lattice index of every cell node, -1 on
+// Dirichlet points (a constraint row without masters), and the per-DoF constrained mask.
+__global__ void structured_cell_dofs_kernel(int64_t n_cells, int nx, int ny, int n, int Mx, int My, int Mz,
+                                            uint32_t dmask, int32_t* __restrict__ cell_dofs) {
+  const int n3 = n * n * n, k = n - 1;
+  const int64_t total = n_cells * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = idx / n3;
+    const int i = (int)(idx - cell * n3);
+    const int64_t I = (cell % nx) * k + i % n, J = ((cell / nx) % ny) * k + (i / n) % n,
+                  L = (cell / ((int64_t)nx * ny)) * k + i / (n * n);
+    cell_dofs[idx] = on_dirichlet(dmask, I, J, L, Mx, My, Mz) ? -1 : (int32_t)(I + (int64_t)Mx * (J + (int64_t)My * L));
+  }
+}
+__global__ void structured_cmask_kernel(int Mx, int My, int Mz, uint32_t dmask, uint8_t* __restrict__ mask) {
+  const int64_t total = (int64_t)Mx * My * Mz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = i % Mx, rest = i / Mx, J = rest % My, L = rest / My;
+    mask[i] = on_dirichlet(dmask, I, J, L, Mx, My, Mz) ? 1 : 0;
+  }
+}
+
+static int grid_for(int64_t work);
+
+mfx_status launch_structured_index_tables(mfx_op* op, cudaStream_t s) {
+  const int Mx = op->k * op->nx + 1, My = op->k * op->ny + 1, Mz = op->k * op->nz + 1;
+  const int64_t work = op->n_cells * op->n * op->n * op->n;
+  structured_cell_dofs_kernel<<<grid_for(work), 256, 0, s>>>(op->n_cells, op->nx, op->ny, op->n, Mx, My, Mz,
+                                                              op->dirichlet, op->d_cell_dofs);
+  structured_cmask_kernel<<<grid_for(op->n_dofs), 256, 0, s>>>(Mx, My, Mz, op->dirichlet, op->d_cmask);
+  MFX_CUDA_TRY(cudaMemsetAsync(op->d_cptr, 0, 2 * sizeof(int64_t), s));
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
 }
 
 static DofView dof_view(const mfx_op* op) {

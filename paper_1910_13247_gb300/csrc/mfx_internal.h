@@ -92,6 +92,7 @@ struct mfx_op {
   bool structured = true;
   uint32_t dirichlet = mfx::kAllFaces;    // Dirichlet faces of the box
   bool dg = false;                        // SIPG operator (cell-major DoFs, no constraints)
+  bool percell32 = false;                 // structured, k >= 6: FP32 vmult by the per-cell kernels
   double dg_h[3] = {0, 0, 0}, dg_penalty = 1.0, dg_coef = 1.0, dg_origin[3] = {0, 0, 0};
   int nx = 0, ny = 0, nz = 0;             // structured cells per direction
   int cells_per_block = 0;
@@ -142,6 +143,8 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
 mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
 // SIPG operator (dg.cu).
+// structured meshes whose FP32 vmult runs on the per-cell kernels (geometry.cu)
+mfx_status launch_structured_index_tables(mfx_op* op, cudaStream_t s);
 mfx_status launch_dg_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                            const int32_t* skip);
 mfx_status launch_dg_diagonal(mfx_op* op, cudaStream_t s);

@@ -267,7 +267,7 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     }
     return run_vmult<N, double>(op, (const double*)src, (double*)dst, s, skip);
   }
-  if (op->structured) {
+  if (op->structured && !op->percell32) {
     if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
     return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
