@@ -278,7 +278,7 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
-                  op->d_err};
+                  op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   if (sync) cudaStreamSynchronize(s);
@@ -569,6 +569,16 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       MFX_CUDA_OP(cudaMemcpyAsync(op->d_cweight32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice, s));
     }
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_cell_hanging, cell_hang.data(), cell_hang.size(), cudaMemcpyHostToDevice, s));
+    // tensor-product form of the hanging constraints (used by the per-cell vmult)
+    MFX_TRY(dev_alloc(op, &op->d_hface, t.hface.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_hedge, t.hedge.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_hoff, t.hoff.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_hdofs, std::max<size_t>(1, t.hdofs.size()), s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_hface, t.hface.data(), t.hface.size() * 4, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_hedge, t.hedge.data(), t.hedge.size() * 4, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_hoff, t.hoff.data(), t.hoff.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!t.hdofs.empty())
+      MFX_CUDA_OP(cudaMemcpyAsync(op->d_hdofs, t.hdofs.data(), t.hdofs.size() * 4, cudaMemcpyHostToDevice, s));
   }
   const size_t nq = (size_t)op->n_cells * n3;
   size_t metric_entries = 6 * nq;
@@ -592,6 +602,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     // run padded)
     // (0: the per-cell kernel's [cell][6][q] layout)
     op->metric_cb32 = octree_pair_cells_for_degree(k);
+    // with hanging nodes from kTensorHangMinDegree on, the per-cell kernel (tensor-product constraints)
+    if (!op->structured && op->n_hanging > 0 && k >= kTensorHangMinDegree) op->metric_cb32 = 0;
     if (op->metric_cb32 > 0) {
       const size_t nb = (size_t)(op->n_cells + op->metric_cb32 - 1) / op->metric_cb32;
       metric32_entries = nb * op->metric_cb32 * 6 * n3;

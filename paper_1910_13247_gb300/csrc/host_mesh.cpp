@@ -331,6 +331,10 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     return true;
   };
   std::vector<std::pair<int32_t, double>> raw;
+  // tensor-product form: per fine cell, its hanging faces (with the coarse face's DoFs) and edges
+  out->hface.assign(C, 0u);
+  out->hedge.assign(C, 0u);
+  std::map<int64_t, std::vector<int32_t>> face_dofs, edge_dofs;  // key: cell * 16 + face / edge
   for (int64_t c = 0; c < C; ++c) {
     const auto& lf = t.leaves[c];
     const int L = lf[0];
@@ -352,6 +356,22 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
             if (it == t.index.end()) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
             const int64_t e = it->second;
             const int ae_d = sd ? 0 : k, ac_d = sd ? k : 0;
+            {
+              const int fe = 2 * d + (sd ? 0 : 1);  // the fine cell's face on the coarse face
+              out->hface[e] |= (1u << fe) | ((uint32_t)cu << (6 + 2 * fe)) | ((uint32_t)cv << (7 + 2 * fe));
+              std::vector<int32_t>& fd = face_dofs[e * 16 + fe];
+              if (fd.empty()) {
+                fd.resize((size_t)n * n);
+                for (int mv = 0; mv < n; ++mv)
+                  for (int mu = 0; mu < n; ++mu) {
+                    int ac[3];
+                    ac[d] = ac_d;
+                    ac[u] = mu;
+                    ac[v] = mv;
+                    fd[mu + n * mv] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
+                  }
+              }
+            }
             for (int bv = 0; bv < n; ++bv)
               for (int bu = 0; bu < n; ++bu) {
                 int ae[3];
@@ -402,6 +422,21 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
               // position of the edge line in the fine leaf
               const int64_t edge_u = 2 * (idx[u] + su), edge_v = 2 * (idx[v] + sv);
               const int au = edge_u == f[u] ? 0 : k, av = edge_v == f[v] ? 0 : k;
+              {
+                const int ee = 4 * d + 2 * (av == k ? 1 : 0) + (au == k ? 1 : 0);
+                if (!(out->hedge[e] >> ee & 1u)) {
+                  out->hedge[e] |= (1u << ee) | ((uint32_t)cd << (12 + ee));
+                  std::vector<int32_t>& ed = edge_dofs[e * 16 + ee];
+                  ed.resize(n);
+                  for (int md = 0; md < n; ++md) {
+                    int ac[3];
+                    ac[d] = md;
+                    ac[u] = su * k;
+                    ac[v] = sv * k;
+                    ed[md] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
+                  }
+                }
+              }
               for (int bd = 0; bd < n; ++bd) {
                 int ae[3];
                 ae[d] = bd;
@@ -425,6 +460,29 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
           }
         }
     }
+  }
+  // compact per-cell lists; an edge on a hanging face of the same cell is left to the face
+  out->hoff.assign(C, 0);
+  out->hdofs.clear();
+  auto coarse = [&](int32_t dof) { return (dirichlet[dof] || hanging.count(dof)) ? -1 : dof; };
+  for (int64_t c = 0; c < C; ++c) {
+    out->hoff[c] = (int64_t)out->hdofs.size();
+    const uint32_t hf = out->hface[c] & 0x3Fu;
+    uint32_t keep = 0u;
+    for (int ee = 0; ee < 12; ++ee) {
+      if (!(out->hedge[c] >> ee & 1u)) continue;
+      const int d = ee >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+      const int su = ee & 1, sv = (ee >> 1) & 1;
+      if ((hf >> (2 * u + su) & 1u) || (hf >> (2 * v + sv) & 1u)) continue;
+      keep |= 1u << ee;
+    }
+    out->hedge[c] = keep | (out->hedge[c] & (keep << 12));
+    for (int f = 0; f < 6; ++f)
+      if (hf >> f & 1u)
+        for (int32_t dof : face_dofs[c * 16 + f]) out->hdofs.push_back(coarse(dof));
+    for (int ee = 0; ee < 12; ++ee)
+      if (keep >> ee & 1u)
+        for (int32_t dof : edge_dofs[c * 16 + ee]) out->hdofs.push_back(coarse(dof));
   }
   out->constrained.clear();
   for (int64_t d = 0; d < N; ++d)

@@ -62,6 +62,11 @@ struct Mesh {
 };
 
 // DoF tables of an octree mesh (host).
+// Degree from which octree vmults apply hanging constraints in tensor-product form (measured on octrees
+// refined twice, FP32 GDoF/s, per-node masters / tensor product: k = 3 17.5 / 16.2, k = 4 13.5 / 17.1,
+// k = 5 7.7 / 20.1, k = 6 6.5 / 17.7, k = 7 4.7 / 18.1)
+constexpr int kTensorHangMinDegree = 4;
+
 struct OctreeTables {
   int64_t n_cells = 0, n_dofs = 0;
   std::vector<double> cell_vertices;   // n_cells x 8 x 3
@@ -70,6 +75,15 @@ struct OctreeTables {
   std::vector<int64_t> cptr;           // n_constrained + 1
   std::vector<int32_t> cmaster;
   std::vector<double> cweight;
+  // tensor-product form of the hanging constraints, per cell: hface bit f (face f = 2 d + side) if the
+  // face lies on a coarser neighbour's face, bits 6 + 2 f / 7 + 2 f the halves (u, v) of that coarse face
+  // it covers; hedge bit e (edge e = 4 d + 2 side_v + side_u, along d) if the edge lies on a coarser
+  // neighbour's edge and on no hanging face of the cell, bit 12 + e the half; hoff: start in hdofs of
+  // the cell's coarse DoFs (per hanging face in f order the (k+1)^2 coarse face DoFs, u fastest, then per
+  // hanging edge in e order the k+1 coarse edge DoFs; constrained coarse DoFs are -1)
+  std::vector<uint32_t> hface, hedge;
+  std::vector<int64_t> hoff;
+  std::vector<int32_t> hdofs;
 };
 mfx_status octree_sort_and_check(Mesh* m);
 mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out);
@@ -116,6 +130,10 @@ struct mfx_op {
   double* d_cweight64 = nullptr;
   float* d_cweight32 = nullptr;
   uint8_t* d_cell_hanging = nullptr; // octree: 1 if a cell touches a hanging node
+  uint32_t* d_hface = nullptr;       // octree: tensor-product hanging constraints (OctreeTables::hface)
+  uint32_t* d_hedge = nullptr;
+  int64_t* d_hoff = nullptr;
+  int32_t* d_hdofs = nullptr;
   // diagonal set-up on cells with hanging nodes (host; cleared once the diagonal is built):
   // one quadratic form v^T A_cell v per (cell, master) pair, v = the master's column of C on the cell
   std::vector<int32_t> hang_job_cell, hang_job_master;

@@ -40,7 +40,67 @@ struct VmultArgs {
   const uint8_t* cmask;
   int64_t n_dofs;
   const int32_t* skip;  // optional: when *skip != 0 the launch does nothing (converged solve)
+  // optional (octree): hanging constraints in tensor-product form, per cell (see OctreeTables::hface):
+  // a hanging face's constrained nodes are the coarse face's Q_k function at the fine nodes, two 1D
+  // interpolations P[c][b][m] = l_m((c + x_b) / 2) (c the half of the coarse face the fine face covers);
+  // a hanging edge's, one
+  const uint32_t* hface;
+  const uint32_t* hedge;
+  const int64_t* hoff;
+  const int32_t* hdofs;
+  Real P[2 * N * N];
 };
+
+// The hanging face (0..5) or edge (6..17) of a cell that owns local node (a1, a2, a3): the first hanging
+// face containing it, else the first hanging edge, else -1.  Each constrained node of a cell with
+// hanging faces or edges is interpolated by exactly one owner, and its transpose goes back through the
+// same owner only.
+__device__ __forceinline__ int hang_owner(uint32_t hf, uint32_t he, int a1, int a2, int a3, int K) {
+  const int a[3] = {a1, a2, a3};
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if ((hf >> f & 1u) && a[f >> 1] == (f & 1) * K) return f;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    if (!(he >> e & 1u)) continue;
+    const int d = e >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+    if (a[u] == (e & 1) * K && a[v] == ((e >> 1) & 1) * K) return 6 + e;
+  }
+  return -1;
+}
+
+// Value at local node (a1, a2, a3) of its owner's interpolation from the coarse values in HB (per cell:
+// 6 faces x n^2, u fastest, then 12 edges x n).
+template <int N, typename Real>
+__device__ __forceinline__ Real hang_value(const Real* P, uint32_t hf, uint32_t he, int own, int a1, int a2, int a3,
+                                           const Real* HB) {
+  constexpr int N2 = N * N;
+  const int a[3] = {a1, a2, a3};
+  if (own < 6) {
+    const int d = own >> 1, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+    const int cu = (hf >> (6 + 2 * own)) & 1, cv = (hf >> (7 + 2 * own)) & 1;
+    const Real* Pu = P + cu * N2 + a[u] * N;
+    const Real* Pv = P + cv * N2 + a[v] * N;
+    const Real* F = HB + own * N2;
+    Real s = Real(0);
+#pragma unroll
+    for (int mv = 0; mv < N; ++mv) {
+      Real t = Real(0);
+#pragma unroll
+      for (int mu = 0; mu < N; ++mu) t += Pu[mu] * F[mu + N * mv];
+      s += Pv[mv] * t;
+    }
+    return s;
+  }
+  const int e = own - 6, d = e >> 2;
+  const int cd = (he >> (12 + e)) & 1;
+  const Real* Pd = P + cd * N2 + a[d] * N;
+  const Real* E = HB + 6 * N2 + e * N;
+  Real s = Real(0);
+#pragma unroll
+  for (int md = 0; md < N; ++md) s += Pd[md] * E[md];
+  return s;
+}
 
 template <int N>
 struct VmultShape {
@@ -124,7 +184,9 @@ __device__ __forceinline__ void scatter_xline(const VmultArgs<N, Real>& a, Real*
   }
 }
 
-template <int N, typename Real>
+// HANG: the mesh has hanging nodes and its constraints are applied in tensor-product form (a separate
+// instantiation, so meshes without them keep the registers and the occupancy of the plain kernel)
+template <int N, typename Real, bool HANG>
 __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ VmultArgs<N, Real> a,
                                                     const Real* __restrict__ src, Real* __restrict__ dst) {
   using Sh = VmultShape<N>;
@@ -134,6 +196,8 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
   Real* buf0 = reinterpret_cast<Real*>(smem_raw);
   Real* buf1 = buf0 + CB * CELL;
   Real* buf2 = buf1 + CB * CELL;
+  Real* hbuf = buf2 + CB * CELL;  // coarse values of hanging faces and edges: CB x (6 n^2 + 12 n)
+  constexpr int HB_CELL = 6 * N2 + 12 * N;
 
   const int t = threadIdx.x;
   const int cl = t / N2;
@@ -149,15 +213,77 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
     const int64_t cell = b * CB + cl;
     const bool act = line_ok && cell < a.n_cells;
     Real g3[N], t3[N];
+    // hanging faces / edges of this thread's cell (tensor-product constraints, when given)
+    const uint32_t hf = (HANG && act) ? __ldg(a.hface + cell) : 0u;
+    const uint32_t he = (HANG && act) ? __ldg(a.hedge + cell) : 0u;
+    const bool hang = (hf | he) != 0u;
+    const bool any_hang = HANG && __syncthreads_or(hang);
+    Real* HB = hbuf + (line_ok ? cl : 0) * HB_CELL;
 
     // 1) gather + S along x: x-line (i2 = ra, i3 = rb)
-    if (act) {
-      Real v[N], o[N];
-      gather_xline<N, Real>(a, src, cell, ra, rb, v);
-      contract<N, Real, MAT_S>(v, o);
-      Real* p = B0 + (rb * N + ra) * NP;
+    if (!any_hang) {
+      if (act) {
+        Real v[N], o[N];
+        gather_xline<N, Real>(a, src, cell, ra, rb, v);
+        contract<N, Real, MAT_S>(v, o);
+        Real* p = B0 + (rb * N + ra) * NP;
 #pragma unroll
-      for (int q = 0; q < N; ++q) p[q] = o[q];
+        for (int q = 0; q < N; ++q) p[q] = o[q];
+      }
+    } else {
+      // free DoFs directly; constrained nodes owned by a hanging face or edge are interpolated from the
+      // coarse values once every thread of the cell has staged them; other constrained nodes as before
+      Real v[N];
+      int own[N];
+      if (act) {
+        const int32_t* cd = a.cell_dofs + cell * N3 + (rb * N + ra) * N;
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1) {
+          const int32_t e = __ldg(cd + i1);
+          own[i1] = (e < 0 && hang) ? hang_owner(hf, he, i1, ra, rb, N - 1) : -1;
+          if (e >= 0) {
+            v[i1] = __ldg(src + e);
+          } else if (own[i1] >= 0) {
+            v[i1] = Real(0);
+          } else {
+            const int32_t row = -e - 1;
+            Real s = Real(0);
+            for (int64_t p = a.cptr[row]; p < a.cptr[row + 1]; ++p) s += a.cweight[p] * __ldg(src + a.cmaster[p]);
+            v[i1] = s;
+          }
+        }
+      }
+      if (act && hang) {
+        const int64_t h0 = __ldg(a.hoff + cell);
+        int slot = 0;
+        for (int f = 0; f < 6; ++f) {
+          if (!(hf >> f & 1u)) continue;
+          const int32_t hd = __ldg(a.hdofs + h0 + slot + r);
+          HB[f * N2 + r] = hd >= 0 ? __ldg(src + hd) : Real(0);
+          slot += N2;
+        }
+        for (int e = 0; e < 12; ++e) {
+          if (!(he >> e & 1u)) continue;
+          if (r < N) {
+            const int32_t hd = __ldg(a.hdofs + h0 + slot + r);
+            HB[6 * N2 + e * N + r] = hd >= 0 ? __ldg(src + hd) : Real(0);
+          }
+          slot += N;
+        }
+      }
+      __syncthreads();
+      if (act) {
+        if (hang) {
+#pragma unroll
+          for (int i1 = 0; i1 < N; ++i1)
+            if (own[i1] >= 0) v[i1] = hang_value<N, Real>(a.P, hf, he, own[i1], i1, ra, rb, HB);
+        }
+        Real o[N];
+        contract<N, Real, MAT_S>(v, o);
+        Real* p = B0 + (rb * N + ra) * NP;
+#pragma unroll
+        for (int q = 0; q < N; ++q) p[q] = o[q];
+      }
     }
     __syncthreads();
     // 2) S along y: y-line (q1 = ra, i3 = rb)
@@ -266,13 +392,92 @@ __global__ void __launch_bounds__(256) vmult_kernel(const __grid_constant__ Vmul
     }
     __syncthreads();
     // 10) S_x^T and scatter (x-line i2 = ra, i3 = rb)
-    if (act) {
-      Real v[N], o[N];
-      const Real* p = B1 + (rb * N + ra) * NP;
+    if (!any_hang) {
+      if (act) {
+        Real v[N], o[N];
+        const Real* p = B1 + (rb * N + ra) * NP;
 #pragma unroll
-      for (int j = 0; j < N; ++j) v[j] = p[j];
-      contract_t<N, Real, MAT_S>(v, o);
-      scatter_xline<N, Real>(a, dst, cell, ra, rb, o);
+        for (int j = 0; j < N; ++j) v[j] = p[j];
+        contract_t<N, Real, MAT_S>(v, o);
+        scatter_xline<N, Real>(a, dst, cell, ra, rb, o);
+      }
+    } else {
+      // nodes owned by a hanging face or edge go to the coarse DoFs through the transposed interpolation
+      // (staged in B0, which phase 4 last read); the other nodes are scattered as before
+      if (act) {
+        Real v[N], o[N];
+        const Real* p = B1 + (rb * N + ra) * NP;
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = p[j];
+        contract_t<N, Real, MAT_S>(v, o);
+        const int32_t* cd = a.cell_dofs + cell * N3 + (rb * N + ra) * N;
+        Real* w = B0 + (rb * N + ra) * NP;
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1) {
+          const int32_t e = __ldg(cd + i1);
+          const int own = (e < 0 && hang) ? hang_owner(hf, he, i1, ra, rb, N - 1) : -1;
+          w[i1] = own >= 0 ? o[i1] : Real(0);
+          if (own >= 0) continue;
+          if (e >= 0) {
+            atomicAdd(dst + e, o[i1]);
+          } else {
+            const int32_t row = -e - 1;
+            for (int64_t q = a.cptr[row]; q < a.cptr[row + 1]; ++q) atomicAdd(dst + a.cmaster[q], a.cweight[q] * o[i1]);
+          }
+        }
+      }
+      __syncthreads();
+      if (act && hang) {
+        constexpr int K = N - 1;
+        const int64_t h0 = __ldg(a.hoff + cell);
+        int slot = 0;
+        for (int f = 0; f < 6; ++f) {
+          if (!(hf >> f & 1u)) continue;
+          // coarse face node (mu, mv) = (r % N, r / N): sum over the fine face nodes this face owns
+          const int d = f >> 1, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+          const int cu = (hf >> (6 + 2 * f)) & 1, cv = (hf >> (7 + 2 * f)) & 1;
+          const int mu = r % N, mv = r / N;
+          const Real* Pu = a.P + cu * N2 + mu;
+          const Real* Pv = a.P + cv * N2 + mv;
+          const int step[3] = {1, NP, N * NP};
+          const int base = (f & 1) * K * step[d];
+          Real s = Real(0);
+          for (int bv = 0; bv < N; ++bv) {
+            // face f owns node (bu, bv) unless a hanging face of lower index also contains it
+            const int sv = bv == 0 ? 0 : (bv == K ? 1 : -1);
+            if (sv >= 0 && 2 * v + sv < f && (hf >> (2 * v + sv) & 1u)) continue;
+            Real t = Real(0);
+            for (int bu = 0; bu < N; ++bu) {
+              const int su = bu == 0 ? 0 : (bu == K ? 1 : -1);
+              if (su >= 0 && 2 * u + su < f && (hf >> (2 * u + su) & 1u)) continue;
+              t += Pu[bu * N] * B0[base + bu * step[u] + bv * step[v]];
+            }
+            s += Pv[bv * N] * t;
+          }
+          const int32_t hd = __ldg(a.hdofs + h0 + slot + r);
+          if (hd >= 0) atomicAdd(dst + hd, s);
+          slot += N2;
+        }
+        for (int e = 0; e < 12; ++e) {
+          if (!(he >> e & 1u)) continue;
+          if (r < N) {
+            const int d = e >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+            const int cdh = (he >> (12 + e)) & 1;
+            Real s = Real(0);
+            for (int bd = 0; bd < N; ++bd) {
+              int aa[3];
+              aa[d] = bd;
+              aa[u] = (e & 1) * K;
+              aa[v] = ((e >> 1) & 1) * K;
+              if (hang_owner(hf, he, aa[0], aa[1], aa[2], K) != 6 + e) continue;
+              s += a.P[cdh * N2 + bd * N + r] * B0[(aa[2] * N + aa[1]) * NP + aa[0]];
+            }
+            const int32_t hd = __ldg(a.hdofs + h0 + slot + r);
+            if (hd >= 0) atomicAdd(dst + hd, s);
+          }
+          slot += N;
+        }
+      }
     }
     __syncthreads();
   }

@@ -37,14 +37,22 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
   a->cweight = std::is_same<Real, double>::value ? (const Real*)op->d_cweight64 : (const Real*)op->d_cweight32;
   a->cmask = op->d_cmask;
   a->n_dofs = op->n_dofs;
+  a->hface = op->d_hface;
+  a->hedge = op->d_hedge;
+  a->hoff = op->d_hoff;
+  a->hdofs = op->d_hdofs;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < N; ++b)
+      for (int m = 0; m < N; ++m)
+        a->P[c * N * N + b * N + m] = (Real)lagrange_value(N, op->basis.gll, m, 0.5 * (c + op->basis.gll[b]));
 }
 
-template <int N, typename Real>
-static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+template <int N, typename Real, bool HANG>
+static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
-  const size_t smem = 3 * (size_t)Sh::CB * Sh::CELL * sizeof(Real);
-  auto kern = vmult_kernel<N, Real>;
+  const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + (HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0)) * sizeof(Real);
+  auto kern = vmult_kernel<N, Real, HANG>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -65,6 +73,15 @@ static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaSt
   }
   MFX_CUDA_TRY(cudaGetLastError());
   return MFX_OK;
+}
+
+// Hanging constraints in tensor-product form where they pay (k >= kTensorHangMinDegree), per-node master
+// expansion otherwise.
+template <int N, typename Real>
+static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+  if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_hface)
+    return run_vmult_h<N, Real, true>(op, src, dst, s, skip);
+  return run_vmult_h<N, Real, false>(op, src, dst, s, skip);
 }
 
 template <int N, typename Real, int CB>
@@ -271,7 +288,9 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
     return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
-  if constexpr (OctreePairFor<N>::value) return run_octree_pair<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
+  // the paired octree kernel where the FP32 metric is laid out for it (k = 1; k = 8 without hanging nodes)
+  if constexpr (OctreePairFor<N>::value)
+    if (op->metric_cb32 > 0) return run_octree_pair<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float>(op, (const float*)src, (float*)dst, s, skip);
 }
 
