@@ -301,7 +301,18 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
         dirichlet[d] = 1;
     }
   // hanging constraints
-  std::map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;
+  std::unordered_map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;
+  hanging.reserve((size_t)C * 8 + 64);
+  // a hanging node is reached once per fine cell around it; the 2:1 balance makes every visit give the
+  // same constraint, so the first one is kept and the others are skipped before their masters are formed
+  std::vector<uint8_t> is_hanging(N, 0);
+  auto known = [&](int32_t dof) { return dirichlet[dof] != 0 || is_hanging[dof] != 0; };
+  // 1D weights of the constraints: W1[c][b][m] = l_m((c + x_b) / 2), the coarse basis at node b of half c
+  std::vector<double> W1((size_t)2 * n * n);
+  for (int c2 = 0; c2 < 2; ++c2)
+    for (int b = 0; b < n; ++b)
+      for (int mm = 0; mm < n; ++mm)
+        W1[((size_t)c2 * n + b) * n + mm] = lagrange_value(n, g, mm, ((double)c2 + g[b]) * 0.5);
   auto add = [&](int32_t dof, std::vector<std::pair<int32_t, double>>& raw) -> mfx_status {
     if (dirichlet[dof]) return MFX_OK;
     std::vector<std::pair<int32_t, double>> clean;
@@ -311,6 +322,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     auto it = hanging.find(dof);
     if (it == hanging.end()) {
       hanging.emplace(dof, std::move(clean));
+      is_hanging[dof] = 1;
       return MFX_OK;
     }
     const auto& old = it->second;
@@ -334,7 +346,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   // tensor-product form: per fine cell, its hanging faces (with the coarse face's DoFs) and edges
   out->hface.assign(C, 0u);
   out->hedge.assign(C, 0u);
-  std::map<int64_t, std::vector<int32_t>> face_dofs, edge_dofs;  // key: cell * 16 + face / edge
+  std::unordered_map<int64_t, std::vector<int32_t>> face_dofs, edge_dofs;  // key: cell * 16 + face / edge
   for (int64_t c = 0; c < C; ++c) {
     const auto& lf = t.leaves[c];
     const int L = lf[0];
@@ -379,8 +391,10 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
                 ae[u] = bu;
                 ae[v] = bv;
                 const int li = ae[0] + n * (ae[1] + n * ae[2]);
+                if (known(out->cell_dofs[e * n3 + li])) continue;
                 if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
-                const double pu = ((double)cu + g[bu]) * 0.5, pv = ((double)cv + g[bv]) * 0.5;
+                const double* Wu = &W1[((size_t)cu * n + bu) * n];
+                const double* Wv = &W1[((size_t)cv * n + bv) * n];
                 raw.clear();
                 for (int mv = 0; mv < n; ++mv)
                   for (int mu = 0; mu < n; ++mu) {
@@ -388,7 +402,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
                     ac[d] = ac_d;
                     ac[u] = mu;
                     ac[v] = mv;
-                    const double w = lagrange_value(n, g, mu, pu) * lagrange_value(n, g, mv, pv);
+                    const double w = Wu[mu] * Wv[mv];
                     raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], w});
                   }
                 mfx_status st = add(out->cell_dofs[e * n3 + li], raw);
@@ -443,15 +457,16 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
                 ae[u] = au;
                 ae[v] = av;
                 const int li = ae[0] + n * (ae[1] + n * ae[2]);
+                if (known(out->cell_dofs[e * n3 + li])) continue;
                 if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
-                const double pd = ((double)cd + g[bd]) * 0.5;
+                const double* Wd = &W1[((size_t)cd * n + bd) * n];
                 raw.clear();
                 for (int md = 0; md < n; ++md) {
                   int ac[3];
                   ac[d] = md;
                   ac[u] = su * k;
                   ac[v] = sv * k;
-                  raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], lagrange_value(n, g, md, pd)});
+                  raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], Wd[md]});
                 }
                 mfx_status st = add(out->cell_dofs[e * n3 + li], raw);
                 if (st != MFX_OK) return st;
@@ -464,7 +479,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   // compact per-cell lists; an edge on a hanging face of the same cell is left to the face
   out->hoff.assign(C, 0);
   out->hdofs.clear();
-  auto coarse = [&](int32_t dof) { return (dirichlet[dof] || hanging.count(dof)) ? -1 : dof; };
+  auto coarse = [&](int32_t dof) { return (dirichlet[dof] || is_hanging[dof]) ? -1 : dof; };
   for (int64_t c = 0; c < C; ++c) {
     out->hoff[c] = (int64_t)out->hdofs.size();
     const uint32_t hf = out->hface[c] & 0x3Fu;
@@ -485,16 +500,21 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
         for (int32_t dof : edge_dofs[c * 16 + ee]) out->hdofs.push_back(coarse(dof));
   }
   out->constrained.clear();
+  size_t n_masters = 0;
   for (int64_t d = 0; d < N; ++d)
-    if (dirichlet[d] || hanging.count((int32_t)d)) out->constrained.push_back((int32_t)d);
+    if (dirichlet[d] || is_hanging[d]) out->constrained.push_back((int32_t)d);
+  for (auto& h : hanging) n_masters += h.second.size();
   out->cptr.assign(1, 0);
+  out->cptr.reserve(out->constrained.size() + 1);
   out->cmaster.clear();
   out->cweight.clear();
+  out->cmaster.reserve(n_masters);
+  out->cweight.reserve(n_masters);
   for (int32_t d : out->constrained) {
-    auto it = hanging.find(d);
+    auto it = is_hanging[d] ? hanging.find(d) : hanging.end();
     if (it != hanging.end())
       for (auto& mw : it->second) {
-        if (hanging.count(mw.first)) return set_error(MFX_EMESH, "constraint master is itself constrained");
+        if (is_hanging[mw.first]) return set_error(MFX_EMESH, "constraint master is itself constrained");
         out->cmaster.push_back(mw.first);
         out->cweight.push_back(mw.second);
       }
