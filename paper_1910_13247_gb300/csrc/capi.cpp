@@ -524,6 +524,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     if (std::find(cell_hang.begin(), cell_hang.end(), 1) != cell_hang.end()) {
       op->hang_simple.assign(enc.size(), 1);
       std::vector<int32_t> ms;
+      std::vector<int64_t> seen(t.n_dofs, -1);  // last cell that listed the DoF as a master
       for (int64_t c = 0; c < t.n_cells; ++c) {
         if (!cell_hang[c]) continue;
         ms.clear();
@@ -531,10 +532,15 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
           const int32_t e = enc[c * n3 + i];
           if (e >= 0) continue;
           const int32_t r = -e - 1;
-          for (int64_t p = t.cptr[r]; p < t.cptr[r + 1]; ++p) ms.push_back(t.cmaster[p]);
+          for (int64_t p = t.cptr[r]; p < t.cptr[r + 1]; ++p) {
+            const int32_t m = t.cmaster[p];
+            if (seen[m] != c) {
+              seen[m] = c;
+              ms.push_back(m);
+            }
+          }
         }
         std::sort(ms.begin(), ms.end());
-        ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
         for (int32_t m : ms) {
           op->hang_job_cell.push_back((int32_t)c);
           op->hang_job_master.push_back(m);
