@@ -63,9 +63,9 @@ struct Mesh {
 
 // DoF tables of an octree mesh (host).
 // Degree from which octree vmults apply hanging constraints in tensor-product form (measured on octrees
-// refined twice, FP32 GDoF/s, per-node masters / tensor product: k = 3 17.5 / 16.2, k = 4 13.5 / 17.1,
-// k = 5 7.7 / 20.1, k = 6 6.5 / 17.7, k = 7 4.7 / 18.1)
-constexpr int kTensorHangMinDegree = 4;
+// refined twice, FP32 GDoF/s, per-node masters / tensor product: k = 2 17.2 / 13.0, k = 3 17.5 / 18.1,
+// k = 4 13.5 / 19.7, k = 6 6.5 / 22.0, k = 8 (paired kernel) about 3 / 14.5)
+constexpr int kTensorHangMinDegree = 3;
 
 struct OctreeTables {
   int64_t n_cells = 0, n_dofs = 0;
