@@ -151,6 +151,27 @@ def test_octree_vmult_with_hanging_nodes(mfx, k):
     assert np.abs(xs.cpu().numpy() - fem.distribute(om, x)).max() < 1e-14
 
 
+@pytest.mark.parametrize("seed,k,nb,radius", [(1, 3, 3, 0.25), (5, 4, 3, 0.25), (2, 5, 2, 0.25), (3, 6, 2, 0.35)])
+def test_octree_tensor_product_hanging_constraints(mfx, seed, k, nb, radius):
+    """Octrees refined twice around a seeded centre, at the degrees whose vmult applies the hanging
+    constraints in tensor-product form (faces, and edges hanging on their own at the rim of the
+    refined region): vmult equals the oracle's condensed matrix."""
+    g = synthetic.rng(300 + seed)
+    leaves = synthetic.octree_leaves(nb, 2, g.uniform(0.3, 0.7, 3), radius)
+    verts = synthetic.deformed_vertices(nb, nb, nb)
+    m = mfx.Mesh.octree(nb, nb, nb, leaves, verts)
+    op = mfx.Operator(m, k, mfx.COEF_TRIG, (1.0, 0.5))
+    assert op.info()["n_hanging"] > 0
+    om = omesh.octree_mesh(nb, nb, nb, k, leaves, verts)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 40 + seed)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    e32, _ = rel_err(run_vmult(op, x, torch.float32), ref)
+    assert e32 < 1e-5, e32
+
+
 @pytest.mark.parametrize("k", [5, 8])
 def test_octree_diagonal_high_degree(mfx, k):
     """Diagonal and vmult on an octree at high degree: the diagonal's sum-factorised paths (cells with
