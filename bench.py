@@ -196,6 +196,8 @@ def main():
                     help="cells of the SIPG hyper-rectangle (profiling on smaller cases)")
     ap.add_argument("--sipg-vmult-only", action="store_true", help="SIPG: time the vmult only, no multigrid solve")
     ap.add_argument("--sipg-degree", type=int, default=4, help="SIPG polynomial degree (the paper's benchmark: 4)")
+    ap.add_argument("--no-octree", action="store_true", help="skip the octree vmult (hanging nodes)")
+    ap.add_argument("--octree-degree", type=int, default=4, help="degree of the octree vmult measurement")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--nx", type=int, default=NX, help="cells per direction (profiling on smaller cases)")
     ap.add_argument("--degree", type=int, default=K_DEG)
@@ -345,6 +347,8 @@ def main():
             line["batched"] = batched_measurement(mfx, synthetic, torch, np)
         if not args.no_serve:
             line["serving"] = serving_measurement(args.serve_requests)
+        if not args.no_octree:
+            line["octree"] = octree_measurement(mfx, synthetic, torch, args.octree_degree)
         if not args.no_sipg:
             line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims), k=args.sipg_degree,
                                             solve=not args.sipg_vmult_only)
@@ -517,6 +521,33 @@ def mixed_solve_measurement(mfx, synthetic, torch, np):
     out["mg_levels"] = g.n_levels
     out["mg_setup_seconds"] = setup
     out["speedup_mg_mixed_over_cheb_mixed"] = out["mixed"]["seconds"] / out["mg_mixed"]["seconds"]
+    return out
+
+
+def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2):
+    """FP32 and FP64 vmult on an octree refined twice inside a ball (hanging nodes; the serving
+    workload's mesh family): nb^3 coarse cells of the deformed cube, the variable coefficient."""
+    leaves = synthetic.octree_leaves(nb, levels, (0.5, 0.45, 0.55), 0.3)
+    mesh = mfx.Mesh.octree(nb, nb, nb, leaves, synthetic.deformed_vertices(nb, nb, nb))
+    op = mfx.Operator(mesh, k, mfx.COEF_TRIG, (1.0, 0.5))
+    info = op.info()
+    n = op.n_dofs
+    out = {"workload": "octree, %d^3 coarse cells refined %d times in a ball, Q%d" % (nb, levels, k), "n_dofs": n,
+           "n_cells": info["n_cells"], "n_hanging": info["n_hanging"]}
+    stream = torch.cuda.current_stream()
+    for name, dt in (("vmult_fp32", torch.float32), ("vmult_fp64", torch.float64)):
+        x = torch.tensor(synthetic.uniform_vector(n, 71), device="cuda", dtype=dt)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.vmult(x, y)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(30)]
+        for e0, e1 in evs:
+            e0.record(stream)
+            op.vmult(x, y)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        out[name] = {"gdofs": n / (ms * 1e-3) / 1e9, "ms": ms}
     return out
 
 
