@@ -278,7 +278,8 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
-                  op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs};
+                  op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs, op->d_cells_plain,
+                  op->d_cells_hang};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   if (sync) cudaStreamSynchronize(s);
@@ -585,6 +586,20 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_hoff, t.hoff.data(), t.hoff.size() * 8, cudaMemcpyHostToDevice, s));
     if (!t.hdofs.empty())
       MFX_CUDA_OP(cudaMemcpyAsync(op->d_hdofs, t.hdofs.data(), t.hdofs.size() * 4, cudaMemcpyHostToDevice, s));
+    if (op->n_hanging > 0 && k >= kTensorHangMinDegree) {
+      // the cells without hanging faces or edges run in the plain kernel, the others in the
+      // tensor-product one
+      std::vector<int32_t> plain, hang;
+      for (int64_t c = 0; c < t.n_cells; ++c) ((t.hface[c] | t.hedge[c]) ? hang : plain).push_back((int32_t)c);
+      op->n_cells_plain = (int64_t)plain.size();
+      op->n_cells_hang = (int64_t)hang.size();
+      MFX_TRY(dev_alloc(op, &op->d_cells_plain, std::max<size_t>(1, plain.size()), s));
+      MFX_TRY(dev_alloc(op, &op->d_cells_hang, std::max<size_t>(1, hang.size()), s));
+      if (!plain.empty())
+        MFX_CUDA_OP(cudaMemcpyAsync(op->d_cells_plain, plain.data(), plain.size() * 4, cudaMemcpyHostToDevice, s));
+      if (!hang.empty())
+        MFX_CUDA_OP(cudaMemcpyAsync(op->d_cells_hang, hang.data(), hang.size() * 4, cudaMemcpyHostToDevice, s));
+    }
   }
   const size_t nq = (size_t)op->n_cells * n3;
   size_t metric_entries = 6 * nq;

@@ -134,6 +134,9 @@ struct mfx_op {
   uint32_t* d_hedge = nullptr;
   int64_t* d_hoff = nullptr;
   int32_t* d_hdofs = nullptr;
+  int32_t* d_cells_plain = nullptr;  // octree, tensor-product constraints: cells without / with hanging
+  int32_t* d_cells_hang = nullptr;   // faces or edges (each list runs in its own kernel instantiation)
+  int64_t n_cells_plain = 0, n_cells_hang = 0;
   // diagonal set-up on cells with hanging nodes (host; cleared once the diagonal is built):
   // one quadratic form v^T A_cell v per (cell, master) pair, v = the master's column of C on the cell
   std::vector<int32_t> hang_job_cell, hang_job_master;

@@ -49,6 +49,9 @@ struct VmultArgs {
   const int64_t* hoff;
   const int32_t* hdofs;
   Real P[2 * N * N];
+  // optional: the launch processes the cells cell_list[0 .. n_list) instead of 0 .. n_cells
+  const int32_t* cell_list;
+  int64_t n_list;
 };
 
 // The hanging face (0..5) or edge (6..17) of a cell that owns local node (a1, a2, a3): the first hanging
@@ -210,10 +213,12 @@ __global__ void __launch_bounds__(256, HANG ? 3 : 1) vmult_kernel(const __grid_c
   Real* B1 = buf1 + cl * CELL;
   Real* B2 = buf2 + cl * CELL;
 
-  const int64_t nbatch = (a.n_cells + CB - 1) / CB;
+  const int64_t n_items = a.cell_list ? a.n_list : a.n_cells;
+  const int64_t nbatch = (n_items + CB - 1) / CB;
   for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
-    const int64_t cell = b * CB + cl;
-    const bool act = line_ok && cell < a.n_cells;
+    const int64_t item = b * CB + cl;
+    const bool act = line_ok && item < n_items;
+    const int64_t cell = act && a.cell_list ? (int64_t)__ldg(a.cell_list + item) : item;
     Real g3[N], t3[N];
     // hanging faces / edges of this thread's cell (tensor-product constraints, when given)
     const uint32_t hf = (HANG && act) ? __ldg(a.hface + cell) : 0u;

@@ -31,6 +31,8 @@ template <int N, typename Real>
 static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
   a->metric = std::is_same<Real, double>::value ? (const Real*)op->d_metric64 : (const Real*)op->d_metric32;
   a->n_cells = op->n_cells;
+  a->cell_list = nullptr;
+  a->n_list = 0;
   a->cell_dofs = op->d_cell_dofs;
   a->cptr = op->d_cptr;
   a->cmaster = op->d_cmaster;
@@ -47,8 +49,11 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
         a->P[c * N * N + b * N + m] = (Real)lagrange_value(N, op->basis.gll, m, 0.5 * (c + op->basis.gll[b]));
 }
 
+// One launch of the per-cell kernel over all cells, or over a cell list (prologue: dst = src on the
+// constrained rows and 0 elsewhere, before the first launch of a vmult).
 template <int N, typename Real, bool HANG>
-static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip,
+                              const int32_t* list, int64_t n_list, bool prologue) {
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
   const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + (HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0)) * sizeof(Real);
@@ -62,11 +67,15 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
   VmultArgs<N, Real> a;
   fill_vmult_args<N, Real>(op, &a);
   a.skip = skip;
+  a.cell_list = list;
+  a.n_list = n_list;
   const int sms = device_sm_count();
-  int pb = (int)std::min<int64_t>((op->n_dofs + 255) / 256, (int64_t)sms * 8);
-  if (pb < 1) pb = 1;
-  vmult_prologue<N, Real><<<pb, 256, 0, s>>>(a, src, dst);
-  const int64_t nbatch = (op->n_cells + Sh::CB - 1) / Sh::CB;
+  if (prologue) {
+    int pb = (int)std::min<int64_t>((op->n_dofs + 255) / 256, (int64_t)sms * 8);
+    if (pb < 1) pb = 1;
+    vmult_prologue<N, Real><<<pb, 256, 0, s>>>(a, src, dst);
+  }
+  const int64_t nbatch = ((list ? n_list : op->n_cells) + Sh::CB - 1) / Sh::CB;
   if (nbatch > 0) {
     const int grid = (int)std::min<int64_t>(nbatch, (int64_t)sms * blocks_per_sm);
     kern<<<grid, Sh::THREADS, smem, s>>>(a, src, dst);
@@ -79,9 +88,13 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
 // expansion otherwise.
 template <int N, typename Real>
 static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
-  if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_hface)
-    return run_vmult_h<N, Real, true>(op, src, dst, s, skip);
-  return run_vmult_h<N, Real, false>(op, src, dst, s, skip);
+  if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_cells_hang) {
+    // cells without hanging faces or edges in the plain kernel, the rest in the tensor-product one
+    mfx_status st = run_vmult_h<N, Real, false>(op, src, dst, s, skip, op->d_cells_plain, op->n_cells_plain, true);
+    if (st != MFX_OK) return st;
+    return run_vmult_h<N, Real, true>(op, src, dst, s, skip, op->d_cells_hang, op->n_cells_hang, false);
+  }
+  return run_vmult_h<N, Real, false>(op, src, dst, s, skip, nullptr, 0, true);
 }
 
 template <int N, typename Real, int CB>
