@@ -39,9 +39,9 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 # DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
 # profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case, 16 cells per batch, scaled by cells).  Valid only for
 # that batch size and the kernel sources it was taken from: anything else reports null.
-TRAFFIC_BYTES = 979.2e6
+TRAFFIC_BYTES = 980.5e6
 TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "a9524b2424c4577c", "vmult_brick_tma.cuh": "731ccc8ecdc21d0b",
-                   "vmult_brick.cuh": "d4348f1901d2181e", "vmult.cuh": "824fb225eb34ba20"}
+                   "vmult_brick.cuh": "d4348f1901d2181e", "vmult.cuh": "31514fc950494b5e"}
 
 
 def measured_traffic(nx, k, cells_per_block):
