@@ -130,8 +130,11 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds=12.0, sub=12, one_core=True):
-    """The FP64 oracle (assembled CSR SpMV, OpenMP) on a sub-mesh of the same workload."""
+def cpu_baseline(seconds=12.0, sub=12, one_core=True, steps=None, warmup=0):
+    """The FP64 oracle (assembled CSR SpMV, OpenMP) on a sub-mesh of the same workload.
+
+    Runs SpMVs for `seconds`, or, with `steps` given, `warmup` untimed SpMVs and then exactly `steps` timed
+    ones (one step = one SpMV over the sub-mesh)."""
     import numpy as np
     from oracle import fem, mesh
     from paper_1910_13247_gb300 import synthetic
@@ -144,11 +147,21 @@ def cpu_baseline(seconds=12.0, sub=12, one_core=True):
     x = synthetic.uniform_vector(om.n_dofs, 1)
     y = np.zeros(om.n_dofs)
     A(x, y)
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        A(x, y)
-        reps += 1
-    dt = (time.perf_counter() - t0) / reps
+    if steps is not None:
+        for _ in range(warmup):
+            A(x, y)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            A(x, y)
+        reps = steps
+        seconds = time.perf_counter() - t0
+    else:
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            A(x, y)
+            reps += 1
+        seconds = time.perf_counter() - t0
+    dt = seconds / reps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     if one_core and cores > 1:
         # the same SpMV on one core (a fresh process: the OpenMP team size is fixed at start)
@@ -159,10 +172,10 @@ def cpu_baseline(seconds=12.0, sub=12, one_core=True):
         one = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 and r.stdout.strip() else None
     else:
         one = None
-    return {"value": om.n_dofs / dt / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+    return {"value": om.n_dofs / dt / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle", "ms_per_spmv": dt * 1e3,
             "one_core_value": one["value"] if one else None,
             "sample": f"FP64 CSR SpMV of the oracle-assembled operator on a {sub}^3-cell sub-mesh of the same "
-                      f"workload ({om.n_dofs} DoFs, {K.nnz} nonzeros), {reps} SpMVs over {seconds:.0f} s; "
+                      f"workload ({om.n_dofs} DoFs, {K.nnz} nonzeros), {reps} SpMVs over {seconds:.1f} s; "
                       f"assembly ({t_asm:.1f} s) excluded"}
 
 
@@ -170,11 +183,14 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(seconds=max(2.0, min(30.0, 0.5 * args.steps)))
+    # one step = one oracle SpMV over the sub-mesh (a few ms on the host cores), so K steps stay bounded
+    cb = cpu_baseline(steps=args.steps, warmup=args.warmup)
     line = {"metric": METRIC, "value": cb["value"], "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": cb["ms_per_spmv"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle sample: CSR SpMV on a 12^3-cell sub-mesh)"},
+            "config": {"workload": WORKLOAD, "n_dofs": (NX * K_DEG + 1) ** 3, "n_cells": NX ** 3, "degree": K_DEG,
+                       "n_q_1d": K_DEG + 1, "step": "one FP64 oracle SpMV over a 12^3-cell sample of the workload",
+                       "parallelism": "host cores"},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -48,3 +48,36 @@ def test_single_process_aggregation():
     import bench
     t, rate = bench.aggregate_ranks(20.0, 500.0)
     assert t == 20.0 and abs(rate - 500.0 / 20e-3) < 1e-9
+
+
+def test_oracle_baseline_times_exactly_the_requested_steps():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.cpu_baseline(sub=3, steps=4, warmup=1, one_core=False)
+    assert cb["kind"] == "oracle" and cb["unit"] == "GDoF/s" and cb["cores"] >= 1
+    assert "4 SpMVs" in cb["sample"] and cb["value"] > 0 and cb["ms_per_spmv"] > 0
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The reference arm prints one JSON line with the main arm's metric, unit, direction and workload,
+    and its own e2e and cpu_baseline objects; ranks other than 0 print nothing."""
+    import argparse
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    fake = {"value": 0.02, "unit": "GDoF/s", "cores": 4, "kind": "oracle", "ms_per_spmv": 6.0,
+            "one_core_value": None, "sample": "test"}
+    monkeypatch.setattr(bench, "cpu_baseline", lambda **kw: dict(fake, steps=kw["steps"]))
+    args = argparse.Namespace(gpus=1, steps=7, warmup=3)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GDoF/s"
+    assert line["higher_is_better"] is True and line["config"]["workload"] == bench.WORKLOAD
+    assert line["steps"] == 7 and line["warmup"] == 3 and line["ms_per_step"] == 6.0
+    assert line["cpu_baseline"]["steps"] == 7 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": 0.02, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
