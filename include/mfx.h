@@ -148,6 +148,35 @@ mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n
 mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_dofs, int32_t* constrained,
                            int64_t* cptr, int32_t* cmaster, double* cweight);
 
+/*
+ * Host-only: the hanging-node constraints of an octree mesh at degree k in the
+ * tensor-product form the octree vmult applies for k >= 3 (Sec. 3.3, Fig. 2:
+ * the values on a refined cell's face or edge that lies on a coarser
+ * neighbour's face or edge are that neighbour's polynomial there).  Per cell:
+ *   hface[c]  bit f set if face f (f = 2 d + side, d = 0,1,2 for x,y,z) lies
+ *             on a coarser neighbour's face; bits 6 + 2 f and 7 + 2 f give
+ *             the half (0 lower, 1 upper) of the coarse face it covers along
+ *             its first and second tangential direction (u, v: the lower and
+ *             the higher of the two other axes);
+ *   hedge[c]  bit e set if edge e (e = 4 d + 2 side_v + side_u, along axis d)
+ *             lies on a coarser cell's edge and on no hanging face of the
+ *             cell; bit 12 + e gives the half of the coarse edge it covers;
+ *   hoff[c]   start in hdofs of the cell's coarse DoFs: for each hanging
+ *             face in f order the (k+1)^2 DoFs of the coarse face (u fastest),
+ *             then for each hanging edge in e order the k+1 DoFs of the coarse
+ *             edge; a coarse DoF that is itself constrained is stored as -1.
+ * A constrained node of the cell on a hanging face (the first in f order)
+ * takes the value  sum_mu,mv l_mu((cu + x_bu)/2) l_mv((cv + x_bv)/2) u_mu,mv
+ * of the coarse face values, with x_b its GLL coordinates on the face and
+ * l the GLL Lagrange basis; one on a hanging edge only the 1D analogue.
+ * Caller-allocated host arrays: hface, hedge, hoff n_cells entries, hdofs
+ * *n_hdofs entries (call once with hdofs = NULL to get the count); NULL skips
+ * an array.  Structured meshes: all zero, *n_hdofs = 0.
+ * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k out of 1..8), MFX_EMESH.
+ */
+mfx_status mfx_mesh_hanging_tables(const mfx_mesh* mesh, int32_t degree, uint32_t* hface, uint32_t* hedge,
+                                   int64_t* hoff, int32_t* hdofs, int64_t* n_hdofs);
+
 typedef struct {
   int32_t degree;        /* k, 1..8                                               */
   int32_t n_q_1d;        /* quadrature points per direction; 0 or k+1 (only k+1)  */

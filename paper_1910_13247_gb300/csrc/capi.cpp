@@ -780,6 +780,30 @@ mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_d
   return MFX_OK;
 }
 
+mfx_status mfx_mesh_hanging_tables(const mfx_mesh* mesh, int32_t degree, uint32_t* hface, uint32_t* hedge,
+                                   int64_t* hoff, int32_t* hdofs, int64_t* n_hdofs) {
+  if (!mesh) return set_error(MFX_EINVAL, "null mesh");
+  if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
+  const Mesh& m = mesh->m;
+  if (m.structured) {  // a structured mesh has no hanging nodes
+    const int64_t C = (int64_t)m.nx * m.ny * m.nz;
+    if (hface) std::fill(hface, hface + C, 0u);
+    if (hedge) std::fill(hedge, hedge + C, 0u);
+    if (hoff) std::fill(hoff, hoff + C, (int64_t)0);
+    if (n_hdofs) *n_hdofs = 0;
+    return MFX_OK;
+  }
+  OctreeTables t;
+  mfx_status st = octree_tables(m, degree, &t);
+  if (st != MFX_OK) return st;
+  if (hface) std::copy(t.hface.begin(), t.hface.end(), hface);
+  if (hedge) std::copy(t.hedge.begin(), t.hedge.end(), hedge);
+  if (hoff) std::copy(t.hoff.begin(), t.hoff.end(), hoff);
+  if (hdofs) std::copy(t.hdofs.begin(), t.hdofs.end(), hdofs);
+  if (n_hdofs) *n_hdofs = (int64_t)t.hdofs.size();
+  return MFX_OK;
+}
+
 mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
                           int32_t* cmaster, double* cweight) {
   if (!op) return set_error(MFX_EINVAL, "null operator");

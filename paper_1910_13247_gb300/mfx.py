@@ -132,6 +132,7 @@ def lib():
         "mfx_rhs_function": (S, [_VP, POINT_FN, _VP, _VP, _VP]),
         "mfx_mesh_table_sizes": (S, [_VP, S, _VP, _VP, _VP, _VP]),
         "mfx_mesh_tables": (S, [_VP, S, _VP, _VP, _VP, _VP, _VP]),
+        "mfx_mesh_hanging_tables": (S, [_VP, S, _VP, _VP, _VP, _VP, _VP]),
         "mfx_operator_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), _VP]),
         "mfx_operator_destroy": (None, [_VP]),
         "mfx_operator_release": (S, [_VP, _VP]),
@@ -281,6 +282,20 @@ class Mesh:
                                     cp.ctypes.data_as(_VP), cm.ctypes.data_as(_VP), cw.ctypes.data_as(_VP)))
         return {"n_dofs": n.value, "cell_dofs": cd.reshape(c.value, n3), "constrained": co, "cptr": cp,
                 "cmaster": cm[:nm.value], "cweight": cw[:nm.value]}
+
+    def hanging_tables(self, degree):
+        """Tensor-product form of the hanging-node constraints at degree k, computed on the host: per cell
+        the hanging-face word, the hanging-edge word and the offset of its coarse DoFs in `hdofs`."""
+        c, nh = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().mfx_mesh_table_sizes(self.handle, degree, ctypes.byref(c), None, None, None))
+        check(lib().mfx_mesh_hanging_tables(self.handle, degree, None, None, None, None, ctypes.byref(nh)))
+        hf = np.zeros(c.value, dtype=np.uint32)
+        he = np.zeros(c.value, dtype=np.uint32)
+        ho = np.zeros(c.value, dtype=np.int64)
+        hd = np.zeros(max(1, nh.value), dtype=np.int32)
+        check(lib().mfx_mesh_hanging_tables(self.handle, degree, hf.ctypes.data_as(_VP), he.ctypes.data_as(_VP),
+                                            ho.ctypes.data_as(_VP), hd.ctypes.data_as(_VP), ctypes.byref(nh)))
+        return {"hface": hf, "hedge": he, "hoff": ho, "hdofs": hd[:nh.value]}
 
 
 class Operator:
