@@ -421,6 +421,33 @@ def test_dirichlet_face_masks(mfx, faces):
     assert np.abs(xs.cpu().numpy() - fem.distribute(oo, xo)).max() < 1e-14
 
 
+@pytest.mark.parametrize("faces", [0, 0b000011, 0b110100])
+@pytest.mark.parametrize("k", [3, 4])
+def test_octree_tensor_product_with_dirichlet_face_masks(mfx, faces, k):
+    """Octrees refined twice in a ball that reaches the x = 0 and y = 0 faces, at the degrees whose vmult
+    applies the hanging constraints in tensor-product form, with Dirichlet on all, some or none of the
+    faces: hanging nodes on natural faces keep their boundary masters, those on Dirichlet faces lose
+    them. FP64 / FP32 vmult, diagonal and distribute against the oracle built with the same mask."""
+    leaves = synthetic.octree_leaves(3, 2, np.array([0.15, 0.2, 0.5]), 0.3)
+    ov = synthetic.deformed_vertices(3, 3, 3)
+    oo = omesh.octree_mesh(3, 3, 3, k, leaves, ov, dirichlet=faces)
+    Ko = fem.assemble(oo, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    xo = synthetic.uniform_vector(oo.n_dofs, 60 + k)
+    ref = Ko @ xo
+    op = mfx.Operator(mfx.Mesh.octree(3, 3, 3, leaves, ov, dirichlet=faces), k, mfx.COEF_TRIG, (1.0, 0.5))
+    assert op.info()["n_hanging"] > 0 and op.info()["n_constrained"] == len(oo.constrained)
+    e2, einf = rel_err(run_vmult(op, xo, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    assert rel_err(run_vmult(op, xo, torch.float32), ref)[0] < 1e-5
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = fem.diagonal(Ko)
+    assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
+    xs = torch.tensor(xo, device=DEV)
+    op.distribute(xs)
+    assert np.abs(xs.cpu().numpy() - fem.distribute(oo, xo)).max() < 1e-14
+
+
 @pytest.mark.parametrize("count", [1, 2, 5])
 def test_vmult_on_host_vectors(mfx, count):
     """mfx_vmult_host: the pipelined host-buffer path gives, for every vector, the oracle's product
