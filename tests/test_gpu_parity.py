@@ -421,6 +421,29 @@ def test_dirichlet_face_masks(mfx, faces):
     assert np.abs(xs.cpu().numpy() - fem.distribute(oo, xo)).max() < 1e-14
 
 
+@pytest.mark.parametrize("faces", [0, 0b110100])
+@pytest.mark.parametrize("k", [6, 7])
+def test_high_degree_structured_dirichlet_face_masks(mfx, faces, k):
+    """From k = 6 on, the FP32 vmult of a structured mesh runs on the per-cell kernels with an index table
+    of the lattice built on the device (Dirichlet points as constraint rows): with natural faces the
+    boundary points there are free DoFs. FP64 / FP32 vmult and diagonal against the oracle."""
+    nx, ny, nz = 3, 2, 2
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts, dirichlet=faces)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, 70 + k)
+    ref = K @ x
+    op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz, verts, dirichlet=faces), k, mfx.COEF_TRIG, (1.0, 0.5))
+    assert op.info()["n_constrained"] == len(om.constrained)
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    assert rel_err(run_vmult(op, x, torch.float32), ref)[0] < 1e-5
+    d = torch.empty(op.n_dofs, dtype=torch.float64, device=DEV)
+    op.diagonal(d)
+    dref = fem.diagonal(K)
+    assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
+
+
 @pytest.mark.parametrize("faces", [0, 0b000011, 0b110100])
 @pytest.mark.parametrize("k", [3, 4])
 def test_octree_tensor_product_with_dirichlet_face_masks(mfx, faces, k):
