@@ -285,6 +285,18 @@ mfx_status mfx_vmult_host(const mfx_op* op, mfx_prec prec, int32_t count, const 
  */
 mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream);
 
+/*
+ * Self-test of the failure detection above, without a fault: launches one
+ * CTA that waits on a shared-memory mbarrier at which nothing ever arrives,
+ * through the same bounded wait (about 2^31 SM clocks, about one second)
+ * that the TMA kernels use.  The wait runs out, the kernel sets the
+ * operator's error word and returns; the next mfx_device_check on the
+ * stream reports MFX_ETIMEOUT (and clears the word), and the operator stays
+ * usable.  Asynchronous on stream.  Errors: MFX_EINVAL (null operator),
+ * MFX_ECUDA.
+ */
+mfx_status mfx_selftest_bounded_wait(const mfx_op* op, mfx_stream stream);
+
 /* diag = diagonal of K (1 on constrained rows), device, n_dofs entries. */
 mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream);
 

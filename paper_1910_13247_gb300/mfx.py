@@ -143,6 +143,7 @@ def lib():
         "mfx_vmult_host": (S, [_VP, S, S, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
         "mfx_diagonal": (S, [_VP, S, _VP, _VP]),
         "mfx_device_check": (S, [_VP, _VP]),
+        "mfx_selftest_bounded_wait": (S, [_VP, _VP]),
         "mfx_quadrature_points": (S, [_VP, _VP, _VP]),
         "mfx_rhs": (S, [_VP, _VP, _VP, _VP]),
         "mfx_distribute": (S, [_VP, _VP, _VP]),
@@ -391,6 +392,11 @@ class Operator:
     def device_check(self):
         """Synchronise and raise if a bounded device wait of this operator ran out."""
         check(lib().mfx_device_check(self.handle, _stream()))
+
+    def selftest_bounded_wait(self):
+        """Launch a kernel whose bounded wait runs out (about one second); the next device_check raises
+        MfxError with code ETIMEOUT."""
+        check(lib().mfx_selftest_bounded_wait(self.handle, _stream()))
 
     def diagonal(self, out):
         assert out.numel() == self.n_dofs

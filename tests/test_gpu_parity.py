@@ -314,6 +314,27 @@ def test_chebyshev_pcg_and_mixed_precision_solve(mfx, mixed):
     assert abs(st["lambda_max"] - lam) < 1e-3 * lam
 
 
+def test_bounded_wait_runs_out_and_is_reported(mfx):
+    """Failure detection without a fault: a kernel waits on an mbarrier at which nothing arrives, through
+    the bounded wait of the TMA kernels; the wait runs out after about a second, the operator's error word
+    is set, device_check raises ETIMEOUT once (the word is cleared), and the operator keeps working."""
+    import time
+    op, om, par = make_pair(mfx, 3, 3, 3, 2)
+    op.device_check()
+    t0 = time.perf_counter()
+    op.selftest_bounded_wait()
+    with pytest.raises(mfx.MfxError) as e:
+        op.device_check()
+    dt = time.perf_counter() - t0
+    assert e.value.code == mfx.ETIMEOUT
+    assert 0.2 < dt < 30, dt
+    op.device_check()
+    K = fem.assemble(om, 3, fem.COEF_TRIG, par)
+    x = synthetic.uniform_vector(om.n_dofs, 9)
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), K @ x)
+    assert e2 < 1e-12 and einf < 1e-12
+
+
 def test_solver_statuses(mfx):
     op, om, par = make_pair(mfx, 4, 4, 4, 2)
     b = synthetic.uniform_vector(om.n_dofs, 9)
