@@ -297,6 +297,49 @@ mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream);
  */
 mfx_status mfx_selftest_bounded_wait(const mfx_op* op, mfx_stream stream);
 
+/*
+ * Checked mode (in place of a memory checker).  Index tables as the
+ * per-cell kernels read them, all device arrays:
+ *   cell_dofs  n_cells x nodes_1d^3 codes: a DoF in [0, n_dofs), or -1 - r
+ *              for constraint row r in [0, n_rows);
+ *   cptr       n_rows + 1 row pointers into cmaster (0 first, non-
+ *              decreasing, n_masters last); NULL when n_rows = 0;
+ *   cmaster    n_masters master DoFs in [0, n_dofs);
+ *   hface, hedge, hoff, hdofs  the tensor-product hanging tables of
+ *              mfx_mesh_hanging_tables (n_cells words and offsets, n_hdofs
+ *              codes in [-1, n_dofs)); hface = NULL skips them;
+ *   cell_list[l]  n_list[l] cell indices in [0, n_cells) (NULL when 0).
+ * mfx_validate_tables checks every entry on the device, reading each array
+ * only below its stated size, and returns MFX_EMESH with *n_bad = the number
+ * of entries out of range or inconsistent (a hanging word with undefined
+ * bits, or whose slots do not end where the next cell's start), else MFX_OK
+ * and *n_bad = 0 (n_bad may be NULL).  Synchronises the stream.
+ * mfx_operator_validate applies it to an operator's own device tables
+ * (octree meshes, and structured meshes whose FP32 vmult uses a lattice
+ * table; nothing to check otherwise).  With the environment variable
+ * MFX_CHECKED set (not "0"), mfx_operator_create runs it before returning
+ * and fails with its status.
+ * Errors: MFX_EINVAL (null descriptor or operator, negative size, a table
+ * with entries but a null pointer), MFX_EMESH, MFX_ECUDA.
+ */
+typedef struct {
+  int64_t n_cells;
+  int32_t nodes_1d;      /* k + 1 */
+  int32_t reserved;
+  int64_t n_dofs, n_rows, n_masters, n_hdofs;
+  const int32_t* cell_dofs;
+  const int64_t* cptr;
+  const int32_t* cmaster;
+  const uint32_t* hface;
+  const uint32_t* hedge;
+  const int64_t* hoff;
+  const int32_t* hdofs;
+  const int32_t* cell_list[2];
+  int64_t n_list[2];
+} mfx_index_tables;
+mfx_status mfx_validate_tables(const mfx_index_tables* tables, int64_t* n_bad, mfx_stream stream);
+mfx_status mfx_operator_validate(const mfx_op* op, int64_t* n_bad, mfx_stream stream);
+
 /* diag = diagonal of K (1 on constrained rows), device, n_dofs entries. */
 mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream);
 

@@ -664,6 +664,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   // the structured FP64 vmult works in double-float arithmetic on a pre-split metric
   if (op->structured) MFX_TRY(launch_metric_to_pairs(op, (int64_t)metric_entries, s));
   MFX_CUDA_OP(cudaStreamSynchronize(s));
+  if (checked_mode()) MFX_TRY(validate_operator(op, nullptr, s));
   *out = op;
   return MFX_OK;
 }

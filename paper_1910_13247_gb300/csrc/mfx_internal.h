@@ -174,6 +174,12 @@ mfx_status launch_dg_rhs(const mfx_op* op, const double* fq, double* b, cudaStre
 
 int device_sm_count();
 
+// Checked mode (validate.cu): device-side validation of an operator's index tables; on when the
+// environment variable MFX_CHECKED is set to anything but "0" (read at every operator creation).
+mfx_status validate_tables(const mfx_index_tables* t, int64_t* n_bad, cudaStream_t s);
+mfx_status validate_operator(const mfx_op* op, int64_t* n_bad, cudaStream_t s);
+bool checked_mode();
+
 // vmult (vmult_k*.cu): one launcher per degree.
 mfx_status launch_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, cudaStream_t s,
                         const int32_t* skip = nullptr);

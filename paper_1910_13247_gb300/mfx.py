@@ -104,6 +104,15 @@ class ServerStats(ctypes.Structure):
                 ("max_concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32), ("now", ctypes.c_double)]
 
 
+class IndexTables(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("nodes_1d", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_dofs", ctypes.c_int64), ("n_rows", ctypes.c_int64), ("n_masters", ctypes.c_int64),
+                ("n_hdofs", ctypes.c_int64), ("cell_dofs", ctypes.c_void_p), ("cptr", ctypes.c_void_p),
+                ("cmaster", ctypes.c_void_p), ("hface", ctypes.c_void_p), ("hedge", ctypes.c_void_p),
+                ("hoff", ctypes.c_void_p), ("hdofs", ctypes.c_void_p), ("cell_list", ctypes.c_void_p * 2),
+                ("n_list", ctypes.c_int64 * 2)]
+
+
 ADMIT_FIFO, ADMIT_SMALLEST_FIRST = 0, 1
 REQ_QUEUED, REQ_SETUP, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(6)
 
@@ -144,6 +153,8 @@ def lib():
         "mfx_diagonal": (S, [_VP, S, _VP, _VP]),
         "mfx_device_check": (S, [_VP, _VP]),
         "mfx_selftest_bounded_wait": (S, [_VP, _VP]),
+        "mfx_validate_tables": (S, [_VP, _VP, _VP]),
+        "mfx_operator_validate": (S, [_VP, _VP, _VP]),
         "mfx_quadrature_points": (S, [_VP, _VP, _VP]),
         "mfx_rhs": (S, [_VP, _VP, _VP, _VP]),
         "mfx_distribute": (S, [_VP, _VP, _VP]),
@@ -393,6 +404,15 @@ class Operator:
         """Synchronise and raise if a bounded device wait of this operator ran out."""
         check(lib().mfx_device_check(self.handle, _stream()))
 
+    def validate(self):
+        """Checked mode: count, on the device, the entries of this operator's index tables that are out of
+        range or inconsistent (mfx_operator_validate); 0 for sound tables."""
+        nb = ctypes.c_int64()
+        code = lib().mfx_operator_validate(self.handle, ctypes.byref(nb), _stream())
+        if code != EMESH:
+            check(code)
+        return nb.value
+
     def selftest_bounded_wait(self):
         """Launch a kernel whose bounded wait runs out (about one second); the next device_check raises
         MfxError with code ETIMEOUT."""
@@ -446,6 +466,26 @@ class Operator:
         st = SolveStats()
         check(lib().mfx_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(st), _stream()))
         return st.as_dict()
+
+
+def validate_tables(n_cells, nodes_1d, n_dofs, cell_dofs, n_rows=0, cptr=None, cmaster=None, hface=None,
+                    hedge=None, hoff=None, hdofs=None, cell_lists=(), stream=None):
+    """Checked mode on caller-supplied device tables (torch tensors; mfx_validate_tables): returns the number
+    of entries out of range or inconsistent."""
+    t = IndexTables()
+    t.n_cells, t.nodes_1d, t.n_dofs, t.n_rows = n_cells, nodes_1d, n_dofs, n_rows
+    t.n_masters = cmaster.numel() if cmaster is not None else 0
+    t.n_hdofs = hdofs.numel() if hdofs is not None else 0
+    for name, v in (("cell_dofs", cell_dofs), ("cptr", cptr), ("cmaster", cmaster), ("hface", hface),
+                    ("hedge", hedge), ("hoff", hoff), ("hdofs", hdofs)):
+        setattr(t, name, v.data_ptr() if v is not None else None)
+    for i, lst in enumerate(cell_lists):
+        t.cell_list[i], t.n_list[i] = lst.data_ptr(), lst.numel()
+    nb = ctypes.c_int64()
+    code = lib().mfx_validate_tables(ctypes.byref(t), ctypes.byref(nb), _stream(stream))
+    if code != EMESH:
+        check(code)
+    return nb.value
 
 
 def make_params(tol=1e-10, max_it=100000, precond=PRECOND_JACOBI, cheb_degree=5, mixed=False, inner_tol=1e-4,
