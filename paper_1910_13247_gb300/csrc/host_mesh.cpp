@@ -155,30 +155,28 @@ struct NodeKey {
 
 inline bool irrational(uint32_t dk) { return (dk >> 31) != 0; }
 
-// Flat open-addressing table NodeKey -> DoF (linear probing, power-of-two capacity).
+// Flat open-addressing table NodeKey -> DoF (linear probing, power-of-two capacity); key and DoF share
+// one 16-byte slot, so a probe touches one cache line.
 class NodeTable {
  public:
   explicit NodeTable(size_t expected) {
     size_t cap = 16;
     while (cap < 2 * expected + 16) cap <<= 1;
-    keys_.assign(cap, NodeKey{{~0u, ~0u, ~0u}});
-    vals_.assign(cap, -1);
+    slots_.assign(cap, Slot{{~0u, ~0u, ~0u}, -1});
     mask_ = cap - 1;
   }
   size_t slot(const NodeKey& k) const { return hash(k) & mask_; }
-  void prefetch(size_t h) const {
-    __builtin_prefetch(&keys_[h]);
-    __builtin_prefetch(&vals_[h]);
-  }
+  void prefetch(size_t h) const { __builtin_prefetch(&slots_[h]); }
   // DoF of the key (whose home slot is h), inserting `next` if absent; returns (dof, inserted).
   std::pair<int32_t, bool> find_or_insert(const NodeKey& k, size_t h, int32_t next) {
     for (;;) {
-      if (vals_[h] < 0) {
-        keys_[h] = k;
-        vals_[h] = next;
+      Slot& s = slots_[h];
+      if (s.dof < 0) {
+        s.key = k;
+        s.dof = next;
         return {next, true};
       }
-      if (keys_[h] == k) return {vals_[h], false};
+      if (s.key == k) return {s.dof, false};
       h = (h + 1) & mask_;
     }
   }
@@ -193,8 +191,11 @@ class NodeTable {
     x ^= x >> 31;
     return (size_t)x;
   }
-  std::vector<NodeKey> keys_;
-  std::vector<int32_t> vals_;
+  struct Slot {
+    NodeKey key;
+    int32_t dof;
+  };
+  std::vector<Slot> slots_;
   size_t mask_ = 0;
 };
 
