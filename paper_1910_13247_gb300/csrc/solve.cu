@@ -27,6 +27,7 @@
 #include <chrono>
 #include <cmath>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "mfx_internal.h"
@@ -355,7 +356,8 @@ static void pinned_status_put(SolveState* p) {
 // is made or freed), a pinned status block and a stream of its own.
 static mfx_status ensure_workspace(mfx_op* op) {
   if (op->d_work) return MFX_OK;
-  auto* ws = new SolveWorkspace();
+  auto* ws = new (std::nothrow) SolveWorkspace();
+  if (!ws) return set_error(MFX_ENOMEM, "solver workspace: host allocation failed");
   const int64_t n = op->n_dofs;
   const size_t n64 = (size_t)n * sizeof(double), n32 = (size_t)n * sizeof(float);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -985,7 +987,8 @@ extern "C" {
 mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
   if (!out || max_slots < 1 || max_slots > 4096) return set_error(MFX_EINVAL, "mfx_batch_create: bad arguments");
   *out = nullptr;
-  auto* bt = new mfx_batch();
+  auto* bt = new (std::nothrow) mfx_batch();
+  if (!bt) return set_error(MFX_ENOMEM, "mfx_batch_create: host allocation failed");
   bt->slots.resize(max_slots);
   bt->chunk = chunk > 0 ? chunk : 8;
   cudaError_t e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
