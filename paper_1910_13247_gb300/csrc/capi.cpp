@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <array>
@@ -18,6 +19,19 @@ static thread_local std::string g_last_error;
 mfx_status set_error(mfx_status code, const std::string& msg) {
   g_last_error = msg;
   return code;
+}
+
+// Called inside a catch handler at the C-ABI boundary: no C++ exception crosses it.
+mfx_status host_exception() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return set_error(MFX_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(MFX_EINVAL, std::string("host error: ") + e.what());
+  } catch (...) {
+    return set_error(MFX_EINVAL, "host error");
+  }
 }
 
 mfx_status cuda_error(cudaError_t e, const char* where) {
@@ -313,7 +327,7 @@ extern "C" {
 const char* mfx_last_error(void) { return g_last_error.c_str(); }
 const char* mfx_version(void) { return "mfx 0.1 (sm_103a)"; }
 
-mfx_status mfx_mesh_create_structured(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz, const double* vertices) {
+mfx_status mfx_mesh_create_structured(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz, const double* vertices) try {
   if (!out) return set_error(MFX_EINVAL, "null output pointer");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return set_error(MFX_EINVAL, "mesh sizes must be positive");
@@ -339,10 +353,12 @@ mfx_status mfx_mesh_create_structured(mfx_mesh** out, int32_t nx, int32_t ny, in
       }
   *out = m;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_t nz, const double* coarse_vertices,
-                                  const int32_t* leaves, int64_t n_leaves) {
+                                  const int32_t* leaves, int64_t n_leaves) try {
   if (!out) return set_error(MFX_EINVAL, "null output pointer");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || !leaves || n_leaves < 1) return set_error(MFX_EINVAL, "bad octree arguments");
@@ -358,6 +374,8 @@ mfx_status mfx_mesh_create_octree(mfx_mesh** out, int32_t nx, int32_t ny, int32_
   }
   *out = m;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void mfx_mesh_destroy(mfx_mesh* mesh) { delete mesh; }
@@ -441,7 +459,7 @@ static mfx_status create_sipg(mfx_op** out, const Mesh& m, const mfx_op_desc* de
   return MFX_OK;
 }
 
-mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) {
+mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) try {
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "null argument");
   *out = nullptr;
   const int k = desc->degree;
@@ -667,6 +685,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (checked_mode()) MFX_TRY(validate_operator(op, nullptr, s));
   *out = op;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void mfx_operator_destroy(mfx_op* op) { destroy_op(op); }
@@ -738,7 +758,7 @@ static void copy_tables(const OctreeTables& tb, int32_t* cell_dofs, int32_t* con
 }
 
 mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n_cells, int64_t* n_dofs,
-                                int64_t* n_constrained, int64_t* n_masters) {
+                                int64_t* n_constrained, int64_t* n_masters) try {
   if (!mesh) return set_error(MFX_EINVAL, "null mesh");
   if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
   const Mesh& m = mesh->m;
@@ -763,10 +783,12 @@ mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n
   if (n_constrained) *n_constrained = NC;
   if (n_masters) *n_masters = NM;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_dofs, int32_t* constrained,
-                           int64_t* cptr, int32_t* cmaster, double* cweight) {
+                           int64_t* cptr, int32_t* cmaster, double* cweight) try {
   if (!mesh) return set_error(MFX_EINVAL, "null mesh");
   if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
   const Mesh& m = mesh->m;
@@ -779,10 +801,12 @@ mfx_status mfx_mesh_tables(const mfx_mesh* mesh, int32_t degree, int32_t* cell_d
   if (st != MFX_OK) return st;
   copy_tables(t, cell_dofs, constrained, cptr, cmaster, cweight);
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_mesh_hanging_tables(const mfx_mesh* mesh, int32_t degree, uint32_t* hface, uint32_t* hedge,
-                                   int64_t* hoff, int32_t* hdofs, int64_t* n_hdofs) {
+                                   int64_t* hoff, int32_t* hdofs, int64_t* n_hdofs) try {
   if (!mesh) return set_error(MFX_EINVAL, "null mesh");
   if (degree < 1 || degree > kMaxDegree) return set_error(MFX_EUNSUPPORTED, "degree must be in 1..8");
   const Mesh& m = mesh->m;
@@ -803,6 +827,8 @@ mfx_status mfx_mesh_hanging_tables(const mfx_mesh* mesh, int32_t degree, uint32_
   if (hdofs) std::copy(t.hdofs.begin(), t.hdofs.end(), hdofs);
   if (n_hdofs) *n_hdofs = (int64_t)t.hdofs.size();
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
@@ -935,7 +961,7 @@ mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double
   return st;
 }
 
-mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user) {
+mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user) try {
   if (!mesh || !phi) return set_error(MFX_EINVAL, "mfx_mesh_transform: null argument");
   std::vector<double>& v = mesh->m.vertices;
   for (size_t i = 0; i + 2 < v.size(); i += 3) {
@@ -947,6 +973,8 @@ mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user) {
     v[i + 2] = out[2];
   }
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream) {

@@ -18,6 +18,7 @@ constexpr int kMaxN = kMaxDegree + 1;
 // ---------------------------------------------------------------- errors
 mfx_status set_error(mfx_status code, const std::string& msg);
 mfx_status cuda_error(cudaError_t e, const char* where);
+mfx_status host_exception();  // inside a catch handler: the current exception as a status code
 #define MFX_CUDA_TRY(call)                                   \
   do {                                                       \
     cudaError_t e_ = (call);                                 \

@@ -480,7 +480,7 @@ void mfx_mg_params_default(mfx_mg_params* p) {
 }
 
 mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* desc, const mfx_mg_params* params,
-                         mfx_stream stream) {
+                         mfx_stream stream) try {
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "mfx_mg_create: null argument");
   *out = nullptr;
   const Mesh& fm = mesh->m;
@@ -672,6 +672,8 @@ mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* 
   MFX_CUDA_TRY(cudaStreamSynchronize(mg->stream));
   *out = mg;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void mfx_mg_destroy(mfx_mg* mg) { mg_free(mg); }

@@ -294,11 +294,12 @@ void scheduler_main(mfx_server* s) {
 
 }  // namespace
 
+using mfx::host_exception;
 using mfx::set_error;
 
 extern "C" {
 
-mfx_status mfx_server_create(mfx_server** out, const mfx_server_config* config) {
+mfx_status mfx_server_create(mfx_server** out, const mfx_server_config* config) try {
   if (!out || !config) return set_error(MFX_EINVAL, "null argument");
   *out = nullptr;
   mfx_server_config c = *config;
@@ -326,6 +327,8 @@ mfx_status mfx_server_create(mfx_server** out, const mfx_server_config* config) 
   s->scheduler = std::thread(scheduler_main, s);
   *out = s;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void mfx_server_destroy(mfx_server* s) {
@@ -348,7 +351,7 @@ void mfx_server_destroy(mfx_server* s) {
   delete s;
 }
 
-mfx_status mfx_server_submit(mfx_server* s, const mfx_request* request, int64_t* ticket) {
+mfx_status mfx_server_submit(mfx_server* s, const mfx_request* request, int64_t* ticket) try {
   if (!s || !request || !ticket) return set_error(MFX_EINVAL, "null argument");
   auto q = std::make_shared<Req>();
   q->r = *request;
@@ -382,6 +385,8 @@ mfx_status mfx_server_submit(mfx_server* s, const mfx_request* request, int64_t*
   }
   s->cv_sched.notify_one();
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_server_poll(mfx_server* s, int64_t ticket, mfx_request_info* info) {

@@ -984,7 +984,7 @@ static mfx_status rebuild_parent(mfx_batch* bt) {
 
 extern "C" {
 
-mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
+mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) try {
   if (!out || max_slots < 1 || max_slots > 4096) return set_error(MFX_EINVAL, "mfx_batch_create: bad arguments");
   *out = nullptr;
   auto* bt = new (std::nothrow) mfx_batch();
@@ -1003,6 +1003,8 @@ mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk) {
   }
   *out = bt;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void mfx_batch_destroy(mfx_batch* bt) {
@@ -1022,7 +1024,7 @@ void mfx_batch_destroy(mfx_batch* bt) {
 }
 
 mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, double* x,
-                         const mfx_solve_params* params, int32_t* slot_out) {
+                         const mfx_solve_params* params, int32_t* slot_out) try {
   mfx_op* op = const_cast<mfx_op*>(op_c);
   if (!bt || !op || !b || !x || !slot_out) return set_error(MFX_EINVAL, "mfx_batch_add: null argument");
   mfx_solve_params p;
@@ -1087,6 +1089,8 @@ mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, dou
   }
   *slot_out = free_slot;
   return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {

@@ -134,3 +134,12 @@ def test_tables_with_dirichlet_face_masks_bit_exact(faces):
         assert np.array_equal(T["cweight"], om.cweight)
     with pytest.raises(mfx.MfxError):
         mfx.Mesh.structured_box(2, 2, 2, dirichlet=64)
+
+
+def test_host_exceptions_become_status_codes():
+    """A host-side failure inside an entry point (here a lattice too large to allocate) is returned as a
+    status code with a message; no C++ exception crosses the C-ABI and the library stays usable."""
+    with pytest.raises(mfx.MfxError) as e:
+        mfx.Mesh.structured_box(1 << 20, 1 << 20, 1 << 20)
+    assert e.value.code in (mfx.EINVAL, mfx.ENOMEM)
+    assert mfx.Mesh.structured_box(2, 2, 2).tables(1)["n_dofs"] == 27
