@@ -1,7 +1,8 @@
 // Double-float arithmetic: a value as an unevaluated sum of two floats (hi + lo, about 48 significant
-// bits).  Products with a constant are formed exactly by FMA-based error-free transformations, sums by
-// two-sum; all operations use the round-to-nearest intrinsics, which the compiler never fuses, so the
-// transformations stay exact.  Used by the FP64 operators, because GB300 runs FP64 FMAs at 1/62 of
+// bits).  Products with a constant are formed exactly by FMA-based error-free transformations (the
+// product error of a*b is fma(a, b, -a*b), as in Ogita, Rump and Oishi's accurate dot product, 2005),
+// sums by Knuth's two-sum; all operations use the round-to-nearest intrinsics, which the compiler
+// never fuses, so the transformations stay exact.  Used by the FP64 operators, because GB300 runs FP64 FMAs at 1/62 of
 // the FP32 rate.
 #pragma once
 

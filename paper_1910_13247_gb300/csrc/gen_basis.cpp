@@ -1,5 +1,6 @@
 // Build-time generator: writes the 1D matrices of every degree as C++ constants (the vmult
-// kernels' S and D, the SIPG double-float kernel's K1, M1 and end derivatives)
+// kernels' S and D: the 1D shape functions and derivatives at the Gauss points on which the sum
+// factorisation of Sec. 3.1 works; the SIPG double-float kernel's K1, M1 and end derivatives)
 // (hexadecimal floating-point literals, exact FP64 values) for the vmult kernels,
 // using the library's own quadrature and Lagrange routines (host_rules.cpp).
 #include <cstdio>

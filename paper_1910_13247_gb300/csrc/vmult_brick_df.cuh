@@ -1,4 +1,6 @@
-// FP64 structured vmult in double-float arithmetic.
+// FP64 structured vmult in double-float arithmetic: the matrix-free operator application of Sec. 3.6
+// with the sum factorisation of Sec. 3.1 (values and gradients at the Gauss points by 1D contractions,
+// the metric of the Q1 map per quadrature point, Sec. 3.4), on a structured box.
 //
 // GB300 runs FP64 FMAs at 1/62 of the FP32 rate, so the FP64 operator keeps its vectors and the
 // metric in FP64 in HBM but does the arithmetic on pairs of floats (hi + lo, about 48 significant

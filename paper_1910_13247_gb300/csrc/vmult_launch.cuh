@@ -1,4 +1,6 @@
-// Host launcher of the vmult kernels for one degree (included by vmult_k*.cu).
+// Host launcher of the vmult kernels for one degree (included by vmult_k*.cu): picks the kernel for the
+// mesh type, precision and degree (structured row batches, per-cell index tables, tensor-product
+// hanging constraints) for the cell loop of the matrix-free operator (Sec. 3.6).
 #pragma once
 
 #include <algorithm>

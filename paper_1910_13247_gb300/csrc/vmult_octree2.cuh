@@ -1,4 +1,6 @@
-// FP32 vmult on meshes with index tables (octrees, hanging nodes), pairs of cells per thread.
+// FP32 vmult on meshes with index tables (octrees, hanging nodes), pairs of cells per thread: the
+// operator of Sec. 3.6 on locally refined meshes, with the hanging-node constraints of Sec. 3.1 and
+// Fig. 2 resolved in the gather and its transpose in the scatter (Sec. 3.3).
 //
 // The compute structure is that of brick_vmult_tma2_kernel: a CTA takes batches of CB consecutive
 // cells (the Morton order keeps them close in space), every thread owns the same 1D line of two
