@@ -35,7 +35,10 @@ def _tables(k, nq):
 
 
 def dg_operator(nx, ny, nz, k, lengths=(1.0, 1.0, 1.0), dirichlet=0x3F, eta=1.0, coef=1.0):
-    """Sparse SIPG matrix of the uniform box [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz cells."""
+    """Sparse SIPG matrix of the uniform box [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz cells.
+
+    The symmetric interior penalty discretisation of the multigrid benchmark of Sec. 6.1.
+    """
     n, n3 = k + 1, (k + 1) ** 3
     h = np.array([lengths[0] / nx, lengths[1] / ny, lengths[2] / nz])
     x, xq, wq, V, Dv, e, de = _tables(k, n)
@@ -132,7 +135,8 @@ def dg_operator(nx, ny, nz, k, lengths=(1.0, 1.0, 1.0), dirichlet=0x3F, eta=1.0,
 
 def dg_mesh(nx, ny, nz, k, lengths=(1.0, 1.0, 1.0)):
     """The DG space as an oracle Mesh (cell-major DoFs, no constraints), for the L2 error and the
-    right-hand side routines."""
+    right-hand side routines.
+    The discontinuous space of Sec. 6.1."""
     n3 = (k + 1) ** 3
     C = nx * ny * nz
     cv = np.zeros((C, 8, 3))
@@ -152,7 +156,8 @@ def dg_mesh(nx, ny, nz, k, lengths=(1.0, 1.0, 1.0)):
 
 def injection(cg_mesh, k):
     """Matrix of the continuous space in the discontinuous one on the same structured mesh: DG DoF
-    (c, i) takes the CG value at the same node (0 for Dirichlet CG DoFs)."""
+    (c, i) takes the CG value at the same node (0 for Dirichlet CG DoFs).
+    The switch from the discontinuous to the continuous space in the hierarchy of Sec. 6.1."""
     C, n3 = cg_mesh.cell_dofs.shape
     keep = np.ones(cg_mesh.n_dofs)
     keep[cg_mesh.constrained] = 0.0

@@ -25,6 +25,7 @@ COEF_TRIG = 1
 
 
 def element_matrices(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), rows=None, cells=None):
+    """Element stiffness matrices of the weak form of Eq. (1), with the coefficient a(x), by the full-quadrature cell loop of the step-4 listing (Sec. 2.4)."""
     k = mesh.k
     n = k + 1
     nodes = gauss_lobatto(k)
@@ -46,6 +47,7 @@ def element_matrices(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), row
 
 
 def element_mass(mesh, nq):
+    """Element mass matrices by the same full-quadrature cell loop (Sec. 2.4)."""
     k = mesh.k
     n = k + 1
     nodes = gauss_lobatto(k)
@@ -58,7 +60,10 @@ def element_mass(mesh, nq):
 
 
 def quadrature_points(mesh, nq):
-    """Physical quadrature points (C, nq^3, 3) and JxW (C, nq^3)."""
+    """Physical quadrature points (C, nq^3, 3) and JxW (C, nq^3).
+
+    The trilinear (Q1) map of each cell (Sec. 3.4).
+    """
     xq, wq = gauss_legendre(nq)
     cv = nat.f64(mesh.cell_vertices)
     X = np.zeros((mesh.n_cells, nq ** 3, 3))
@@ -68,7 +73,10 @@ def quadrature_points(mesh, nq):
 
 
 def global_from_elements(mesh, Ae):
-    """A_full = sum_e P_e^T A^e P_e as CSR; duplicates summed in (cell, i, j) order."""
+    """A_full = sum_e P_e^T A^e P_e as CSR; duplicates summed in (cell, i, j) order.
+
+    Global assembly of the element matrices (Sec. 2.4): the matrix that the matrix-free operator of Sec. 3.6 never forms.
+    """
     C, nd, _ = Ae.shape
     rows = np.repeat(mesh.cell_dofs, nd, axis=1).ravel()
     cols = np.tile(mesh.cell_dofs, (1, nd)).ravel()
@@ -76,7 +84,10 @@ def global_from_elements(mesh, Ae):
 
 
 def constraint_matrix(mesh):
-    """C with x_full = C x: identity on free DoFs, masters/weights on hanging, 0 on Dirichlet."""
+    """C with x_full = C x: identity on free DoFs, masters/weights on hanging, 0 on Dirichlet.
+
+    The hanging-node constraints of Sec. 3.1 (Fig. 2) and the Dirichlet constraints, as applied in Sec. 3.3.
+    """
     N = mesh.n_dofs
     is_c = np.zeros(N, dtype=bool)
     is_c[mesh.constrained] = True
@@ -93,7 +104,10 @@ def constraint_matrix(mesh):
 
 
 def condense(mesh, A_full):
-    """K = C^T A_full C (free rows/cols) + identity on constrained DoFs."""
+    """K = C^T A_full C (free rows/cols) + identity on constrained DoFs.
+
+    Condensation of the constraints (Sec. 3.3).
+    """
     Cm, is_c = constraint_matrix(mesh)
     K = (Cm.T @ A_full @ Cm).tocsr()
     K = K + sp.diags(is_c.astype(np.float64))
@@ -103,11 +117,15 @@ def condense(mesh, A_full):
 
 
 def assemble(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0)):
+    """The condensed operator K whose action the matrix-free vmult computes (Sec. 3.6), assembled by the step-4 loop (Sec. 2.4)."""
     return condense(mesh, global_from_elements(mesh, element_matrices(mesh, nq, coef_kind, coef_par)))
 
 
 def spmv(K, x):
-    """y = K x with the oracle's plain CSR row loop."""
+    """y = K x with the oracle's plain CSR row loop.
+
+    The action K x that the matrix-free operator of Sec. 3.6 reproduces.
+    """
     K = K.tocsr()
     rp = np.ascontiguousarray(K.indptr, dtype=np.int64)
     ci = np.ascontiguousarray(K.indices, dtype=np.int64)
@@ -119,7 +137,10 @@ def spmv(K, x):
 
 
 class CSR:
-    """Pre-converted CSR arrays for repeated oracle SpMVs."""
+    """Pre-converted CSR arrays for repeated oracle SpMVs.
+
+    Used for the action K x that the matrix-free operator of Sec. 3.6 reproduces.
+    """
 
     def __init__(self, K):
         K = K.tocsr()
@@ -141,6 +162,7 @@ def sampled_rows(mesh, nq, dofs, x, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0)
 
     Constrained entries of x are replaced by 0 (Dirichlet) before the product;
     constrained rows return x itself (identity rows).
+    Entries of the action of Sec. 3.6 built from the element rows of the step-4 loop (Sec. 2.4).
     """
     if len(mesh.cmaster):
         raise NotImplementedError("sampled rows support Dirichlet-only meshes")
@@ -171,7 +193,10 @@ def sampled_rows(mesh, nq, dofs, x, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0)
 
 
 def cell_rhs(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), fq=None):
-    """Element right-hand sides (C, n^3): manufactured forcing, or f given at quadrature points."""
+    """Element right-hand sides (C, n^3): manufactured forcing, or f given at quadrature points.
+
+    The right-hand-side integrals of the step-4 cell loop (Sec. 2.4).
+    """
     k = mesh.k
     n = k + 1
     nodes = gauss_lobatto(k)
@@ -190,7 +215,10 @@ def cell_rhs(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), fq=None):
 
 
 def rhs(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), fq=None):
-    """b = C^T b_full on free DoFs, 0 on constrained DoFs."""
+    """b = C^T b_full on free DoFs, 0 on constrained DoFs.
+
+    Condensed with the constraints of Sec. 3.3.
+    """
     be = cell_rhs(mesh, nq, coef_kind, coef_par, fq)
     bfull = np.zeros(mesh.n_dofs)
     np.add.at(bfull, mesh.cell_dofs.ravel(), be.ravel())
@@ -201,19 +229,24 @@ def rhs(mesh, nq, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), fq=None):
 
 
 def distribute(mesh, x):
-    """Fill constrained entries: hanging -> weighted masters, Dirichlet -> 0."""
+    """Fill constrained entries: hanging -> weighted masters, Dirichlet -> 0.
+
+    Distribution of constrained values after the solve (Sec. 3.3).
+    """
     Cm, is_c = constraint_matrix(mesh)
     xf = np.where(is_c, 0.0, x)
     return Cm @ xf
 
 
 def diagonal(K):
+    """Diagonal of the condensed operator: the Jacobi preconditioner of the CG solves (Sec. 3.5, Sec. 6.1)."""
     return K.diagonal().copy()
 
 
 def l2_error(mesh, x, nq_err=None, exact="sinxyz"):
     """||u_h - u||_L2 with a (k+3)-point Gauss rule; u = sin(pi x) sin(pi y) sin(pi z) ("sinxyz", zero on
-    every face) or u = sin(pi x) ("sinx", zero on the x faces, zero normal derivative on the others)."""
+    every face) or u = sin(pi x) ("sinx", zero on the x faces, zero normal derivative on the others).
+    Error of the Poisson problem of Sec. 2.4 against a manufactured solution."""
     k = mesh.k
     nq_err = nq_err or k + 3
     nodes = gauss_lobatto(k)
@@ -230,6 +263,7 @@ BREAKDOWN = 2
 
 
 class SolveResult:
+    """Outcome of the CG solves of Sec. 6.1."""
     def __init__(self, x, iterations, rel_residual, status, history=None, alphas=None, betas=None):
         self.x = x
         self.iterations = iterations
@@ -245,6 +279,7 @@ def pcg(A, b, precond, tol=1e-10, max_it=100000, dtype=np.float64, x0=None):
 
     A and precond are callables on vectors of `dtype`; scalars are kept in
     `dtype` as well (float32 for the inner single-precision solve).
+    The conjugate-gradient solver of Sec. 6.1 with a Jacobi or Chebyshev-Jacobi preconditioner (Sec. 3.5).
     """
     b = b.astype(dtype)
     x = np.zeros_like(b) if x0 is None else x0.astype(dtype).copy()
@@ -284,6 +319,7 @@ def lanczos_tridiagonal(alphas, betas):
     """Lanczos tridiagonal of the preconditioned operator from CG's coefficients.
 
     T_ii = 1/alpha_i + beta_{i-1}/alpha_{i-1},  T_{i,i+1} = sqrt(beta_i)/alpha_i.
+    The eigenvalue estimate behind the Chebyshev interval (Sec. 3.5).
     """
     m = len(alphas)
     T = np.zeros((m, m))
@@ -295,7 +331,10 @@ def lanczos_tridiagonal(alphas, betas):
 
 
 def lanczos_lambda_max(A, dinv, start, steps=15):
-    """Largest eigenvalue estimate of D^-1 A after `steps` Jacobi-PCG steps from `start`."""
+    """Largest eigenvalue estimate of D^-1 A after `steps` Jacobi-PCG steps from `start`.
+
+    The eigenvalue estimate behind the Chebyshev interval (Sec. 3.5).
+    """
     res = pcg(A, start, lambda r: dinv * r, tol=0.0, max_it=steps)
     m = min(len(res.alphas), len(res.betas) + 1)
     T = lanczos_tridiagonal(res.alphas[:m], res.betas[:m - 1])
@@ -308,6 +347,7 @@ def chebyshev(A, dinv, r, degree, lo, hi, dtype=np.float64):
     sigma(lambda) = (hi + lo - 2 lambda) / (hi - lo).  Computed by `degree`
     steps of the Chebyshev iteration for D^-1 A z = D^-1 r from z = 0
     (three-term recurrence; degree - 1 operator products).
+    The Chebyshev-Jacobi smoother of Sec. 3.5, used as a CG preconditioner (Sec. 6.1).
     """
     theta = dtype((hi + lo) / 2.0)
     delta = dtype((hi - lo) / 2.0)
@@ -332,6 +372,7 @@ def defect_correction(A64, A32, dinv64, b, inner_precond, tol=1e-10, inner_tol=1
 
     x = 0; repeat: r = b - A64 x (FP64); stop if ||r|| <= tol ||b||;
     solve A32 d = r / ||r|| to inner_tol in FP32; x += ||r|| d.
+    The single-precision solver inside a double-precision correction of Sec. 6.1.
     """
     x = np.zeros_like(b)
     bnorm = float(np.linalg.norm(b))

@@ -41,7 +41,10 @@ from .rules import gauss_lobatto, lagrange
 
 
 class Mesh:
-    """Cells with 8 physical vertices each, plus the DoF tables of degree k."""
+    """Cells with 8 physical vertices each, plus the DoF tables of degree k.
+
+    The triangulation with its DoF numbering and constraints (Sec. 3.1).
+    """
 
     def __init__(self, cell_vertices, cell_dofs, n_dofs, constrained, cptr, cmaster,
                  cweight, k):
@@ -60,7 +63,10 @@ class Mesh:
 
 
 def unit_vertices(nx, ny, nz):
-    """Vertex coordinates (i/nx, j/ny, l/nz), lexicographic, x fastest."""
+    """Vertex coordinates (i/nx, j/ny, l/nz), lexicographic, x fastest.
+
+    Vertices of the structured box (Sec. 3.1).
+    """
     i = np.arange(nx + 1) / nx
     j = np.arange(ny + 1) / ny
     l = np.arange(nz + 1) / nz
@@ -69,7 +75,10 @@ def unit_vertices(nx, ny, nz):
 
 
 def structured_mesh(nx, ny, nz, k, vertices=None, dirichlet=0x3F):
-    """Structured box mesh of nx*ny*nz cells with degree-k lexicographic DoFs."""
+    """Structured box mesh of nx*ny*nz cells with degree-k lexicographic DoFs.
+
+    Tensor-product Q_k DoFs of a structured box (Sec. 3.1).
+    """
     if vertices is None:
         vertices = unit_vertices(nx, ny, nz)
     vertices = np.asarray(vertices, dtype=np.float64).reshape(-1, 3)
@@ -108,6 +117,7 @@ def structured_mesh(nx, ny, nz, k, vertices=None, dirichlet=0x3F):
 # ----------------------------------------------------------------------------
 
 class MeshError(ValueError):
+    """An octree that violates the 2:1 balance or does not tile its box (Sec. 3.1)."""
     pass
 
 
@@ -159,7 +169,10 @@ def _check_balance(owner, levels):
 
 
 def octree_mesh(nx, ny, nz, k, leaves, coarse_vertices=None, dirichlet=0x3F):
-    """Octree mesh from leaves (level, i, j, l), with DoF tables and constraints."""
+    """Octree mesh from leaves (level, i, j, l), with DoF tables and constraints.
+
+    Locally refined mesh with hanging nodes (Sec. 3.1, Fig. 2; constraints as in Sec. 3.3).
+    """
     faces = int(dirichlet)  # Dirichlet face mask (the name is reused below for the Dirichlet DoF set)
     leaves = [tuple(int(v) for v in lf) for lf in np.asarray(leaves).reshape(-1, 4)]
     if not leaves:

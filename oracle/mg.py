@@ -35,7 +35,10 @@ from .rules import gauss_lobatto, lagrange
 
 
 def coarsen_vertices(vertices, nx, ny, nz):
-    """Every other vertex of an (nx+1)(ny+1)(nz+1) lattice (x fastest): the next coarser level's."""
+    """Every other vertex of an (nx+1)(ny+1)(nz+1) lattice (x fastest): the next coarser level's.
+
+    The geometric multigrid hierarchy of Sec. 3.5.
+    """
     v = np.asarray(vertices, dtype=np.float64).reshape(nz + 1, ny + 1, nx + 1, 3)
     return v[::2, ::2, ::2].reshape(-1, 3).copy()
 
@@ -51,6 +54,7 @@ def level_sizes(nx, ny, nz, max_levels=0):
 
 
 def level_meshes(nx, ny, nz, k, vertices=None, max_levels=0, dirichlet=0x3F):
+    """Levels of the geometric multigrid hierarchy of Sec. 3.5 (coarsest: the 2 x 1 x 1 mesh of Sec. 6.1 for the 2:1:1 box)."""
     sizes = level_sizes(nx, ny, nz, max_levels)
     if vertices is None:
         vertices = unit_vertices(nx, ny, nz)
@@ -61,7 +65,10 @@ def level_meshes(nx, ny, nz, k, vertices=None, max_levels=0, dirichlet=0x3F):
 
 
 def prolongation_1d(nc, k):
-    """Fine lattice (2 k nc + 1 points) from coarse lattice (k nc + 1 points), one direction."""
+    """Fine lattice (2 k nc + 1 points) from coarse lattice (k nc + 1 points), one direction.
+
+    The transfer between multigrid levels (Sec. 3.5).
+    """
     x = gauss_lobatto(k)
     Mf, Mc = 2 * k * nc + 1, k * nc + 1
     P = np.zeros((Mf, Mc))
@@ -75,6 +82,7 @@ def prolongation_1d(nc, k):
 
 
 def prolongation(mc, mf, size_c, k, condensed=True):
+    """The transfer between multigrid levels (Sec. 3.5)."""
     nxc, nyc, nzc = size_c
     P = sp.kron(sp.csr_matrix(prolongation_1d(nzc, k)),
                 sp.kron(sp.csr_matrix(prolongation_1d(nyc, k)), sp.csr_matrix(prolongation_1d(nxc, k))))
@@ -90,7 +98,10 @@ def prolongation(mc, mf, size_c, k, condensed=True):
 
 
 class Hierarchy:
-    """Assembled levels: condensed K, inverse diagonal, Chebyshev interval, prolongation from below."""
+    """Assembled levels: condensed K, inverse diagonal, Chebyshev interval, prolongation from below.
+
+    The geometric multigrid V-cycle with Chebyshev smoothing (Sec. 3.5), the CG preconditioner of Sec. 6.1.
+    """
 
     def __init__(self, meshes, sizes, k, coef_kind=fem.COEF_CONSTANT, coef_par=(1.0, 0.0), degree=6,
                  bounds=None, smoothing_range=20.0, lanczos_steps=15, dg_top=None):

@@ -16,7 +16,10 @@ import numpy as np
 
 
 def legendre(n, t):
-    """P_n(t) and P_{n-1}(t) by the three-term recurrence (Bonnet)."""
+    """P_n(t) and P_{n-1}(t) by the three-term recurrence (Bonnet).
+
+    Building block of the Gauss and Gauss-Lobatto rules of the tensor-product elements (Sec. 3.1, Sec. 3.4).
+    """
     t = np.asarray(t, dtype=np.float64)
     p_prev = np.ones_like(t)
     if n == 0:
@@ -28,7 +31,10 @@ def legendre(n, t):
 
 
 def legendre_deriv(n, t):
-    """P_n'(t) = n (t P_n - P_{n-1}) / (t^2 - 1), valid for |t| < 1."""
+    """P_n'(t) = n (t P_n - P_{n-1}) / (t^2 - 1), valid for |t| < 1.
+
+    Building block of the Gauss and Gauss-Lobatto rules (Sec. 3.1, Sec. 3.4).
+    """
     p, pm = legendre(n, t)
     return n * (t * p - pm) / (t * t - 1.0), p
 
@@ -47,6 +53,7 @@ def gauss_legendre(n):
 
     The roots are symmetric about 0; the negative half is computed and
     mirrored so that the rule is exactly symmetric (midpoint exactly 1/2).
+    The quadrature of the cell integrals (Sec. 2.4, Sec. 3.6).
     """
     if n < 1:
         raise ValueError("n >= 1")
@@ -71,6 +78,7 @@ def gauss_lobatto(k):
 
     Interior nodes are the roots of P_k'; Newton uses P_k'' from the
     Legendre equation (1 - t^2) P'' = 2 t P' - k (k+1) P.
+    The nodes of the Lagrange shape functions (Sec. 3.1).
     """
     if k < 1:
         raise ValueError("k >= 1")
@@ -93,7 +101,10 @@ def gauss_lobatto(k):
 
 
 def lagrange(nodes, j, x):
-    """l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m)."""
+    """l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m).
+
+    The 1D factors of the tensor-product shape functions (Sec. 3.1).
+    """
     x = np.asarray(x, dtype=np.float64)
     v = np.ones_like(x)
     for m, xm in enumerate(nodes):
@@ -103,7 +114,10 @@ def lagrange(nodes, j, x):
 
 
 def lagrange_deriv(nodes, j, x):
-    """l_j'(x) = sum_{m != j} 1/(x_j - x_m) prod_{l != j, m} (x - x_l)/(x_j - x_l)."""
+    """l_j'(x) = sum_{m != j} 1/(x_j - x_m) prod_{l != j, m} (x - x_l)/(x_j - x_l).
+
+    The 1D factors of the tensor-product shape functions (Sec. 3.1).
+    """
     x = np.asarray(x, dtype=np.float64)
     total = np.zeros_like(x)
     for m, xm in enumerate(nodes):
@@ -122,6 +136,7 @@ def basis_tables(k, nq):
 
     Returns (gll_nodes, gauss_points, gauss_weights, V, Dv) with V[q, j] =
     l_j(xi_q) and Dv[q, j] = l_j'(xi_q).
+    The 1D shape values and derivatives at the Gauss points that the tensor-product structure of Sec. 3.1 factorises.
     """
     nodes = gauss_lobatto(k)
     xq, wq = gauss_legendre(nq)
