@@ -70,7 +70,7 @@ static double forcing(int kind, const double* p, const double x[3]) {
   return -(ga[0] * gu[0] + ga[1] * gu[1] + ga[2] * gu[2] + a * lap_u);
 }
 
-/* Q1 map at reference point xi: physical point x, Jacobian J[i][j] = dx_i/dxi_j */
+/* Q1 map at reference point xi: physical point x, Jacobian J[i][j] = dx_i/dxi_j (Sec. 3.4) */
 static void q1_map(const double* V /* 8x3 */, const double xi[3], double x[3], double J[3][3]) {
   for (int i = 0; i < 3; ++i) {
     x[i] = 0;
@@ -139,7 +139,8 @@ static void shape(int k, const double* nodes, int i, const double xi[3], double*
 }
 
 /*
- * Element matrices of `ncell` cells: out[c][i][j], i, j < n^3.
+ * Element matrices of `ncell` cells: out[c][i][j], i, j < n^3 (Eq. 1 by the
+ * step-4 cell loop of Sec. 2.4).
  * rows: optional list of local rows to compute (nrows > 0); then out[c][r][j].
  */
 int or_cell_matrices(int ncell, int k, int nq, const double* nodes, const double* xq,
@@ -177,7 +178,7 @@ int or_cell_matrices(int ncell, int k, int nq, const double* nodes, const double
   return 0;
 }
 
-/* Element mass matrices out[c][i][j] = sum_q phi_i phi_j JxW. */
+/* Element mass matrices out[c][i][j] = sum_q phi_i phi_j JxW (the loop of Sec. 2.4). */
 int or_cell_mass(int ncell, int k, int nq, const double* nodes, const double* xq,
                  const double* wq, const double* verts, double* out) {
   int n = k + 1, nd = n * n * n, NQ = nq * nq * nq;
@@ -201,7 +202,8 @@ int or_cell_mass(int ncell, int k, int nq, const double* nodes, const double* xq
 }
 
 /*
- * Element right-hand sides out[c][i] = sum_q phi_i(x_q) f(x_q) JxW.
+ * Element right-hand sides out[c][i] = sum_q phi_i(x_q) f(x_q) JxW (step-4
+ * loop, Sec. 2.4).
  * force_kind 0: manufactured forcing for coefficient (coef_kind, cpar);
  * force_kind 2: fq[c][q] given.
  */
@@ -271,7 +273,7 @@ double or_l2_error_sq(int ncell, int k, int nq, const double* nodes, const doubl
   return total;
 }
 
-/* y = A x for a CSR matrix, plain row loop. */
+/* y = A x for a CSR matrix, plain row loop: the action the matrix-free operator of Sec. 3.6 computes. */
 int or_csr_spmv(int64_t nrows, const int64_t* rowptr, const int64_t* col, const double* val,
                 const double* x, double* y) {
 #pragma omp parallel for schedule(static)
