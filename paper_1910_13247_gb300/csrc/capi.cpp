@@ -11,6 +11,9 @@
 #include <mutex>
 
 #include "mfx_internal.h"
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#endif
 
 namespace mfx {
 
@@ -20,6 +23,14 @@ mfx_status set_error(mfx_status code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+
+#if __has_include(<nvtx3/nvToolsExt.h>)
+TraceRange::TraceRange(const char* name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
+#else
+TraceRange::TraceRange(const char*) {}
+TraceRange::~TraceRange() {}
+#endif
 
 // Called inside a catch handler at the C-ABI boundary: no C++ exception crosses it.
 mfx_status host_exception() {
@@ -460,6 +471,7 @@ static mfx_status create_sipg(mfx_op** out, const Mesh& m, const mfx_op_desc* de
 }
 
 mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc, mfx_stream stream) try {
+  MFX_TRACE("mfx_operator_create");
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "null argument");
   *out = nullptr;
   const int k = desc->degree;
@@ -858,6 +870,7 @@ mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst
 
 mfx_status mfx_vmult_host(const mfx_op* op, mfx_prec prec, int32_t count, const void* const* src, void* const* dst,
                           mfx_stream stream) {
+  MFX_TRACE("mfx_vmult_host");
   if (!op || count < 0 || (count > 0 && (!src || !dst))) return set_error(MFX_EINVAL, "mfx_vmult_host: bad argument");
   if ((prec == MFX_F64 && !op->has_f64) || (prec == MFX_F32 && !op->has_f32) || (prec != MFX_F64 && prec != MFX_F32))
     return set_error(MFX_EINVAL, "mfx_vmult_host: precision not built for this operator");

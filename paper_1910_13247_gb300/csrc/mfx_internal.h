@@ -19,6 +19,17 @@ constexpr int kMaxN = kMaxDegree + 1;
 mfx_status set_error(mfx_status code, const std::string& msg);
 mfx_status cuda_error(cudaError_t e, const char* where);
 mfx_status host_exception();  // inside a catch handler: the current exception as a status code
+
+// Tracing: NVTX ranges around the library's host-side phases (operator and multigrid set-up, solves,
+// batch ticks, server set-up of a request), visible to ncu --nvtx and other NVTX tools; without an
+// attached tool each range costs a no-op call.  Compiled out where the NVTX headers are missing.
+struct TraceRange {
+  explicit TraceRange(const char* name);
+  ~TraceRange();
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define MFX_TRACE(name) ::mfx::TraceRange mfx_trace_range_(name)
 #define MFX_CUDA_TRY(call)                                   \
   do {                                                       \
     cudaError_t e_ = (call);                                 \

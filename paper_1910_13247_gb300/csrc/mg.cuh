@@ -481,6 +481,7 @@ void mfx_mg_params_default(mfx_mg_params* p) {
 
 mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* desc, const mfx_mg_params* params,
                          mfx_stream stream) try {
+  MFX_TRACE("mfx_mg_create");
   if (!out || !mesh || !desc) return set_error(MFX_EINVAL, "mfx_mg_create: null argument");
   *out = nullptr;
   const Mesh& fm = mesh->m;
@@ -715,6 +716,7 @@ mfx_status mfx_mg_vcycle(mfx_mg* mg, mfx_prec prec, const void* r, void* z, mfx_
 
 mfx_status mfx_mg_solve(mfx_mg* mg, const double* b, double* x, const mfx_solve_params* params,
                         mfx_solve_stats* stats, mfx_stream stream) {
+  MFX_TRACE("mfx_mg_solve");
   if (!mg) return set_error(MFX_EINVAL, "null multigrid");
   return solve_impl(mg->levels.back().op, b, x, params, mg, stats, stream);
 }

@@ -142,7 +142,15 @@ void worker_main(mfx_server* s) {
       s->setup_jobs.pop_front();
     }
     const double t = s->now();
-    const mfx_status rc = setup_request(*q, st, hb);
+    mfx_status rc;
+    {
+      MFX_TRACE("mfx_server_setup");
+      try {
+        rc = setup_request(*q, st, hb);
+      } catch (...) {  // a host failure fails the request, not the process
+        rc = mfx::host_exception();
+      }
+    }
     {
       std::lock_guard<std::mutex> g(s->mu);
       q->setup_s = s->now() - t;

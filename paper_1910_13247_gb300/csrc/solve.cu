@@ -790,6 +790,7 @@ mfx_status mfx_chebyshev(const mfx_op* op_c, mfx_prec prec, const void* r, void*
 
 mfx_status mfx_solve(const mfx_op* op_c, const double* b, double* x, const mfx_solve_params* params,
                      mfx_solve_stats* stats, mfx_stream stream) {
+  MFX_TRACE("mfx_solve");
   return solve_impl(const_cast<mfx_op*>(op_c), b, x, params, nullptr, stats, stream);
 }
 
@@ -1094,6 +1095,7 @@ mfx_status mfx_batch_add(mfx_batch* bt, const mfx_op* op_c, const double* b, dou
 }
 
 mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
+  MFX_TRACE("mfx_batch_step");
   if (!bt) return set_error(MFX_EINVAL, "null batch");
   // 1) outer steps: residuals of the OUTER slots, then decide
   bool any_outer = false;
@@ -1160,6 +1162,7 @@ mfx_status mfx_batch_step(mfx_batch* bt, int32_t* n_active) {
 // Independent stepping: every slot whose previous work has finished takes its next step right
 // away (residual, decision, inner start, next chunk), each on its own stream; nothing waits.
 mfx_status mfx_batch_advance(mfx_batch* bt, int32_t* n_active) {
+  MFX_TRACE("mfx_batch_advance");
   if (!bt) return set_error(MFX_EINVAL, "null batch");
   int active = 0;
   for (auto& sl : bt->slots) {
