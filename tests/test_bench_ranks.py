@@ -81,3 +81,17 @@ def test_reference_arm_line(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(args)
     assert capsys.readouterr().out == ""
+
+
+def test_clock_record_rejection_rule():
+    """Slowdown reasons or SM clocks well below their maximum with no reason reject a timed region (it is
+    measured once more); a power cap alone does not."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 9}
+    assert not bench.clocks_rejected(ok) and not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1600.0, reasons=["sw_power_cap"]))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))
