@@ -191,7 +191,20 @@ typedef struct {
                                 point during create (on the calling thread)      */
   void* coef_user;
   double dg_penalty;         /* MFX_SIPG: eta of the penalty (0 means 1)            */
+  int32_t structured_kernel; /* FP32 vmult kernel of a structured continuous
+                                operator at k = 1..4: MFX_KERNEL_* (0 = autotuned)  */
 } mfx_op_desc;
+
+/*
+ * Kernels of the FP32 vmult on structured meshes (the cell loop of Sec. 3.6; the choice does not
+ * change the result beyond rounding).  TEN_PHASE: collocation derivative after the interpolation
+ * to the Gauss points, ten synchronised sweeps per batch of cells.  FIVE_PHASE: values and
+ * derivatives of the nodal basis at the Gauss points taken from the same line in each sweep
+ * (sixteen 1D contractions per line in five synchronised sweeps), metric read where it is used;
+ * FIVE_PHASE_STAGED: the same with each batch's metric copied into shared memory first.
+ * Degrees above 4 always use their own kernels.  No counterpart in the paper.
+ */
+enum { MFX_KERNEL_AUTO = 0, MFX_KERNEL_TEN_PHASE = 1, MFX_KERNEL_FIVE_PHASE = 2, MFX_KERNEL_FIVE_PHASE_STAGED = 3 };
 
 /*
  * MFX_SIPG: the symmetric interior penalty DG Laplacian of the paper's multigrid benchmark
@@ -242,7 +255,7 @@ typedef struct {
   int64_t bytes_device; /* device memory owned by the operator */
   int32_t degree, n_q_1d, structured, cells_per_block;
   int32_t discretization;  /* MFX_CONTINUOUS or MFX_SIPG */
-  int32_t reserved;
+  int32_t structured_kernel; /* MFX_KERNEL_* of the FP32 structured vmult (0 where none applies) */
 } mfx_op_info;
 
 mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info);

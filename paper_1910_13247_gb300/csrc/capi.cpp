@@ -109,15 +109,28 @@ int brick_cells_candidates_for_degree(int k, int* out) {
   }
 }
 
-// Time the FP32 vmult of a structured operator with the metric laid out for `cb` cells per
-// batch (geometry rebuilt in that layout); returns milliseconds per application.
-static mfx_status time_layout(mfx_op* op, int cb, int coef_kind, const double* par, const double* coef_q,
-                              float* x, float* y, cudaStream_t s, float* ms) {
+int brick_kernel_candidates_for_degree(int k, int* out) {
+  switch (k + 1) {
+    case 2: return brick_kernel_candidates<2>(out);
+    case 3: return brick_kernel_candidates<3>(out);
+    case 4: return brick_kernel_candidates<4>(out);
+    case 5: return brick_kernel_candidates<5>(out);
+    case 6: return brick_kernel_candidates<6>(out);
+    case 7: return brick_kernel_candidates<7>(out);
+    case 8: return brick_kernel_candidates<8>(out);
+    case 9: return brick_kernel_candidates<9>(out);
+    default: return 0;
+  }
+}
+
+// Time the FP32 vmult of a structured operator with the metric laid out for `cb` cells per batch and
+// kernel `kern`; milliseconds per application.  The metric's values do not change the time, so the
+// candidates run on whatever the FP32 metric buffer holds (zeros before the geometry exists).
+static mfx_status time_layout(mfx_op* op, int cb, int kern, float* x, float* y, cudaStream_t s, float* ms) {
   op->metric_cb = cb;
   op->nchunk = (op->nx + cb - 1) / cb;
-  mfx_status st = launch_geometry(op, coef_kind, par, coef_q, s);
-  if (st != MFX_OK) return st;
-  st = launch_vmult(op, MFX_F32, x, y, s);  // warm-up (first launch sets kernel attributes)
+  op->f32_kernel = kern;
+  mfx_status st = launch_vmult(op, MFX_F32, x, y, s);  // warm-up (first launch sets kernel attributes)
   if (st != MFX_OK) return st;
   cudaEvent_t e0, e1;
   MFX_CUDA_TRY(cudaEventCreate(&e0));
@@ -136,34 +149,48 @@ static mfx_status time_layout(mfx_op* op, int cb, int coef_kind, const double* p
   return MFX_OK;
 }
 
-// Autotuner: cells per batch for (degree, mesh size), measured once per process and device.
-static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kind, const double* par,
-                                         const double* coef_q, cudaStream_t s) {
-  int cand[4];
+// Autotuner: cells per batch and FP32 kernel for (degree, mesh size), measured once per process and
+// device before the geometry is built (the geometry is then computed once, in the chosen layout).
+// A requested batch size or kernel restricts the candidates to it.
+static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int requested_kernel, cudaStream_t s) {
+  int cand[4], kcand[4];
   const int nc = brick_cells_candidates_for_degree(op->k, cand);
-  if (requested > 0) {
-    for (int i = 0; i < nc; ++i)
-      if (cand[i] == requested) {
-        op->metric_cb = requested;
-        op->nchunk = (op->nx + requested - 1) / requested;
-        return MFX_OK;
-      }
-    return set_error(MFX_EUNSUPPORTED, "cells_per_block not compiled for this degree");
+  const int nk = brick_kernel_candidates_for_degree(op->k, kcand);
+  std::vector<std::pair<int, int>> tries;
+  for (int i = 0; i < nc; ++i) {
+    if (requested > 0 && cand[i] != requested) continue;
+    for (int j = 0; j < nk; ++j) {
+      if (requested_kernel > 0 && kcand[j] != requested_kernel) continue;
+      tries.push_back({cand[i], kcand[j]});
+    }
   }
-  op->metric_cb = cand[0];
-  op->nchunk = (op->nx + cand[0] - 1) / cand[0];
-  if (nc < 2 || !op->has_f32) return MFX_OK;
+  if (requested > 0 && tries.empty()) {
+    bool cb_ok = false;
+    for (int i = 0; i < nc; ++i) cb_ok = cb_ok || cand[i] == requested;
+    if (!cb_ok) return set_error(MFX_EUNSUPPORTED, "cells_per_block not compiled for this degree");
+  }
+  if (tries.empty()) {
+    if (requested_kernel > 0 && requested_kernel != MFX_KERNEL_TEN_PHASE)
+      return set_error(MFX_EUNSUPPORTED, "structured_kernel not available for this degree");
+    tries.push_back({requested > 0 ? requested : cand[0], MFX_KERNEL_TEN_PHASE});
+  }
+  auto take = [op](int cb, int kern) {
+    op->metric_cb = cb;
+    op->nchunk = (op->nx + cb - 1) / cb;
+    op->f32_kernel = kern;
+  };
+  take(tries[0].first, tries[0].second);
+  if (tries.size() < 2 || !op->has_f32) return MFX_OK;
   static std::mutex lock;
-  static std::map<std::array<int64_t, 5>, int> cache;
+  static std::map<std::array<int64_t, 7>, std::pair<int, int>> cache;
   int dev = 0;
   cudaGetDevice(&dev);
-  const std::array<int64_t, 5> key = {op->k, op->nx, op->ny, op->nz, dev};
+  const std::array<int64_t, 7> key = {op->k, op->nx, op->ny, op->nz, dev, requested, requested_kernel};
   {
     std::lock_guard<std::mutex> g(lock);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      op->metric_cb = it->second;
-      op->nchunk = (op->nx + it->second - 1) / it->second;
+      take(it->second.first, it->second.second);
       return MFX_OK;
     }
   }
@@ -176,23 +203,22 @@ static mfx_status choose_cells_per_batch(mfx_op* op, int requested, int coef_kin
     return cuda_error(e, "autotune vectors");
   }
   cudaMemsetAsync(x, 0, sizeof(float) * op->n_dofs, s);
-  int best = cand[0];
+  std::pair<int, int> best = tries[0];
   float best_ms = 1e30f;
   mfx_status st = MFX_OK;
-  for (int i = 0; i < nc && st == MFX_OK; ++i) {
+  for (size_t i = 0; i < tries.size() && st == MFX_OK; ++i) {
     float ms = 0;
-    st = time_layout(op, cand[i], coef_kind, par, coef_q, x, y, s, &ms);
+    st = time_layout(op, tries[i].first, tries[i].second, x, y, s, &ms);
     if (st == MFX_OK && ms < best_ms) {
       best_ms = ms;
-      best = cand[i];
+      best = tries[i];
     }
   }
   cudaFreeAsync(x, s);
   cudaFreeAsync(y, s);
   cudaStreamSynchronize(s);
   if (st != MFX_OK) return st;
-  op->metric_cb = best;
-  op->nchunk = (op->nx + best - 1) / best;
+  take(best.first, best.second);
   std::lock_guard<std::mutex> g(lock);
   cache[key] = best;
   return MFX_OK;
@@ -683,7 +709,10 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     coef_q = coef_tmp;
   }
   mfx_status geo_st = MFX_OK;
-  if (op->structured) geo_st = choose_cells_per_batch(op, desc->cells_per_block, coef_kind, desc->coef_par, coef_q, s);
+  if (op->structured) {
+    if (op->has_f32) MFX_CUDA_OP(cudaMemsetAsync(op->d_metric32, 0, sizeof(float) * metric32_entries, s));
+    geo_st = choose_cells_per_batch(op, desc->cells_per_block, desc->structured_kernel, s);
+  }
   if (geo_st == MFX_OK) geo_st = launch_geometry(op, coef_kind, desc->coef_par, coef_q, s);
   if (coef_tmp) cudaFreeAsync(coef_tmp, s);
   MFX_TRY(geo_st);
@@ -729,7 +758,7 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   info->cells_per_block = op->structured ? op->metric_cb : (op->metric_cb32 > 0 ? op->metric_cb32 : 256 / (op->n * op->n));
   info->discretization = op->dg ? MFX_SIPG : MFX_CONTINUOUS;
   if (op->dg) info->cells_per_block = std::max(1, 128 / (op->n * op->n));
-  info->reserved = 0;
+  info->structured_kernel = (op->structured && !op->dg && !op->percell32) ? op->f32_kernel : 0;
   return MFX_OK;
 }
 

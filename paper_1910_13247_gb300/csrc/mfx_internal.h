@@ -125,6 +125,7 @@ struct mfx_op {
   int metric_cb = 0;                  // 0: metric [cell][6][q]; > 0: [batch][6][q][metric_cb] (structured)
   int nchunk = 0;                     // structured: batches per row of cells
   int metric_cb32 = 0;                // octree FP32 metric: 0 [cell][6][q]; > 0 [cell / cb][6][q][cb]
+  int f32_kernel = MFX_KERNEL_TEN_PHASE;  // structured FP32 vmult kernel (MFX_KERNEL_*)
   bool has_f64 = false, has_f32 = false;
   mfx::BasisTables basis;
   // host tables (octree) or empty (structured)
@@ -203,6 +204,9 @@ int octree_pair_cells();
 template <int N>
 int brick_cells_candidates(int* out);
 int brick_cells_candidates_for_degree(int k, int* out);
+template <int N>
+int brick_kernel_candidates(int* out);
+int brick_kernel_candidates_for_degree(int k, int* out);
 template <int N>
 mfx_status prepare_vmult_n(const mfx_op* op);
 mfx_status prepare_vmult(const mfx_op* op);

@@ -118,12 +118,13 @@ struct VmultShape {
 // The 1D matrices are compile-time constants (generated at build time from the library's
 // own rules, basis_tables.h), so every contraction is a chain of FMAs with immediate
 // operands: S[q*N + j] = l_j(xi_q) (GLL basis at Gauss points), D[q*N + p] = L_p'(xi_q)
-// (collocation derivative on the Gauss points).
-enum { MAT_S = 0, MAT_D = 1 };
+// (collocation derivative on the Gauss points), Sd[q*N + j] = l_j'(xi_q) (derivative of the GLL
+// basis at the Gauss points, Sd = D S).
+enum { MAT_S = 0, MAT_D = 1, MAT_SD = 2 };
 
 template <int N, int MAT>
 __device__ __forceinline__ constexpr double basis_entry(int i) {
-  return MAT == MAT_S ? BasisConst<N>::S(i) : BasisConst<N>::D(i);
+  return MAT == MAT_S ? BasisConst<N>::S(i) : MAT == MAT_D ? BasisConst<N>::D(i) : BasisConst<N>::Sd(i);
 }
 
 // out = M in

@@ -1,0 +1,413 @@
+// FP32 brick-row vmult in five synchronised phases (the cell loop of the matrix-free operator,
+// Sec. 3.6, with the tensor-product evaluation of Sec. 3.1 on pairs of cells).
+//
+// The reference gradient at the Gauss points is taken with the derivative of the nodal basis at
+// the Gauss points, Sd[q][j] = l_j'(xi_q), next to the values S[q][j] = l_j(xi_q):
+//   d/dx u = Sd_x S_y S_z u,  d/dy u = S_x Sd_y S_z u,  d/dz u = S_x S_y Sd_z u,
+// so every line of a direction is read from shared memory once and both of its contractions come
+// from the same registers.  Per batch of CB cells of one row (lattice rows in shared memory by TMA,
+// as in the ten-phase kernel of vmult_brick_tma2.cuh):
+//   1) z-lines of the input tile:  A = S_z u,  C = Sd_z u
+//   2) y-lines:  A <- S_y A,  B = Sd_y A,  C <- S_y C
+//   3) x-lines:  grad = (Sd_x A, S_x B, S_x C) at the Gauss points, h = G_q grad (G_q the merged
+//      metric), A <- Sd_x^T h_1, B <- S_x^T h_2, C <- S_x^T h_3, all in registers; the lattice
+//      point that neighbouring cells of the batch share in x is summed here (in registers within
+//      a pair, one shuffle between pairs), so from here on every point of the batch has one owner
+//   4) y-lines:  A <- S_y^T A + Sd_y^T B,  C <- S_y^T C   (shared x-points: owner only)
+//   5) z-lines:  out = S_z^T A + Sd_z^T C  into the output tile, one plain store per point, which
+//      the TMA engine adds to dst (dst holds src on Dirichlet rows and 0 elsewhere beforehand).
+// That is sixteen 1D contractions per line instead of twelve, in five phases instead of ten.
+// Every thread owns the same line of two neighbouring cells (2c, 2c + 1) held as a float pair, so
+// each contraction is a chain of packed FMAs and every shared-memory access moves 8 bytes; the
+// cube paddings are those of the ten-phase kernel (same line access patterns).
+//
+// Input tile, output tile and (MS) the metric are single buffers: the next batch's rows are loaded
+// once phase 1 has read the tile, the next batch's metric once phase 3 has read it, and the output
+// tile is rewritten only after the TMA engine has read the previous batch's.  MS = 0 reads the
+// metric at its point of use from L2 (the TMA engine prefetches each batch's metric into L2 one
+// batch ahead); MS = 1 copies each batch's metric into shared memory with one bulk copy.  Every
+// mbarrier wait is bounded; on timeout the CTA sets the error word, drains its copies and returns.
+#pragma once
+
+#include "vmult_brick_tma2.cuh"
+
+namespace mfx {
+
+template <int N, int CB, int MS>
+struct F5Shape {
+  static constexpr int PP = CB / 2;
+  static constexpr int LINES = PP * N * N;
+  static constexpr int THREADS = (LINES + 31) / 32 * 32;
+  static constexpr int CUBES = PP * BrickShape<N, CB, float>::CELL;  // float2 elements per cube
+  static constexpr int METRIC = 6 * N * N * N * CB;                  // floats of one batch's metric
+  static constexpr size_t SMEM = (size_t)2 * TmaShape<N, CB>::TILE * sizeof(float) +
+                                 (MS ? (size_t)METRIC * sizeof(float) : 0) + 3 * (size_t)CUBES * sizeof(float2) +
+                                 2 * sizeof(uint64_t);
+  static_assert(32 % PP == 0, "the pairs of one line must share a warp (x-point shuffle)");
+  static_assert((METRIC * sizeof(float)) % 16 == 0, "bulk copy size");
+};
+
+// one bulk copy (no tensor map) global -> shared, completion on an mbarrier; both addresses 16-byte
+// aligned, size a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// out = M1^T a + M2^T b
+template <int N, int M1, int M2>
+__device__ __forceinline__ void contract2_tt(const float2 (&a)[N], const float2 (&b)[N], float2 (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float m0 = (float)basis_entry<N, M1>(i);
+    float2 s = __fmul2_rn(make_float2(m0, m0), a[0]);
+#pragma unroll
+    for (int j = 1; j < N; ++j) {
+      const float mj = (float)basis_entry<N, M1>(j * N + i);
+      s = __ffma2_rn(make_float2(mj, mj), a[j], s);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const float mj = (float)basis_entry<N, M2>(j * N + i);
+      s = __ffma2_rn(make_float2(mj, mj), b[j], s);
+    }
+    out[i] = s;
+  }
+}
+
+// row q of M times in
+template <int N, int MAT>
+__device__ __forceinline__ float2 row2(const float2 (&in)[N], int q) {
+  const float m0 = (float)basis_entry<N, MAT>(q * N);
+  float2 s = __fmul2_rn(make_float2(m0, m0), in[0]);
+#pragma unroll
+  for (int j = 1; j < N; ++j) {
+    const float mj = (float)basis_entry<N, MAT>(q * N + j);
+    s = __ffma2_rn(make_float2(mj, mj), in[j], s);
+  }
+  return s;
+}
+
+// acc[i] (+)= M[q][i] h  (column q of M^T)
+template <int N, int MAT>
+__device__ __forceinline__ void axpy_col2(float2 (&acc)[N], float2 h, int q, bool first) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float m = (float)basis_entry<N, MAT>(q * N + i);
+    acc[i] = first ? __fmul2_rn(make_float2(m, m), h) : __ffma2_rn(make_float2(m, m), h, acc[i]);
+  }
+}
+
+template <int N, int CB, int MS, int MB>
+__global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
+    brick_vmult_f5_kernel(const __grid_constant__ TmaArgs<N> a) {
+  using Sh = BrickShape<N, CB, float>;  // cube paddings of CB cells = paddings of CB / 2 float pairs
+  using Tm = TmaShape<N, CB>;
+  using Fs = F5Shape<N, CB, MS>;
+  constexpr int PP = Fs::PP;
+  constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
+  constexpr int PITCH = Tm::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
+  constexpr unsigned MBYTES = Fs::METRIC * 4u;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* T = reinterpret_cast<float*>(smem_raw);  // input tile
+  float* O = T + Tm::TILE;                         // output tile
+  float* Msm = O + Tm::TILE;                       // MS: the batch's metric [6][N^3][CB]
+  float2* A = reinterpret_cast<float2*>(Msm + (MS ? Fs::METRIC : 0));
+  float2* B = A + Fs::CUBES;
+  float2* C = B + Fs::CUBES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(C + Fs::CUBES);  // [0] input tile, [1] metric
+
+  const int t = threadIdx.x;
+  const int c = t % PP;  // pair: cells 2c and 2c + 1 of the batch
+  const int r = t / PP;
+  const int f = r % N, s = r / N;
+  const bool line_ok = t < Fs::LINES;
+  const int xa2 = Sh::XSWAP ? s : f, xa3 = Sh::XSWAP ? f : s;
+  const int xbase = c * CELL + xa3 * P2 + xa2 * NP;
+  const int ybase = c * CELL + s * P2 + f;
+  const int zbase = c * CELL + s * NP + f;
+  const int zx = 2 * c * K + f;  // tile point of this thread's z-line in the first cell of the pair; + K for the second
+  const int lane = t & 31;
+  const bool tma_warp = (t >> 5) == Fs::THREADS / 32 - 1;  // the last warp (idle lanes) issues the copies
+  // this thread's x-line of quadrature points in the metric of a batch (float2 units: cells 2c, 2c + 1)
+  const int gq = (xa2 * N + xa3 * N * N) * PP + c;
+
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue_rows = [&](const BatchPos& pb) {
+    const BatchInfo bi = batch_info_at<CB, K>(a, pb);
+    fence_proxy_async();
+    if (lane == 0) mbar_arrive_expect_tx(&bars[0], ROWS * BOX * 4);
+    __syncwarp();
+    for (int row = lane; row < ROWS; row += 32) {
+      const int a2 = row % N, a3 = row / N;
+      tma_load_1d(T + row * PITCH, &a.tsrc, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, &bars[0]);
+    }
+  };
+  // MS: the batch's metric in four bulk copies (lanes 0..3)
+  auto issue_metric = [&](int bn) {
+    constexpr unsigned CH = (MBYTES / 4 + 15u) & ~15u;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[1], MBYTES);
+    __syncwarp();
+    const unsigned off = lane * CH;
+    if (lane < 4 && off < MBYTES)
+      bulk_load(reinterpret_cast<char*>(Msm) + off, reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off,
+                off + CH <= MBYTES ? CH : MBYTES - off, &bars[1]);
+  };
+
+  int it = 0;
+  bool failed = false;
+  // copies in flight that no wait has seen yet, and the parity of the barrier phase they complete
+  // (one buffer per barrier: at most one copy per barrier is outstanding)
+  bool rows_pending = false, metric_pending = false;
+  unsigned rows_par = 0, metric_par = 0;
+  BatchPos pos = batch_pos(a, blockIdx.x);
+  if (tma_warp && (int)blockIdx.x < a.n_batches) {
+    issue_rows(pos);
+    if (MS) issue_metric(blockIdx.x);
+  }
+  if ((int)blockIdx.x < a.n_batches) {
+    rows_pending = true;
+    metric_pending = MS != 0;
+  }
+
+  for (int b = blockIdx.x; b < a.n_batches; b += gridDim.x, ++it) {
+    const BatchInfo bi = batch_info_at<CB, K>(a, pos);
+    const int m = bi.m;
+    const bool act = line_ok && 2 * c < m;       // first cell of the pair valid
+    const bool act1 = line_ok && 2 * c + 1 < m;  // second cell valid
+    // pairs that hold the batch's last cell also own its last lattice point in x (a1 = K)
+    const bool own_k = 2 * c == m - 1 || 2 * c + 1 == m - 1;
+    const bool act45 = act && (f < K || own_k);
+    const bool has_next = b + (int)gridDim.x < a.n_batches;
+    const int zrow0 = bi.gbase + a.Mx * s;
+    const bool ebnd = (s == 0 && (bi.eflags & 1)) || (s == K && (bi.eflags & 2));
+    const bool lbnd0 = ebnd || (zx == 0 && bi.xlo) || (zx == bi.Wm - 1 && bi.xhi);
+    const bool lbnd1 = ebnd || (zx + K == 0 && bi.xlo) || (zx + K == bi.Wm - 1 && bi.xhi);
+    const bool zlo = (bi.eflags & 4) != 0, zhi = (bi.eflags & 8) != 0;
+
+    // the metric MDIST batches ahead into L2 (TMA engine, nothing waits for it)
+    if (tma_warp && lane >= 4 && lane < 7) {
+      const int bn = b + (MS ? 2 : 1) * (int)gridDim.x;
+      if (bn < a.n_batches) {
+        constexpr unsigned CHUNK = (MBYTES / 3 + 15u) & ~15u;
+        const unsigned off = (lane - 4) * CHUNK;
+        if (off < MBYTES)
+          prefetch_l2_bulk(reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off,
+                           off + CHUNK <= MBYTES ? CHUNK : MBYTES - off);
+      }
+    }
+    {
+      const bool ok = mbar_wait(&bars[0], it & 1);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      rows_pending = false;
+    }
+    // 1) z-lines of the input tile (Dirichlet points read as 0): A = S_z u, C = Sd_z u
+    if (act) {
+      float2 v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int g = zrow0 + a.Mx * a.My * j;
+        const float* row = T + (j * N + s) * PITCH + (g & 3) + zx;
+        v[j] = make_float2(lbnd0 ? 0.0f : row[0], lbnd1 ? 0.0f : row[K]);
+      }
+      if (zlo) v[0] = make_float2(0.0f, 0.0f);
+      if (zhi) v[K] = make_float2(0.0f, 0.0f);
+      contract2<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
+      contract2<N, MAT_SD>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
+    }
+    __syncthreads();
+    // the input tile is free: the next batch's rows
+    if (tma_warp && has_next) {
+      BatchPos next = pos;
+      batch_advance(next, a);
+      issue_rows(next);
+    }
+    rows_pending = has_next;
+    rows_par = (it + 1) & 1;
+    // 2) y-lines: A <- S_y A, B = Sd_y A, C <- S_y C
+    if (act) {
+      float2 v[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
+      contract2<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
+      contract2<N, MAT_SD>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = C[ybase + j * NP];
+      contract2<N, MAT_S>(v, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) C[ybase + j * NP] = o[j];
+    }
+    if (MS) {
+      const bool ok = mbar_wait(&bars[1], it & 1);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      metric_pending = false;
+    } else {
+      __syncthreads();
+    }
+    // 3) x-lines: gradient at the Gauss points, metric, transposed x-contractions, in registers
+    float2 ra[N], rb[N], rc[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) ra[i] = rb[i] = rc[i] = make_float2(0.0f, 0.0f);
+    if (act) {
+      float2 va[N], vb[N], vc[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        va[j] = A[xbase + j];
+        vb[j] = B[xbase + j];
+        vc[j] = C[xbase + j];
+      }
+      const float2* Gm = MS ? reinterpret_cast<const float2*>(Msm) + gq
+                            : reinterpret_cast<const float2*>(a.metric + (int64_t)b * Fs::METRIC) + gq;
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        const float2 u1 = row2<N, MAT_SD>(va, q), u2 = row2<N, MAT_S>(vb, q), u3 = row2<N, MAT_S>(vc, q);
+        float2 G00, G01, G02, G11, G12, G22;
+        if constexpr (MS != 0) {
+          G00 = Gm[(0 * N3 + q) * PP]; G01 = Gm[(1 * N3 + q) * PP]; G02 = Gm[(2 * N3 + q) * PP];
+          G11 = Gm[(3 * N3 + q) * PP]; G12 = Gm[(4 * N3 + q) * PP]; G22 = Gm[(5 * N3 + q) * PP];
+        } else {
+          G00 = __ldg(Gm + (0 * N3 + q) * PP); G01 = __ldg(Gm + (1 * N3 + q) * PP);
+          G02 = __ldg(Gm + (2 * N3 + q) * PP); G11 = __ldg(Gm + (3 * N3 + q) * PP);
+          G12 = __ldg(Gm + (4 * N3 + q) * PP); G22 = __ldg(Gm + (5 * N3 + q) * PP);
+        }
+        const float2 h1 = __ffma2_rn(G02, u3, __ffma2_rn(G01, u2, __fmul2_rn(G00, u1)));
+        const float2 h2 = __ffma2_rn(G12, u3, __ffma2_rn(G11, u2, __fmul2_rn(G01, u1)));
+        const float2 h3 = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
+        axpy_col2<N, MAT_SD>(ra, h1, q, q == 0);
+        axpy_col2<N, MAT_S>(rb, h2, q, q == 0);
+        axpy_col2<N, MAT_S>(rc, h3, q, q == 0);
+      }
+    }
+    // the x-point shared by cells 2c - 1 and 2c (pair c - 1's second cell, lane - 1) and the one
+    // shared by cells 2c and 2c + 1 (this pair): summed into the higher cell's a1 = 0 node
+    {
+      const float ua = __shfl_up_sync(0xffffffffu, ra[K].y, 1);
+      const float ub = __shfl_up_sync(0xffffffffu, rb[K].y, 1);
+      const float uc = __shfl_up_sync(0xffffffffu, rc[K].y, 1);
+      if (c > 0) {
+        ra[0].x += ua;
+        rb[0].x += ub;
+        rc[0].x += uc;
+      }
+      if (act1) {
+        ra[0].y += ra[K].x;
+        rb[0].y += rb[K].x;
+        rc[0].y += rc[K].x;
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        A[xbase + j] = ra[j];
+        B[xbase + j] = rb[j];
+        C[xbase + j] = rc[j];
+      }
+    }
+    __syncthreads();
+    // the metric buffer is free: the next batch's metric
+    if (MS) {
+      if (tma_warp && has_next) issue_metric(b + (int)gridDim.x);
+      metric_pending = has_next;
+      metric_par = (it + 1) & 1;
+    }
+    // 4) y-lines: A <- S_y^T A + Sd_y^T B, C <- S_y^T C
+    if (act45) {
+      float2 va[N], vb[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        va[j] = A[ybase + j * NP];
+        vb[j] = B[ybase + j * NP];
+      }
+      contract2_tt<N, MAT_S, MAT_SD>(va, vb, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
+#pragma unroll
+      for (int j = 0; j < N; ++j) va[j] = C[ybase + j * NP];
+      contract2_t<N, MAT_S>(va, o);
+#pragma unroll
+      for (int j = 0; j < N; ++j) C[ybase + j * NP] = o[j];
+    }
+    // the output tile was last read by the previous batch's reduce-adds
+    if (tma_warp) bulk_wait_read<0>();
+    __syncthreads();
+    // 5) z-lines: out = S_z^T A + Sd_z^T C into the output tile (Dirichlet points 0); the TMA warp
+    //    clears the points of each tile row outside the batch
+    if (act45) {
+      float2 va[N], vc[N], o[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        va[j] = A[zbase + j * P2];
+        vc[j] = C[zbase + j * P2];
+      }
+      contract2_tt<N, MAT_S, MAT_SD>(va, vc, o);
+      const bool w0 = f < K || 2 * c == m - 1;
+      const bool w1 = act1 && (f < K || 2 * c + 1 == m - 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        if (lbnd0) o[j].x = 0.0f;
+        if (lbnd1) o[j].y = 0.0f;
+      }
+      if (zlo) o[0] = make_float2(0.0f, 0.0f);
+      if (zhi) o[K] = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int g = zrow0 + a.Mx * a.My * j;
+        float* row = O + (j * N + s) * PITCH + (g & 3) + zx;
+        if (w0) row[0] = o[j].x;
+        if (w1) row[K] = o[j].y;
+      }
+    }
+    if (tma_warp) {
+      for (int row = lane; row < ROWS; row += 32) {
+        const int a2 = row % N, a3 = row / N;
+        const int off = (bi.gbase + a.Mx * (a2 + a.My * a3)) & 3;
+        float* p = O + row * PITCH;
+        for (int x = 0; x < off; ++x) p[x] = 0.0f;
+        for (int x = off + bi.Wm; x < BOX; ++x) p[x] = 0.0f;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    // reduce-add the output rows into dst (one bulk group per lane and batch)
+    if (tma_warp) {
+      for (int row = lane; row < ROWS; row += 32) {
+        const int a2 = row % N, a3 = row / N;
+        tma_reduce_add_1d(&a.tdst, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, O + row * PITCH);
+      }
+      bulk_commit();
+    }
+    batch_advance(pos, a);
+  }
+  if (tma_warp) bulk_wait_all();
+  if (failed && tma_warp && lane == 0) {
+    atomicExch(a.err, 1);
+    // drain the copies that may still be in flight before the CTA ends (bounded waits)
+    if (rows_pending) mbar_wait(&bars[0], rows_par);
+    if (MS && metric_pending) mbar_wait(&bars[1], metric_par);
+  }
+}
+
+}  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<2>();
 template int octree_pair_cells<2>();
 template mfx_status prepare_vmult_n<2>(const mfx_op*);
 template int brick_cells_candidates<2>(int*);
+template int brick_kernel_candidates<2>(int*);
 }  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<3>();
 template int octree_pair_cells<3>();
 template mfx_status prepare_vmult_n<3>(const mfx_op*);
 template int brick_cells_candidates<3>(int*);
+template int brick_kernel_candidates<3>(int*);
 }  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<4>();
 template int octree_pair_cells<4>();
 template mfx_status prepare_vmult_n<4>(const mfx_op*);
 template int brick_cells_candidates<4>(int*);
+template int brick_kernel_candidates<4>(int*);
 }  // namespace mfx

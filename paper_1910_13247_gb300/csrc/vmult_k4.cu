@@ -10,4 +10,5 @@ template int brick_cells_per_batch<5>();
 template int octree_pair_cells<5>();
 template mfx_status prepare_vmult_n<5>(const mfx_op*);
 template int brick_cells_candidates<5>(int*);
+template int brick_kernel_candidates<5>(int*);
 }  // namespace mfx

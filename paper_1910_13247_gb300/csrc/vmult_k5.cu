@@ -10,4 +10,5 @@ template int brick_cells_per_batch<6>();
 template int octree_pair_cells<6>();
 template mfx_status prepare_vmult_n<6>(const mfx_op*);
 template int brick_cells_candidates<6>(int*);
+template int brick_kernel_candidates<6>(int*);
 }  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<7>();
 template int octree_pair_cells<7>();
 template mfx_status prepare_vmult_n<7>(const mfx_op*);
 template int brick_cells_candidates<7>(int*);
+template int brick_kernel_candidates<7>(int*);
 }  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<8>();
 template int octree_pair_cells<8>();
 template mfx_status prepare_vmult_n<8>(const mfx_op*);
 template int brick_cells_candidates<8>(int*);
+template int brick_kernel_candidates<8>(int*);
 }  // namespace mfx

@@ -10,4 +10,5 @@ template int brick_cells_per_batch<9>();
 template int octree_pair_cells<9>();
 template mfx_status prepare_vmult_n<9>(const mfx_op*);
 template int brick_cells_candidates<9>(int*);
+template int brick_kernel_candidates<9>(int*);
 }  // namespace mfx

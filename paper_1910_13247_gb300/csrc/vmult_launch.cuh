@@ -13,6 +13,7 @@
 #include "vmult_brick_tma.cuh"
 #include "vmult_brick_df.cuh"
 #include "vmult_brick_tma2.cuh"
+#include "vmult_brick_f5.cuh"
 #include "vmult_octree2.cuh"
 
 namespace mfx {
@@ -24,7 +25,8 @@ int device_sm_count();
 template <int N>
 mfx_status prepare_vmult_n(const mfx_op* op) {
   for (int i = 0; i < N * N; ++i)
-    if (BasisConst<N>::S(i) != op->basis.S[i] || BasisConst<N>::D(i) != op->basis.D[i])
+    if (BasisConst<N>::S(i) != op->basis.S[i] || BasisConst<N>::D(i) != op->basis.D[i] ||
+        BasisConst<N>::Sd(i) != op->basis.Sd[i])
       return set_error(MFX_EUNSUPPORTED, "build-time basis tables differ from the run-time ones");
   return MFX_OK;
 }
@@ -248,6 +250,78 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
   return MFX_OK;
 }
 
+// The five-phase FP32 kernel (vmult_brick_f5.cuh) for degrees 1..4; MS: metric staged in shared
+// memory (1) or read from L2 at its point of use (0).
+template <int N>
+struct F5For {
+  static constexpr bool value = N >= 2 && N <= 5;
+};
+
+template <int N, int CB, int MS>
+static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  using Fs = F5Shape<N, CB, MS>;
+  using Tm = TmaShape<N, CB>;
+  // resident CTAs per SM the register budget is sized for: about 672 threads per SM, fewer when the
+  // staged metric bounds the shared memory
+  constexpr int MB0 = 672 / Fs::THREADS > 0 ? 672 / Fs::THREADS : 1;
+  constexpr int MBS = (int)((220u * 1024u) / Fs::SMEM) > 0 ? (int)((220u * 1024u) / Fs::SMEM) : 1;
+  constexpr int MB = MB0 < MBS ? MB0 : MBS;
+  static int blocks_per_sm = -1;
+  const size_t smem = Fs::SMEM;
+  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB>;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, Fs::THREADS, smem));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  if (op->metric_cb != CB) return set_error(MFX_EINVAL, "metric layout does not match the kernel");
+  TmaArgs<N> a;
+  mfx_status st = encode_1d_map(&a.tsrc, src, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  st = encode_1d_map(&a.tdst, dst, op->n_dofs, Tm::BOX);
+  if (st != MFX_OK) return st;
+  a.metric = op->d_metric32;
+  a.nx = op->nx;
+  a.ny = op->ny;
+  a.nz = op->nz;
+  a.nchunk = (op->nx + CB - 1) / CB;
+  a.Mx = op->k * op->nx + 1;
+  a.My = op->k * op->ny + 1;
+  a.Mz = op->k * op->nz + 1;
+  a.n_batches = a.nchunk * op->ny * op->nz;
+  a.err = op->d_err;
+  a.skip = skip;
+  a.dmask = op->dirichlet;
+  const int rows = a.My * a.Mz;
+  init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
+  const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
+  set_batch_steps(&a, grid);
+  kern<<<grid, Fs::THREADS, smem, s>>>(a);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+template <int N, int CB>
+static mfx_status run_brick_f32(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  if constexpr (F5For<N>::value) {
+    if (op->f32_kernel == MFX_KERNEL_FIVE_PHASE) return run_brick_f5<N, CB, 0>(op, src, dst, s, skip);
+    if (op->f32_kernel == MFX_KERNEL_FIVE_PHASE_STAGED) return run_brick_f5<N, CB, 1>(op, src, dst, s, skip);
+  }
+  return run_brick_tma2<N, CB>(op, src, dst, s, skip);
+}
+
+template <int N>
+int brick_kernel_candidates(int* out) {
+  int n = 0;
+  out[n++] = MFX_KERNEL_TEN_PHASE;
+  if (F5For<N>::value) {
+    out[n++] = MFX_KERNEL_FIVE_PHASE;
+    out[n++] = MFX_KERNEL_FIVE_PHASE_STAGED;
+  }
+  return n;
+}
+
 template <int N, int CB>
 static mfx_status run_octree_pair(const mfx_op* op, const float* src, float* dst, cudaStream_t s,
                                   const int32_t* skip) {
@@ -300,8 +374,8 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     return run_vmult<N, double>(op, (const double*)src, (double*)dst, s, skip);
   }
   if (op->structured && !op->percell32) {
-    if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_tma2<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
-    return run_brick_tma2<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
+    if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_f32<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
+    return run_brick_f32<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
   // the paired octree kernel where the FP32 metric is laid out for it (k = 1; k = 8 without hanging nodes)
   if constexpr (OctreePairFor<N>::value)

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libmfx.so")
 F64, F32 = 0, 1
 COEF_CONSTANT, COEF_TRIG, COEF_QPOINT, COEF_FUNCTION = 0, 1, 2, 3
 CONTINUOUS, SIPG = 0, 1  # discretization of an operator (mfx_op_desc.discretization)
+# FP32 vmult kernel of a structured operator at k = 1..4 (mfx_op_desc.structured_kernel)
+KERNEL_AUTO, KERNEL_TEN_PHASE, KERNEL_FIVE_PHASE, KERNEL_FIVE_PHASE_STAGED = 0, 1, 2, 3
 PRECOND_JACOBI, PRECOND_CHEBYSHEV = 0, 1
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, EMESH, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 NOT_CONVERGED, BREAKDOWN = 1, 2
@@ -41,7 +43,7 @@ class OpDesc(ctypes.Structure):
                 ("precisions", ctypes.c_int32), ("coef_par", ctypes.c_double * 2),
                 ("coef_qpoint", ctypes.c_void_p), ("cells_per_block", ctypes.c_int32),
                 ("discretization", ctypes.c_int32), ("coef_fn", POINT_FN), ("coef_user", ctypes.c_void_p),
-                ("dg_penalty", ctypes.c_double)]
+                ("dg_penalty", ctypes.c_double), ("structured_kernel", ctypes.c_int32)]
 
 
 class OpInfo(ctypes.Structure):
@@ -49,7 +51,7 @@ class OpInfo(ctypes.Structure):
                 ("n_masters", ctypes.c_int64), ("n_hanging", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
                 ("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("structured", ctypes.c_int32),
                 ("cells_per_block", ctypes.c_int32), ("discretization", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("structured_kernel", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):
@@ -315,9 +317,10 @@ class Operator:
 
     def __init__(self, mesh, degree, coef_kind=COEF_CONSTANT, coef_par=(1.0, 0.0), precisions=3,
                  coef_qpoint=None, stream=None, cells_per_block=0, coef_fn=None, discretization=CONTINUOUS,
-                 dg_penalty=1.0):
+                 dg_penalty=1.0, structured_kernel=KERNEL_AUTO):
         """discretization=SIPG: the symmetric interior penalty DG operator (uniform box, constant
-        coefficient coef_par[0], penalty eta = dg_penalty, cell-major DoFs)."""
+        coefficient coef_par[0], penalty eta = dg_penalty, cell-major DoFs).  structured_kernel: the
+        FP32 vmult kernel of a structured operator at k = 1..4 (KERNEL_*; KERNEL_AUTO: timed)."""
         d = OpDesc()
         if coef_fn is not None:  # a(x, y, z) on the host at every quadrature point
             coef_kind = COEF_FUNCTION
@@ -331,6 +334,7 @@ class Operator:
         d.cells_per_block = cells_per_block
         d.discretization = discretization
         d.dg_penalty = dg_penalty
+        d.structured_kernel = structured_kernel
         h = ctypes.c_void_p()
         check(lib().mfx_operator_create(ctypes.byref(h), mesh.handle, ctypes.byref(d), _stream(stream)))
         self.handle = h

@@ -1,0 +1,122 @@
+"""GPU parity of every FP32 vmult kernel of structured meshes against the FP64 oracle.
+
+The structured FP32 vmult has several kernels (ten-phase collocation form, five-phase form with the
+metric read at its point of use or staged in shared memory) and two compiled batch sizes per degree;
+the autotuner picks one pair per mesh.  Each is compared here, element by element, with the oracle's
+assembled condensed matrix (full quadrature, Sec. 2.4 / Sec. 3.6) on meshes whose rows of cells hold
+at least two full batches and a ragged tail, on degenerate rows of one and two cells, and with
+natural (non-Dirichlet) faces.  FP32 tolerance: 1e-5 relative, norm-wise and per entry against the
+max-norm (single-precision sums of O(100) terms give about 1e-6).
+"""
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle import mesh as omesh
+from paper_1910_13247_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DEV = "cuda:0"
+TOL32 = 1e-5
+# compiled batch sizes (cells per batch) per degree
+BATCH_SIZES = {1: (32,), 2: (16, 32), 3: (16, 8), 4: (16, 8)}
+
+
+@pytest.fixture(scope="module")
+def mfx():
+    from paper_1910_13247_gb300 import build, mfx as m
+    build.build()
+    m.lib()
+    return m
+
+
+def kernels(mfx):
+    return (mfx.KERNEL_TEN_PHASE, mfx.KERNEL_FIVE_PHASE, mfx.KERNEL_FIVE_PHASE_STAGED)
+
+
+def vmult(op, x, dtype):
+    xd = torch.tensor(x, device=DEV, dtype=dtype)
+    yd = torch.empty_like(xd)
+    op.vmult(xd, yd)
+    torch.cuda.synchronize()
+    op.device_check()
+    return yd.double().cpu().numpy()
+
+
+def errs(y, ref):
+    return np.linalg.norm(y - ref) / np.linalg.norm(ref), np.abs(y - ref).max() / np.abs(ref).max()
+
+
+def oracle_case(nx, ny, nz, k, seed, dirichlet=0x3F):
+    verts = synthetic.deformed_vertices(nx, ny, nz)
+    om = omesh.structured_mesh(nx, ny, nz, k, verts, dirichlet=dirichlet)
+    K = fem.assemble(om, k + 1, fem.COEF_TRIG, (1.0, 0.5))
+    x = synthetic.uniform_vector(om.n_dofs, seed)
+    return verts, om, K, x
+
+
+def make_op(mfx, nx, ny, nz, k, verts, cb, kern, dirichlet=0x3F):
+    m = mfx.Mesh.structured_box(nx, ny, nz, verts, dirichlet=dirichlet)
+    op = mfx.Operator(m, k, mfx.COEF_TRIG, (1.0, 0.5), cells_per_block=cb, structured_kernel=kern)
+    info = op.info()
+    assert info["cells_per_block"] == cb and info["structured_kernel"] == kern
+    return op
+
+
+@pytest.mark.parametrize("k", sorted(BATCH_SIZES))
+def test_full_batches_and_ragged_tail_every_kernel(mfx, k):
+    """Rows of 2 CB + 3 cells (two full batches and a 3-cell tail) for every compiled batch size and
+    every FP32 kernel; the FP64 vmult of the same operator is checked at 1e-12."""
+    for cb in BATCH_SIZES[k]:
+        nx, ny, nz = 2 * cb + 3, 2, 2
+        verts, om, K, x = oracle_case(nx, ny, nz, k, 500 + 10 * k + cb)
+        ref = K @ x
+        for kern in kernels(mfx):
+            op = make_op(mfx, nx, ny, nz, k, verts, cb, kern)
+            e2, einf = errs(vmult(op, x, torch.float32), ref)
+            assert e2 < TOL32 and einf < TOL32, (cb, kern, e2, einf)
+        e2, einf = errs(vmult(op, x, torch.float64), ref)
+        assert e2 < 1e-12 and einf < 1e-12, (cb, e2, einf)
+
+
+@pytest.mark.parametrize("k", sorted(BATCH_SIZES))
+@pytest.mark.parametrize("dims", [(1, 3, 2), (2, 2, 3), (5, 1, 1)])
+def test_degenerate_rows_every_kernel(mfx, k, dims):
+    """Rows of one, two and five cells: a single partial batch, pairs whose second cell is absent."""
+    verts, om, K, x = oracle_case(*dims, k, 600 + k)
+    ref = K @ x
+    for kern in kernels(mfx):
+        op = make_op(mfx, *dims, k, verts, BATCH_SIZES[k][0], kern)
+        e2, einf = errs(vmult(op, x, torch.float32), ref)
+        assert e2 < TOL32 and einf < TOL32, (dims, kern, e2, einf)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("mask", [0b000001, 0b110100, 0])
+def test_natural_faces_every_kernel(mfx, k, mask):
+    """Dirichlet on a subset of the faces (x-low only; y-low and both z faces; none): the natural faces'
+    points are free rows and take the x-point merging and the output ownership of the kernels."""
+    nx, ny, nz = 19, 3, 2
+    verts, om, K, x = oracle_case(nx, ny, nz, k, 700 + k + mask, dirichlet=mask)
+    ref = K @ x
+    for cb in BATCH_SIZES[k]:
+        for kern in kernels(mfx):
+            op = make_op(mfx, nx, ny, nz, k, verts, cb, kern, dirichlet=mask)
+            e2, einf = errs(vmult(op, x, torch.float32), ref)
+            assert e2 < TOL32 and einf < TOL32, (cb, kern, mask, e2, einf)
+
+
+def test_autotuned_choice_is_a_compiled_pair(mfx):
+    """The autotuner (no request) picks one of the compiled (batch size, kernel) pairs, and its result
+    equals the oracle's."""
+    k, (nx, ny, nz) = 4, (35, 3, 2)
+    verts, om, K, x = oracle_case(nx, ny, nz, k, 800)
+    op = mfx.Operator(mfx.Mesh.structured_box(nx, ny, nz, verts), k, mfx.COEF_TRIG, (1.0, 0.5))
+    info = op.info()
+    assert info["cells_per_block"] in BATCH_SIZES[k]
+    assert info["structured_kernel"] in kernels(mfx)
+    e2, einf = errs(vmult(op, x, torch.float32), K @ x)
+    assert e2 < TOL32 and einf < TOL32
