@@ -10,7 +10,13 @@ Everything here is the textbook definition:
 * Gauss-Lobatto: {-1, 1} and the k-1 roots of P_k', mapped to [0, 1];
 * Lagrange basis by the product formula.
 
-Roots are found by Newton's method in FP64 from Chebyshev starting points.
+Roots are found by Newton's method from Chebyshev starting points, in the
+platform's extended precision (numpy longdouble: 64- or 113-bit
+significand), and rounded to FP64 once at the end, after the affine map to
+[0, 1]: each node and point is then the FP64 number nearest to the root it
+is defined as (an FP64 Newton iteration in [-1, 1] followed by the map lost
+up to three bits near the ends of the interval).  The weights are evaluated
+from the rounded points.
 """
 import numpy as np
 
@@ -20,7 +26,9 @@ def legendre(n, t):
 
     Building block of the Gauss and Gauss-Lobatto rules of the tensor-product elements (Sec. 3.1, Sec. 3.4).
     """
-    t = np.asarray(t, dtype=np.float64)
+    t = np.asarray(t)
+    if t.dtype != np.longdouble:
+        t = t.astype(np.float64)
     p_prev = np.ones_like(t)
     if n == 0:
         return p_prev, np.zeros_like(t)
@@ -40,12 +48,18 @@ def legendre_deriv(n, t):
 
 
 def _mirror(t_low, n):
-    """Full symmetric node set on [-1, 1] from its negative half (t = 0 exact in the middle)."""
-    t = np.zeros(n)
+    """Full symmetric node set on [-1, 1] from its negative half (t = 0 exact in the middle), in the
+    precision of t_low."""
+    t = np.zeros(n, dtype=t_low.dtype)
     h = n // 2
     t[:h] = t_low[:h]
     t[n - h:] = -t_low[:h][::-1]
     return t
+
+
+def _newton_tol():
+    """Step size below which the extended-precision Newton iteration stops (a few units of its last place)."""
+    return 8 * float(np.finfo(np.longdouble).eps)
 
 
 def gauss_legendre(n):
@@ -58,19 +72,21 @@ def gauss_legendre(n):
     if n < 1:
         raise ValueError("n >= 1")
     h = n // 2
-    t = -np.cos(np.pi * (np.arange(h) + 0.75) / (n + 0.5))  # ascending guesses
+    t = -np.cos(np.pi * (np.arange(h) + 0.75) / (n + 0.5)).astype(np.longdouble)  # ascending guesses
     for _ in range(100):
         if h == 0:
             break
         dp, p = legendre_deriv(n, t)
         dt = p / dp
         t = t - dt
-        if np.max(np.abs(dt)) < 1e-16:
+        if np.max(np.abs(dt)) < _newton_tol():
             break
     t = _mirror(t, n)
-    dp, _ = legendre_deriv(n, t)
-    w = 2.0 / ((1.0 - t * t) * dp * dp)
-    return 0.5 * (t + 1.0), 0.5 * w
+    x = (0.5 * (t + 1.0)).astype(np.float64)  # one rounding, after the map to [0, 1]
+    tr = 2.0 * x - 1.0  # the rounded points in [-1, 1] (exact)
+    dp, _ = legendre_deriv(n, tr)
+    w = 2.0 / ((1.0 - tr * tr) * dp * dp)
+    return x, 0.5 * w
 
 
 def gauss_lobatto(k):
@@ -85,7 +101,7 @@ def gauss_lobatto(k):
     if k == 1:
         return np.array([0.0, 1.0])
     h = (k - 1) // 2  # interior roots in the negative half
-    t = -np.cos(np.pi * np.arange(1, h + 1) / k)
+    t = -np.cos(np.pi * np.arange(1, h + 1) / k).astype(np.longdouble)
     for _ in range(100):
         if h == 0:
             break
@@ -93,11 +109,11 @@ def gauss_lobatto(k):
         d2p = (2.0 * t * dp - k * (k + 1) * p) / (1.0 - t * t)
         dt = dp / d2p
         t = t - dt
-        if np.max(np.abs(dt)) < 1e-16:
+        if np.max(np.abs(dt)) < _newton_tol():
             break
     interior = _mirror(t, k - 1)
-    nodes = np.concatenate(([-1.0], interior, [1.0]))
-    return 0.5 * (nodes + 1.0)
+    nodes = np.concatenate((np.array([-1.0], dtype=np.longdouble), interior, np.array([1.0], dtype=np.longdouble)))
+    return (0.5 * (nodes + 1.0)).astype(np.float64)  # one rounding, after the map to [0, 1]
 
 
 def lagrange(nodes, j, x):

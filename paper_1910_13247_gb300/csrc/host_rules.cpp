@@ -2,22 +2,28 @@
 //
 // Gauss-Legendre points are the roots of P_n; Gauss-Lobatto nodes are
 // {0, 1} and the roots of P_k'.  Both are found by Newton's method from
-// Chebyshev-type starting values; only the lower half is iterated and the
-// upper half is its mirror image, so the rules are exactly symmetric and an
-// odd-count middle node is exactly 1/2 (Sec. 3.4: tensor-product Lagrange
-// elements and Gauss quadrature).
+// Chebyshev-type starting values on [-1, 1]; only the lower half is iterated
+// and the upper half is its mirror image, and an odd-count middle node is
+// exactly 1/2 (Sec. 3.4: tensor-product Lagrange elements and Gauss
+// quadrature).  The iteration runs in long double (64- or 113-bit
+// significand) and each point is rounded to double once, after the affine map
+// to [0, 1], so it is the double nearest to the root it is defined as (a
+// double-precision iteration followed by the map loses up to three bits near
+// the ends of the interval).  Weights are evaluated at the rounded points.
 #include <cmath>
+#include <limits>
 
 #include "mfx_internal.h"
 
 namespace mfx {
 
 // P_n(t) and P_{n-1}(t) by Bonnet's recurrence.
-static void legendre(int n, double t, double* p, double* pm1) {
-  double a = 1.0, b = t;
-  if (n == 0) { *p = 1.0; *pm1 = 0.0; return; }
+template <typename R>
+static void legendre(int n, R t, R* p, R* pm1) {
+  R a = 1, b = t;
+  if (n == 0) { *p = 1; *pm1 = 0; return; }
   for (int m = 2; m <= n; ++m) {
-    double c = ((2 * m - 1) * t * b - (m - 1) * a) / m;
+    R c = ((2 * m - 1) * t * b - (m - 1) * a) / m;
     a = b;
     b = c;
   }
@@ -25,55 +31,59 @@ static void legendre(int n, double t, double* p, double* pm1) {
   *pm1 = a;
 }
 
+// Newton steps stop below a few units in the last place of long double
+static const long double kNewtonTol = 8 * std::numeric_limits<long double>::epsilon();
+
 void gauss_legendre(int n, double* x, double* w) {
   const double pi = 3.14159265358979323846;
-  double t[kMaxN * 2];
+  long double t[kMaxN * 2];
   int h = n / 2;
   for (int i = 0; i < h; ++i) {
-    double r = -std::cos(pi * (i + 0.75) / (n + 0.5));
+    long double r = -std::cos(pi * (i + 0.75) / (n + 0.5));
     for (int it = 0; it < 100; ++it) {
-      double p, pm;
-      legendre(n, r, &p, &pm);
-      double dp = n * (r * p - pm) / (r * r - 1.0);
-      double dr = p / dp;
+      long double p, pm;
+      legendre<long double>(n, r, &p, &pm);
+      long double dp = n * (r * p - pm) / (r * r - 1);
+      long double dr = p / dp;
       r -= dr;
-      if (std::fabs(dr) < 1e-16) break;
+      if (std::fabs(dr) < kNewtonTol) break;
     }
     t[i] = r;
     t[n - 1 - i] = -r;
   }
-  if (n % 2) t[h] = 0.0;
+  if (n % 2) t[h] = 0;
   for (int i = 0; i < n; ++i) {
+    x[i] = (double)(0.5L * (t[i] + 1));  // one rounding, after the map to [0, 1]
+    const double tr = 2.0 * x[i] - 1.0;  // the rounded point in [-1, 1] (exact)
     double p, pm;
-    legendre(n, t[i], &p, &pm);
-    double dp = n * (t[i] * p - pm) / (t[i] * t[i] - 1.0);
-    x[i] = 0.5 * (t[i] + 1.0);
-    w[i] = 0.5 * (2.0 / ((1.0 - t[i] * t[i]) * dp * dp));
+    legendre<double>(n, tr, &p, &pm);
+    double dp = n * (tr * p - pm) / (tr * tr - 1.0);
+    w[i] = 0.5 * (2.0 / ((1.0 - tr * tr) * dp * dp));
   }
 }
 
 void gauss_lobatto(int k, double* x) {
   const double pi = 3.14159265358979323846;
-  double t[kMaxN * 2];
-  t[0] = -1.0;
-  t[k] = 1.0;
+  long double t[kMaxN * 2];
+  t[0] = -1;
+  t[k] = 1;
   int interior = k - 1, h = interior / 2;
   for (int j = 0; j < h; ++j) {
-    double r = -std::cos(pi * (j + 1) / k);
+    long double r = -std::cos(pi * (j + 1) / k);
     for (int it = 0; it < 100; ++it) {
-      double p, pm;
-      legendre(k, r, &p, &pm);
-      double dp = k * (r * p - pm) / (r * r - 1.0);
-      double d2p = (2.0 * r * dp - k * (k + 1) * p) / (1.0 - r * r);
-      double dr = dp / d2p;
+      long double p, pm;
+      legendre<long double>(k, r, &p, &pm);
+      long double dp = k * (r * p - pm) / (r * r - 1);
+      long double d2p = (2 * r * dp - k * (k + 1) * p) / (1 - r * r);
+      long double dr = dp / d2p;
       r -= dr;
-      if (std::fabs(dr) < 1e-16) break;
+      if (std::fabs(dr) < kNewtonTol) break;
     }
     t[1 + j] = r;
     t[k - 1 - j] = -r;
   }
-  if (interior % 2) t[1 + h] = 0.0;
-  for (int i = 0; i <= k; ++i) x[i] = 0.5 * (t[i] + 1.0);
+  if (interior % 2) t[1 + h] = 0;
+  for (int i = 0; i <= k; ++i) x[i] = (double)(0.5L * (t[i] + 1));  // one rounding, after the map
 }
 
 double lagrange_value(int n, const double* nodes, int j, double x) {

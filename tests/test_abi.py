@@ -55,13 +55,35 @@ def test_structured_tables_bit_exact(k):
     assert np.array_equal(T["cptr"], om.cptr)
 
 
-@pytest.mark.parametrize("seed,nb,levels", [(0, 4, 2), (1, 4, 2), (2, 3, 1), (3, 4, 3)])
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
-def test_octree_tables_bit_exact(seed, nb, levels, k):
-    if levels == 3 and k > 3:
-        pytest.skip("oracle tables take long at this size")
+# octrees: (seed, coarse cells per direction, refinement levels, ball centre or None = seeded, radius or None)
+OCTREES = {
+    "seeded4x2a": (0, 4, 2, None, None), "seeded4x2b": (1, 4, 2, None, None), "seeded3x1": (2, 3, 1, None, None),
+    "seeded4x3": (3, 4, 3, None, None),
+    # small meshes that the oracle tabulates in seconds at every degree
+    "seeded2x2": (5, 2, 2, None, 0.3),
+    # three levels (leaves on levels 0..3): a ball around nested cell centres of levels 0, 1 and 2
+    "nested2x3": (0, 2, 3, (0.3125, 0.3125, 0.3125), 0.12),
+}
+OCTREE_CASES = ([(k, c) for k in range(1, 6) for c in ("seeded4x2a", "seeded4x2b", "seeded3x1")] +
+                [(k, "seeded4x3") for k in (1, 2, 3)] + [(k, "seeded2x2") for k in (6, 7, 8)] +
+                [(k, "nested2x3") for k in range(1, 9)])
+
+
+def octree_case(name):
+    seed, nb, levels, centre, radius = OCTREES[name]
     g = synthetic.rng(100 + seed)
-    leaves = synthetic.octree_leaves(nb, levels, g.uniform(0.25, 0.75, 3), float(g.uniform(0.15, 0.35)))
+    c, r = g.uniform(0.25, 0.75, 3), float(g.uniform(0.15, 0.35))
+    leaves = synthetic.octree_leaves(nb, levels, np.asarray(centre) if centre else c, radius if radius else r)
+    return nb, leaves
+
+
+@pytest.mark.parametrize("k,case", OCTREE_CASES)
+def test_octree_tables_bit_exact(k, case):
+    """DoF numbering, constrained DoFs, constraint rows, masters and weights of octree meshes (1-3 levels of
+    refinement, hanging faces and edges, Dirichlet faces) equal the oracle's bit for bit at every degree."""
+    nb, leaves = octree_case(case)
+    if case == "nested2x3":
+        assert set(leaves[:, 0]) == {0, 1, 2, 3}
     T = mfx.Mesh.octree(nb, nb, nb, leaves).tables(k)
     om = omesh.octree_mesh(nb, nb, nb, k, leaves)
     assert T["n_dofs"] == om.n_dofs

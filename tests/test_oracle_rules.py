@@ -92,3 +92,22 @@ def test_lagrange_rational_k2():
         for j in range(3):
             assert abs(rules.lagrange(nodes, j, x) - float(ref[j])) < 1e-15
             assert abs(rules.lagrange_deriv(nodes, j, x) - float(dref[j])) < 1e-14
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_nodes_and_points_are_the_correctly_rounded_roots(k):
+    """Each GLL node and Gauss point is the FP64 number nearest to the root that defines it (interior
+    GLL nodes: roots of P_k'; Gauss points: roots of P_{k+1}; both mapped to [0, 1]), checked against
+    roots computed independently to 50 digits.  Equal nodes on both sides of the parity tests rest on this."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    nodes = rules.gauss_lobatto(k)
+    assert nodes[0] == 0.0 and nodes[-1] == 1.0
+    for i in range(1, k):
+        r = mp.findroot(lambda t: mp.diff(lambda s: mp.legendre(k, s), t), 2 * mp.mpf(nodes[i]) - 1)
+        assert float((r + 1) / 2) == nodes[i], (k, i)
+    n = k + 1
+    x, _ = rules.gauss_legendre(n)
+    for i in range(n):
+        r = mp.findroot(lambda t: mp.legendre(n, t), 2 * mp.mpf(x[i]) - 1)
+        assert float((r + 1) / 2) == x[i], (n, i)
