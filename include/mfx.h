@@ -72,9 +72,9 @@ typedef struct mfx_mesh mfx_mesh;
 typedef struct mfx_op mfx_op;
 typedef void* mfx_stream; /* cudaStream_t */
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  No counterpart in the paper. */
 const char* mfx_last_error(void);
-/* Library version string. */
+/* Library version string (static storage).  No counterpart in the paper. */
 const char* mfx_version(void);
 
 /*
@@ -115,6 +115,8 @@ void mfx_mesh_destroy(mfx_mesh* mesh);
  * constrained set (and with it the tables, the identity rows of the operator and the diagonal)
  * follows the mask; operators built earlier keep theirs.  A DoF on several faces is Dirichlet if
  * any of them is.  With no Dirichlet face the operator is singular (constants are in its kernel).
+ * The Dirichlet constraints are those of Sec. 3.3 (constrained DoFs with no masters), the natural
+ * faces the boundary term that the weak form of Eq. 1 (Sec. 2.4) drops.
  * Errors: MFX_EINVAL (null mesh, faces > 0x3F).
  */
 enum { MFX_FACE_X0 = 1, MFX_FACE_X1 = 2, MFX_FACE_Y0 = 4, MFX_FACE_Y1 = 8, MFX_FACE_Z0 = 16,
@@ -134,14 +136,16 @@ mfx_status mfx_mesh_transform(mfx_mesh* mesh, mfx_map_fn phi, void* user);
 
 /*
  * Host-only (no GPU needed): sizes of the DoF and constraint tables of the
- * mesh at degree k (numbering and constraint rules as described above).
+ * mesh at degree k (numbering and constraint rules as described above: the
+ * DoF enumeration of Sec. 3.1 / Sec. 3.4 and the constraints of Sec. 3.3).
  * Any output pointer may be NULL.
+ * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k out of 1..8), MFX_EMESH.
  */
 mfx_status mfx_mesh_table_sizes(const mfx_mesh* mesh, int32_t degree, int64_t* n_cells, int64_t* n_dofs,
                                 int64_t* n_constrained, int64_t* n_masters);
 
 /*
- * Host-only: the tables themselves, laid out as for mfx_get_tables below
+ * Host-only: the tables themselves (Sec. 3.1, Sec. 3.3), laid out as for mfx_get_tables below
  * (caller-allocated host arrays of the sizes above; NULL skips a table).
  * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k out of 1..8), MFX_EMESH.
  */
@@ -225,13 +229,16 @@ enum { MFX_CONTINUOUS = 0, MFX_SIPG = 1 };
  * per-quadrature-point geometry on the device in FP64 (Jacobian of the Q1
  * map, det J, J^-1, coefficient at the physical point) merged into the
  * symmetric 3x3 metric a |det J| w_q J^-1 J^-T (plus an FP32 copy), and the
- * diagonal of the operator.  Synchronises the stream.
+ * diagonal of the operator.  This is the set-up of the matrix-free operator of
+ * Sec. 3.6 (geometry precomputed at the quadrature points) for the mesh,
+ * element, mapping and quadrature of Sec. 3.4.  Synchronises the stream.
  * Errors: MFX_EINVAL, MFX_EUNSUPPORTED (k > 8, n_q != k+1), MFX_EMESH,
  * MFX_ENOMEM, MFX_ECUDA.
  */
 mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_desc* desc,
                                mfx_stream stream);
-/* Frees the operator after waiting for all work on the device (safe whatever is still queued). */
+/* Frees the operator after waiting for all work on the device (safe whatever is still queued).
+ * No counterpart in the paper. */
 void mfx_operator_destroy(mfx_op* op);
 /*
  * Frees the operator without waiting for the device: its memory (and its solver workspace) is
@@ -258,13 +265,25 @@ typedef struct {
   int32_t structured_kernel; /* MFX_KERNEL_* of the FP32 structured vmult (0 where none applies) */
 } mfx_op_info;
 
+/*
+ * Sizes and layout of an operator: the DoF count of the Q_k space on the mesh
+ * (Sec. 3.1 and Sec. 3.4), the cells, the constrained DoFs and constraint
+ * entries of the hanging-node and Dirichlet constraints (Sec. 3.3), the
+ * device bytes, and the chosen batch size and FP32 kernel (the last three
+ * have no counterpart in the paper).  Errors: MFX_EINVAL (null argument).
+ */
 mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info);
 
 /*
- * Host copies of the integer and constraint tables (for bit-exact checks).
+ * Host copies of the integer and constraint tables (for bit-exact checks):
+ * the enumeration of the DoFs of each cell (Sec. 3.1, Sec. 3.4) and the
+ * constraints of hanging nodes and Dirichlet boundaries (Sec. 3.3, Fig. 2:
+ * each constrained DoF a weighted sum of masters, Dirichlet DoFs none).
  * cell_dofs: n_cells x (k+1)^3 (local i1 + n (i2 + n i3)); constrained:
  * n_constrained sorted DoFs; cptr: n_constrained + 1; cmaster, cweight:
- * n_masters.  Any pointer may be NULL to skip that table.
+ * n_masters.  Any pointer may be NULL to skip that table.  Caller-owned host
+ * arrays of those sizes (mfx_operator_info gives them).  Synchronous.
+ * Errors: MFX_EINVAL (null operator).
  */
 mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constrained, int64_t* cptr,
                           int32_t* cmaster, double* cweight);
@@ -294,7 +313,8 @@ mfx_status mfx_vmult_host(const mfx_op* op, mfx_prec prec, int32_t count, const 
 /*
  * Synchronise the stream and report device-side failures of this operator's
  * kernels: MFX_ETIMEOUT if a bounded wait inside a kernel ran out (the word
- * is then cleared), MFX_ECUDA for a CUDA error, else MFX_OK.
+ * is then cleared), MFX_ECUDA for a CUDA error, else MFX_OK.  No counterpart
+ * in the paper (failure detection of this library's kernels).
  */
 mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream);
 
@@ -305,13 +325,14 @@ mfx_status mfx_device_check(const mfx_op* op, mfx_stream stream);
  * that the TMA kernels use.  The wait runs out, the kernel sets the
  * operator's error word and returns; the next mfx_device_check on the
  * stream reports MFX_ETIMEOUT (and clears the word), and the operator stays
- * usable.  Asynchronous on stream.  Errors: MFX_EINVAL (null operator),
- * MFX_ECUDA.
+ * usable.  Asynchronous on stream.  No counterpart in the paper.
+ * Errors: MFX_EINVAL (null operator), MFX_ECUDA.
  */
 mfx_status mfx_selftest_bounded_wait(const mfx_op* op, mfx_stream stream);
 
 /*
- * Checked mode (in place of a memory checker).  Index tables as the
+ * Checked mode (in place of a memory checker; no counterpart in the paper; the
+ * tables are those of Sec. 3.1 and Sec. 3.3).  Index tables as the
  * per-cell kernels read them, all device arrays:
  *   cell_dofs  n_cells x nodes_1d^3 codes: a DoF in [0, n_dofs), or -1 - r
  *              for constraint row r in [0, n_rows);
@@ -353,10 +374,21 @@ typedef struct {
 mfx_status mfx_validate_tables(const mfx_index_tables* tables, int64_t* n_bad, mfx_stream stream);
 mfx_status mfx_operator_validate(const mfx_op* op, int64_t* n_bad, mfx_stream stream);
 
-/* diag = diagonal of K (1 on constrained rows), device, n_dofs entries. */
+/*
+ * diag = diagonal of K (1 on constrained rows), device, n_dofs entries of the
+ * precision: the Jacobi preconditioner of the CG solve and the diagonal of
+ * the Chebyshev smoother (Sec. 3.5, Sec. 6.1), computed in FP64 when the
+ * operator is created.  Asynchronous on stream.
+ * Errors: MFX_EINVAL (null, precision not built).
+ */
 mfx_status mfx_diagonal(const mfx_op* op, mfx_prec prec, void* diag, mfx_stream stream);
 
-/* Physical quadrature points, device, n_cells x n_q^3 x 3 doubles. */
+/*
+ * Physical quadrature points (the mapping of Sec. 3.4 applied to the tensor
+ * Gauss points of each cell), device, n_cells x n_q^3 x 3 doubles, q = q1 +
+ * n_q (q2 + n_q q3), caller-allocated.  Asynchronous on stream.
+ * Errors: MFX_EINVAL (null argument).
+ */
 mfx_status mfx_quadrature_points(const mfx_op* op, double* xq, mfx_stream stream);
 
 /*
@@ -374,8 +406,9 @@ mfx_status mfx_rhs(const mfx_op* op, const double* fq, double* b, mfx_stream str
 mfx_status mfx_rhs_function(const mfx_op* op, mfx_point_fn f, void* user, double* b, mfx_stream stream);
 
 /*
- * Fill constrained entries of x (device, FP64) from the free ones: hanging
- * DoFs get their weighted masters, Dirichlet DoFs 0.
+ * Fill constrained entries of x (device, FP64, n_dofs) from the free ones:
+ * hanging DoFs get their weighted masters (the constraint rows of Sec. 3.3),
+ * Dirichlet DoFs 0.  Asynchronous on stream.  Errors: MFX_EINVAL (null).
  */
 mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream);
 
@@ -383,19 +416,23 @@ mfx_status mfx_distribute(const mfx_op* op, double* x, mfx_stream stream);
 
 /*
  * result[0] = sum_i a_i b_i, accumulated in FP64 in a fixed order (device
- * scalar).  a, b: device vectors of n entries of the precision.  The
+ * scalar): the inner products of the CG solve with the multigrid or
+ * Chebyshev preconditioner and of the double-precision correction (Sec.
+ * 6.1).  a, b: device vectors of n entries of the precision.  The
  * reduction partials live in scratch memory owned by the operator, so
  * calls on one operator must not overlap on the GPU.
+ * Errors: MFX_EINVAL (null, n < 0).
  */
 mfx_status mfx_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, const void* b,
                    double* result, mfx_stream stream);
 
 /*
- * Allocation-free variant of mfx_dot (the paper has no counterpart: this is an
- * interface for callers that may not allocate device memory, such as code running
- * during CUDA graph capture or inside another runtime's memory pool).  Same result
- * as mfx_dot, without an operator: the reduction partials live in a fixed array of
- * about 8 KB compiled into the library (kept on every GPU that loads it until exit).
+ * Allocation-free variant of mfx_dot (the paper has no counterpart).  It serves
+ * callers that cannot call cudaMalloc: a plug-in whose host application owns all
+ * device memory, code that runs inside another runtime's memory pool, or a loop
+ * that must not block on the allocator.  Same result as mfx_dot, without an
+ * operator: the reduction partials live in a fixed array of about 8 KB compiled
+ * into the library (kept on every GPU that loads it until exit).
  * a, b: device vectors of n entries of the precision; result: device FP64 scalar.
  * n above MFX_NOALLOC_MAX_N is rejected with MFX_EINVAL.  The first call on a device
  * looks up the array's address; make it before any stream capture.  Calls share the
@@ -444,7 +481,7 @@ typedef struct {
   double seconds;        /* wall time of the call (mfx_solve, mfx_mg_solve)         */
 } mfx_solve_stats;
 
-/* Fill params with the defaults listed above. */
+/* Fill params with the defaults listed above (this library's choices; the paper states none). */
 void mfx_solve_params_default(mfx_solve_params* params);
 
 /*
@@ -470,6 +507,10 @@ mfx_status mfx_solve(const mfx_op* op, const double* b, double* x, const mfx_sol
  * (the slots' kernels overlap on the GPU), then bookkeeping.  Problems may be
  * added and released between ticks.  x0 = 0; stopping rules as mfx_solve.
  * An operator may be in one active slot at a time (else MFX_EBUSY).
+ * No counterpart in the paper: batching is this library's; each slot's solve
+ * is the mixed-precision or FP64 solve of mfx_solve (Sec. 6.1).
+ * Errors of every mfx_batch_* call: MFX_EINVAL (null, bad slot or size),
+ * MFX_EBUSY, MFX_ENOMEM, MFX_ECUDA.
  */
 typedef struct mfx_batch mfx_batch;
 mfx_status mfx_batch_create(mfx_batch** out, int32_t max_slots, int32_t chunk);
@@ -531,21 +572,30 @@ typedef struct {
   int32_t lanczos_steps;    /* steps of the eigenvalue estimate per level (15)       */
   int32_t reserved;
 } mfx_mg_params;
+/* Defaults of the hierarchy: Chebyshev degree 6 on every level as in Sec. 6.1; range 20 and 15
+ * Lanczos steps are this library's readings (the paper states neither). */
 void mfx_mg_params_default(mfx_mg_params* params);
+/* Builds the hierarchy above (Sec. 3.5, Sec. 6.1); synchronises the stream. */
 mfx_status mfx_mg_create(mfx_mg** out, const mfx_mesh* mesh, const mfx_op_desc* desc, const mfx_mg_params* params,
                          mfx_stream stream);
+/* Frees the hierarchy and its level operators after waiting for the device (no counterpart in the paper). */
 void mfx_mg_destroy(mfx_mg* mg);
-/* Number of levels and free DoFs of the coarsest level. */
+/* Number of levels and free DoFs of the coarsest level (the coarse solve of Sec. 3.5).
+ * Errors: MFX_EINVAL (null argument). */
 mfx_status mfx_mg_info(const mfx_mg* mg, int32_t* n_levels, int32_t* coarse_free_dofs);
-/* The operator of a level (0 = coarsest, n_levels - 1 = the given mesh); owned by the hierarchy. */
+/* The operator of a level (0 = coarsest, n_levels - 1 = the given mesh) of the level hierarchy of Sec. 3.5;
+ * owned by the hierarchy; NULL for a level out of range. */
 const mfx_op* mfx_mg_operator(const mfx_mg* mg, int32_t level);
-/* Chebyshev interval of a level's smoother (levels >= 1); set replaces the Lanczos-based one. */
+/* Chebyshev interval of a level's smoother (levels >= 1; the Chebyshev smoothing of Sec. 3.5 and Sec. 6.1);
+ * set replaces the Lanczos-based one.  Errors: MFX_EINVAL (null, level out of range, lo >= hi). */
 mfx_status mfx_mg_get_bounds(const mfx_mg* mg, int32_t level, double* lo, double* hi);
 mfx_status mfx_mg_set_bounds(mfx_mg* mg, int32_t level, double lo, double hi);
-/* z = V(r) on the finest level (device vectors of its precision, not aliased); asynchronous. */
+/* z = V(r) on the finest level, the V-cycle of Sec. 3.5 and Sec. 6.1 (device vectors of its precision,
+ * not aliased); asynchronous.  Errors: MFX_EINVAL (null, precision not built), MFX_ECUDA. */
 mfx_status mfx_mg_vcycle(mfx_mg* mg, mfx_prec prec, const void* r, void* z, mfx_stream stream);
-/* mfx_solve on the finest operator with the V-cycle as preconditioner (params.precond is ignored;
- * mixed = 1: FP32 PCG with the FP32 V-cycle inside FP64 defect correction). */
+/* mfx_solve on the finest operator with the V-cycle as preconditioner, the solver of Sec. 6.1
+ * (params.precond is ignored; mixed = 1: FP32 PCG with the FP32 V-cycle inside FP64 defect correction,
+ * the single-precision cycle with a double-precision correction of Sec. 6.1). */
 mfx_status mfx_mg_solve(mfx_mg* mg, const double* b, double* x, const mfx_solve_params* params,
                         mfx_solve_stats* stats, mfx_stream stream);
 
@@ -621,7 +671,9 @@ typedef struct {
   double now;                      /* seconds since creation                     */
 } mfx_server_stats;
 
-/* Errors: MFX_EINVAL (bad config), MFX_ENOMEM, MFX_ECUDA. */
+/* The mfx_server_* calls have no counterpart in the paper (see above); each request's solve is
+ * that of mfx_solve (Sec. 6.1) on an octree mesh with hanging nodes (Sec. 3.3).
+ * Errors: MFX_EINVAL (bad config), MFX_ENOMEM, MFX_ECUDA. */
 mfx_status mfx_server_create(mfx_server** out, const mfx_server_config* config);
 /* Cancels what is queued, waits for running and set-up work, frees everything. */
 void mfx_server_destroy(mfx_server* server);
@@ -640,6 +692,7 @@ mfx_status mfx_server_operator(mfx_server* server, int64_t ticket, const mfx_op*
 /* Free a finished (done, cancelled or failed) request's device data and forget the ticket.
  * Errors: MFX_EINVAL (unknown ticket), MFX_EBUSY (still queued, in set-up or running). */
 mfx_status mfx_server_retire(mfx_server* server, int64_t ticket);
+/* Counters of the server so far.  Errors: MFX_EINVAL (null argument). */
 mfx_status mfx_server_stats_get(mfx_server* server, mfx_server_stats* stats);
 
 #ifdef __cplusplus

@@ -1,8 +1,9 @@
 // mfx_dot_noalloc: the FP64-accumulated dot product of mfx_dot for callers that cannot
-// allocate device memory.  Some callers may not call cudaMalloc at all: code that runs while
-// a CUDA graph is being captured (allocation calls are not capturable), and host code that
-// lives inside another runtime's memory budget, where every device byte must come from that
-// runtime's pool.  mfx_dot keeps its reduction partials in memory owned by an operator; this
+// allocate device memory.  Some callers may not call cudaMalloc at all: a plug-in whose host
+// application owns every device byte and hands out only the buffers it works on, host code
+// that lives inside another runtime's memory budget, where every device byte must come from
+// that runtime's pool, and loops that must not block on the allocator (cudaMalloc may
+// synchronise the device).  mfx_dot keeps its reduction partials in memory owned by an operator; this
 // variant keeps them in a fixed array compiled into the library instead, so it needs neither
 // an operator nor an allocation.
 //

@@ -91,18 +91,22 @@ void free_request(mfx_server* s, Req& q) {
 }
 
 // Runs on a set-up thread: mesh (octree description), operator, workspace, b, x.
+// Every resource a set-up makes is owned by q (operator, vectors; freed by free_request when the
+// set-up fails, whether by a status or a host exception) or by a local RAII owner (the mesh).
 mfx_status setup_request(Req& q, cudaStream_t st, std::vector<double>& hb) {
-  mfx_mesh* own = nullptr;
+  std::unique_ptr<mfx_mesh, void (*)(mfx_mesh*)> own(nullptr, mfx_mesh_destroy);
   const mfx_mesh* mesh = q.r.mesh;
   if (!mesh) {
-    mfx_status rc = mfx_mesh_create_octree(&own, q.r.nx, q.r.ny, q.r.nz, q.verts.empty() ? nullptr : q.verts.data(),
+    mfx_mesh* m = nullptr;
+    mfx_status rc = mfx_mesh_create_octree(&m, q.r.nx, q.r.ny, q.r.nz, q.verts.empty() ? nullptr : q.verts.data(),
                                            q.leaves.data(), (int64_t)q.leaves.size() / 4);
     if (rc != MFX_OK) return rc;
-    mesh = own;
+    own.reset(m);
+    mesh = m;
   }
   mfx_op* op = nullptr;
   mfx_status rc = mfx_operator_create(&op, mesh, &q.r.desc, (mfx_stream)st);
-  if (own) mfx_mesh_destroy(own);
+  own.reset();
   if (rc != MFX_OK) return rc;
   q.op = op;
   rc = mfx_solver_prepare(op);

@@ -1,8 +1,8 @@
 """The allocation-free dot product (mfx_dot_noalloc) against the regular one (mfx_dot).
 
-mfx_dot_noalloc exists for callers that may not allocate device memory (code running
-during CUDA graph capture, or inside another runtime's memory pool): it keeps its
-reduction partials in a fixed array compiled into the library.  This file is collected
+mfx_dot_noalloc exists for callers that may not allocate device memory (a plug-in whose
+host application owns all device memory, or code inside another runtime's memory pool):
+it keeps its reduction partials in a fixed array compiled into the library.  This file is collected
 last so that a failure here cannot hide any other test's result.
 """
 import numpy as np
