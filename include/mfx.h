@@ -599,6 +599,76 @@ mfx_status mfx_mg_vcycle(mfx_mg* mg, mfx_prec prec, const void* r, void* z, mfx_
 mfx_status mfx_mg_solve(mfx_mg* mg, const double* b, double* x, const mfx_solve_params* params,
                         mfx_solve_stats* stats, mfx_stream stream);
 
+/* ------------------------------------------------------------- partitions */
+
+/*
+ * Partitioned operator (the distributed path of Sec. 2.6 and Sec. 3.7: one part of the mesh per GPU,
+ * each adding its neighbours' contributions on the DoFs they share).  A structured box of nx x ny x nz
+ * cells is split into n_parts slabs of whole cells along z (part p gets nz / n_parts cells, one more
+ * for the first nz % n_parts parts).  Part p's lattice is a contiguous slice of the global DoF vector,
+ * entries dof0 .. dof0 + n_dofs - 1; its first `plane` entries are shared with part p - 1 (has_lo) and
+ * its last `plane` entries with part p + 1 (has_hi).  Build the part's operator from
+ * mfx_mesh_create_structured(nx, ny, nz_part, global_vertices + 3 * vertex0) with Dirichlet faces
+ * `dirichlet` (the global mask without the interface faces, which are natural on the part).  On a
+ * shared DoF each part's vmult then gives its own cells' contribution; adding the neighbour's
+ * (mfx_halo_accumulate) gives the global operator's row.  A part owns its lattice without its upper
+ * shared plane (n_owned entries, a prefix of the slice), so sums over the owned entries of all parts
+ * count every DoF once.  Host-only, no GPU needed.
+ * Errors: MFX_EINVAL (null info, empty box, n_parts outside 1..nz, part outside 0..n_parts - 1, mask
+ * above 0x3F), MFX_EUNSUPPORTED (degree outside 1..8).
+ */
+typedef struct {
+  int32_t cz0, nz;          /* the part's cells along z: cz0 .. cz0 + nz - 1                  */
+  uint32_t dirichlet;       /* Dirichlet faces of the part's box                              */
+  int32_t has_lo, has_hi;   /* a neighbour below / above                                      */
+  int32_t reserved;
+  int64_t dof0, n_dofs;     /* the part's lattice in the global DoF vector                   */
+  int64_t n_owned;          /* owned DoFs: the first n_owned entries of the part's lattice    */
+  int64_t plane;            /* DoFs of one shared lattice plane ((k nx + 1)(k ny + 1))       */
+  int64_t vertex0;          /* index of the part's first vertex in the global vertex lattice  */
+} mfx_part_info;
+mfx_status mfx_partition_box(int32_t nx, int32_t ny, int32_t nz, int32_t degree, uint32_t dirichlet, int32_t n_parts,
+                             int32_t part, mfx_part_info* info);
+
+/*
+ * The exchange step of the partitioned vmult: y's shared plane on `side` (0: the first `plane` entries,
+ * below; 1: the last `plane` entries, above) += recv, except on Dirichlet points of the plane (identity
+ * rows on both parts).  recv: device, plane entries of the precision (the neighbour's partial plane of
+ * its vmult); y: device, the part's vmult result.  Structured continuous operators only.  Asynchronous.
+ * Errors: MFX_EINVAL (null, side not 0 or 1, unknown precision), MFX_EUNSUPPORTED, MFX_ECUDA.
+ */
+mfx_status mfx_halo_accumulate(const mfx_op* op, mfx_prec prec, int32_t side, const void* recv, void* y,
+                               mfx_stream stream);
+
+/*
+ * Communication of a partitioned solve, supplied by the caller (NCCL, MPI, a host-side coupler, ...):
+ * send[d], recv[d] are caller-owned device buffers of `plane` FP64 entries for side d (0 below, 1
+ * above; NULL where the part has no neighbour).  exchange(user): send[d] to the neighbour on side d,
+ * its partial plane into recv[d], for every side with a neighbour; called with the stream
+ * synchronised, returns 0 on success.  allreduce(user, vals, n): vals[0 .. n) summed over all parts,
+ * in place (host doubles), returns 0 on success.  Every part makes the same sequence of calls.
+ */
+typedef struct {
+  void* send[2];
+  void* recv[2];
+  int32_t (*exchange)(void* user);
+  int32_t (*allreduce)(void* user, double* vals, int32_t n);
+  void* user;
+} mfx_comm;
+
+/*
+ * Jacobi-preconditioned CG on the partitioned operator (FP64; the solve of Sec. 6.1 in the distributed
+ * form of Sec. 2.6): every vmult is followed by the exchange; the diagonal is exchanged once; each
+ * iteration makes two allreduces, (p, Kp) and then (r, z) with (r, r) together, over owned DoFs.  b, x:
+ * device FP64, the part's slice of the global vectors (b equal on both copies of a shared DoF); x0 = 0;
+ * stopping rule and statuses as mfx_solve (params.tol, params.max_it; other fields ignored).  The host
+ * drives the loop (the callbacks are host calls).  Synchronises the stream.
+ * Errors: MFX_EINVAL (null, a description that does not match the operator, a missing buffer, a
+ * callback that failed), MFX_EUNSUPPORTED (not structured continuous FP64), MFX_ECUDA.
+ */
+mfx_status mfx_solve_partitioned(const mfx_op* op, const mfx_part_info* part, const mfx_comm* comm, const double* b,
+                                 double* x, const mfx_solve_params* params, mfx_solve_stats* stats, mfx_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /*

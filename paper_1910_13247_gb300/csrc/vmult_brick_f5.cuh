@@ -33,18 +33,21 @@
 
 namespace mfx {
 
-template <int N, int CB, int MS>
+template <int N, int CB, int MS, int TB = 1, int MBF = 1>
 struct F5Shape {
   static constexpr int PP = CB / 2;
   static constexpr int LINES = PP * N * N;
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int CUBES = PP * BrickShape<N, CB, float>::CELL;  // float2 elements per cube
   static constexpr int METRIC = 6 * N * N * N * CB;                  // floats of one batch's metric
-  static constexpr size_t SMEM = (size_t)2 * TmaShape<N, CB>::TILE * sizeof(float) +
-                                 (MS ? (size_t)METRIC * sizeof(float) : 0) + 3 * (size_t)CUBES * sizeof(float2) +
-                                 2 * sizeof(uint64_t);
+  // TB input tiles and one output tile, MBF staged metric buffers (MS), three cubes, four mbarriers
+  static constexpr size_t SMEM = (size_t)(TB + 1) * TmaShape<N, CB>::TILE * sizeof(float) +
+                                 (MS ? (size_t)MBF * METRIC * sizeof(float) : 0) + 3 * (size_t)CUBES * sizeof(float2) +
+                                 4 * sizeof(uint64_t);
   static_assert(32 % PP == 0, "the pairs of one line must share a warp (x-point shuffle)");
   static_assert((METRIC * sizeof(float)) % 16 == 0, "bulk copy size");
+  static_assert(TB == 1 || TB == 2, "one or two input tiles");
+  static_assert(MBF == 1 || MBF == 2, "one or two metric buffers");
 };
 
 // one bulk copy (no tensor map) global -> shared, completion on an mbarrier; both addresses 16-byte
@@ -54,6 +57,23 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// L2 policy for data read once (the metric stream): evicted first, so that the vectors' lines stay
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_l2_bulk_hint(const void* p, unsigned bytes, uint64_t pol) {
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;\n" ::"l"(p), "r"(bytes), "l"(pol) : "memory");
 }
 
 // out = M1^T a + M2^T b
@@ -100,25 +120,30 @@ __device__ __forceinline__ void axpy_col2(float2 (&acc)[N], float2 h, int q, boo
   }
 }
 
-template <int N, int CB, int MS, int MB>
-__global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
+// MS: metric staged in shared memory (1) or read from L2 (0); MB: CTAs per SM the registers are sized for;
+// TB: input tiles (2: the next batch's rows are requested when a batch starts, 1: once phase 1 has read
+// the tile); MBF: staged metric buffers (2: the next batch's metric is requested when a batch starts);
+// EF: the metric stream carries the L2 evict-first policy
+template <int N, int CB, int MS, int MB, int TB, int MBF, int EF>
+__global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
     brick_vmult_f5_kernel(const __grid_constant__ TmaArgs<N> a) {
   using Sh = BrickShape<N, CB, float>;  // cube paddings of CB cells = paddings of CB / 2 float pairs
   using Tm = TmaShape<N, CB>;
-  using Fs = F5Shape<N, CB, MS>;
+  using Fs = F5Shape<N, CB, MS, TB, MBF>;
   constexpr int PP = Fs::PP;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
   constexpr int PITCH = Tm::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
   constexpr unsigned MBYTES = Fs::METRIC * 4u;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* T = reinterpret_cast<float*>(smem_raw);  // input tile
-  float* O = T + Tm::TILE;                         // output tile
-  float* Msm = O + Tm::TILE;                       // MS: the batch's metric [6][N^3][CB]
-  float2* A = reinterpret_cast<float2*>(Msm + (MS ? Fs::METRIC : 0));
+  float* T0 = reinterpret_cast<float*>(smem_raw);  // input tile(s)
+  float* O = T0 + TB * Tm::TILE;                    // output tile
+  float* M0 = O + Tm::TILE;                         // MS: staged metric buffer(s), [6][N^3][CB] each
+  float2* A = reinterpret_cast<float2*>(M0 + (MS ? MBF * Fs::METRIC : 0));
   float2* B = A + Fs::CUBES;
   float2* C = B + Fs::CUBES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(C + Fs::CUBES);  // [0] input tile, [1] metric
+  // [0], [1]: input tiles, [2], [3]: metric buffers
+  uint64_t* bars = reinterpret_cast<uint64_t*>(C + Fs::CUBES);
 
   const int t = threadIdx.x;
   const int c = t % PP;  // pair: cells 2c and 2c + 1 of the batch
@@ -134,49 +159,60 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
   const bool tma_warp = (t >> 5) == Fs::THREADS / 32 - 1;  // the last warp (idle lanes) issues the copies
   // this thread's x-line of quadrature points in the metric of a batch (float2 units: cells 2c, 2c + 1)
   const int gq = (xa2 * N + xa3 * N * N) * PP + c;
+  const uint64_t pol = (EF && tma_warp) ? policy_evict_first() : 0ull;
 
   if (t == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  auto issue_rows = [&](const BatchPos& pb) {
+  auto issue_rows = [&](const BatchPos& pb, int buf) {
     const BatchInfo bi = batch_info_at<CB, K>(a, pb);
     fence_proxy_async();
-    if (lane == 0) mbar_arrive_expect_tx(&bars[0], ROWS * BOX * 4);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[buf], ROWS * BOX * 4);
     __syncwarp();
+    float* T = T0 + buf * Tm::TILE;
     for (int row = lane; row < ROWS; row += 32) {
       const int a2 = row % N, a3 = row / N;
-      tma_load_1d(T + row * PITCH, &a.tsrc, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, &bars[0]);
+      tma_load_1d(T + row * PITCH, &a.tsrc, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, &bars[buf]);
     }
   };
   // MS: the batch's metric in four bulk copies (lanes 0..3)
-  auto issue_metric = [&](int bn) {
+  auto issue_metric = [&](int bn, int buf) {
     constexpr unsigned CH = (MBYTES / 4 + 15u) & ~15u;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[1], MBYTES);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[2 + buf], MBYTES);
     __syncwarp();
     const unsigned off = lane * CH;
-    if (lane < 4 && off < MBYTES)
-      bulk_load(reinterpret_cast<char*>(Msm) + off, reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off,
-                off + CH <= MBYTES ? CH : MBYTES - off, &bars[1]);
+    if (lane < 4 && off < MBYTES) {
+      char* d = reinterpret_cast<char*>(M0 + buf * Fs::METRIC) + off;
+      const char* g = reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off;
+      const unsigned n = off + CH <= MBYTES ? CH : MBYTES - off;
+      if (EF)
+        bulk_load_hint(d, g, n, &bars[2 + buf], pol);
+      else
+        bulk_load(d, g, n, &bars[2 + buf]);
+    }
   };
 
   int it = 0;
   bool failed = false;
-  // copies in flight that no wait has seen yet, and the parity of the barrier phase they complete
-  // (one buffer per barrier: at most one copy per barrier is outstanding)
-  bool rows_pending = false, metric_pending = false;
-  unsigned rows_par = 0, metric_par = 0;
+  // copies in flight that no wait has seen yet (bit i: mbarrier i), and the parity of the phase they
+  // complete (bit i)
+  unsigned pend = 0u, par = 0u;
+  auto mark = [&](int i, bool on, unsigned parity) {
+    pend = on ? (pend | (1u << i)) : (pend & ~(1u << i));
+    par = (par & ~(1u << i)) | (parity << i);
+  };
   BatchPos pos = batch_pos(a, blockIdx.x);
-  if (tma_warp && (int)blockIdx.x < a.n_batches) {
-    issue_rows(pos);
-    if (MS) issue_metric(blockIdx.x);
-  }
   if ((int)blockIdx.x < a.n_batches) {
-    rows_pending = true;
-    metric_pending = MS != 0;
+    if (tma_warp) {
+      issue_rows(pos, 0);
+      if (MS) issue_metric(blockIdx.x, 0);
+    }
+    mark(0, true, 0u);
+    mark(2, MS != 0, 0u);
   }
 
   for (int b = blockIdx.x; b < a.n_batches; b += gridDim.x, ++it) {
@@ -194,24 +230,49 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
     const bool lbnd1 = ebnd || (zx + K == 0 && bi.xlo) || (zx + K == bi.Wm - 1 && bi.xhi);
     const bool zlo = (bi.eflags & 4) != 0, zhi = (bi.eflags & 8) != 0;
 
+    const int rbuf = TB == 2 ? (it & 1) : 0;
+    const unsigned rpar = TB == 2 ? ((it >> 1) & 1) : (it & 1);
+    const int mbuf = MBF == 2 ? (it & 1) : 0;
+    const unsigned mpar = MBF == 2 ? ((it >> 1) & 1) : (it & 1);
+    float* T = T0 + rbuf * Tm::TILE;
+    const float* Msm = M0 + mbuf * Fs::METRIC;
     // the metric MDIST batches ahead into L2 (TMA engine, nothing waits for it)
     if (tma_warp && lane >= 4 && lane < 7) {
       const int bn = b + (MS ? 2 : 1) * (int)gridDim.x;
       if (bn < a.n_batches) {
         constexpr unsigned CHUNK = (MBYTES / 3 + 15u) & ~15u;
         const unsigned off = (lane - 4) * CHUNK;
-        if (off < MBYTES)
-          prefetch_l2_bulk(reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off,
-                           off + CHUNK <= MBYTES ? CHUNK : MBYTES - off);
+        if (off < MBYTES) {
+          const char* g = reinterpret_cast<const char*>(a.metric + (int64_t)bn * Fs::METRIC) + off;
+          const unsigned n = off + CHUNK <= MBYTES ? CHUNK : MBYTES - off;
+          if (EF)
+            prefetch_l2_bulk_hint(g, n, pol);
+          else
+            prefetch_l2_bulk(g, n);
+        }
       }
     }
+    // double buffers: the next batch's rows and metric go into the buffers the previous batch read
+    // (phases 1 and 3 of the previous batch ended with barriers)
+    if (TB == 2 && has_next) {
+      if (tma_warp) {
+        BatchPos next = pos;
+        batch_advance(next, a);
+        issue_rows(next, rbuf ^ 1);
+      }
+      mark(rbuf ^ 1, true, ((it + 1) >> 1) & 1);
+    }
+    if (MS && MBF == 2 && has_next) {
+      if (tma_warp) issue_metric(b + (int)gridDim.x, mbuf ^ 1);
+      mark(2 + (mbuf ^ 1), true, ((it + 1) >> 1) & 1);
+    }
     {
-      const bool ok = mbar_wait(&bars[0], it & 1);
+      const bool ok = mbar_wait(&bars[rbuf], rpar);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
-      rows_pending = false;
+      mark(rbuf, false, 0u);
     }
     // 1) z-lines of the input tile (Dirichlet points read as 0): A = S_z u, C = Sd_z u
     if (act) {
@@ -232,14 +293,15 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
       for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
     }
     __syncthreads();
-    // the input tile is free: the next batch's rows
-    if (tma_warp && has_next) {
-      BatchPos next = pos;
-      batch_advance(next, a);
-      issue_rows(next);
+    // one input tile: it is free now, the next batch's rows
+    if (TB == 1 && has_next) {
+      if (tma_warp) {
+        BatchPos next = pos;
+        batch_advance(next, a);
+        issue_rows(next, 0);
+      }
+      mark(0, true, (it + 1) & 1);
     }
-    rows_pending = has_next;
-    rows_par = (it + 1) & 1;
     // 2) y-lines: A <- S_y A, B = Sd_y A, C <- S_y C
     if (act) {
       float2 v[N], o[N];
@@ -258,12 +320,12 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
       for (int j = 0; j < N; ++j) C[ybase + j * NP] = o[j];
     }
     if (MS) {
-      const bool ok = mbar_wait(&bars[1], it & 1);
+      const bool ok = mbar_wait(&bars[2 + mbuf], mpar);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
-      metric_pending = false;
+      mark(2 + mbuf, false, 0u);
     } else {
       __syncthreads();
     }
@@ -327,11 +389,10 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
       }
     }
     __syncthreads();
-    // the metric buffer is free: the next batch's metric
-    if (MS) {
-      if (tma_warp && has_next) issue_metric(b + (int)gridDim.x);
-      metric_pending = has_next;
-      metric_par = (it + 1) & 1;
+    // one metric buffer: it is free now, the next batch's metric
+    if (MS && MBF == 1 && has_next) {
+      if (tma_warp) issue_metric(b + (int)gridDim.x, 0);
+      mark(2, true, (it + 1) & 1);
     }
     // 4) y-lines: A <- S_y^T A + Sd_y^T B, C <- S_y^T C
     if (act45) {
@@ -405,8 +466,9 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS>::THREADS, MB)
   if (failed && tma_warp && lane == 0) {
     atomicExch(a.err, 1);
     // drain the copies that may still be in flight before the CTA ends (bounded waits)
-    if (rows_pending) mbar_wait(&bars[0], rows_par);
-    if (MS && metric_pending) mbar_wait(&bars[1], metric_par);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (pend >> i & 1u) mbar_wait(&bars[i], par >> i & 1u);
   }
 }
 

@@ -257,18 +257,30 @@ struct F5For {
   static constexpr bool value = N >= 2 && N <= 5;
 };
 
+// Buffering of the five-phase kernel: one input tile and one staged metric buffer, no L2 policy.
+// Measured on 64^3 Q4 / 86^3 Q3 / 128^3 Q2 against two input tiles, two metric buffers and the
+// evict-first policy on the metric stream: the tiles and the policy within 2 % either way, the second
+// metric buffer 26 % slower at Q2 (fewer CTAs per SM).
+template <int N, int CB, int MS>
+struct F5Config {
+  static constexpr int TB = 1;
+  static constexpr int MBF = 1;
+  static constexpr int EF = 0;
+};
+
 template <int N, int CB, int MS>
 static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
-  using Fs = F5Shape<N, CB, MS>;
+  using Cf = F5Config<N, CB, MS>;
+  using Fs = F5Shape<N, CB, MS, Cf::TB, Cf::MBF>;
   using Tm = TmaShape<N, CB>;
   // resident CTAs per SM the register budget is sized for: about 672 threads per SM, fewer when the
-  // staged metric bounds the shared memory
+  // shared memory bounds them
   constexpr int MB0 = 672 / Fs::THREADS > 0 ? 672 / Fs::THREADS : 1;
   constexpr int MBS = (int)((220u * 1024u) / Fs::SMEM) > 0 ? (int)((220u * 1024u) / Fs::SMEM) : 1;
   constexpr int MB = MB0 < MBS ? MB0 : MBS;
   static int blocks_per_sm = -1;
   const size_t smem = Fs::SMEM;
-  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB>;
+  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB, Cf::TB, Cf::MBF, Cf::EF>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;

@@ -71,6 +71,25 @@ class SolveStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class PartInfo(ctypes.Structure):
+    _fields_ = [("cz0", ctypes.c_int32), ("nz", ctypes.c_int32), ("dirichlet", ctypes.c_uint32),
+                ("has_lo", ctypes.c_int32), ("has_hi", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dof0", ctypes.c_int64), ("n_dofs", ctypes.c_int64), ("n_owned", ctypes.c_int64),
+                ("plane", ctypes.c_int64), ("vertex0", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32)
+
+
+class Comm(ctypes.Structure):
+    _fields_ = [("send", ctypes.c_void_p * 2), ("recv", ctypes.c_void_p * 2), ("exchange", EXCHANGE_FN),
+                ("allreduce", ALLREDUCE_FN), ("user", ctypes.c_void_p)]
+
+
 class MgParams(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int32), ("smoother_degree", ctypes.c_int32),
                 ("smoothing_range", ctypes.c_double), ("lanczos_steps", ctypes.c_int32),
@@ -181,6 +200,10 @@ def lib():
         "mfx_mg_set_bounds": (S, [_VP, S, ctypes.c_double, ctypes.c_double]),
         "mfx_mg_vcycle": (S, [_VP, S, _VP, _VP, _VP]),
         "mfx_mg_solve": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
+        "mfx_partition_box": (S, [S, S, S, S, ctypes.c_uint32, S, S, ctypes.POINTER(PartInfo)]),
+        "mfx_halo_accumulate": (S, [_VP, S, S, _VP, _VP, _VP]),
+        "mfx_solve_partitioned": (S, [_VP, ctypes.POINTER(PartInfo), ctypes.POINTER(Comm), _VP, _VP,
+                                      ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _VP]),
         "mfx_server_create": (S, [ctypes.POINTER(_VP), ctypes.POINTER(ServerConfig)]),
         "mfx_server_destroy": (None, [_VP]),
         "mfx_server_submit": (S, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
@@ -222,6 +245,61 @@ def _prec_of(t):
     if t.dtype == torch.float32:
         return F32
     raise TypeError("vectors must be float64 or float32")
+
+
+def partition_box(nx, ny, nz, degree, n_parts, part, dirichlet=0x3F):
+    """The slab of cells along z that part `part` of n_parts takes, and its DoF bookkeeping (host-only,
+    mfx_partition_box): a dict with cz0, nz, dirichlet, has_lo, has_hi, dof0, n_dofs, n_owned, plane,
+    vertex0."""
+    info = PartInfo()
+    check(lib().mfx_partition_box(nx, ny, nz, degree, dirichlet, n_parts, part, ctypes.byref(info)))
+    return info
+
+
+def halo_accumulate(op, side, recv, y, stream=None):
+    """y's shared plane on `side` (0 below, 1 above) += recv, except on Dirichlet points (mfx_halo_accumulate)."""
+    check(lib().mfx_halo_accumulate(op.handle, _prec_of(y), side, _ptr(recv), _ptr(y), _stream(stream)))
+
+
+def solve_partitioned(op, part, b, x, exchange, allreduce, send, recv, tol=1e-10, max_it=100000, stream=None):
+    """Jacobi-PCG on a partitioned operator (mfx_solve_partitioned).  part: the PartInfo of this part;
+    send, recv: two device FP64 tensors each (or None where the part has no neighbour), `plane` entries;
+    exchange(): send to the neighbours, fill recv; allreduce(list of floats) -> list of floats summed over
+    the parts.  Returns the solve statistics."""
+    c = Comm()
+    for d in range(2):
+        c.send[d] = send[d].data_ptr() if send[d] is not None else None
+        c.recv[d] = recv[d].data_ptr() if recv[d] is not None else None
+
+    def _ex(_user):
+        try:
+            exchange()
+            return 0
+        except Exception:  # reported to the library as a failed callback
+            import traceback
+            traceback.print_exc()
+            return 1
+
+    def _ar(_user, vals, n):
+        try:
+            out = allreduce([vals[i] for i in range(n)])
+            for i in range(n):
+                vals[i] = float(out[i])
+            return 0
+        except Exception:
+            import traceback
+            traceback.print_exc()
+            return 1
+
+    c.exchange = EXCHANGE_FN(_ex)
+    c.allreduce = ALLREDUCE_FN(_ar)
+    p = make_params(tol=tol, max_it=max_it)
+    st = SolveStats()
+    rc = lib().mfx_solve_partitioned(op.handle, ctypes.byref(part), ctypes.byref(c), _ptr(b), _ptr(x), ctypes.byref(p),
+                                     ctypes.byref(st), _stream(stream))
+    if rc < 0:
+        check(rc)
+    return st.as_dict()
 
 
 def dot_noalloc(a, b, out, n=None, stream=None):
