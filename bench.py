@@ -472,8 +472,9 @@ def serving_measurement(n_requests, rate=200.0, seed=5):
 
 def batched_measurement(mfx, synthetic, torch, np, n_problems=64, seed=4):
     """64 independent Poisson problems (unit cube, N^3 cells with N uniform in [4, 32], degree uniform in 1..6,
-    uniform[-1, 1] right-hand sides, FP32 inner / FP64 outer Jacobi-PCG to 1e-10) advanced together by one
-    graph launch per tick, against the same solves run one after another."""
+    uniform[-1, 1] right-hand sides, FP32 inner / FP64 outer Jacobi-PCG to 1e-10) solved together in one graph
+    launch (mfx_batch_run), and by host-driven ticks (mfx_batch_step), against the same solves run one after
+    another."""
     g = synthetic.rng(seed)
     Ns = g.integers(4, 33, size=n_problems)
     ks = g.integers(1, 7, size=n_problems)
@@ -494,28 +495,36 @@ def batched_measurement(mfx, synthetic, torch, np, n_problems=64, seed=4):
         seq_inner += st["inner_iterations"] * op.n_dofs
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    # together
-    batch = mfx.Batch(n_problems, chunk=16)
-    xs = [torch.zeros_like(b) for b in bs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    slots = [batch.add(op, b, x, tol=1e-10, mixed=True) for op, b, x in zip(ops, bs, xs)]
-    ticks = batch.run()
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    dof_iters, worst, statuses = 0, 0.0, set()
-    for op, s in zip(ops, slots):
-        done, st = batch.poll(s)
-        statuses.add(st["status"])
-        dof_iters += st["inner_iterations"] * op.n_dofs
-        worst = max(worst, st["rel_residual"])
+    def together(one_launch):
+        batch = mfx.Batch(n_problems, chunk=16)
+        xs = [torch.zeros_like(b) for b in bs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slots = [batch.add(op, b, x, tol=1e-10, mixed=True) for op, b, x in zip(ops, bs, xs)]
+        # one graph launch whose device-side loops decide when each problem stops, or host-driven ticks
+        launches = 1 if one_launch and batch.run_once() else batch.run()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        dof_iters, worst, statuses = 0, 0.0, set()
+        for op, s in zip(ops, slots):
+            done, st = batch.poll(s)
+            statuses.add(st["status"] if done else -99)
+            dof_iters += st["inner_iterations"] * op.n_dofs
+            worst = max(worst, st["rel_residual"])
+        return t, launches, dof_iters, worst, sorted(statuses)
+
+    t_batch, launches, dof_iters, worst, statuses = together(True)
+    t_ticks, ticks, _, worst_ticks, statuses_ticks = together(False)
     chosen = {}
     for op, n_, k_ in zip(ops, Ns, ks):
-        chosen.setdefault(f"k{int(k_)}", {})[int(n_)] = op.info()["cells_per_block"]
-    return {"problems": n_problems, "total_dofs": total_dofs, "seconds": t_batch, "ticks": ticks,
-            "autotuned_cells_per_block": chosen,
-            "dof_iterations_per_s": dof_iters / t_batch, "statuses": sorted(statuses), "max_rel_residual": worst,
+        chosen.setdefault(f"k{int(k_)}", {})[int(n_)] = [op.info()["cells_per_block"], op.info()["structured_kernel"]]
+    return {"problems": n_problems, "total_dofs": total_dofs, "seconds": t_batch, "graph_launches": launches,
+            "mode": "one graph launch; per problem a device-decided WHILE loop (outer corrections, inner PCG)",
+            "autotuned_cells_per_block_and_kernel": chosen,
+            "dof_iterations_per_s": dof_iters / t_batch, "statuses": statuses, "max_rel_residual": worst,
             "sequential_seconds": t_seq, "speedup_over_sequential": t_seq / t_batch,
+            "ticks_mode": {"seconds": t_ticks, "ticks": ticks, "statuses": statuses_ticks,
+                           "max_rel_residual": worst_ticks, "speedup_over_sequential": t_seq / t_ticks},
             "sizes": {"N": [int(v) for v in Ns], "k": [int(v) for v in ks]}}
 
 

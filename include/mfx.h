@@ -531,6 +531,17 @@ mfx_status mfx_batch_step(mfx_batch* batch, int32_t* n_active);
  * same slots while work is in flight.
  */
 mfx_status mfx_batch_advance(mfx_batch* batch, int32_t* n_active);
+/*
+ * Every active slot's whole solve, from x = 0, in ONE graph launch.  Each slot is a graph WHILE loop
+ * whose condition a kernel sets on the device: for mixed = 1 the outer defect-correction loop (FP64
+ * residual and stopping test, FP32 PCG inner solve, FP64 correction) with the inner PCG loop nested in
+ * it, for mixed = 0 the PCG loop; so the device decides when each problem stops, and the slots run
+ * concurrently.  Every loop also ends after a capped number of passes (max_it outer passes; inner_max_it
+ * or max_it iterations in chunks), so the launch always ends.  Synchronises; every slot run is done
+ * afterwards (mfx_batch_poll gives its statistics).  n_done (may be NULL): the slots run.  Built and
+ * launched per call (nothing persists between calls).  No counterpart in the paper.
+ */
+mfx_status mfx_batch_run(mfx_batch* batch, int32_t* n_done);
 /* done = 1 once the slot's solve has finished; stats as mfx_solve (iterations: outer for mixed). */
 mfx_status mfx_batch_poll(mfx_batch* batch, int32_t slot, int32_t* done, mfx_solve_stats* stats);
 /* Free a slot (its operator and vectors can then be reused or destroyed). */

@@ -838,6 +838,8 @@ struct mfx_batch {
   cudaGraphExec_t parent = nullptr;
   std::vector<int> parent_members;
   int64_t ticks = 0;
+  void* run_state = nullptr;  // device RunState per slot (mfx_batch_run), allocated at the first run
+  int64_t runs = 0;
 };
 
 namespace mfx {
@@ -981,6 +983,264 @@ static mfx_status rebuild_parent(mfx_batch* bt) {
   return MFX_OK;
 }
 
+// ------------------------------------------------------------------ whole solves in one launch
+//
+// mfx_batch_run builds one graph that holds every active slot's complete solve and launches it once.
+// The loops are graph WHILE nodes whose conditions kernels set on the device: the outer loop of the
+// mixed solve (FP64 residual, stopping test, FP32 inner solve, correction) and, nested in it, the
+// inner PCG loop (a chunk of iterations, then the test of the inner state).  The device decides when
+// each problem stops; the host only builds the graph and reads the states afterwards.  Every loop
+// condition kernel also counts its passes and ends the loop beyond a cap (max_it for the outer loop,
+// inner_max_it / chunk + 2 chunks for the inner one), so every loop ends.
+
+struct RunState {
+  double bb, rr;  // (b, b) and the last FP64 (r, r)
+  int32_t outer, inner_total, status, done;
+  int32_t inner_passes, outer_passes;
+};
+
+// start of a slot's run: (b, b) from the value mfx_batch_add computed; outer loop on
+__global__ void run_start_kernel(RunState* rs, const double* bb, cudaGraphConditionalHandle outer) {
+  rs->bb = *bb;
+  rs->rr = 0.0;
+  rs->outer = 0;
+  rs->inner_total = 0;
+  rs->status = MFX_NOT_CONVERGED;
+  rs->done = 0;
+  rs->inner_passes = 0;
+  rs->outer_passes = 0;
+  cudaGraphSetConditional(outer, 1u);
+}
+
+// mixed solve, top of an outer pass: stopping test on the FP64 residual; otherwise the inner solve's
+// state is reset (tolerance and cap of the inner solve) and its loop switched on
+__global__ void run_decide_kernel(RunState* rs, SolveState* st, double tol2, int max_outer, double inner_tol2,
+                                  int inner_max_it, cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner) {
+  const double rr = rs->rr, bb = rs->bb;
+  rs->outer_passes += 1;
+  int done = 0;
+  if (!isfinite(rr) || !isfinite(bb)) {
+    rs->status = MFX_BREAKDOWN;
+    done = 1;
+  } else if (rr <= tol2 * bb) {
+    rs->status = MFX_OK;
+    done = 1;
+  } else if (rs->outer >= max_outer || rs->outer_passes > max_outer + 1) {
+    rs->status = MFX_NOT_CONVERGED;
+    done = 1;
+  }
+  rs->done = done;
+  rs->inner_passes = 0;
+  st->tol2 = inner_tol2;
+  st->max_it = inner_max_it;
+  st->record = 0;
+  st->it = 0;
+  st->done = done;  // the inner solve's kernels do nothing for a finished slot
+  cudaGraphSetConditional(outer, done ? 0u : 1u);
+  cudaGraphSetConditional(inner, done ? 0u : 1u);
+}
+
+// inner loop test after a chunk of PCG iterations
+__global__ void run_inner_check_kernel(RunState* rs, const SolveState* st, int max_passes,
+                                       cudaGraphConditionalHandle inner) {
+  rs->inner_passes += 1;
+  cudaGraphSetConditional(inner, (!st->done && rs->inner_passes < max_passes) ? 1u : 0u);
+}
+
+// FP32 start of the inner solve on r / ||r|| (skipped for a finished slot)
+__global__ void run_scale_kernel(int64_t n, const double* __restrict__ r, const RunState* rs,
+                                 float* __restrict__ out) {
+  if (rs->done) return;
+  const double sc = 1.0 / sqrt(rs->rr);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)(r[i] * sc);
+}
+
+// x += ||r|| d after an inner solve that did not break down (skipped for a finished slot)
+__global__ void run_correct_kernel(int64_t n, double* __restrict__ x, const float* __restrict__ d,
+                                   const RunState* rs, const SolveState* st) {
+  if (rs->done || st->status == MFX_BREAKDOWN) return;
+  const double sc = sqrt(rs->rr);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += sc * (double)d[i];
+}
+
+// end of an outer pass: count the inner iterations; an inner breakdown ends the slot
+__global__ void run_advance_kernel(RunState* rs, const SolveState* st, cudaGraphConditionalHandle outer) {
+  if (rs->done) return;
+  rs->inner_total += st->it;
+  if (st->status == MFX_BREAKDOWN) {
+    rs->status = MFX_BREAKDOWN;
+    rs->done = 1;
+    cudaGraphSetConditional(outer, 0u);
+    return;
+  }
+  rs->outer += 1;
+}
+
+// FP64 solve: the PCG state before its start kernel
+__global__ void run_state64_kernel(SolveState* st, double tol2, int max_it) {
+  st->tol2 = tol2;
+  st->max_it = max_it;
+  st->record = 0;
+  st->it = 0;
+  st->done = 0;
+  st->status = MFX_OK;
+}
+
+// FP64 solve: final state of the PCG
+__global__ void run_finish64_kernel(RunState* rs, const SolveState* st) {
+  rs->status = st->status;
+  rs->inner_total = st->it;
+  rs->rr = st->rr;
+  rs->done = 1;
+}
+
+// Appends what `body` launches on stream s to graph g after the nodes deps[0..nd), and returns the
+// captured work's last node in *leaf (or the first dependency if nothing was captured).
+template <typename F>
+static mfx_status capture_segment(cudaStream_t s, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                  cudaGraphNode_t* leaf, F&& body) {
+  MFX_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
+  mfx_status rc = body();
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* out = nullptr;
+  size_t n_out = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &out, nullptr, &n_out);
+  cudaGraphNode_t last = (e == cudaSuccess && n_out > 0) ? out[n_out - 1] : (nd > 0 ? deps[0] : nullptr);
+  const size_t n_leaves = n_out;
+  cudaGraph_t tmp = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
+  if (rc != MFX_OK) return rc;
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamGetCaptureInfo");
+  if (e2 != cudaSuccess) return cuda_error(e2, "cudaStreamEndCapture (segment)");
+  if (n_leaves > 1) return set_error(MFX_ECUDA, "batch run: a captured segment ended in several nodes");
+  *leaf = last;
+  return MFX_OK;
+}
+
+static mfx_status add_while(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, cudaGraphNode_t* node,
+                            cudaGraph_t* body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  MFX_CUDA_TRY(cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &p));
+  *body = p.conditional.phGraph_out[0];
+  return MFX_OK;
+}
+
+// The inner PCG loop of a slot (precision Real) after node dep of graph g: WHILE(inner) { chunk of
+// iterations; test }.  The loop's condition must be set upstream.
+template <typename Real>
+static mfx_status add_inner_loop(BatchSlot& sl, int chunk, RunState* rs, cudaGraph_t g, cudaGraphNode_t dep,
+                                 cudaGraphConditionalHandle inner, cudaGraphNode_t* node) {
+  SolveWorkspace* ws = workspace(sl.op);
+  Work<Real>& w = work_of<Real>(ws);
+  cudaGraph_t body = nullptr;
+  mfx_status rc = add_while(g, dep, inner, node, &body);
+  if (rc != MFX_OK) return rc;
+  const int max_it = sl.mixed ? sl.p.inner_max_it : sl.p.max_it;
+  const int max_passes = max_it / chunk + 2;
+  const Precond pc{sl.cheb ? 1 : 0, sl.p.cheb_degree, sl.lo, sl.hi, nullptr};
+  cudaGraphNode_t leaf = nullptr;
+  return capture_segment(sl.stream, body, nullptr, 0, &leaf, [&]() -> mfx_status {
+    for (int i = 0; i < chunk; ++i) {
+      mfx_status r2 = pcg_iteration<Real>(sl.op, ws, w, pc, sl.stream);
+      if (r2 != MFX_OK) return r2;
+    }
+    run_inner_check_kernel<<<1, 1, 0, sl.stream>>>(rs, ws->st, max_passes, inner);
+    MFX_CUDA_TRY(cudaGetLastError());
+    return MFX_OK;
+  });
+}
+
+// One slot's whole solve, appended to graph g (no edges to other slots).
+static mfx_status add_slot_solve(BatchSlot& sl, int chunk, RunState* rs, cudaGraph_t g) {
+  SolveWorkspace* ws = workspace(sl.op);
+  const int64_t n = sl.op->n_dofs;
+  const int red = reduction_blocks(n);
+  cudaStream_t s = sl.stream;
+  if (!sl.mixed) {
+    // FP64 PCG on b: start, loop, copy the solution out
+    cudaGraphConditionalHandle inner;
+    MFX_CUDA_TRY(cudaGraphConditionalHandleCreate(&inner, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNode_t start = nullptr, loop = nullptr, fin = nullptr;
+    mfx_status rc = capture_segment(s, g, nullptr, 0, &start, [&]() -> mfx_status {
+      run_start_kernel<<<1, 1, 0, s>>>(rs, ws->scal + 1, inner);  // the start sets this loop's condition
+      run_state64_kernel<<<1, 1, 0, s>>>(ws->st, sl.p.tol * sl.p.tol, sl.p.max_it);
+      MFX_CUDA_TRY(cudaMemcpyAsync(ws->w64.b, sl.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      cg_init_kernel<double><<<red, kRedThreads, 0, s>>>(n, ws->w64.b, ws->w64.x, ws->w64.r, ws->w64.p, ws->w64.dinv,
+                                                         !sl.cheb, ws->st, sl.op->d_partials, sl.op->d_counter);
+      if (sl.cheb) {
+        mfx_status r2 = cheb_apply<double>(sl.op, ws->w64, ws->w64.r, ws->w64.p, sl.p.cheb_degree, sl.lo, sl.hi,
+                                           &ws->st->done, s);
+        if (r2 != MFX_OK) return r2;
+        dot_kernel<double><<<red, kRedThreads, 0, s>>>(n, ws->w64.r, ws->w64.p, &ws->st->rz, sl.op->d_partials,
+                                                       sl.op->d_counter);
+      }
+      MFX_CUDA_TRY(cudaGetLastError());
+      return MFX_OK;
+    });
+    if (rc != MFX_OK) return rc;
+    rc = add_inner_loop<double>(sl, chunk, rs, g, start, inner, &loop);
+    if (rc != MFX_OK) return rc;
+    return capture_segment(s, g, &loop, 1, &fin, [&]() -> mfx_status {
+      MFX_CUDA_TRY(cudaMemcpyAsync(sl.x, ws->w64.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      run_finish64_kernel<<<1, 1, 0, s>>>(rs, ws->st);
+      MFX_CUDA_TRY(cudaGetLastError());
+      return MFX_OK;
+    });
+  }
+  // mixed: WHILE(outer) { residual, decide; scale, FP32 PCG start; WHILE(inner) {...}; correct, advance }
+  cudaGraphConditionalHandle outer;
+  MFX_CUDA_TRY(cudaGraphConditionalHandleCreate(&outer, g, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t start = nullptr, oloop = nullptr;
+  mfx_status rc = capture_segment(s, g, nullptr, 0, &start, [&]() -> mfx_status {
+    // a mixed solve starts from x = 0 (a slot that was stepped before starts over)
+    MFX_CUDA_TRY(cudaMemsetAsync(sl.x, 0, sizeof(double) * n, s));
+    run_start_kernel<<<1, 1, 0, s>>>(rs, ws->scal + 1, outer);
+    MFX_CUDA_TRY(cudaGetLastError());
+    return MFX_OK;
+  });
+  if (rc != MFX_OK) return rc;
+  cudaGraph_t obody = nullptr;
+  rc = add_while(g, start, outer, &oloop, &obody);
+  if (rc != MFX_OK) return rc;
+  cudaGraphConditionalHandle inner;
+  MFX_CUDA_TRY(cudaGraphConditionalHandleCreate(&inner, obody, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t head = nullptr, iloop = nullptr, tail = nullptr;
+  rc = capture_segment(s, obody, nullptr, 0, &head, [&]() -> mfx_status {
+    mfx_status r2 = launch_vmult(sl.op, MFX_F64, sl.x, ws->y64, s);
+    if (r2 != MFX_OK) return r2;
+    residual_kernel<<<red, kRedThreads, 0, s>>>(n, sl.b, ws->y64, ws->r64, &rs->rr, sl.op->d_partials,
+                                                sl.op->d_counter);
+    run_decide_kernel<<<1, 1, 0, s>>>(rs, ws->st, sl.p.tol * sl.p.tol, sl.p.max_it, sl.p.inner_tol * sl.p.inner_tol,
+                                      sl.p.inner_max_it, outer, inner);
+    run_scale_kernel<<<vec_grid(n), 256, 0, s>>>(n, ws->r64, rs, ws->w32.b);
+    cg_init_kernel<float><<<red, kRedThreads, 0, s>>>(n, ws->w32.b, ws->w32.x, ws->w32.r, ws->w32.p, ws->w32.dinv,
+                                                      !sl.cheb, ws->st, sl.op->d_partials, sl.op->d_counter);
+    if (sl.cheb) {
+      r2 = cheb_apply<float>(sl.op, ws->w32, ws->w32.r, ws->w32.p, sl.p.cheb_degree, sl.lo, sl.hi, &ws->st->done, s);
+      if (r2 != MFX_OK) return r2;
+      dot_kernel<float><<<red, kRedThreads, 0, s>>>(n, ws->w32.r, ws->w32.p, &ws->st->rz, sl.op->d_partials,
+                                                    sl.op->d_counter);
+    }
+    MFX_CUDA_TRY(cudaGetLastError());
+    return MFX_OK;
+  });
+  if (rc != MFX_OK) return rc;
+  rc = add_inner_loop<float>(sl, chunk, rs, obody, head, inner, &iloop);
+  if (rc != MFX_OK) return rc;
+  return capture_segment(s, obody, &iloop, 1, &tail, [&]() -> mfx_status {
+    run_correct_kernel<<<vec_grid(n), 256, 0, s>>>(n, sl.x, ws->w32.x, rs, ws->st);
+    run_advance_kernel<<<1, 1, 0, s>>>(rs, ws->st, outer);
+    MFX_CUDA_TRY(cudaGetLastError());
+    return MFX_OK;
+  });
+}
+
 }  // namespace mfx
 
 extern "C" {
@@ -1021,6 +1281,7 @@ void mfx_batch_destroy(mfx_batch* bt) {
     if (sl.h_scal) cudaFreeHost(sl.h_scal);
   }
   if (bt->stream) cudaStreamDestroy(bt->stream);
+  if (bt->run_state) cudaFree(bt->run_state);
   delete bt;
 }
 
@@ -1227,6 +1488,60 @@ mfx_status mfx_batch_advance(mfx_batch* bt, int32_t* n_active) {
   }
   if (n_active) *n_active = active;
   return MFX_OK;
+}
+
+// Every active slot's whole solve (from x = 0) in one graph launch; the device decides when each
+// problem stops (graph WHILE nodes whose conditions kernels set).
+mfx_status mfx_batch_run(mfx_batch* bt, int32_t* n_done) try {
+  MFX_TRACE("mfx_batch_run");
+  if (!bt) return set_error(MFX_EINVAL, "null batch");
+  std::vector<int> members;
+  for (size_t i = 0; i < bt->slots.size(); ++i)
+    if (bt->slots[i].phase == SLOT_OUTER || bt->slots[i].phase == SLOT_INNER) members.push_back((int)i);
+  if (n_done) *n_done = 0;
+  if (members.empty()) return MFX_OK;
+  if (!bt->run_state) MFX_CUDA_TRY(cudaMalloc(&bt->run_state, sizeof(RunState) * bt->slots.size()));
+  RunState* rs = reinterpret_cast<RunState*>(bt->run_state);
+  for (int i : members) MFX_CUDA_TRY(cudaStreamSynchronize(bt->slots[i].stream));  // (b, b), x = 0 of the adds
+  cudaGraph_t g = nullptr;
+  MFX_CUDA_TRY(cudaGraphCreate(&g, 0));
+  mfx_status rc = MFX_OK;
+  for (int i : members) {
+    BatchSlot& sl = bt->slots[i];
+    rc = add_slot_solve(sl, bt->chunk, rs + i, g);
+    if (rc != MFX_OK) break;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (rc == MFX_OK) {
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) rc = cuda_error(e, "batch run: instantiate");
+  }
+  cudaGraphDestroy(g);
+  if (rc != MFX_OK) return rc;
+  cudaError_t e = cudaGraphLaunch(exec, bt->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_error(e, "batch run: launch");
+  ++bt->runs;
+  std::vector<RunState> h(bt->slots.size());
+  MFX_CUDA_TRY(cudaMemcpy(h.data(), rs, sizeof(RunState) * h.size(), cudaMemcpyDeviceToHost));
+  int done = 0;
+  for (int i : members) {
+    BatchSlot& sl = bt->slots[i];
+    const RunState& r = h[i];
+    sl.status = r.status;
+    sl.bb = r.bb;
+    sl.bb_pending = false;
+    sl.rr = r.rr;
+    sl.outer = sl.mixed ? r.outer : 0;
+    sl.inner_total = r.inner_total;
+    sl.phase = SLOT_DONE;
+    ++done;
+  }
+  if (n_done) *n_done = done;
+  return MFX_OK;
+} catch (...) {
+  return host_exception();
 }
 
 mfx_status mfx_batch_poll(mfx_batch* bt, int32_t slot, int32_t* done, mfx_solve_stats* stats) {

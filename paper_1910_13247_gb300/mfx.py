@@ -190,6 +190,7 @@ def lib():
         "mfx_batch_step": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_advance": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_poll": (S, [_VP, S, ctypes.POINTER(S), ctypes.POINTER(SolveStats)]),
+        "mfx_batch_run": (S, [_VP, ctypes.POINTER(S)]),
         "mfx_batch_release": (S, [_VP, S]),
         "mfx_mg_params_default": (None, [ctypes.POINTER(MgParams)]),
         "mfx_mg_create": (S, [ctypes.POINTER(_VP), _VP, ctypes.POINTER(OpDesc), ctypes.POINTER(MgParams), _VP]),
@@ -625,10 +626,18 @@ class Batch:
         self._keep.pop(slot, None)
 
     def run(self, max_ticks=1000000):
+        """Host-driven ticks (mfx_batch_step) until every slot is done; returns the ticks."""
         ticks = 0
         while self.step() > 0 and ticks < max_ticks:
             ticks += 1
         return ticks
+
+    def run_once(self):
+        """Every active slot's whole solve in one graph launch, the device deciding when each problem
+        stops (mfx_batch_run); returns the number of slots run."""
+        n = ctypes.c_int32()
+        check(lib().mfx_batch_run(self.handle, ctypes.byref(n)))
+        return n.value
 
 
 class Server:

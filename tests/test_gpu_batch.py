@@ -36,8 +36,9 @@ def problems(mfx):
     return out
 
 
+@pytest.mark.parametrize("one_launch", [False, True])
 @pytest.mark.parametrize("mixed", [True, False])
-def test_batch_results_equal_standalone_results(mfx, mixed):
+def test_batch_results_equal_standalone_results(mfx, mixed, one_launch):
     probs = problems(mfx)
     bs, alone, kmats = [], [], []
     for i, (op, om) in enumerate(probs):
@@ -55,8 +56,10 @@ def test_batch_results_equal_standalone_results(mfx, mixed):
         x = torch.full_like(bd, float("nan"))
         slots.append(batch.add(op, bd, x, tol=1e-10, mixed=mixed))
         xs.append(x)
-    ticks = batch.run()
-    assert ticks > 0
+    if one_launch:
+        assert batch.run_once() == len(probs)
+    else:
+        assert batch.run() > 0
     for i, ((op, om), slot) in enumerate(zip(probs, slots)):
         done, st = batch.poll(slot)
         assert done and st["status"] == 0, st
@@ -89,7 +92,7 @@ def test_batch_slot_reuse_and_busy_operator(mfx):
 
 
 @pytest.mark.parametrize("mixed", [True, False])
-@pytest.mark.parametrize("independent", [False, True])
+@pytest.mark.parametrize("independent", [False, True, "one_launch"])
 def test_batch_degenerate_right_hand_sides(mfx, mixed, independent):
     """A zero right-hand side finishes with x = 0 and status OK, a NaN one with MFX_BREAKDOWN, and a
     regular one beside them converges; both schedulers (ticks and independent stepping), both modes."""
@@ -102,7 +105,9 @@ def test_batch_degenerate_right_hand_sides(mfx, mixed, independent):
     batch = mfx.Batch(4, chunk=4)
     xs = [torch.full_like(b0, float("nan")) for _ in range(3)]
     slots = [batch.add(op, b, x, tol=1e-10, mixed=mixed) for op, b, x in zip(ops, (b0, bz, bn), xs)]
-    if independent:
+    if independent == "one_launch":
+        assert batch.run_once() == 3
+    elif independent:
         for _ in range(200000):
             if batch.advance() == 0:
                 break
@@ -137,3 +142,22 @@ def test_operator_release_after_batch_completion(mfx):
     x2 = solve_once()
     # the FP32 inner solves scatter with reduce-adds whose order varies: equal up to rounding
     assert torch.allclose(x1, x2, rtol=0, atol=1e-12 * x1.abs().max().item())
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_one_launch_caps_end_every_loop(mfx, mixed):
+    """A tolerance no solve can reach ends every device-decided loop at its cap: NOT_CONVERGED after
+    max_it outer corrections (mixed) or max_it iterations (FP64), and the launch returns."""
+    op = mfx.Operator(mfx.Mesh.structured_box(4, 4, 4), 2)
+    b = torch.tensor(synthetic.uniform_vector(op.n_dofs, 73), device="cuda")
+    op.distribute(b)
+    x = torch.zeros_like(b)
+    batch = mfx.Batch(2, chunk=4)
+    s = batch.add(op, b, x, tol=0.0, mixed=mixed, max_it=3 if mixed else 10, inner_max_it=6)
+    assert batch.run_once() == 1
+    done, st = batch.poll(s)
+    assert done and st["status"] == mfx.NOT_CONVERGED, st
+    if mixed:
+        assert st["iterations"] == 3 and st["inner_iterations"] <= 3 * 6
+    else:
+        assert st["iterations"] == 10
