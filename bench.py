@@ -37,16 +37,21 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 
 
 # DRAM traffic of one FP32 vmult launch on the 64^3 Q4 workload, from the ncu capture summarised in
-# profiles/vmult_fp32_tma2_q4_48cube.md (48^3 case, 16 cells per batch, scaled by cells).  Valid only for
-# that batch size and the kernel sources it was taken from: anything else reports null.
-TRAFFIC_BYTES = 980.5e6
-TRAFFIC_SOURCES = {"vmult_brick_tma2.cuh": "a9524b2424c4577c", "vmult_brick_tma.cuh": "731ccc8ecdc21d0b",
-                   "vmult_brick.cuh": "d4348f1901d2181e", "vmult.cuh": "31514fc950494b5e"}
+# profiles/vmult_fp32_f5_staged_q4_48cube.md (48^3 case, five-phase kernel with the staged metric, 8 cells per
+# batch; 412.85 MB read + written, scaled by cells to 64^3).  Valid only for that kernel, batch size and the
+# kernel sources it was taken from: anything else reports null.
+TRAFFIC_BYTES = 978.6e6
+TRAFFIC_KERNEL = (3, 8)  # (structured_kernel, cells_per_block): five-phase, staged metric, 8 cells per batch
+TRAFFIC_SOURCES = {"vmult_brick_f5.cuh": "ce4f42337c1edf7b", "vmult_brick_tma2.cuh": "a9524b2424c4577c",
+                   "vmult_brick_tma.cuh": "731ccc8ecdc21d0b", "vmult_brick.cuh": "d4348f1901d2181e",
+                   "vmult.cuh": "29a1c345486f59d9", "vmult_launch.cuh": "9219b8b645dc7e51"}
+KERNEL_NAMES = {1: "brick_vmult_tma2_kernel (ten phases)", 2: "brick_vmult_f5_kernel (five phases, metric from L2)",
+                3: "brick_vmult_f5_kernel (five phases, metric staged in shared memory)"}
 
 
-def measured_traffic(nx, k, cells_per_block):
+def measured_traffic(nx, k, cells_per_block, kernel):
     import hashlib
-    if (nx, k, cells_per_block) != (NX, K_DEG, 16):
+    if (nx, k) != (NX, K_DEG) or (kernel, cells_per_block) != TRAFFIC_KERNEL:
         return None
     csrc = os.path.join(ROOT, "paper_1910_13247_gb300", "csrc")
     for name, digest in TRAFFIC_SOURCES.items():
@@ -363,12 +368,15 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if (nx, kdeg) == (NX, K_DEG) else f"{nx}^3 cells, Q{kdeg} (profiling case)",
                    "n_dofs": N, "n_cells": C, "degree": kdeg, "n_q_1d": kdeg + 1,
-                   "cells_per_block": op.info()["cells_per_block"],
+                   "cells_per_block": op.info()["cells_per_block"], "fp32_kernel": op.info()["structured_kernel"],
                    "step": "one FP32 vmult", "l2": "inputs larger than L2 (%.2f GB read+written per step)" % (b32 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": measured_traffic(nx, kdeg, op.info()["cells_per_block"]), "peak_kind": peak_kind,
-                     "kernel": "FP32 vmult (init_rows_kernel + brick_vmult_tma2_kernel), timed together",
+                     "traffic": measured_traffic(nx, kdeg, op.info()["cells_per_block"], op.info()["structured_kernel"]),
+                     "peak_kind": peak_kind,
+                     "kernel": "FP32 vmult (init_rows_kernel + %s, %d cells per batch), timed together"
+                               % (KERNEL_NAMES.get(op.info()["structured_kernel"], "per-cell kernel"),
+                                  op.info()["cells_per_block"]),
                      "algorithmic_bytes": b32,
                      # secondary model: coefficient per q-point and vertices instead of the stored metric
                      "algorithmic_bytes_minimal": 2 * 4 * N + 4 * C * (kdeg + 1) ** 3 + 24 * C},
