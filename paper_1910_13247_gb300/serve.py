@@ -35,11 +35,12 @@ class Request:
         self.iterations = None
 
 
-def make_requests(n, rate=200.0, seed=5, size_range=(1e3, 1e7), max_fine=128):
+def make_requests(n, rate=200.0, seed=5, size_range=(1e3, 1e7), max_fine=512):
     """Seeded request stream: exponential inter-arrival times (Poisson process of the given rate),
     degree uniform in 1..8, target size log-uniform in size_range, 1-3 refinement levels inside a
     seeded ball.  The coarse grid n_b^3 is the one whose estimated size is closest to the target,
-    with n_b 2^levels <= max_fine (the generator's voxel limit), so the largest targets are clamped."""
+    with n_b 2^levels <= max_fine (the generator's finest voxel grid, 512^3 by default: targets up to
+    10^7 DoFs are reached at every degree and level count)."""
     g = synthetic.rng(seed)
     t = 0.0
     reqs = []
