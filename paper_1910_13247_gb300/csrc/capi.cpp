@@ -341,9 +341,6 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   if (sync) cudaStreamSynchronize(s);
-  if (op->aux_stream) cudaStreamDestroy(op->aux_stream);  // released once its work is done
-  if (op->fork_event) cudaEventDestroy(op->fork_event);
-  if (op->join_event) cudaEventDestroy(op->join_event);
   delete op;
 }
 
@@ -665,9 +662,6 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
         MFX_CUDA_OP(cudaMemcpyAsync(op->d_cells_plain, plain.data(), plain.size() * 4, cudaMemcpyHostToDevice, s));
       if (!hang.empty())
         MFX_CUDA_OP(cudaMemcpyAsync(op->d_cells_hang, hang.data(), hang.size() * 4, cudaMemcpyHostToDevice, s));
-      MFX_CUDA_OP(cudaStreamCreateWithFlags(&op->aux_stream, cudaStreamNonBlocking));
-      MFX_CUDA_OP(cudaEventCreateWithFlags(&op->fork_event, cudaEventDisableTiming));
-      MFX_CUDA_OP(cudaEventCreateWithFlags(&op->join_event, cudaEventDisableTiming));
     }
   }
   const size_t nq = (size_t)op->n_cells * n3;

@@ -150,10 +150,6 @@ struct mfx_op {
   int32_t* d_cells_plain = nullptr;  // octree, tensor-product constraints: cells without / with hanging
   int32_t* d_cells_hang = nullptr;   // faces or edges (each list runs in its own kernel instantiation)
   int64_t n_cells_plain = 0, n_cells_hang = 0;
-  // the two cell-list launches of an octree vmult run side by side: the second on this stream, forked
-  // from and joined back to the caller's stream with the two events
-  cudaStream_t aux_stream = nullptr;
-  cudaEvent_t fork_event = nullptr, join_event = nullptr;
   // diagonal set-up on cells with hanging nodes (host; cleared once the diagonal is built):
   // one quadratic form v^T A_cell v per (cell, master) pair, v = the master's column of C on the cell
   std::vector<int32_t> hang_job_cell, hang_job_master;

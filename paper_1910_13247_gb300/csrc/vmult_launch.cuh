@@ -54,11 +54,10 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
 }
 
 // One launch of the per-cell kernel over all cells, or over a cell list (prologue: dst = src on the
-// constrained rows and 0 elsewhere, before the first launch of a vmult).  share < 1: the launch gets that
-// share of the resident CTAs (it runs beside another launch).
+// constrained rows and 0 elsewhere, before the first launch of a vmult).
 template <int N, typename Real, bool HANG>
 static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip,
-                              const int32_t* list, int64_t n_list, bool prologue, double share = 1.0) {
+                              const int32_t* list, int64_t n_list, bool prologue) {
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
   const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + (HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0)) * sizeof(Real);
@@ -82,8 +81,7 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
   }
   const int64_t nbatch = ((list ? n_list : op->n_cells) + Sh::CB - 1) / Sh::CB;
   if (nbatch > 0) {
-    const int64_t slots = std::max<int64_t>(1, (int64_t)(share * sms * blocks_per_sm + 0.5));
-    const int grid = (int)std::min<int64_t>(nbatch, slots);
+    const int grid = (int)std::min<int64_t>(nbatch, (int64_t)sms * blocks_per_sm);
     kern<<<grid, Sh::THREADS, smem, s>>>(a, src, dst);
   }
   MFX_CUDA_TRY(cudaGetLastError());
@@ -95,32 +93,12 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
 template <int N, typename Real>
 static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
   if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_cells_hang) {
-    // cells without hanging faces or edges in the plain kernel, the rest in the tensor-product one; after
-    // the prologue both add into dst independently, so they run side by side (the hanging cells on the
-    // operator's second stream), each with the share of the GPU of its share of the work (a cell with
-    // hanging faces or edges costs about 2.5 plain ones, measured on octrees refined twice)
-    const double wp = (double)op->n_cells_plain, wh = 2.5 * (double)op->n_cells_hang;
-    const double fp = wp + wh > 0 ? wp / (wp + wh) : 0.5;
-    if (!op->aux_stream) {
-      mfx_status st = run_vmult_h<N, Real, false>(op, src, dst, s, skip, op->d_cells_plain, op->n_cells_plain, true);
-      if (st != MFX_OK) return st;
-      return run_vmult_h<N, Real, true>(op, src, dst, s, skip, op->d_cells_hang, op->n_cells_hang, false);
-    }
-    // prologue, fork
-    mfx_status st = run_vmult_h<N, Real, false>(op, src, dst, s, skip, op->d_cells_plain, 0, true);
+    // cells without hanging faces or edges in the plain kernel, the rest in the tensor-product one, one
+    // launch after the other (side by side on two streams with grids split by work share measured slower:
+    // 0.089 -> 0.111 ms on 16^3 coarse cells refined twice, Q4)
+    mfx_status st = run_vmult_h<N, Real, false>(op, src, dst, s, skip, op->d_cells_plain, op->n_cells_plain, true);
     if (st != MFX_OK) return st;
-    MFX_CUDA_TRY(cudaEventRecord(op->fork_event, s));
-    MFX_CUDA_TRY(cudaStreamWaitEvent(op->aux_stream, op->fork_event, 0));
-    st = run_vmult_h<N, Real, true>(op, src, dst, op->aux_stream, skip, op->d_cells_hang, op->n_cells_hang, false,
-                                    std::max(0.1, 1.0 - fp));
-    if (st != MFX_OK) return st;
-    st = run_vmult_h<N, Real, false>(op, src, dst, s, skip, op->d_cells_plain, op->n_cells_plain, false,
-                                     std::max(0.1, fp));
-    if (st != MFX_OK) return st;
-    // join
-    MFX_CUDA_TRY(cudaEventRecord(op->join_event, op->aux_stream));
-    MFX_CUDA_TRY(cudaStreamWaitEvent(s, op->join_event, 0));
-    return MFX_OK;
+    return run_vmult_h<N, Real, true>(op, src, dst, s, skip, op->d_cells_hang, op->n_cells_hang, false);
   }
   return run_vmult_h<N, Real, false>(op, src, dst, s, skip, nullptr, 0, true);
 }
