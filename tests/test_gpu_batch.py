@@ -161,3 +161,32 @@ def test_one_launch_caps_end_every_loop(mfx, mixed):
         assert st["iterations"] == 3 and st["inner_iterations"] <= 3 * 6
     else:
         assert st["iterations"] == 10
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_one_launch_with_chebyshev_preconditioner(mfx, mixed):
+    """Chebyshev(5)-Jacobi-preconditioned solves in one launch (the preconditioner's kernels inside the
+    device-decided loops) equal the same solves alone within 1e-9 and meet the residual bound."""
+    probs = problems(mfx)[:4]
+    batch = mfx.Batch(4, chunk=4)
+    xs, alone, bs, slots = [], [], [], []
+    for i, (op, om) in enumerate(probs):
+        b = synthetic.uniform_vector(op.n_dofs, 80 + i)
+        b[om.constrained] = 0.0
+        bd = torch.tensor(b, device="cuda")
+        xa = torch.zeros_like(bd)
+        st = op.solve(bd, xa, tol=1e-10, mixed=mixed, precond=mfx.PRECOND_CHEBYSHEV, cheb_degree=5)
+        assert st["status"] == 0
+        alone.append(xa.cpu().numpy())
+        x = torch.full_like(bd, float("nan"))
+        slots.append(batch.add(op, bd, x, tol=1e-10, mixed=mixed, precond=mfx.PRECOND_CHEBYSHEV, cheb_degree=5))
+        xs.append(x)
+        bs.append(b)
+    assert batch.run_once() == len(probs)
+    for i, ((op, om), slot) in enumerate(zip(probs, slots)):
+        done, st = batch.poll(slot)
+        assert done and st["status"] == 0, st
+        xb = xs[i].cpu().numpy()
+        assert np.linalg.norm(xb - alone[i]) <= 1e-9 * np.linalg.norm(alone[i])
+        K = fem.assemble(om, om.k + 1, fem.COEF_TRIG, (1.0, 0.5))
+        assert np.linalg.norm(bs[i] - K @ xb) <= 1.0001e-10 * np.linalg.norm(bs[i])
