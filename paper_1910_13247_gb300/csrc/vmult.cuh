@@ -58,16 +58,26 @@ struct VmultArgs {
 // face containing it, else the first hanging edge, else -1.  Each constrained node of a cell with
 // hanging faces or edges is interpolated by exactly one owner, and its transpose goes back through the
 // same owner only.
+// A node lies on at most one face and one edge per axis, found from its coordinates: face 2 d + side if
+// a_d is 0 or K, edge 4 d + 2 side_v + side_u (u, v the lower and the higher of the other two axes) if
+// a_u and a_v both are; the faces and then the edges are tried in ascending index order.
 __device__ __forceinline__ int hang_owner(uint32_t hf, uint32_t he, int a1, int a2, int a3, int K) {
-  const int a[3] = {a1, a2, a3};
-#pragma unroll
-  for (int f = 0; f < 6; ++f)
-    if ((hf >> f & 1u) && a[f >> 1] == (f & 1) * K) return f;
-#pragma unroll
-  for (int e = 0; e < 12; ++e) {
-    if (!(he >> e & 1u)) continue;
-    const int d = e >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
-    if (a[u] == (e & 1) * K && a[v] == ((e >> 1) & 1) * K) return 6 + e;
+  const bool lo1 = a1 == 0, hi1 = a1 == K, lo2 = a2 == 0, hi2 = a2 == K, lo3 = a3 == 0, hi3 = a3 == K;
+  const bool e1 = lo1 || hi1, e2 = lo2 || hi2, e3 = lo3 || hi3;
+  if (e1 && (hf >> (hi1 ? 1 : 0) & 1u)) return hi1 ? 1 : 0;
+  if (e2 && (hf >> (hi2 ? 3 : 2) & 1u)) return hi2 ? 3 : 2;
+  if (e3 && (hf >> (hi3 ? 5 : 4) & 1u)) return hi3 ? 5 : 4;
+  if (e2 && e3) {  // edge along x: u = y, v = z
+    const int e = 2 * (hi3 ? 1 : 0) + (hi2 ? 1 : 0);
+    if (he >> e & 1u) return 6 + e;
+  }
+  if (e1 && e3) {  // edge along y: u = x, v = z
+    const int e = 4 + 2 * (hi3 ? 1 : 0) + (hi1 ? 1 : 0);
+    if (he >> e & 1u) return 6 + e;
+  }
+  if (e1 && e2) {  // edge along z: u = x, v = y
+    const int e = 8 + 2 * (hi2 ? 1 : 0) + (hi1 ? 1 : 0);
+    if (he >> e & 1u) return 6 + e;
   }
   return -1;
 }
