@@ -407,6 +407,8 @@ def main():
             line["serving"] = serving_measurement(args.serve_requests)
         if not args.no_octree:
             line["octree"] = octree_measurement(mfx, synthetic, torch, args.octree_degree)
+            # the same refinement on 32^3 coarse cells (17.5M DoFs at Q4): the kernels at a serving-size mesh
+            line["octree"]["large"] = octree_measurement(mfx, synthetic, torch, args.octree_degree, nb=32, fp64=False)
         if not args.no_sipg:
             line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims), k=args.sipg_degree,
                                             solve=not args.sipg_vmult_only)
@@ -595,7 +597,15 @@ def mixed_solve_measurement(mfx, synthetic, torch, np):
     return out
 
 
-def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2):
+def octree_bytes(n_dofs, n_cells, k, s):
+    """Algorithmic bytes of an octree vmult: src read and dst written, the 6-entry metric per quadrature
+    point, the int32 cell DoF table; the hanging constraints' words and coarse-DoF lists are left out
+    (they are a few bytes per hanging cell)."""
+    n3 = (k + 1) ** 3
+    return 2 * s * n_dofs + 6 * s * n_cells * n3 + 4 * n_cells * n3
+
+
+def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2, fp64=True):
     """FP32 and FP64 vmult on an octree refined twice inside a ball (hanging nodes; the serving
     workload's mesh family): nb^3 coarse cells of the deformed cube, the variable coefficient."""
     leaves = synthetic.octree_leaves(nb, levels, (0.5, 0.45, 0.55), 0.3)
@@ -603,10 +613,11 @@ def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2):
     op = mfx.Operator(mesh, k, mfx.COEF_TRIG, (1.0, 0.5))
     info = op.info()
     n = op.n_dofs
+    hbm, peak_kind = peaks()
     out = {"workload": "octree, %d^3 coarse cells refined %d times in a ball, Q%d" % (nb, levels, k), "n_dofs": n,
            "n_cells": info["n_cells"], "n_hanging": info["n_hanging"]}
     stream = torch.cuda.current_stream()
-    for name, dt in (("vmult_fp32", torch.float32), ("vmult_fp64", torch.float64)):
+    for name, dt in (("vmult_fp32", torch.float32), ("vmult_fp64", torch.float64))[:2 if fp64 else 1]:
         x = torch.tensor(synthetic.uniform_vector(n, 71), device="cuda", dtype=dt)
         y = torch.empty_like(x)
         for _ in range(3):
@@ -618,7 +629,11 @@ def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2):
             e1.record(stream)
         torch.cuda.synchronize()
         ms = statistics.median(a.elapsed_time(b) for a, b in evs)
-        out[name] = {"gdofs": n / (ms * 1e-3) / 1e9, "ms": ms}
+        byt = octree_bytes(n, info["n_cells"], k, 4 if dt == torch.float32 else 8)
+        out[name] = {"gdofs": n / (ms * 1e-3) / 1e9, "ms": ms,
+                     "roofline": {"bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": byt / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": byt,
+                                  "peak_kind": peak_kind}}
     return out
 
 
