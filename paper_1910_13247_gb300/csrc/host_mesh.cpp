@@ -303,7 +303,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     }
   // hanging constraints
   std::unordered_map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;
-  hanging.reserve((size_t)C * 8 + 64);
+  hanging.reserve((size_t)C / 8 + 1024);  // hanging nodes lie on coarse-fine interfaces only
   // a hanging node is reached once per fine cell around it; the 2:1 balance makes every visit give the
   // same constraint, so the first one is kept and the others are skipped before their masters are formed
   std::vector<uint8_t> is_hanging(N, 0);
@@ -351,6 +351,8 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   for (int64_t c = 0; c < C; ++c) {
     const auto& lf = t.leaves[c];
     const int L = lf[0];
+    // a leaf of the finest level has no finer neighbour: none of its faces or edges is refined across
+    if (L == Lmax) continue;
     const int64_t idx[3] = {lf[1], lf[2], lf[3]};
     // faces
     for (int d = 0; d < 3; ++d) {
