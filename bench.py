@@ -40,11 +40,11 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 # profiles/vmult_fp32_f5_staged_q4_48cube.md (48^3 case, five-phase kernel with the staged metric, 8 cells per
 # batch; 412.85 MB read + written, scaled by cells to 64^3).  Valid only for that kernel, batch size and the
 # kernel sources it was taken from: anything else reports null.
-TRAFFIC_BYTES = 978.6e6
+TRAFFIC_BYTES = 979.2e6
 TRAFFIC_KERNEL = (3, 8)  # (structured_kernel, cells_per_block): five-phase, staged metric, 8 cells per batch
-TRAFFIC_SOURCES = {"vmult_brick_f5.cuh": "ce4f42337c1edf7b", "vmult_brick_tma2.cuh": "a9524b2424c4577c",
+TRAFFIC_SOURCES = {"vmult_brick_f5.cuh": "093bf4cbec21cefb", "vmult_brick_tma2.cuh": "a9524b2424c4577c",
                    "vmult_brick_tma.cuh": "731ccc8ecdc21d0b", "vmult_brick.cuh": "d4348f1901d2181e",
-                   "vmult.cuh": "29a1c345486f59d9", "vmult_launch.cuh": "9219b8b645dc7e51"}
+                   "vmult.cuh": "34f4b0003dba199b", "vmult_launch.cuh": "b62118a6a0632ffc"}
 KERNEL_NAMES = {1: "brick_vmult_tma2_kernel (ten phases)", 2: "brick_vmult_f5_kernel (five phases, metric from L2)",
                 3: "brick_vmult_f5_kernel (five phases, metric staged in shared memory)"}
 
@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--degree", type=int, default=K_DEG)
     ap.add_argument("--cells-per-block", type=int, default=0,
                     help="fix the structured kernel's cells per batch (0: autotuned at operator creation)")
+    ap.add_argument("--fp32-kernel", type=int, default=0,
+                    help="fix the structured FP32 kernel (1 ten-phase, 2 five-phase, 3 five-phase staged; 0: autotuned)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,7 +262,8 @@ def main():
     nx, kdeg = args.nx, args.degree
     verts = synthetic.deformed_vertices(nx, nx, nx)
     mesh = mfx.Mesh.structured_box(nx, nx, nx, verts)
-    op = mfx.Operator(mesh, kdeg, mfx.COEF_TRIG, (1.0, 0.5), cells_per_block=args.cells_per_block)
+    op = mfx.Operator(mesh, kdeg, mfx.COEF_TRIG, (1.0, 0.5), cells_per_block=args.cells_per_block,
+                      structured_kernel=args.fp32_kernel)
     N, C = op.n_dofs, op.n_cells
     x64 = torch.tensor(synthetic.uniform_vector(N, 1), device="cuda")
     x32 = x64.float()
