@@ -333,7 +333,7 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   if (!op) return;
   if (sync) cudaDeviceSynchronize();
   free_workspace(op, s);
-  void* ptrs[] = {op->d_vertices, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
+  void* ptrs[] = {op->d_vertices, op->d_leaves, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
                   op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs, op->d_cells_plain,
@@ -618,7 +618,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     std::vector<uint8_t> mask(t.n_dofs, 0);
     for (int32_t c : t.constrained) mask[c] = 1;
     std::vector<float> w32(t.cweight.begin(), t.cweight.end());
-    MFX_TRY(dev_alloc(op, &op->d_vertices, t.cell_vertices.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_vertices, m.vertices.size(), s));
+    MFX_TRY(dev_alloc(op, &op->d_leaves, m.leaves.size(), s));
     MFX_TRY(dev_alloc(op, &op->d_cell_dofs, enc.size(), s));
     MFX_TRY(dev_alloc(op, &op->d_cmask, mask.size(), s));
     MFX_TRY(dev_alloc(op, &op->d_constrained, t.constrained.size(), s));
@@ -627,7 +628,8 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
     MFX_TRY(dev_alloc(op, &op->d_cweight64, std::max<size_t>(1, t.cweight.size()), s));
     MFX_TRY(dev_alloc(op, &op->d_cweight32, std::max<size_t>(1, w32.size()), s));
     MFX_TRY(dev_alloc(op, &op->d_cell_hanging, cell_hang.size(), s));
-    MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, t.cell_vertices.data(), t.cell_vertices.size() * 8, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_vertices, m.vertices.data(), m.vertices.size() * 8, cudaMemcpyHostToDevice, s));
+    MFX_CUDA_OP(cudaMemcpyAsync(op->d_leaves, m.leaves.data(), m.leaves.size() * 4, cudaMemcpyHostToDevice, s));
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_cell_dofs, enc.data(), enc.size() * 4, cudaMemcpyHostToDevice, s));
     MFX_CUDA_OP(cudaMemcpyAsync(op->d_cmask, mask.data(), mask.size(), cudaMemcpyHostToDevice, s));
     if (!t.constrained.empty())

@@ -21,7 +21,8 @@ struct GeoArgs {
   int64_t n_cells;
   bool structured;
   int nx, ny, nz;
-  const double* vertices;  // structured lattice or cell x 8 x 3
+  const double* vertices;  // the (coarse) vertex lattice
+  const int32_t* leaves;   // octree: (level, i, j, l) per cell
   int coef_kind;
   double par0, par1;
   const double* coef_q;
@@ -67,8 +68,28 @@ __device__ __forceinline__ void cell_vertices(const GeoArgs& g, int64_t cell, do
       for (int d = 0; d < 3; ++d) V[v][d] = g.vertices[3 * idx + d];
     }
   } else {
-    for (int v = 0; v < 8; ++v)
-      for (int d = 0; d < 3; ++d) V[v][d] = g.vertices[cell * 24 + 3 * v + d];
+    // the leaf's corners: the trilinear map of its coarse cell at the reference points (I + a) / 2^L
+    const int L = g.leaves[4 * cell], li = g.leaves[4 * cell + 1], lj = g.leaves[4 * cell + 2],
+              ll = g.leaves[4 * cell + 3];
+    const int ci = li >> L, cj = lj >> L, cl = ll >> L;
+    double X[8][3];
+    for (int w = 0; w < 8; ++w) {
+      const int a = w & 1, b = (w >> 1) & 1, c = (w >> 2) & 1;
+      const int64_t idx = (ci + a) + (int64_t)(g.nx + 1) * ((cj + b) + (int64_t)(g.ny + 1) * (cl + c));
+      for (int d = 0; d < 3; ++d) X[w][d] = g.vertices[3 * idx + d];
+    }
+    const double h = 1.0 / (double)(1 << L);
+    for (int v = 0; v < 8; ++v) {
+      const double s = (double)(li - (ci << L) + (v & 1)) * h;
+      const double t = (double)(lj - (cj << L) + ((v >> 1) & 1)) * h;
+      const double u = (double)(ll - (cl << L) + ((v >> 2) & 1)) * h;
+      for (int d = 0; d < 3; ++d) {
+        double p = 0.0;
+        for (int w = 0; w < 8; ++w)
+          p += ((w & 1) ? s : 1.0 - s) * ((w & 2) ? t : 1.0 - t) * ((w & 4) ? u : 1.0 - u) * X[w][d];
+        V[v][d] = p;
+      }
+    }
   }
 }
 
@@ -457,6 +478,7 @@ static GeoArgs geo_args(const mfx_op* op) {
   g.ny = op->ny;
   g.nz = op->nz;
   g.vertices = op->d_vertices;
+  g.leaves = op->d_leaves;
   g.coef_kind = MFX_COEF_CONSTANT;
   g.par0 = 1.0;
   g.par1 = 0.0;

@@ -18,6 +18,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <utility>
 
@@ -26,31 +28,6 @@
 namespace mfx {
 
 namespace {
-
-inline uint64_t leaf_key(int L, int64_t i, int64_t j, int64_t l) {
-  return ((uint64_t)L << 60) | ((uint64_t)i << 40) | ((uint64_t)j << 20) | (uint64_t)l;
-}
-
-struct Octree {
-  int nx, ny, nz, Lmax;
-  std::vector<std::array<int32_t, 4>> leaves;
-  std::unordered_map<uint64_t, int32_t> index;
-
-  int64_t extent(int d, int L) const { return (int64_t)(d == 0 ? nx : d == 1 ? ny : nz) << L; }
-
-  // Leaf of level <= L covering the level-L cell p, or -1 if p is inside the box and refined
-  // deeper, or -2 if p is outside the box.
-  int32_t covering(int L, const int64_t p[3]) const {
-    for (int d = 0; d < 3; ++d)
-      if (p[d] < 0 || p[d] >= extent(d, L)) return -2;
-    for (int Lc = L; Lc >= 0; --Lc) {
-      const int sh = L - Lc;
-      auto it = index.find(leaf_key(Lc, p[0] >> sh, p[1] >> sh, p[2] >> sh));
-      if (it != index.end()) return it->second;
-    }
-    return -1;
-  }
-};
 
 uint64_t morton(uint64_t x, uint64_t y, uint64_t z, int bits) {
   uint64_t m = 0;
@@ -62,28 +39,115 @@ uint64_t morton(uint64_t x, uint64_t y, uint64_t z, int bits) {
   return m;
 }
 
-mfx_status build(const Mesh& m, Octree* t) {
+// f(lo, hi) on contiguous chunks of [0, n), on up to 16 threads for large n
+template <typename F>
+void parallel_chunks(int64_t n, const F& f) {
+  const int64_t grain = 1 << 16;
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>(std::min(hw, 16), (n + grain - 1) / grain);
+  if (nt <= 1) {
+    if (n > 0) f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int i = 0; i < nt; ++i) th.emplace_back([&f, i, nt, n] { f(n * i / nt, n * (i + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
+// Sorted leaves with a point locator: leaves ordered by (coarse cell, Morton code of the lower corner at
+// the finest level Lmax); the leaves of one coarse cell tile its Morton range [0, 8^Lmax), so the leaf
+// containing a point is found by one binary search among the leaves of its coarse cell.
+struct Octree {
+  int nx, ny, nz, Lmax;
+  std::vector<std::array<int32_t, 4>> leaves;
+  std::vector<uint64_t> code;   // per leaf: Morton code of its lower corner at level Lmax
+  std::vector<int64_t> first;   // per coarse cell: its first leaf (n_coarse + 1 entries)
+
+  int64_t extent(int d, int L) const { return (int64_t)(d == 0 ? nx : d == 1 ? ny : nz) << L; }
+
+  // coarse cell and Morton code at level Lmax of the lower corner of the level-L cell p (inside the box)
+  void key_of(int L, const int64_t p[3], int64_t* cc, uint64_t* mo) const {
+    const int64_t c0 = p[0] >> L, c1 = p[1] >> L, c2 = p[2] >> L;
+    const int sh = Lmax - L;
+    *cc = c0 + (int64_t)nx * (c1 + (int64_t)ny * c2);
+    *mo = morton((uint64_t)(p[0] - (c0 << L)) << sh, (uint64_t)(p[1] - (c1 << L)) << sh,
+                 (uint64_t)(p[2] - (c2 << L)) << sh, Lmax);
+  }
+  // the leaf containing the lower corner of the level-L cell p (L <= Lmax), or -2 if p is outside the box
+  int32_t locate(int L, const int64_t p[3]) const {
+    for (int d = 0; d < 3; ++d)
+      if (p[d] < 0 || p[d] >= extent(d, L)) return -2;
+    int64_t cc;
+    uint64_t mo;
+    key_of(L, p, &cc, &mo);
+    const uint64_t* b = code.data() + first[cc];
+    const uint64_t* e = code.data() + first[cc + 1];
+    return (int32_t)(std::upper_bound(b, e, mo) - code.data() - 1);
+  }
+  // Leaf of level <= L covering the level-L cell p, or -1 if p is inside the box and refined
+  // deeper, or -2 if p is outside the box.
+  int32_t covering(int L, const int64_t p[3]) const {
+    const int32_t q = locate(L, p);
+    if (q < 0) return q;
+    return leaves[q][0] <= L ? q : -1;
+  }
+  // some coarse cell across a face or an edge of the coarse cell c holds more than one leaf
+  bool refined_near(const int64_t c[3]) const {
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int nnz = (dx != 0) + (dy != 0) + (dz != 0);
+          if (nnz == 0 || nnz == 3) continue;
+          const int64_t p[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+          if (p[0] < 0 || p[0] >= nx || p[1] < 0 || p[1] >= ny || p[2] < 0 || p[2] >= nz) continue;
+          const int64_t cc = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
+          if (first[cc + 1] - first[cc] > 1) return true;
+        }
+    return false;
+  }
+  // the leaf that is the level-L cell p, or -1
+  int32_t exact(int L, const int64_t p[3]) const {
+    const int32_t q = locate(L, p);
+    return q >= 0 && leaves[q][0] == L ? q : -1;
+  }
+};
+
+// the locator of leaves already sorted (octree_sort_and_check)
+void build(const Mesh& m, Octree* t) {
   t->nx = m.nx;
   t->ny = m.ny;
   t->nz = m.nz;
-  const size_t nl = m.leaves.size() / 4;
+  t->Lmax = m.max_level;
+  const int64_t nl = (int64_t)m.leaves.size() / 4;
   t->leaves.resize(nl);
-  t->Lmax = 0;
-  for (size_t q = 0; q < nl; ++q) {
-    for (int c = 0; c < 4; ++c) t->leaves[q][c] = m.leaves[4 * q + c];
-    t->Lmax = std::max(t->Lmax, t->leaves[q][0]);
+  t->code.resize(nl);
+  const int64_t ncoarse = (int64_t)m.nx * m.ny * m.nz;
+  t->first.assign(ncoarse + 1, nl);
+  parallel_chunks(nl, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; ++q) {
+      for (int c = 0; c < 4; ++c) t->leaves[q][c] = m.leaves[4 * q + c];
+      const int64_t p[3] = {t->leaves[q][1], t->leaves[q][2], t->leaves[q][3]};
+      int64_t cc;
+      t->key_of(t->leaves[q][0], p, &cc, &t->code[q]);
+    }
+  });
+  // first[cc]: the first leaf of coarse cell cc (leaves are grouped by coarse cell in increasing order)
+  for (int64_t q = nl - 1; q >= 0; --q) {
+    const auto& lf = t->leaves[q];
+    const int L = lf[0];
+    t->first[(lf[1] >> L) + (int64_t)m.nx * ((lf[2] >> L) + (int64_t)m.ny * (lf[3] >> L))] = q;
   }
-  t->index.reserve(nl * 2);
-  for (size_t q = 0; q < nl; ++q) t->index[leaf_key(t->leaves[q][0], t->leaves[q][1], t->leaves[q][2], t->leaves[q][3])] = (int32_t)q;
-  return MFX_OK;
+  for (int64_t cc = ncoarse - 1; cc >= 0; --cc) t->first[cc] = std::min(t->first[cc], t->first[cc + 1]);
 }
 
 }  // namespace
 
 mfx_status octree_sort_and_check(Mesh* m) {
-  const size_t nl = m->leaves.size() / 4;
+  const int64_t nl = (int64_t)m->leaves.size() / 4;
+  if (nl >= (int64_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 2 leaves");
   int Lmax = 0;
-  for (size_t q = 0; q < nl; ++q) {
+  for (int64_t q = 0; q < nl; ++q) {
     const int L = m->leaves[4 * q];
     if (L < 0 || L > 8) return set_error(MFX_EMESH, "leaf level out of range 0..8");
     const int64_t e[3] = {(int64_t)m->nx << L, (int64_t)m->ny << L, (int64_t)m->nz << L};
@@ -93,53 +157,103 @@ mfx_status octree_sort_and_check(Mesh* m) {
     }
     Lmax = std::max(Lmax, L);
   }
-  Octree t;
-  build(*m, &t);
-  if (t.index.size() != nl) return set_error(MFX_EMESH, "duplicate leaves");
-  // disjoint: no leaf has a leaf ancestor; complete: volumes add up
-  unsigned __int128 vol = 0;
-  for (size_t q = 0; q < nl; ++q) {
-    const auto& lf = t.leaves[q];
-    for (int La = lf[0] - 1; La >= 0; --La) {
-      const int sh = lf[0] - La;
-      if (t.index.count(leaf_key(La, lf[1] >> sh, lf[2] >> sh, lf[3] >> sh)))
-        return set_error(MFX_EMESH, "overlapping leaves");
+  // cell order: coarse cell lexicographic, then Morton order of the lower corner at level Lmax
+  // (every coarse cell holds a leaf, so n_coarse <= n_leaves < 2^31 and the key (coarse cell, Morton code)
+  // fits in 31 + 24 bits)
+  const int64_t ncoarse = (int64_t)m->nx * m->ny * m->nz;
+  if (ncoarse > nl) return set_error(MFX_EMESH, "leaves do not cover the coarse box");
+  const int mbits = 3 * Lmax;
+  std::vector<uint64_t> key(nl);
+  parallel_chunks(nl, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; ++q) {
+      const int32_t* lf = &m->leaves[4 * q];
+      const int L = lf[0], sh = Lmax - L;
+      const int64_t ci = lf[1] >> L, cj = lf[2] >> L, cl = lf[3] >> L;
+      const uint64_t mo = morton((uint64_t)(lf[1] - (ci << L)) << sh, (uint64_t)(lf[2] - (cj << L)) << sh,
+                                 (uint64_t)(lf[3] - (cl << L)) << sh, Lmax);
+      key[q] = ((uint64_t)(ci + (int64_t)m->nx * (cj + (int64_t)m->ny * cl)) << mbits) | mo;
     }
-    vol += (unsigned __int128)1 << (3 * (Lmax - lf[0]));
+  });
+  // stable LSD radix sort of (key, leaf) by key, 11 bits per pass (equal keys keep input order)
+  std::vector<int32_t> order(nl);
+  for (int64_t q = 0; q < nl; ++q) order[q] = (int32_t)q;
+  {
+    int bits = mbits;
+    while (bits < 64 && ((uint64_t)(ncoarse - 1) >> (bits - mbits)) != 0) ++bits;
+    std::vector<uint64_t> key2(nl);
+    std::vector<int32_t> order2(nl);
+    std::vector<int64_t> cnt(2049);
+    for (int shift = 0; shift < bits; shift += 11) {
+      std::fill(cnt.begin(), cnt.end(), 0);
+      for (int64_t q = 0; q < nl; ++q) ++cnt[((key[q] >> shift) & 2047) + 1];
+      for (int i = 0; i < 2048; ++i) cnt[i + 1] += cnt[i];
+      for (int64_t q = 0; q < nl; ++q) {
+        const int64_t dst = cnt[(key[q] >> shift) & 2047]++;
+        key2[dst] = key[q];
+        order2[dst] = order[q];
+      }
+      key.swap(key2);
+      order.swap(order2);
+    }
   }
-  if (vol != ((unsigned __int128)m->nx * m->ny * m->nz) << (3 * Lmax))
-    return set_error(MFX_EMESH, "leaves do not cover the coarse box");
-  // 2:1 balance: the same-size face and edge neighbours of every leaf are covered by
-  // leaves at most one level coarser (finer neighbours are checked from their side)
-  for (size_t q = 0; q < nl; ++q) {
-    const auto& lf = t.leaves[q];
-    const int L = lf[0];
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int nnz = (dx != 0) + (dy != 0) + (dz != 0);
-          if (nnz == 0 || nnz == 3) continue;
-          const int64_t p[3] = {lf[1] + dx, lf[2] + dy, lf[3] + dz};
-          const int32_t c = t.covering(L, p);
-          if (c >= 0 && t.leaves[c][0] < L - 1) return set_error(MFX_EMESH, "mesh is not 2:1 balanced across faces and edges");
+  // the leaves of every coarse cell tile its Morton range: each starts where the previous one ends
+  // (a leaf of level L spans 8^(Lmax - L) codes), the first at 0 and the last ending at 8^Lmax
+  const uint64_t full = 1ull << mbits;
+  {
+    int64_t q = 0;
+    for (int64_t cc = 0; cc < ncoarse; ++cc) {
+      uint64_t next = 0;
+      for (; q < nl && (int64_t)(key[q] >> mbits) == cc; ++q) {
+        const uint64_t mo = key[q] & (full - 1);
+        const int L = m->leaves[4 * (int64_t)order[q]];
+        if (mo > next) return set_error(MFX_EMESH, "leaves do not cover the coarse box");
+        if (mo < next) {
+          const bool dup = q > 0 && key[q - 1] == key[q] && m->leaves[4 * (int64_t)order[q - 1]] == L;
+          return set_error(MFX_EMESH, dup ? "duplicate leaves" : "overlapping leaves");
         }
+        next = mo + (1ull << (3 * (Lmax - L)));
+      }
+      if (next != full) return set_error(MFX_EMESH, "leaves do not cover the coarse box");
+    }
   }
-  // cell order
-  std::vector<std::pair<std::pair<int64_t, uint64_t>, size_t>> order(nl);
-  for (size_t q = 0; q < nl; ++q) {
-    const auto& lf = t.leaves[q];
-    const int L = lf[0], sh = Lmax - L;
-    const int64_t ci = lf[1] >> L, cj = lf[2] >> L, cl = lf[3] >> L;
-    const uint64_t mo = morton((uint64_t)(lf[1] - (ci << L)) << sh, (uint64_t)(lf[2] - (cj << L)) << sh,
-                               (uint64_t)(lf[3] - (cl << L)) << sh, Lmax);
-    order[q] = {{ci + (int64_t)m->nx * (cj + (int64_t)m->ny * cl), mo}, q};
-  }
-  std::sort(order.begin(), order.end());
+  key.clear();
+  key.shrink_to_fit();
   std::vector<int32_t> sorted(4 * nl);
-  for (size_t q = 0; q < nl; ++q)
-    for (int c = 0; c < 4; ++c) sorted[4 * q + c] = t.leaves[order[q].second][c];
+  parallel_chunks(nl, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; ++q)
+      for (int c = 0; c < 4; ++c) sorted[4 * q + c] = m->leaves[4 * (int64_t)order[q] + c];
+  });
+  order.clear();
+  order.shrink_to_fit();
   m->leaves.swap(sorted);
   m->max_level = Lmax;
+  // 2:1 balance: the same-size face and edge neighbours of every leaf are covered by
+  // leaves at most one level coarser (finer neighbours are checked from their side)
+  Octree t;
+  build(*m, &t);
+  bool balanced = true;
+  std::mutex mu;
+  parallel_chunks(nl, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; ++q) {
+      const auto& lf = t.leaves[q];
+      const int L = lf[0];
+      if (L < 2) continue;  // no leaf is coarser than level 0
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int nnz = (dx != 0) + (dy != 0) + (dz != 0);
+            if (nnz == 0 || nnz == 3) continue;
+            const int64_t p[3] = {lf[1] + dx, lf[2] + dy, lf[3] + dz};
+            const int32_t c = t.covering(L, p);
+            if (c >= 0 && t.leaves[c][0] < L - 1) {
+              std::lock_guard<std::mutex> g(mu);
+              balanced = false;
+              return;
+            }
+          }
+    }
+  });
+  if (!balanced) return set_error(MFX_EMESH, "mesh is not 2:1 balanced across faces and edges");
   return MFX_OK;
 }
 
@@ -159,21 +273,33 @@ inline bool irrational(uint32_t dk) { return (dk >> 31) != 0; }
 // one 16-byte slot, so a probe touches one cache line.
 class NodeTable {
  public:
-  explicit NodeTable(size_t expected) {
-    size_t cap = 16;
-    while (cap < 2 * expected + 16) cap <<= 1;
-    slots_.assign(cap, Slot{{~0u, ~0u, ~0u}, -1});
-    mask_ = cap - 1;
-  }
+  explicit NodeTable(size_t expected) { init(capacity_for(expected)); }
   size_t slot(const NodeKey& k) const { return hash(k) & mask_; }
   void prefetch(size_t h) const { __builtin_prefetch(&slots_[h]); }
+  // room for `more` inserts at a load of at most 0.7 (doubles the table and rehashes if needed; home
+  // slots taken before a call are invalid after it)
+  bool reserve_more(size_t more) {
+    if ((size_ + more) * 10 <= slots_.size() * 7) return false;
+    std::vector<Slot> old;
+    old.swap(slots_);
+    init(capacity_for(size_ + more));
+    for (const Slot& s : old)
+      if (s.dof >= 0) {
+        size_t h = slot(s.key);
+        while (slots_[h].dof >= 0) h = (h + 1) & mask_;
+        slots_[h] = s;
+      }
+    return true;
+  }
   // DoF of the key (whose home slot is h), inserting `next` if absent; returns (dof, inserted).
+  // The caller keeps the load below 1 (reserve_more), so a free slot is always found.
   std::pair<int32_t, bool> find_or_insert(const NodeKey& k, size_t h, int32_t next) {
     for (;;) {
       Slot& s = slots_[h];
       if (s.dof < 0) {
         s.key = k;
         s.dof = next;
+        ++size_;
         return {next, true};
       }
       if (s.key == k) return {s.dof, false};
@@ -195,8 +321,17 @@ class NodeTable {
     NodeKey key;
     int32_t dof;
   };
+  static size_t capacity_for(size_t n) {  // power of two, load at most 2/3
+    size_t cap = 16;
+    while (2 * cap < 3 * n + 16) cap <<= 1;
+    return cap;
+  }
+  void init(size_t cap) {
+    slots_.assign(cap, Slot{{~0u, ~0u, ~0u}, -1});
+    mask_ = cap - 1;
+  }
   std::vector<Slot> slots_;
-  size_t mask_ = 0;
+  size_t mask_ = 0, size_ = 0;
 };
 
 }  // namespace
@@ -210,32 +345,6 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   double g[kMaxN];
   gauss_lobatto(k, g);
   out->n_cells = C;
-  out->cell_vertices.assign(C * 24, 0.0);
-  // vertices: trilinear map of the coarse cell at the leaf's reference corners
-  for (int64_t c = 0; c < C; ++c) {
-    const auto& lf = t.leaves[c];
-    const int L = lf[0];
-    const int64_t ci = lf[1] >> L, cj = lf[2] >> L, cl = lf[3] >> L;
-    double X[8][3];
-    for (int w = 0; w < 8; ++w) {
-      const int a = w & 1, b = (w >> 1) & 1, e = (w >> 2) & 1;
-      const size_t vi = (ci + a) + (size_t)(m.nx + 1) * ((cj + b) + (size_t)(m.ny + 1) * (cl + e));
-      for (int d = 0; d < 3; ++d) X[w][d] = m.vertices[3 * vi + d];
-    }
-    for (int v = 0; v < 8; ++v) {
-      const int a = v & 1, b = (v >> 1) & 1, e = (v >> 2) & 1;
-      const double s = (double)((lf[1] - (ci << L)) + a) / (double)(1 << L);
-      const double tt = (double)((lf[2] - (cj << L)) + b) / (double)(1 << L);
-      const double u = (double)((lf[3] - (cl << L)) + e) / (double)(1 << L);
-      double p[3] = {0, 0, 0};
-      for (int w = 0; w < 8; ++w) {
-        const int wa = w & 1, wb = (w >> 1) & 1, we = (w >> 2) & 1;
-        const double f = (wa ? s : 1 - s) * (wb ? tt : 1 - tt) * (we ? u : 1 - u);
-        for (int d = 0; d < 3; ++d) p[d] = p[d] + f * X[w][d];
-      }
-      for (int d = 0; d < 3; ++d) out->cell_vertices[c * 24 + 3 * v + d] = p[d];
-    }
-  }
   const uint32_t R2 = 1u << (Lmax + 1);
   if ((uint64_t)std::max(m.nx, std::max(m.ny, m.nz)) * R2 >= (1ull << 31) ||
       ((uint64_t)std::max(m.nx, std::max(m.ny, m.nz)) << Lmax) >= (1ull << 23))
@@ -258,31 +367,41 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   int interior_1d = 0;
   for (int a = 0; a <= k; ++a)
     if (a != 0 && a != k && 2 * a != k) ++interior_1d;
-  // shared (non-interior) node visits; each distinct shared node is visited about twice or more
-  const size_t shared_visits = (size_t)C * (size_t)(n3 - interior_1d * interior_1d * interior_1d);
-  NodeTable dof_of(shared_visits / 2 + 64);
+  // distinct shared (non-interior) nodes: about k^3 - interior_1d^3 per cell away from refinement
+  // interfaces (the table grows if there are more)
+  const size_t shared_per_cell = (size_t)std::max(1, k * k * k - interior_1d * interior_1d * interior_1d);
+  NodeTable dof_of((size_t)C * shared_per_cell + 1024);
   out->cell_dofs.assign(C * n3, 0);
   std::vector<NodeKey> keys_by_dof;
   keys_by_dof.reserve((size_t)C * n3 / 2 + 16);
-  // keys of one cell, with their home slots prefetched before the (sequential) first-encounter pass
-  std::vector<NodeKey> ck(n3);
-  std::vector<size_t> cs(n3);
-  for (int64_t c = 0; c < C; ++c) {
+  // first-encounter pass over the cells in order; the keys of the next D cells are formed and their
+  // home slots prefetched ahead of it (a ring of D cells)
+  const int D = std::max(2, 64 / n3);
+  std::vector<NodeKey> ck((size_t)D * n3);
+  std::vector<size_t> cs((size_t)D * n3);
+  auto stage = [&](int64_t c) {
+    const size_t o = (size_t)(c % D) * n3;
     for (int a3 = 0; a3 < n; ++a3)
       for (int a2 = 0; a2 < n; ++a2)
         for (int a1 = 0; a1 < n; ++a1) {
-          const int li = a1 + n * (a2 + n * a3);
+          const size_t li = o + a1 + n * (a2 + n * a3);
           ck[li] = node_key(c, a1, a2, a3);
           cs[li] = dof_of.slot(ck[li]);
           dof_of.prefetch(cs[li]);
         }
+  };
+  for (int64_t c = 0; c < std::min<int64_t>(D, C); ++c) stage(c);
+  for (int64_t c = 0; c < C; ++c) {
+    if (dof_of.reserve_more((size_t)D * n3))  // rehashed: the staged home slots moved
+      for (size_t i = 0; i < ck.size(); ++i) cs[i] = dof_of.slot(ck[i]);
+    const size_t o = (size_t)(c % D) * n3;
     for (int li = 0; li < n3; ++li) {
-      const NodeKey& key = ck[li];
+      const NodeKey& key = ck[o + li];
       if (keys_by_dof.size() >= (size_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
       const int32_t next = (int32_t)keys_by_dof.size();
       int32_t dof = next;
       if (!(irrational(key.d[0]) && irrational(key.d[1]) && irrational(key.d[2]))) {
-        auto r = dof_of.find_or_insert(key, cs[li], next);
+        auto r = dof_of.find_or_insert(key, cs[o + li], next);
         dof = r.first;
         if (r.second) keys_by_dof.push_back(key);
       } else {
@@ -290,6 +409,7 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
       }
       out->cell_dofs[c * n3 + li] = dof;
     }
+    if (c + D < C) stage(c + D);
   }
   const int64_t N = (int64_t)keys_by_dof.size();
   out->n_dofs = N;
@@ -354,6 +474,9 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     // a leaf of the finest level has no finer neighbour: none of its faces or edges is refined across
     if (L == Lmax) continue;
     const int64_t idx[3] = {lf[1], lf[2], lf[3]};
+    // a level-0 leaf is a whole coarse cell: it has a finer face or edge neighbour only if one of the
+    // coarse cells across its faces and edges holds more than one leaf
+    if (L == 0 && !t.refined_near(idx)) continue;
     // faces
     for (int d = 0; d < 3; ++d) {
       const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
@@ -367,9 +490,9 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
             f[d] = 2 * p[d] + (sd ? 0 : 1);
             f[u] = 2 * idx[u] + cu;
             f[v] = 2 * idx[v] + cv;
-            auto it = t.index.find(leaf_key(L + 1, f[0], f[1], f[2]));
-            if (it == t.index.end()) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
-            const int64_t e = it->second;
+            const int32_t fe_leaf = t.exact(L + 1, f);
+            if (fe_leaf < 0) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
+            const int64_t e = fe_leaf;
             const int ae_d = sd ? 0 : k, ac_d = sd ? k : 0;
             {
               const int fe = 2 * d + (sd ? 0 : 1);  // the fine cell's face on the coarse face
@@ -433,9 +556,9 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
               f[d] = 2 * idx[d] + cd;
               f[u] = 2 * p[u] + (o[0] == 0 ? su : (su ? 0 : 1));
               f[v] = 2 * p[v] + (o[1] == 0 ? sv : (sv ? 0 : 1));
-              auto it = t.index.find(leaf_key(L + 1, f[0], f[1], f[2]));
-              if (it == t.index.end()) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
-              const int64_t e = it->second;
+              const int32_t fe_leaf = t.exact(L + 1, f);
+              if (fe_leaf < 0) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
+              const int64_t e = fe_leaf;
               // position of the edge line in the fine leaf
               const int64_t edge_u = 2 * (idx[u] + su), edge_v = 2 * (idx[v] + sv);
               const int au = edge_u == f[u] ? 0 : k, av = edge_v == f[v] ? 0 : k;

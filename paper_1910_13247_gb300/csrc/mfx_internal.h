@@ -81,7 +81,6 @@ constexpr int kTensorHangMinDegree = 3;
 
 struct OctreeTables {
   int64_t n_cells = 0, n_dofs = 0;
-  std::vector<double> cell_vertices;   // n_cells x 8 x 3
   std::vector<int32_t> cell_dofs;      // n_cells x n^3
   std::vector<int32_t> constrained;    // sorted
   std::vector<int64_t> cptr;           // n_constrained + 1
@@ -131,7 +130,8 @@ struct mfx_op {
   // host tables (octree) or empty (structured)
   mfx::OctreeTables tables;
   // device data
-  double* d_vertices = nullptr;      // structured: lattice (nx+1)(ny+1)(nz+1) x 3; else cell x 8 x 3
+  double* d_vertices = nullptr;      // the (coarse) vertex lattice (nx+1)(ny+1)(nz+1) x 3
+  int32_t* d_leaves = nullptr;       // octree: the sorted leaves, (level, i, j, l) per cell
   double* d_metric64 = nullptr;      // FP64 metric; structured operators: float pairs after creation
   float* d_metric32 = nullptr;
   double* d_jxw = nullptr;           // n_cells x n^3 (for the right-hand side)
