@@ -507,8 +507,27 @@ __global__ void vmult_prologue(const __grid_constant__ VmultArgs<N, Real> a, con
                                Real* __restrict__ dst) {
   if (a.skip && *a.skip) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_dofs; i += stride)
-    dst[i] = a.cmask[i] != 0 ? src[i] : Real(0);
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t i0 = 0;
+  // four DoFs per step where src and dst allow 4-element vector stores (the mask is the library's own,
+  // 256-byte aligned): one 4-byte mask load, src read only on constrained DoFs
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & (4 * sizeof(Real) - 1)) == 0) {
+    const int64_t n4 = a.n_dofs >> 2;
+    for (int64_t i = tid; i < n4; i += stride) {
+      const uchar4 m = reinterpret_cast<const uchar4*>(a.cmask)[i];
+      const Real* s = src + 4 * i;
+      const Real v0 = m.x ? s[0] : Real(0), v1 = m.y ? s[1] : Real(0);
+      const Real v2 = m.z ? s[2] : Real(0), v3 = m.w ? s[3] : Real(0);
+      if constexpr (sizeof(Real) == 4) {
+        reinterpret_cast<float4*>(dst)[i] = make_float4(v0, v1, v2, v3);
+      } else {
+        reinterpret_cast<double2*>(dst)[2 * i] = make_double2(v0, v1);
+        reinterpret_cast<double2*>(dst)[2 * i + 1] = make_double2(v2, v3);
+      }
+    }
+    i0 = 4 * n4;
+  }
+  for (int64_t i = i0 + tid; i < a.n_dofs; i += stride) dst[i] = a.cmask[i] != 0 ? src[i] : Real(0);
 }
 
 }  // namespace mfx

@@ -14,6 +14,7 @@
 #include "vmult_brick_df.cuh"
 #include "vmult_brick_tma2.cuh"
 #include "vmult_brick_f5.cuh"
+#include "vmult_cell5.cuh"
 #include "vmult_octree2.cuh"
 
 namespace mfx {
@@ -61,7 +62,12 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
   const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + (HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0)) * sizeof(Real);
-  auto kern = vmult_kernel<N, Real, HANG>;
+  // FP32: the five-phase kernel except at k = 7 (measured on octrees refined twice, ms, ten / five phases:
+  // k = 1 0.0209 / 0.0204, k = 2 0.0276 / 0.0276, k = 4 0.0890 / 0.0859, k = 5 0.1353 / 0.1289, k = 6
+  // 0.2177 / 0.2128, k = 7 0.1666 / 0.1705, k = 8 0.2570 / 0.2307); FP64: the ten-phase kernel (the
+  // five-phase one spills at the 80-register bound of the hanging variant: k = 4 0.750 / 0.914)
+  constexpr bool five = sizeof(Real) == 4 && N != 8;
+  auto kern = five ? vmult5_kernel<N, Real, HANG> : vmult_kernel<N, Real, HANG>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
