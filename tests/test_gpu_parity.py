@@ -172,10 +172,11 @@ def test_octree_tensor_product_hanging_constraints(mfx, seed, k, nb, radius):
     assert e32 < 1e-5, e32
 
 
-@pytest.mark.parametrize("k", [5, 8])
+@pytest.mark.parametrize("k", [5, 7, 8])
 def test_octree_diagonal_high_degree(mfx, k):
     """Diagonal and vmult on an octree at high degree: the diagonal's sum-factorised paths (cells with
-    and without hanging nodes) and both FP32 octree kernels."""
+    and without hanging nodes) and the FP32 octree kernels (five phases at k = 5 and 8, ten phases at
+    k = 7)."""
     leaves = synthetic.octree_leaves(2, 1, np.array([0.3, 0.3, 0.3]), 0.2)
     verts = synthetic.deformed_vertices(2, 2, 2)
     m = mfx.Mesh.octree(2, 2, 2, leaves, verts)
@@ -187,7 +188,7 @@ def test_octree_diagonal_high_degree(mfx, k):
     op.diagonal(d)
     dref = fem.diagonal(K)
     assert np.abs(d.cpu().numpy() - dref).max() < 1e-12 * np.abs(dref).max()
-    # vmult at high degree (k = 8: the paired octree kernel in FP32; k = 5: the per-cell kernel)
+    # vmult at high degree
     x = synthetic.uniform_vector(om.n_dofs, 40 + k)
     ref = K @ x
     e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
