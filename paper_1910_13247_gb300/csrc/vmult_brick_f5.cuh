@@ -121,6 +121,138 @@ __device__ __forceinline__ void axpy_col2(float2 (&acc)[N], float2 h, int q, boo
   }
 }
 
+// Even-odd form of the 1D contractions (used from N = 5 on, where it saves multiply-adds).  The 1D
+// matrices are centro-symmetric (S: the nodal basis at Gauss points symmetric about 1/2) or
+// centro-antisymmetric (Sd): M[N-1-i][N-1-j] = sg M[i][j] with sg = +1 / -1, and so are their
+// transposes.  With e_j = v_j + v_{N-1-j}, d_j = v_j - v_{N-1-j} (j < N/2) and m = v_{N/2} (odd N):
+//   out_i = E_i + O_i,  out_{N-1-i} = sg (E_i - O_i)   (i < N/2),
+//   E_i = sum_j P_ij e_j + M_{i,N/2} m,  O_i = sum_j Q_ij d_j,  P_ij, Q_ij = (M_ij +- M_{i,N-1-j}) / 2,
+// and the middle row of odd N is sum_j M_{N/2,j} e_j + M_{N/2,N/2} m (sg = +1) or sum_j M_{N/2,j} d_j
+// (sg = -1).  T: apply the transpose.
+template <int N>
+constexpr bool kEvenOdd = N >= 5;
+
+template <int N, int MAT, bool T>
+__device__ __forceinline__ constexpr double eo_entry(int i, int j) {
+  return T ? basis_entry<N, MAT>(j * N + i) : basis_entry<N, MAT>(i * N + j);
+}
+
+__device__ __forceinline__ float2 f2(double c) { return make_float2((float)c, (float)c); }
+
+template <int N>
+__device__ __forceinline__ void eo_split(const float2 (&v)[N], float2 (&e)[N / 2], float2 (&d)[N / 2]) {
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    e[j] = __fadd2_rn(v[j], v[N - 1 - j]);
+    d[j] = __ffma2_rn(make_float2(-1.0f, -1.0f), v[N - 1 - j], v[j]);
+  }
+}
+
+// E_i (with the middle term) and O_i of row i < N/2
+template <int N, int MAT, bool T>
+__device__ __forceinline__ void eo_row(const float2 (&e)[N / 2], const float2 (&d)[N / 2], float2 m, int i, float2& E,
+                                       float2& O) {
+  constexpr int H = N / 2;
+  E = __fmul2_rn(f2(0.5 * (eo_entry<N, MAT, T>(i, 0) + eo_entry<N, MAT, T>(i, N - 1))), e[0]);
+  O = __fmul2_rn(f2(0.5 * (eo_entry<N, MAT, T>(i, 0) - eo_entry<N, MAT, T>(i, N - 1))), d[0]);
+#pragma unroll
+  for (int j = 1; j < H; ++j) {
+    E = __ffma2_rn(f2(0.5 * (eo_entry<N, MAT, T>(i, j) + eo_entry<N, MAT, T>(i, N - 1 - j))), e[j], E);
+    O = __ffma2_rn(f2(0.5 * (eo_entry<N, MAT, T>(i, j) - eo_entry<N, MAT, T>(i, N - 1 - j))), d[j], O);
+  }
+  if constexpr ((N & 1) != 0) E = __ffma2_rn(f2(eo_entry<N, MAT, T>(i, H)), m, E);
+}
+
+// the middle row of odd N
+template <int N, int MAT, bool T>
+__device__ __forceinline__ float2 eo_mid(const float2 (&e)[N / 2], const float2 (&d)[N / 2], float2 m) {
+  constexpr int H = N / 2;
+  if constexpr (MAT == MAT_S) {
+    float2 s = __fmul2_rn(f2(eo_entry<N, MAT, T>(H, H)), m);
+#pragma unroll
+    for (int j = 0; j < H; ++j) s = __ffma2_rn(f2(eo_entry<N, MAT, T>(H, j)), e[j], s);
+    return s;
+  } else {
+    float2 s = __fmul2_rn(f2(eo_entry<N, MAT, T>(H, 0)), d[0]);
+#pragma unroll
+    for (int j = 1; j < H; ++j) s = __ffma2_rn(f2(eo_entry<N, MAT, T>(H, j)), d[j], s);
+    return s;
+  }
+}
+
+// out = M v (T: M^T v) from a split input
+template <int N, int MAT, bool T>
+__device__ __forceinline__ void eo_apply(const float2 (&e)[N / 2], const float2 (&d)[N / 2], float2 m,
+                                         float2 (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    float2 E, O;
+    eo_row<N, MAT, T>(e, d, m, i, E, O);
+    out[i] = __fadd2_rn(E, O);
+    if constexpr (MAT == MAT_S)
+      out[N - 1 - i] = __ffma2_rn(make_float2(-1.0f, -1.0f), O, E);  // E - O
+    else
+      out[N - 1 - i] = __ffma2_rn(make_float2(-1.0f, -1.0f), E, O);  // -(E - O)
+  }
+  if constexpr ((N & 1) != 0) out[N / 2] = eo_mid<N, MAT, T>(e, d, m);
+}
+
+// out = S^T a + Sd^T b (T) or S a + Sd b from split inputs: with X = E_S(a) + O_Sd(b) and
+// Y = O_S(a) + E_Sd(b), out_i = X + Y and out_{N-1-i} = X - Y
+template <int N, bool T>
+__device__ __forceinline__ void eo_apply_s_sd(const float2 (&ea)[N / 2], const float2 (&da)[N / 2], float2 ma,
+                                              const float2 (&eb)[N / 2], const float2 (&db)[N / 2], float2 mb,
+                                              float2 (&out)[N]) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    float2 Ea, Oa, Eb, Ob;
+    eo_row<N, MAT_S, T>(ea, da, ma, i, Ea, Oa);
+    eo_row<N, MAT_SD, T>(eb, db, mb, i, Eb, Ob);
+    const float2 X = __fadd2_rn(Ea, Ob), Y = __fadd2_rn(Oa, Eb);
+    out[i] = __fadd2_rn(X, Y);
+    out[N - 1 - i] = __ffma2_rn(make_float2(-1.0f, -1.0f), Y, X);
+  }
+  if constexpr ((N & 1) != 0)
+    out[N / 2] = __fadd2_rn(eo_mid<N, MAT_S, T>(ea, da, ma), eo_mid<N, MAT_SD, T>(eb, db, mb));
+}
+
+// The contractions of the phases, in even-odd form from N = 5 on
+template <int N>
+__device__ __forceinline__ void c2_s_sd(const float2 (&v)[N], float2 (&os)[N], float2 (&od)[N]) {  // S v, Sd v
+  if constexpr (kEvenOdd<N>) {
+    float2 e[N / 2], d[N / 2];
+    eo_split<N>(v, e, d);
+    eo_apply<N, MAT_S, false>(e, d, v[N / 2], os);
+    eo_apply<N, MAT_SD, false>(e, d, v[N / 2], od);
+  } else {
+    contract2<N, MAT_S>(v, os);
+    contract2<N, MAT_SD>(v, od);
+  }
+}
+template <int N, int MAT, bool T>
+__device__ __forceinline__ void c2_one(const float2 (&v)[N], float2 (&o)[N]) {  // M v or M^T v
+  if constexpr (kEvenOdd<N>) {
+    float2 e[N / 2], d[N / 2];
+    eo_split<N>(v, e, d);
+    eo_apply<N, MAT, T>(e, d, v[N / 2], o);
+  } else if constexpr (T) {
+    contract2_t<N, MAT>(v, o);
+  } else {
+    contract2<N, MAT>(v, o);
+  }
+}
+template <int N>
+__device__ __forceinline__ void c2_tt(const float2 (&a)[N], const float2 (&b)[N], float2 (&o)[N]) {  // S^T a + Sd^T b
+  if constexpr (kEvenOdd<N>) {
+    float2 ea[N / 2], da[N / 2], eb[N / 2], db[N / 2];
+    eo_split<N>(a, ea, da);
+    eo_split<N>(b, eb, db);
+    eo_apply_s_sd<N, true>(ea, da, a[N / 2], eb, db, b[N / 2], o);
+  } else {
+    contract2_tt<N, MAT_S, MAT_SD>(a, b, o);
+  }
+}
+
 // MS: metric staged in shared memory (1) or read from L2 (0); MB: CTAs per SM the registers are sized for;
 // TB: input tiles (2: the next batch's rows are requested when a batch starts, 1: once phase 1 has read
 // the tile); MBF: staged metric buffers (2: the next batch's metric is requested when a batch starts);
@@ -288,12 +420,13 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
       }
       if (zlo) v[0] = make_float2(0.0f, 0.0f);
       if (zhi) v[K] = make_float2(0.0f, 0.0f);
-      contract2<N, MAT_S>(v, o);
+      float2 od[N];
+      c2_s_sd<N>(v, o, od);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A[zbase + j * P2] = o[j];
-      contract2<N, MAT_SD>(v, o);
-#pragma unroll
-      for (int j = 0; j < N; ++j) C[zbase + j * P2] = o[j];
+      for (int j = 0; j < N; ++j) {
+        A[zbase + j * P2] = o[j];
+        C[zbase + j * P2] = od[j];
+      }
     }
     __syncthreads();
     // one input tile: it is free now, the next batch's rows
@@ -310,15 +443,16 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
       float2 v[N], o[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = A[ybase + j * NP];
-      contract2<N, MAT_S>(v, o);
+      float2 od[N];
+      c2_s_sd<N>(v, o, od);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
-      contract2<N, MAT_SD>(v, o);
-#pragma unroll
-      for (int j = 0; j < N; ++j) B[ybase + j * NP] = o[j];
+      for (int j = 0; j < N; ++j) {
+        A[ybase + j * NP] = o[j];
+        B[ybase + j * NP] = od[j];
+      }
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = C[ybase + j * NP];
-      contract2<N, MAT_S>(v, o);
+      c2_one<N, MAT_S, false>(v, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) C[ybase + j * NP] = o[j];
     }
@@ -346,9 +480,8 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
       }
       const float2* Gm = MS ? reinterpret_cast<const float2*>(Msm) + gq
                             : reinterpret_cast<const float2*>(a.metric + (int64_t)b * Fs::METRIC) + gq;
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        const float2 u1 = row2<N, MAT_SD>(va, q), u2 = row2<N, MAT_S>(vb, q), u3 = row2<N, MAT_S>(vc, q);
+      // the merged metric at Gauss point q of this x-line: h = G grad
+      auto qpoint = [&](int q, float2 u1, float2 u2, float2 u3, float2& h1, float2& h2, float2& h3) {
         float2 G00, G01, G02, G11, G12, G22;
         if constexpr (MS != 0) {
           G00 = Gm[(0 * N3 + q) * PP]; G01 = Gm[(1 * N3 + q) * PP]; G02 = Gm[(2 * N3 + q) * PP];
@@ -358,12 +491,36 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
           G02 = __ldg(Gm + (2 * N3 + q) * PP); G11 = __ldg(Gm + (3 * N3 + q) * PP);
           G12 = __ldg(Gm + (4 * N3 + q) * PP); G22 = __ldg(Gm + (5 * N3 + q) * PP);
         }
-        const float2 h1 = __ffma2_rn(G02, u3, __ffma2_rn(G01, u2, __fmul2_rn(G00, u1)));
-        const float2 h2 = __ffma2_rn(G12, u3, __ffma2_rn(G11, u2, __fmul2_rn(G01, u1)));
-        const float2 h3 = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
-        axpy_col2<N, MAT_SD>(ra, h1, q, q == 0);
-        axpy_col2<N, MAT_S>(rb, h2, q, q == 0);
-        axpy_col2<N, MAT_S>(rc, h3, q, q == 0);
+        h1 = __ffma2_rn(G02, u3, __ffma2_rn(G01, u2, __fmul2_rn(G00, u1)));
+        h2 = __ffma2_rn(G12, u3, __ffma2_rn(G11, u2, __fmul2_rn(G01, u1)));
+        h3 = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
+      };
+      if constexpr (kEvenOdd<N>) {
+        // gradient at all Gauss points of the line, h in place, then the transposed contractions
+        float2 u1[N], u2[N], u3[N];
+        c2_one<N, MAT_SD, false>(va, u1);
+        c2_one<N, MAT_S, false>(vb, u2);
+        c2_one<N, MAT_S, false>(vc, u3);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          float2 h1, h2, h3;
+          qpoint(q, u1[q], u2[q], u3[q], h1, h2, h3);
+          u1[q] = h1;
+          u2[q] = h2;
+          u3[q] = h3;
+        }
+        c2_one<N, MAT_SD, true>(u1, ra);
+        c2_one<N, MAT_S, true>(u2, rb);
+        c2_one<N, MAT_S, true>(u3, rc);
+      } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          float2 h1, h2, h3;
+          qpoint(q, row2<N, MAT_SD>(va, q), row2<N, MAT_S>(vb, q), row2<N, MAT_S>(vc, q), h1, h2, h3);
+          axpy_col2<N, MAT_SD>(ra, h1, q, q == 0);
+          axpy_col2<N, MAT_S>(rb, h2, q, q == 0);
+          axpy_col2<N, MAT_S>(rc, h3, q, q == 0);
+        }
       }
     }
     // the x-point shared by cells 2c - 1 and 2c (pair c - 1's second cell, lane - 1) and the one
@@ -405,12 +562,12 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
         va[j] = A[ybase + j * NP];
         vb[j] = B[ybase + j * NP];
       }
-      contract2_tt<N, MAT_S, MAT_SD>(va, vb, o);
+      c2_tt<N>(va, vb, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) A[ybase + j * NP] = o[j];
 #pragma unroll
       for (int j = 0; j < N; ++j) va[j] = C[ybase + j * NP];
-      contract2_t<N, MAT_S>(va, o);
+      c2_one<N, MAT_S, true>(va, o);
 #pragma unroll
       for (int j = 0; j < N; ++j) C[ybase + j * NP] = o[j];
     }
@@ -426,7 +583,7 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
         va[j] = A[zbase + j * P2];
         vc[j] = C[zbase + j * P2];
       }
-      contract2_tt<N, MAT_S, MAT_SD>(va, vc, o);
+      c2_tt<N>(va, vc, o);
       const bool w0 = f < K || 2 * c == m - 1;
       const bool w1 = act1 && (f < K || 2 * c + 1 == m - 1);
 #pragma unroll
