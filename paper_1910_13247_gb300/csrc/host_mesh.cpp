@@ -15,9 +15,11 @@
 //    weights and Dirichlet masters are dropped; masters sorted by DoF.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -269,43 +271,48 @@ struct NodeKey {
 
 inline bool irrational(uint32_t dk) { return (dk >> 31) != 0; }
 
-// Flat open-addressing table NodeKey -> DoF (linear probing, power-of-two capacity); key and DoF share
-// one 16-byte slot, so a probe touches one cache line.
-class NodeTable {
+// Open-addressing table NodeKey -> (smallest visit, DoF) filled by several threads at once (linear
+// probing, power-of-two capacity).  A slot is claimed by one compare-and-swap of its visit word (empty ->
+// busy), its key written and the visit published; a thread that meets its key lowers the visit word to
+// its own visit if that is smaller.  Readers compare keys only after seeing a published visit.
+class VisitTable {
  public:
-  explicit NodeTable(size_t expected) { init(capacity_for(expected)); }
-  size_t slot(const NodeKey& k) const { return hash(k) & mask_; }
-  void prefetch(size_t h) const { __builtin_prefetch(&slots_[h]); }
-  // room for `more` inserts at a load of at most 0.7 (doubles the table and rehashes if needed; home
-  // slots taken before a call are invalid after it)
-  bool reserve_more(size_t more) {
-    if ((size_ + more) * 10 <= slots_.size() * 7) return false;
-    std::vector<Slot> old;
-    old.swap(slots_);
-    init(capacity_for(size_ + more));
-    for (const Slot& s : old)
-      if (s.dof >= 0) {
-        size_t h = slot(s.key);
-        while (slots_[h].dof >= 0) h = (h + 1) & mask_;
-        slots_[h] = s;
-      }
-    return true;
+  static constexpr int64_t kEmpty = -1, kBusy = -2;
+  explicit VisitTable(size_t cap) : slots_(cap), mask_(cap - 1) {
+    for (auto& s : slots_) s.visit.store(kEmpty, std::memory_order_relaxed);
   }
-  // DoF of the key (whose home slot is h), inserting `next` if absent; returns (dof, inserted).
-  // The caller keeps the load below 1 (reserve_more), so a free slot is always found.
-  std::pair<int32_t, bool> find_or_insert(const NodeKey& k, size_t h, int32_t next) {
-    for (;;) {
+  size_t capacity() const { return slots_.size(); }
+  // slot of the key (whose home slot is h), inserted with `visit` if absent (*added: whether this call
+  // inserted it); SIZE_MAX when every slot was probed (the table is full)
+  size_t home(const NodeKey& k) const { return hash(k) & mask_; }
+  void prefetch(size_t h) const { __builtin_prefetch(&slots_[h], 1); }
+  size_t insert(const NodeKey& k, size_t h, int64_t visit, bool* added) {
+    *added = false;
+    for (size_t probes = 0; probes <= mask_;) {
       Slot& s = slots_[h];
-      if (s.dof < 0) {
-        s.key = k;
-        s.dof = next;
-        ++size_;
-        return {next, true};
+      int64_t v = s.visit.load(std::memory_order_acquire);
+      if (v == kEmpty) {
+        if (s.visit.compare_exchange_strong(v, kBusy, std::memory_order_acq_rel)) {
+          s.key = k;
+          s.visit.store(visit, std::memory_order_release);
+          *added = true;
+          return h;
+        }
+        continue;  // claimed meanwhile: look at this slot again
       }
-      if (s.key == k) return {s.dof, false};
+      if (v == kBusy) continue;  // its key is being written
+      if (s.key == k) {
+        while (visit < v && !s.visit.compare_exchange_weak(v, visit, std::memory_order_acq_rel)) {
+        }
+        return h;
+      }
       h = (h + 1) & mask_;
+      ++probes;
     }
+    return SIZE_MAX;
   }
+  int64_t visit(size_t h) const { return slots_[h].visit.load(std::memory_order_relaxed); }
+  int32_t& dof(size_t h) { return slots_[h].dof; }
 
  private:
   static size_t hash(const NodeKey& k) {
@@ -320,18 +327,10 @@ class NodeTable {
   struct Slot {
     NodeKey key;
     int32_t dof;
+    std::atomic<int64_t> visit;
   };
-  static size_t capacity_for(size_t n) {  // power of two, load at most 2/3
-    size_t cap = 16;
-    while (2 * cap < 3 * n + 16) cap <<= 1;
-    return cap;
-  }
-  void init(size_t cap) {
-    slots_.assign(cap, Slot{{~0u, ~0u, ~0u}, -1});
-    mask_ = cap - 1;
-  }
   std::vector<Slot> slots_;
-  size_t mask_ = 0, size_ = 0;
+  size_t mask_;
 };
 
 }  // namespace
@@ -367,50 +366,126 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
   int interior_1d = 0;
   for (int a = 0; a <= k; ++a)
     if (a != 0 && a != k && 2 * a != k) ++interior_1d;
-  // distinct shared (non-interior) nodes: about k^3 - interior_1d^3 per cell away from refinement
-  // interfaces (the table grows if there are more)
-  const size_t shared_per_cell = (size_t)std::max(1, k * k * k - interior_1d * interior_1d * interior_1d);
-  NodeTable dof_of((size_t)C * shared_per_cell + 1024);
-  out->cell_dofs.assign(C * n3, 0);
-  std::vector<NodeKey> keys_by_dof;
-  keys_by_dof.reserve((size_t)C * n3 / 2 + 16);
-  // first-encounter pass over the cells in order; the keys of the next D cells are formed and their
-  // home slots prefetched ahead of it (a ring of D cells)
-  const int D = std::max(2, 64 / n3);
-  std::vector<NodeKey> ck((size_t)D * n3);
-  std::vector<size_t> cs((size_t)D * n3);
-  auto stage = [&](int64_t c) {
-    const size_t o = (size_t)(c % D) * n3;
-    for (int a3 = 0; a3 < n; ++a3)
-      for (int a2 = 0; a2 < n; ++a2)
-        for (int a1 = 0; a1 < n; ++a1) {
-          const size_t li = o + a1 + n * (a2 + n * a3);
-          ck[li] = node_key(c, a1, a2, a3);
-          cs[li] = dof_of.slot(ck[li]);
-          dof_of.prefetch(cs[li]);
-        }
+  // DoF numbering in first-encounter order (the order of the visits c n^3 + li of the cells' local
+  // nodes), on threads: (1) every visit of a shared node enters the table, which keeps the smallest
+  // visit of each key; (2) per chunk of cells the first visits are counted (interior nodes belong to one
+  // cell: each of their visits is a first one); (3) they are numbered in visit order, each chunk from the
+  // sum of the counts before it; (4) the other visits read the number of their key.
+  const int64_t nv = C * n3;
+  out->cell_dofs.assign(nv, 0);
+  constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+  std::vector<uint32_t> vslot(nv);  // table slot of each visit, kNoSlot for interior nodes
+  std::vector<uint8_t> first(nv);   // the visit is the first of its node
+  auto interior_key = [](const NodeKey& key) {
+    return irrational(key.d[0]) && irrational(key.d[1]) && irrational(key.d[2]);
   };
-  for (int64_t c = 0; c < std::min<int64_t>(D, C); ++c) stage(c);
-  for (int64_t c = 0; c < C; ++c) {
-    if (dof_of.reserve_more((size_t)D * n3))  // rehashed: the staged home slots moved
-      for (size_t i = 0; i < ck.size(); ++i) cs[i] = dof_of.slot(ck[i]);
-    const size_t o = (size_t)(c % D) * n3;
-    for (int li = 0; li < n3; ++li) {
-      const NodeKey& key = ck[o + li];
-      if (keys_by_dof.size() >= (size_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
-      const int32_t next = (int32_t)keys_by_dof.size();
-      int32_t dof = next;
-      if (!(irrational(key.d[0]) && irrational(key.d[1]) && irrational(key.d[2]))) {
-        auto r = dof_of.find_or_insert(key, cs[o + li], next);
-        dof = r.first;
-        if (r.second) keys_by_dof.push_back(key);
-      } else {
-        keys_by_dof.push_back(key);
+  // distinct shared nodes: about k^3 - interior_1d^3 per cell away from refinement interfaces; a table
+  // that passes 70 % load is dropped and the pass repeated with twice the capacity
+  size_t expect = (size_t)C * (size_t)std::max(1, k * k * k - interior_1d * interior_1d * interior_1d) + 1024;
+  std::unique_ptr<VisitTable> table;
+  for (;;) {
+    size_t cap = 16;
+    while (2 * cap < 3 * expect) cap <<= 1;
+    if (cap > (size_t)kNoSlot) return set_error(MFX_EUNSUPPORTED, "octree too large for the node table");
+    table.reset(new VisitTable(cap));
+    std::atomic<size_t> inserted{0};
+    std::atomic<bool> full{false};
+    const size_t limit = cap / 10 * 7;
+    parallel_chunks(C, [&](int64_t lo, int64_t hi) {
+      // keys and home slots of the next D cells formed and prefetched ahead (a ring of D cells)
+      const int D = std::max(2, 64 / n3);
+      std::vector<NodeKey> ck((size_t)D * n3);
+      std::vector<size_t> cs((size_t)D * n3);
+      auto stage = [&](int64_t c) {
+        const size_t o = (size_t)(c % D) * n3;
+        for (int a3 = 0; a3 < n; ++a3)
+          for (int a2 = 0; a2 < n; ++a2)
+            for (int a1 = 0; a1 < n; ++a1) {
+              const size_t li = o + a1 + n * (a2 + n * a3);
+              ck[li] = node_key(c, a1, a2, a3);
+              if (!interior_key(ck[li])) {
+                cs[li] = table->home(ck[li]);
+                table->prefetch(cs[li]);
+              }
+            }
+      };
+      for (int64_t c = lo; c < std::min<int64_t>(lo + D, hi); ++c) stage(c);
+      size_t mine = 0;
+      for (int64_t c = lo; c < hi; ++c) {
+        const size_t o = (size_t)(c % D) * n3;
+        for (int li = 0; li < n3; ++li) {
+          const int64_t v = c * n3 + li;
+          if (interior_key(ck[o + li])) {
+            vslot[v] = kNoSlot;
+            first[v] = 1;
+            continue;
+          }
+          bool added;
+          const size_t h = table->insert(ck[o + li], cs[o + li], v, &added);
+          if (h == SIZE_MAX) {
+            full.store(true);
+            return;
+          }
+          vslot[v] = (uint32_t)h;
+          mine += added ? 1 : 0;
+        }
+        if (c + D < hi) stage(c + D);
+        // the shared count, at most every 64k node visits of this thread
+        if (mine >= 65536 || (c + 1) % std::max<int64_t>(1, 65536 / n3) == 0 || c + 1 == hi) {
+          if (inserted.fetch_add(mine) + mine > limit) full.store(true);
+          mine = 0;
+          if (full.load(std::memory_order_relaxed)) return;
+        }
       }
-      out->cell_dofs[c * n3 + li] = dof;
-    }
-    if (c + D < C) stage(c + D);
+    });
+    if (!full.load()) break;
+    expect *= 2;
   }
+  // first visits of shared nodes: the smallest visit each slot of the table holds
+  parallel_chunks((int64_t)table->capacity(), [&](int64_t lo, int64_t hi) {
+    for (int64_t h = lo; h < hi; ++h) {
+      const int64_t v = table->visit((size_t)h);
+      if (v >= 0) first[v] = 1;
+    }
+  });
+  auto is_first = [&](int64_t v) { return first[v] != 0; };
+  const int64_t csz = std::max<int64_t>(4096, (C + 255) / 256);  // cells per chunk
+  const int64_t nch = (C + csz - 1) / csz;
+  std::vector<int64_t> base(nch + 1, 0);
+  parallel_chunks(nch, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      int64_t cnt = 0;
+      for (int64_t v = ch * csz * n3; v < std::min(C, (ch + 1) * csz) * n3; ++v) cnt += is_first(v) ? 1 : 0;
+      base[ch + 1] = cnt;
+    }
+  });
+  for (int64_t ch = 0; ch < nch; ++ch) base[ch + 1] += base[ch];
+  if (base[nch] >= (int64_t)INT32_MAX) return set_error(MFX_EUNSUPPORTED, "more than 2^31 - 1 DoFs");
+  std::vector<NodeKey> keys_by_dof(base[nch]);
+  parallel_chunks(nch, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      int32_t next = (int32_t)base[ch];
+      for (int64_t v = ch * csz * n3; v < std::min(C, (ch + 1) * csz) * n3; ++v) {
+        if (!is_first(v)) continue;
+        const int64_t c = v / n3;
+        const int li = (int)(v - c * n3);
+        keys_by_dof[next] = node_key(c, li % n, (li / n) % n, li / (n * n));
+        if (vslot[v] != kNoSlot) table->dof(vslot[v]) = next;
+        out->cell_dofs[v] = next++;
+      }
+    }
+  });
+  parallel_chunks(nv, [&](int64_t lo, int64_t hi) {
+    for (int64_t v = lo; v < hi; ++v) {
+      if (v + 32 < hi && !first[v + 32]) table->prefetch(vslot[v + 32]);
+      if (!is_first(v)) out->cell_dofs[v] = table->dof(vslot[v]);
+    }
+  });
+  table.reset();
+  vslot.clear();
+  vslot.shrink_to_fit();
+  first.clear();
+  first.shrink_to_fit();
   const int64_t N = (int64_t)keys_by_dof.size();
   out->n_dofs = N;
   const uint32_t ext[3] = {(uint32_t)m.nx * R2, (uint32_t)m.ny * R2, (uint32_t)m.nz * R2};
