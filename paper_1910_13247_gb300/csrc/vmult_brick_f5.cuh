@@ -34,19 +34,23 @@
 
 namespace mfx {
 
-template <int N, int CB, int MS, int TB = 1, int MBF = 1>
+template <int N, int CB, int MS, int TB = 1, int MBF = 1, int PK = 0>
 struct F5Shape {
   static constexpr int PP = CB / 2;
   static constexpr int LINES = PP * N * N;
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int CUBES = PP * BrickShape<N, CB, float>::CELL;  // float2 elements per cube
   static constexpr int METRIC = 6 * N * N * N * CB;                  // floats of one batch's metric
+  // tile rows: 128-byte pitch for tensor copies, or packed at the box width (PK: untiled bulk copies)
+  static constexpr int PITCH = PK ? TmaShape<N, CB>::BOX : TmaShape<N, CB>::PITCH;
+  static constexpr int TILE = TmaShape<N, CB>::ROWS * PITCH;
   // TB input tiles and one output tile, MBF staged metric buffers (MS), three cubes, four mbarriers
-  static constexpr size_t SMEM = (size_t)(TB + 1) * TmaShape<N, CB>::TILE * sizeof(float) +
+  static constexpr size_t SMEM = (size_t)(TB + 1) * TILE * sizeof(float) +
                                  (MS ? (size_t)MBF * METRIC * sizeof(float) : 0) + 3 * (size_t)CUBES * sizeof(float2) +
                                  4 * sizeof(uint64_t);
   static_assert(32 % PP == 0, "the pairs of one line must share a warp (x-point shuffle)");
   static_assert((METRIC * sizeof(float)) % 16 == 0, "bulk copy size");
+  static_assert((TILE * sizeof(float)) % 16 == 0 && (PITCH * sizeof(float)) % 16 == 0, "16-byte tile rows");
   static_assert(TB == 1 || TB == 2, "one or two input tiles");
   static_assert(MBF == 1 || MBF == 2, "one or two metric buffers");
 };
@@ -58,6 +62,14 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// dst[0 .. bytes / 4) += src[...] (untiled bulk reduce-add, bulk-group completion); both addresses
+// 16-byte aligned, size a multiple of 16
+__device__ __forceinline__ void bulk_reduce_add_f32(float* dst, const float* src, unsigned bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
 }
 
 // L2 policy for data read once (the metric stream): evicted first, so that the vectors' lines stay
@@ -257,21 +269,21 @@ __device__ __forceinline__ void c2_tt(const float2 (&a)[N], const float2 (&b)[N]
 // TB: input tiles (2: the next batch's rows are requested when a batch starts, 1: once phase 1 has read
 // the tile); MBF: staged metric buffers (2: the next batch's metric is requested when a batch starts);
 // EF: the metric stream carries the L2 evict-first policy
-template <int N, int CB, int MS, int MB, int TB, int MBF, int EF>
-__global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
+template <int N, int CB, int MS, int MB, int TB, int MBF, int EF, int PK = 0>
+__global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF, PK>::THREADS, MB)
     brick_vmult_f5_kernel(const __grid_constant__ TmaArgs<N> a) {
   using Sh = BrickShape<N, CB, float>;  // cube paddings of CB cells = paddings of CB / 2 float pairs
   using Tm = TmaShape<N, CB>;
-  using Fs = F5Shape<N, CB, MS, TB, MBF>;
+  using Fs = F5Shape<N, CB, MS, TB, MBF, PK>;
   constexpr int PP = Fs::PP;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
-  constexpr int PITCH = Tm::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
+  constexpr int PITCH = Fs::PITCH, ROWS = Tm::ROWS, BOX = Tm::BOX;
   constexpr unsigned MBYTES = Fs::METRIC * 4u;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* T0 = reinterpret_cast<float*>(smem_raw);  // input tile(s)
-  float* O = T0 + TB * Tm::TILE;                    // output tile
-  float* M0 = O + Tm::TILE;                         // MS: staged metric buffer(s), [6][N^3][CB] each
+  float* O = T0 + TB * Fs::TILE;                    // output tile
+  float* M0 = O + Fs::TILE;                         // MS: staged metric buffer(s), [6][N^3][CB] each
   float2* A = reinterpret_cast<float2*>(M0 + (MS ? MBF * Fs::METRIC : 0));
   float2* B = A + Fs::CUBES;
   float2* C = B + Fs::CUBES;
@@ -304,12 +316,36 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
   auto issue_rows = [&](const BatchPos& pb, int buf) {
     const BatchInfo bi = batch_info_at<CB, K>(a, pb);
     fence_proxy_async();
-    if (lane == 0) mbar_arrive_expect_tx(&bars[buf], ROWS * BOX * 4);
-    __syncwarp();
-    float* T = T0 + buf * Tm::TILE;
-    for (int row = lane; row < ROWS; row += 32) {
-      const int a2 = row % N, a3 = row / N;
-      tma_load_1d(T + row * PITCH, &a.tsrc, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, &bars[buf]);
+    float* T = T0 + buf * Fs::TILE;
+    if constexpr (PK) {
+      // untiled bulk copies of the rows, clipped at the end of src: the whole 16-byte words inside src
+      // by the copy engine, the last 0..3 points by plain loads, the rest of the box zero
+      unsigned bytes = 0;
+      for (int row = lane; row < ROWS; row += 32) {
+        const int a2 = row % N, a3 = row / N;
+        const int64_t g0 = (int64_t)((bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3);
+        const int len = (int)(a.n - g0 < BOX ? a.n - g0 : BOX);
+        bytes += (unsigned)(len & ~3) * 4u;
+      }
+      bytes = __reduce_add_sync(0xffffffffu, bytes);
+      if (lane == 0) mbar_arrive_expect_tx(&bars[buf], bytes);
+      __syncwarp();
+      for (int row = lane; row < ROWS; row += 32) {
+        const int a2 = row % N, a3 = row / N;
+        const int64_t g0 = (int64_t)((bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3);
+        const int len = (int)(a.n - g0 < BOX ? a.n - g0 : BOX);
+        const int whole = len & ~3;
+        float* dst = T + row * PITCH;
+        if (whole > 0) bulk_load(dst, a.src + g0, (unsigned)whole * 4u, &bars[buf]);
+        for (int x = whole; x < BOX; ++x) dst[x] = x < len ? a.src[g0 + x] : 0.0f;
+      }
+    } else {
+      if (lane == 0) mbar_arrive_expect_tx(&bars[buf], ROWS * BOX * 4);
+      __syncwarp();
+      for (int row = lane; row < ROWS; row += 32) {
+        const int a2 = row % N, a3 = row / N;
+        tma_load_1d(T + row * PITCH, &a.tsrc, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, &bars[buf]);
+      }
     }
   };
   // MS: the batch's metric in four bulk copies (lanes 0..3)
@@ -367,7 +403,7 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
     const unsigned rpar = TB == 2 ? ((it >> 1) & 1) : (it & 1);
     const int mbuf = MBF == 2 ? (it & 1) : 0;
     const unsigned mpar = MBF == 2 ? ((it >> 1) & 1) : (it & 1);
-    float* T = T0 + rbuf * Tm::TILE;
+    float* T = T0 + rbuf * Fs::TILE;
     const float* Msm = M0 + mbuf * Fs::METRIC;
     // metric read from L2 (MS = 0): the TMA engine brings the next batch's metric into L2 (nothing waits
     // for it); with the staged metric the bulk copy alone measured faster (Q4 0.2585 -> 0.2503 ms, Q2
@@ -616,7 +652,16 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF>::THREADS, MB)
     if (tma_warp) {
       for (int row = lane; row < ROWS; row += 32) {
         const int a2 = row % N, a3 = row / N;
-        tma_reduce_add_1d(&a.tdst, (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3, O + row * PITCH);
+        const int g0 = (bi.gbase + a.Mx * (a2 + a.My * a3)) & ~3;
+        if constexpr (PK) {
+          // the whole 16-byte words inside dst by the copy engine, the last 0..3 points by atomics
+          const int len = (int)(a.n - g0 < BOX ? a.n - g0 : BOX);
+          const int whole = len & ~3;
+          if (whole > 0) bulk_reduce_add_f32(a.dst + g0, O + row * PITCH, (unsigned)whole * 4u);
+          for (int x = whole; x < len; ++x) atomicAdd(a.dst + g0 + x, O[row * PITCH + x]);
+        } else {
+          tma_reduce_add_1d(&a.tdst, g0, O + row * PITCH);
+        }
       }
       bulk_commit();
     }

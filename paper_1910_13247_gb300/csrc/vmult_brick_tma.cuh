@@ -37,6 +37,10 @@ struct TmaArgs {
   const int32_t* skip;
   uint32_t dmask;         // Dirichlet faces
   int step_chunk, step_y, step_z;  // the grid size as (chunk, y, z) steps of batch positions
+  // plain pointers and length of src and dst (kernels that move tile rows by untiled bulk copies)
+  const float* src;
+  float* dst;
+  int64_t n;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -274,12 +274,18 @@ struct F5Config {
   static constexpr int TB = 1;
   static constexpr int MBF = 1;
   static constexpr int EF = 0;
+  // tile rows packed at the box width and moved by untiled bulk copies (clipped at the vector end) where
+  // the smaller tiles give one more CTA per SM: staged metric at Q4 with 8 cells per batch (five CTAs
+  // instead of four: 64^3 0.2409 -> 0.2332 ms); elsewhere measured slower (Q4 16 cells 0.2563 -> 0.2735,
+  // Q3 8 cells 0.3181 -> 0.3354, Q2 32 cells 0.3262 -> 0.3477 ms)
+  static constexpr int PK = (MS && N == 5 && CB == 8) ? 1 : 0;
 };
 
 template <int N, int CB, int MS>
 static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
   using Cf = F5Config<N, CB, MS>;
-  using Fs = F5Shape<N, CB, MS, Cf::TB, Cf::MBF>;
+  constexpr int PK = Cf::PK;
+  using Fs = F5Shape<N, CB, MS, Cf::TB, Cf::MBF, PK>;
   using Tm = TmaShape<N, CB>;
   // resident CTAs per SM the register budget is sized for: about 672 threads per SM, fewer when the
   // shared memory bounds them
@@ -288,7 +294,7 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
   constexpr int MB = MB0 < MBS ? MB0 : MBS;
   static int blocks_per_sm = -1;
   const size_t smem = Fs::SMEM;
-  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB, Cf::TB, Cf::MBF, Cf::EF>;
+  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB, Cf::TB, Cf::MBF, Cf::EF, PK>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -302,6 +308,9 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
   st = encode_1d_map(&a.tdst, dst, op->n_dofs, Tm::BOX);
   if (st != MFX_OK) return st;
   a.metric = op->d_metric32;
+  a.src = src;
+  a.dst = dst;
+  a.n = op->n_dofs;
   a.nx = op->nx;
   a.ny = op->ny;
   a.nz = op->nz;
