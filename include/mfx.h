@@ -435,8 +435,8 @@ mfx_status mfx_dot(const mfx_op* op, mfx_prec prec, int64_t n, const void* a, co
  * into the library (kept on every GPU that loads it until exit).
  * a, b: device vectors of n entries of the precision; result: device FP64 scalar.
  * n above MFX_NOALLOC_MAX_N is rejected with MFX_EINVAL.  The first call on a device
- * looks up the array's address; make it before any stream capture.  Calls share the
- * array: calls that overlap on the GPU race and give wrong results.
+ * looks up the array's address (cudaGetSymbolAddress).  Calls share the array: calls
+ * that overlap on the GPU race and give wrong results.
  */
 #define MFX_NOALLOC_MAX_N 2147483647LL
 mfx_status mfx_dot_noalloc(mfx_prec prec, int64_t n, const void* a, const void* b, double* result,

@@ -9,8 +9,7 @@
 //
 // The array (kPartials doubles plus a counter, about 8 KB) lives in every GPU that loads the
 // library until the process exits.  Its device address is looked up once per device, on the
-// first call made with that device current (cudaGetSymbolAddress); that first call should be
-// made before any stream capture begins.  All calls share the array and it keeps the last
+// first call made with that device current (cudaGetSymbolAddress).  All calls share the array and it keeps the last
 // call's contents: each call clears the counter itself, and calls that overlap on the GPU
 // (different streams, or different host threads) race on the array and give wrong results.
 #include <cuda_runtime.h>
