@@ -57,6 +57,13 @@ __device__ __forceinline__ void contract_tt1(const Real (&x)[N], const Real (&y)
   }
 }
 
+// Scratch of the tensor-product interpolation of hanging values (per cell 6 n^2 + 12 n values): the B and
+// C cubes of the cell where they are large enough, else a region of its own after the coarse values
+template <int N>
+struct Cell5Scratch {
+  static constexpr bool OWN = 2 * VmultShape<N>::CELL < 6 * N * N + 12 * N;
+};
+
 // HANG: hanging constraints in tensor-product form (bounded to 80 registers for three CTAs per SM, as
 // the ten-phase kernel)
 template <int N, typename Real, bool HANG>
@@ -77,7 +84,9 @@ __global__ void __launch_bounds__(256, HANG ? 3 : (sizeof(Real) == 4 ? 4 : 1)) v
   Real* A = reinterpret_cast<Real*>(smem_raw) + (line_ok ? cl : 0) * CELL;
   Real* B = A + CB * CELL;
   Real* C = B + CB * CELL;
+  Real* const B0 = reinterpret_cast<Real*>(smem_raw) + CB * CELL;  // the B and C cubes of all cells
   Real* HB = reinterpret_cast<Real*>(smem_raw) + 3 * CB * CELL + (line_ok ? cl : 0) * HB_CELL;
+
   const int xl = (rb * N + ra) * NP;  // x-line (i2 = ra, i3 = rb)
   const int yl = rb * N * NP + ra;    // y-line (x = ra, z = rb), stride NP
   const int zl = rb * NP + ra;        // z-line (x = ra, y = rb), stride N NP
@@ -139,10 +148,62 @@ __global__ void __launch_bounds__(256, HANG ? 3 : (sizeof(Real) == 4 ? 4 : 1)) v
         }
       }
       __syncthreads();
+      // the coarse values interpolated to the fine face and edge nodes in tensor-product form, N^3 instead
+      // of N^4 multiply-adds per face: along u into the scratch TS (B and C, free until the contractions
+      // of this phase), then along v back into HB; an edge's 1D interpolation goes through TS unchanged
+      Real* TS = Cell5Scratch<N>::OWN ? HB + CB * HB_CELL : B0 + (line_ok ? cl : 0) * 2 * CELL;
+      if (act && hang) {
+        const int au = r % N, mw = r / N;
+        for (int f = 0; f < 6; ++f) {
+          if (!(hf >> f & 1u)) continue;
+          const Real* Pu = a.P + ((hf >> (6 + 2 * f)) & 1) * N2 + au * N;
+          const Real* F = HB + f * N2 + N * mw;
+          Real t = Real(0);
+#pragma unroll
+          for (int mu = 0; mu < N; ++mu) t += Pu[mu] * F[mu];
+          TS[f * N2 + r] = t;
+        }
+        if (r < N)
+          for (int e = 0; e < 12; ++e) {
+            if (!(he >> e & 1u)) continue;
+            const Real* Pd = a.P + ((he >> (12 + e)) & 1) * N2 + r * N;
+            const Real* E = HB + 6 * N2 + e * N;
+            Real t = Real(0);
+#pragma unroll
+            for (int md = 0; md < N; ++md) t += Pd[md] * E[md];
+            TS[6 * N2 + e * N + r] = t;
+          }
+      }
+      __syncthreads();
+      if (act && hang) {
+        const int au = r % N, av = r / N;
+        for (int f = 0; f < 6; ++f) {
+          if (!(hf >> f & 1u)) continue;
+          const Real* Pv = a.P + ((hf >> (7 + 2 * f)) & 1) * N2 + av * N;
+          const Real* Tf = TS + f * N2 + au;
+          Real t = Real(0);
+#pragma unroll
+          for (int mv = 0; mv < N; ++mv) t += Pv[mv] * Tf[N * mv];
+          HB[f * N2 + r] = t;
+        }
+        if (r < N)
+          for (int e = 0; e < 12; ++e)
+            if (he >> e & 1u) HB[6 * N2 + e * N + r] = TS[6 * N2 + e * N + r];
+      }
+      __syncthreads();
       if (act && hang) {
 #pragma unroll
-        for (int i1 = 0; i1 < N; ++i1)
-          if (own[i1] >= 0) v[i1] = hang_value<N, Real>(a.P, hf, he, own[i1], i1, ra, rb, HB);
+        for (int i1 = 0; i1 < N; ++i1) {
+          const int o = own[i1];
+          if (o < 0) continue;
+          const int ac[3] = {i1, ra, rb};
+          if (o < 6) {
+            const int d = o >> 1, u = d == 0 ? 1 : 0, w = d == 2 ? 1 : 2;
+            v[i1] = HB[o * N2 + ac[u] + N * ac[w]];
+          } else {
+            v[i1] = HB[6 * N2 + (o - 6) * N + ac[(o - 6) >> 2]];
+          }
+        }
       }
     }
     if (act) {
@@ -257,33 +318,42 @@ __global__ void __launch_bounds__(256, HANG ? 3 : (sizeof(Real) == 4 ? 4 : 1)) v
     }
     if (HANG && any_hang) {
       __syncthreads();
+      constexpr int K = N - 1;
+      const int step[3] = {1, NP, N * NP};
+      // the transposed interpolation onto the coarse face DoFs in tensor-product form: along u into HB
+      // (free since the gather), then along v; a fine node on a hanging face of lower index belongs to
+      // that face and adds nothing here
       if (act && hang) {
-        constexpr int K = N - 1;
-        const int64_t h0 = __ldg(a.hoff + cell);
-        int slot = 0;
+        const int mu = r % N, bv = r / N;
+        const int sv = bv == 0 ? 0 : (bv == K ? 1 : -1);
         for (int f = 0; f < 6; ++f) {
           if (!(hf >> f & 1u)) continue;
-          // coarse face node (mu, mv) = (r % N, r / N): sum over the fine face nodes this face owns
           const int d = f >> 1, u = d == 0 ? 1 : 0, w = d == 2 ? 1 : 2;
-          const int cu = (hf >> (6 + 2 * f)) & 1, cv = (hf >> (7 + 2 * f)) & 1;
-          const int mu = r % N, mv = r / N;
-          const Real* Pu = a.P + cu * N2 + mu;
-          const Real* Pv = a.P + cv * N2 + mv;
-          const int step[3] = {1, NP, N * NP};
-          const int base = (f & 1) * K * step[d];
-          Real s = Real(0);
-          for (int bv = 0; bv < N; ++bv) {
-            // face f owns node (bu, bv) unless a hanging face of lower index also contains it
-            const int sv = bv == 0 ? 0 : (bv == K ? 1 : -1);
-            if (sv >= 0 && 2 * w + sv < f && (hf >> (2 * w + sv) & 1u)) continue;
-            Real tt = Real(0);
+          Real t = Real(0);
+          if (!(sv >= 0 && 2 * w + sv < f && (hf >> (2 * w + sv) & 1u))) {
+            const Real* Pu = a.P + ((hf >> (6 + 2 * f)) & 1) * N2 + mu;
+            const int base = (f & 1) * K * step[d] + bv * step[w];
             for (int bu = 0; bu < N; ++bu) {
               const int su = bu == 0 ? 0 : (bu == K ? 1 : -1);
               if (su >= 0 && 2 * u + su < f && (hf >> (2 * u + su) & 1u)) continue;
-              tt += Pu[bu * N] * B[base + bu * step[u] + bv * step[w]];
+              t += Pu[bu * N] * B[base + bu * step[u]];
             }
-            s += Pv[bv * N] * tt;
           }
+          HB[f * N2 + r] = t;
+        }
+      }
+      __syncthreads();
+      if (act && hang) {
+        const int64_t h0 = __ldg(a.hoff + cell);
+        int slot = 0;
+        const int mu = r % N, mv = r / N;
+        for (int f = 0; f < 6; ++f) {
+          if (!(hf >> f & 1u)) continue;
+          const Real* Pv = a.P + ((hf >> (7 + 2 * f)) & 1) * N2 + mv;
+          const Real* Tf = HB + f * N2 + mu;
+          Real s = Real(0);
+#pragma unroll
+          for (int bv = 0; bv < N; ++bv) s += Pv[bv * N] * Tf[N * bv];
           const int32_t hd = __ldg(a.hdofs + h0 + slot + r);
           if (hd >= 0) atomicAdd(dst + hd, s);
           slot += N2;

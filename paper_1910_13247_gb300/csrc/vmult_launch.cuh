@@ -61,7 +61,10 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
                               const int32_t* list, int64_t n_list, bool prologue) {
   using Sh = VmultShape<N>;
   static int blocks_per_sm = -1;
-  const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + (HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0)) * sizeof(Real);
+  // three cubes per cell, the coarse values of hanging faces and edges, and (five-phase kernel, small n)
+  // the interpolation scratch
+  const size_t hb = HANG ? (size_t)Sh::CB * (6 * N * N + 12 * N) : 0;
+  const size_t smem = (3 * (size_t)Sh::CB * Sh::CELL + hb + (Cell5Scratch<N>::OWN ? hb : 0)) * sizeof(Real);
   // FP32: the five-phase kernel except at k = 7 (measured on octrees refined twice, ms, ten / five phases:
   // k = 1 0.0209 / 0.0204, k = 2 0.0276 / 0.0276, k = 4 0.0890 / 0.0859, k = 5 0.1353 / 0.1289, k = 6
   // 0.2177 / 0.2128, k = 7 0.1666 / 0.1705, k = 8 0.2570 / 0.2307); FP64: the ten-phase kernel (the
