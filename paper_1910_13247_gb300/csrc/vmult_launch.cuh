@@ -279,9 +279,10 @@ struct F5Config {
   static constexpr int EF = 0;
   // tile rows packed at the box width and moved by untiled bulk copies (clipped at the vector end) where
   // the smaller tiles give one more CTA per SM: staged metric at Q4 with 8 cells per batch (five CTAs
-  // instead of four: 64^3 0.2409 -> 0.2332 ms); elsewhere measured slower (Q4 16 cells 0.2563 -> 0.2735,
-  // Q3 8 cells 0.3181 -> 0.3354, Q2 32 cells 0.3262 -> 0.3477 ms)
-  static constexpr int PK = (MS && N == 5 && CB == 8) ? 1 : 0;
+  // instead of four: 64^3 0.2409 -> 0.2332 ms) and at Q3 with 16 (86^3 0.2912 -> 0.2831 ms); elsewhere
+  // measured slower (Q4 16 cells 0.2563 -> 0.2735, Q3 8 cells 0.3179 -> 0.3322, Q2 32 cells 0.3261 ->
+  // 0.3485 ms)
+  static constexpr int PK = (MS && ((N == 5 && CB == 8) || (N == 4 && CB == 16))) ? 1 : 0;
 };
 
 template <int N, int CB, int MS>
@@ -291,9 +292,9 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
   using Fs = F5Shape<N, CB, MS, Cf::TB, Cf::MBF, PK>;
   using Tm = TmaShape<N, CB>;
   // resident CTAs per SM the register budget is sized for: about 672 threads per SM, fewer when the
-  // shared memory bounds them
+  // shared memory bounds them (228 KB per SM, 1 KB of it reserved per CTA)
   constexpr int MB0 = 672 / Fs::THREADS > 0 ? 672 / Fs::THREADS : 1;
-  constexpr int MBS = (int)((220u * 1024u) / Fs::SMEM) > 0 ? (int)((220u * 1024u) / Fs::SMEM) : 1;
+  constexpr int MBS = (int)((228u * 1024u) / (Fs::SMEM + 1024u)) > 0 ? (int)((228u * 1024u) / (Fs::SMEM + 1024u)) : 1;
   constexpr int MB = MB0 < MBS ? MB0 : MBS;
   static int blocks_per_sm = -1;
   const size_t smem = Fs::SMEM;
