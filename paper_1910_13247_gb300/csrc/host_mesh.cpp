@@ -23,6 +23,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <utility>
 
 #include "mfx_internal.h"
@@ -54,6 +55,25 @@ void parallel_chunks(int64_t n, const F& f) {
   std::vector<std::thread> th;
   th.reserve(nt);
   for (int i = 0; i < nt; ++i) th.emplace_back([&f, i, nt, n] { f(n * i / nt, n * (i + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
+// f(i) for i in [0, n) on up to 16 threads, each taking the next index when done (uneven work per index)
+template <typename F>
+void parallel_dynamic(int64_t n, const F& f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>(std::min(hw, 16), n);
+  std::atomic<int64_t> next{0};
+  auto work = [&] {
+    for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+  };
+  if (nt <= 1) {
+    work();
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int i = 0; i < nt; ++i) th.emplace_back(work);
   for (auto& x : th) x.join();
 }
 
@@ -496,38 +516,17 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
       if (!irrational(dk) && ((dk == 0 && (m.dirichlet >> (2 * e) & 1u)) || (dk == ext[e] && (m.dirichlet >> (2 * e + 1) & 1u))))
         dirichlet[d] = 1;
     }
-  // hanging constraints
-  std::unordered_map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;
-  hanging.reserve((size_t)C / 8 + 1024);  // hanging nodes lie on coarse-fine interfaces only
-  // a hanging node is reached once per fine cell around it; the 2:1 balance makes every visit give the
-  // same constraint, so the first one is kept and the others are skipped before their masters are formed
-  std::vector<uint8_t> is_hanging(N, 0);
-  auto known = [&](int32_t dof) { return dirichlet[dof] != 0 || is_hanging[dof] != 0; };
+  // hanging constraints, on threads: each part of the leaf range records the constraints of the hanging
+  // nodes it reaches (every visit of a hanging node gives the same constraint under the 2:1 balance; a part
+  // keeps its first visit, the merge keeps the first in leaf order and checks the others against it), and
+  // the coarse DoFs of its fine cells' hanging faces and edges; the cells' face and edge words are set
+  // with atomic ORs (an edge word's bits once, by the first visitor)
   // 1D weights of the constraints: W1[c][b][m] = l_m((c + x_b) / 2), the coarse basis at node b of half c
   std::vector<double> W1((size_t)2 * n * n);
   for (int c2 = 0; c2 < 2; ++c2)
     for (int b = 0; b < n; ++b)
       for (int mm = 0; mm < n; ++mm)
         W1[((size_t)c2 * n + b) * n + mm] = lagrange_value(n, g, mm, ((double)c2 + g[b]) * 0.5);
-  auto add = [&](int32_t dof, std::vector<std::pair<int32_t, double>>& raw) -> mfx_status {
-    if (dirichlet[dof]) return MFX_OK;
-    std::vector<std::pair<int32_t, double>> clean;
-    for (auto& mw : raw)
-      if (mw.second != 0.0 && !dirichlet[mw.first]) clean.push_back(mw);
-    std::sort(clean.begin(), clean.end());
-    auto it = hanging.find(dof);
-    if (it == hanging.end()) {
-      hanging.emplace(dof, std::move(clean));
-      is_hanging[dof] = 1;
-      return MFX_OK;
-    }
-    const auto& old = it->second;
-    bool same = old.size() == clean.size();
-    for (size_t i = 0; same && i < old.size(); ++i)
-      same = old[i].first == clean[i].first && std::fabs(old[i].second - clean[i].second) <= 1e-12;
-    if (!same) return set_error(MFX_EMESH, "inconsistent hanging-node constraints");
-    return MFX_OK;
-  };
   // is the key a node of leaf c: every per-dimension key is one of c's per-dimension keys
   auto is_node_of = [&](int64_t c, const NodeKey& key) {
     const auto& lf = t.leaves[c];
@@ -538,168 +537,274 @@ mfx_status octree_tables(const Mesh& m, int k, OctreeTables* out) {
     }
     return true;
   };
-  std::vector<std::pair<int32_t, double>> raw;
-  // tensor-product form: per fine cell, its hanging faces (with the coarse face's DoFs) and edges
   out->hface.assign(C, 0u);
   out->hedge.assign(C, 0u);
-  std::unordered_map<int64_t, std::vector<int32_t>> face_dofs, edge_dofs;  // key: cell * 16 + face / edge
-  for (int64_t c = 0; c < C; ++c) {
-    const auto& lf = t.leaves[c];
-    const int L = lf[0];
-    // a leaf of the finest level has no finer neighbour: none of its faces or edges is refined across
-    if (L == Lmax) continue;
-    const int64_t idx[3] = {lf[1], lf[2], lf[3]};
-    // a level-0 leaf is a whole coarse cell: it has a finer face or edge neighbour only if one of the
-    // coarse cells across its faces and edges holds more than one leaf
-    if (L == 0 && !t.refined_near(idx)) continue;
-    // faces
-    for (int d = 0; d < 3; ++d) {
-      const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
-      for (int sd = 0; sd < 2; ++sd) {
-        int64_t p[3] = {idx[0], idx[1], idx[2]};
-        p[d] += sd ? 1 : -1;
-        if (t.covering(L, p) != -1) continue;  // not refined across this face
-        for (int cv = 0; cv < 2; ++cv)
-          for (int cu = 0; cu < 2; ++cu) {
-            int64_t f[3];
-            f[d] = 2 * p[d] + (sd ? 0 : 1);
-            f[u] = 2 * idx[u] + cu;
-            f[v] = 2 * idx[v] + cv;
-            const int32_t fe_leaf = t.exact(L + 1, f);
-            if (fe_leaf < 0) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
-            const int64_t e = fe_leaf;
-            const int ae_d = sd ? 0 : k, ac_d = sd ? k : 0;
-            {
-              const int fe = 2 * d + (sd ? 0 : 1);  // the fine cell's face on the coarse face
-              out->hface[e] |= (1u << fe) | ((uint32_t)cu << (6 + 2 * fe)) | ((uint32_t)cv << (7 + 2 * fe));
-              std::vector<int32_t>& fd = face_dofs[e * 16 + fe];
-              if (fd.empty()) {
-                fd.resize((size_t)n * n);
-                for (int mv = 0; mv < n; ++mv)
-                  for (int mu = 0; mu < n; ++mu) {
-                    int ac[3];
-                    ac[d] = ac_d;
-                    ac[u] = mu;
-                    ac[v] = mv;
-                    fd[mu + n * mv] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
-                  }
-              }
-            }
-            for (int bv = 0; bv < n; ++bv)
-              for (int bu = 0; bu < n; ++bu) {
-                int ae[3];
-                ae[d] = ae_d;
-                ae[u] = bu;
-                ae[v] = bv;
-                const int li = ae[0] + n * (ae[1] + n * ae[2]);
-                if (known(out->cell_dofs[e * n3 + li])) continue;
-                if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
-                const double* Wu = &W1[((size_t)cu * n + bu) * n];
-                const double* Wv = &W1[((size_t)cv * n + bv) * n];
-                raw.clear();
-                for (int mv = 0; mv < n; ++mv)
-                  for (int mu = 0; mu < n; ++mu) {
-                    int ac[3];
-                    ac[d] = ac_d;
-                    ac[u] = mu;
-                    ac[v] = mv;
-                    const double w = Wu[mu] * Wv[mv];
-                    raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], w});
-                  }
-                mfx_status st = add(out->cell_dofs[e * n3 + li], raw);
-                if (st != MFX_OK) return st;
-              }
-          }
-      }
-    }
-    // edges along d at sides (su, sv) of the two other dimensions
-    for (int d = 0; d < 3; ++d) {
-      const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
-      for (int sv = 0; sv < 2; ++sv)
-        for (int su = 0; su < 2; ++su) {
-          // the three other cells around the edge
-          const int64_t du = su ? 1 : -1, dv = sv ? 1 : -1;
-          const int64_t offs[3][2] = {{du, 0}, {0, dv}, {du, dv}};
-          for (auto& o : offs) {
+  struct HangRec {
+    int32_t dof;
+    int64_t order;  // visit order: leaf * 4096 + visit within the leaf
+    std::vector<std::pair<int32_t, double>> masters;
+  };
+  struct DofsRec {
+    int64_t key;  // cell * 16 + face / edge
+    std::vector<int32_t> dofs;
+  };
+  struct Scan {
+    std::vector<HangRec> hang;
+    std::vector<DofsRec> faces, edges;
+    mfx_status st = MFX_OK;
+    const char* msg = nullptr;
+  };
+  const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(256, C / 4096));
+  std::vector<Scan> scans((size_t)nparts);
+  parallel_dynamic(nparts, [&](int64_t part) {
+    {
+      Scan& sc = scans[part];
+      std::unordered_set<int32_t> seen;  // hanging nodes this part has recorded
+      std::vector<std::pair<int32_t, double>> raw;
+      int64_t order = 0;
+      auto known = [&](int32_t dof) { return dirichlet[dof] != 0 || seen.count(dof) != 0; };
+      auto add = [&](int32_t dof, std::vector<std::pair<int32_t, double>>& masters) {
+        std::vector<std::pair<int32_t, double>> clean;
+        for (auto& mw : masters)
+          if (mw.second != 0.0 && !dirichlet[mw.first]) clean.push_back(mw);
+        std::sort(clean.begin(), clean.end());
+        sc.hang.push_back({dof, order++, std::move(clean)});
+        seen.insert(dof);
+      };
+      auto fail = [&](const char* m) {
+        sc.st = MFX_EMESH;
+        sc.msg = m;
+      };
+      for (int64_t c = C * part / nparts; c < C * (part + 1) / nparts && sc.st == MFX_OK; ++c) {
+        order = c * 4096;
+        const auto& lf = t.leaves[c];
+        const int L = lf[0];
+        // a leaf of the finest level has no finer neighbour: none of its faces or edges is refined across
+        if (L == Lmax) continue;
+        const int64_t idx[3] = {lf[1], lf[2], lf[3]};
+        // a level-0 leaf is a whole coarse cell: it has a finer face or edge neighbour only if one of the
+        // coarse cells across its faces and edges holds more than one leaf
+        if (L == 0 && !t.refined_near(idx)) continue;
+        // faces
+        for (int d = 0; d < 3; ++d) {
+          const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+          for (int sd = 0; sd < 2; ++sd) {
             int64_t p[3] = {idx[0], idx[1], idx[2]};
-            p[u] += o[0];
-            p[v] += o[1];
-            if (t.covering(L, p) != -1) continue;
-            // the two children of p along d that touch our edge
-            for (int cd = 0; cd < 2; ++cd) {
-              int64_t f[3];
-              f[d] = 2 * idx[d] + cd;
-              f[u] = 2 * p[u] + (o[0] == 0 ? su : (su ? 0 : 1));
-              f[v] = 2 * p[v] + (o[1] == 0 ? sv : (sv ? 0 : 1));
-              const int32_t fe_leaf = t.exact(L + 1, f);
-              if (fe_leaf < 0) return set_error(MFX_EMESH, "mesh is not 2:1 balanced");
-              const int64_t e = fe_leaf;
-              // position of the edge line in the fine leaf
-              const int64_t edge_u = 2 * (idx[u] + su), edge_v = 2 * (idx[v] + sv);
-              const int au = edge_u == f[u] ? 0 : k, av = edge_v == f[v] ? 0 : k;
-              {
-                const int ee = 4 * d + 2 * (av == k ? 1 : 0) + (au == k ? 1 : 0);
-                if (!(out->hedge[e] >> ee & 1u)) {
-                  out->hedge[e] |= (1u << ee) | ((uint32_t)cd << (12 + ee));
-                  std::vector<int32_t>& ed = edge_dofs[e * 16 + ee];
-                  ed.resize(n);
-                  for (int md = 0; md < n; ++md) {
-                    int ac[3];
-                    ac[d] = md;
-                    ac[u] = su * k;
-                    ac[v] = sv * k;
-                    ed[md] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
+            p[d] += sd ? 1 : -1;
+            if (t.covering(L, p) != -1) continue;  // not refined across this face
+            for (int cv = 0; cv < 2; ++cv)
+              for (int cu = 0; cu < 2; ++cu) {
+                int64_t f[3];
+                f[d] = 2 * p[d] + (sd ? 0 : 1);
+                f[u] = 2 * idx[u] + cu;
+                f[v] = 2 * idx[v] + cv;
+                const int32_t fe_leaf = t.exact(L + 1, f);
+                if (fe_leaf < 0) {
+                  fail("mesh is not 2:1 balanced");
+                  break;
+                }
+                const int64_t e = fe_leaf;
+                const int ae_d = sd ? 0 : k, ac_d = sd ? k : 0;
+                {
+                  const int fe = 2 * d + (sd ? 0 : 1);  // the fine cell's face on the coarse face
+                  __atomic_fetch_or(&out->hface[e], (1u << fe) | ((uint32_t)cu << (6 + 2 * fe)) | ((uint32_t)cv << (7 + 2 * fe)),
+                                    __ATOMIC_RELAXED);
+                  {
+                    sc.faces.push_back({e * 16 + fe, std::vector<int32_t>((size_t)n * n)});
+                    std::vector<int32_t>& fd = sc.faces.back().dofs;
+                    for (int mv = 0; mv < n; ++mv)
+                      for (int mu = 0; mu < n; ++mu) {
+                        int ac[3];
+                        ac[d] = ac_d;
+                        ac[u] = mu;
+                        ac[v] = mv;
+                        fd[mu + n * mv] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
+                      }
                   }
                 }
+                for (int bv = 0; bv < n; ++bv)
+                  for (int bu = 0; bu < n; ++bu) {
+                    int ae[3];
+                    ae[d] = ae_d;
+                    ae[u] = bu;
+                    ae[v] = bv;
+                    const int li = ae[0] + n * (ae[1] + n * ae[2]);
+                    if (known(out->cell_dofs[e * n3 + li])) continue;
+                    if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
+                    const double* Wu = &W1[((size_t)cu * n + bu) * n];
+                    const double* Wv = &W1[((size_t)cv * n + bv) * n];
+                    raw.clear();
+                    for (int mv = 0; mv < n; ++mv)
+                      for (int mu = 0; mu < n; ++mu) {
+                        int ac[3];
+                        ac[d] = ac_d;
+                        ac[u] = mu;
+                        ac[v] = mv;
+                        const double w = Wu[mu] * Wv[mv];
+                        raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], w});
+                      }
+                    add(out->cell_dofs[e * n3 + li], raw);
+                  }
               }
-              for (int bd = 0; bd < n; ++bd) {
-                int ae[3];
-                ae[d] = bd;
-                ae[u] = au;
-                ae[v] = av;
-                const int li = ae[0] + n * (ae[1] + n * ae[2]);
-                if (known(out->cell_dofs[e * n3 + li])) continue;
-                if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
-                const double* Wd = &W1[((size_t)cd * n + bd) * n];
-                raw.clear();
-                for (int md = 0; md < n; ++md) {
-                  int ac[3];
-                  ac[d] = md;
-                  ac[u] = su * k;
-                  ac[v] = sv * k;
-                  raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], Wd[md]});
-                }
-                mfx_status st = add(out->cell_dofs[e * n3 + li], raw);
-                if (st != MFX_OK) return st;
-              }
-            }
           }
         }
+        // edges along d at sides (su, sv) of the two other dimensions
+        for (int d = 0; d < 3; ++d) {
+          const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+          for (int sv = 0; sv < 2; ++sv)
+            for (int su = 0; su < 2; ++su) {
+              // the three other cells around the edge
+              const int64_t du = su ? 1 : -1, dv = sv ? 1 : -1;
+              const int64_t offs[3][2] = {{du, 0}, {0, dv}, {du, dv}};
+              for (auto& o : offs) {
+                int64_t p[3] = {idx[0], idx[1], idx[2]};
+                p[u] += o[0];
+                p[v] += o[1];
+                if (t.covering(L, p) != -1) continue;
+                // the two children of p along d that touch our edge
+                for (int cd = 0; cd < 2; ++cd) {
+                  int64_t f[3];
+                  f[d] = 2 * idx[d] + cd;
+                  f[u] = 2 * p[u] + (o[0] == 0 ? su : (su ? 0 : 1));
+                  f[v] = 2 * p[v] + (o[1] == 0 ? sv : (sv ? 0 : 1));
+                  const int32_t fe_leaf = t.exact(L + 1, f);
+                  if (fe_leaf < 0) {
+                  fail("mesh is not 2:1 balanced");
+                  break;
+                }
+                  const int64_t e = fe_leaf;
+                  // position of the edge line in the fine leaf
+                  const int64_t edge_u = 2 * (idx[u] + su), edge_v = 2 * (idx[v] + sv);
+                  const int au = edge_u == f[u] ? 0 : k, av = edge_v == f[v] ? 0 : k;
+                  {
+                    const int ee = 4 * d + 2 * (av == k ? 1 : 0) + (au == k ? 1 : 0);
+                    const uint32_t bits = (1u << ee) | ((uint32_t)cd << (12 + ee));
+                    uint32_t old = __atomic_load_n(&out->hedge[e], __ATOMIC_RELAXED);
+                    bool mine = false;
+                    while (!(old >> ee & 1u) &&
+                           !(mine = __atomic_compare_exchange_n(&out->hedge[e], &old, old | bits, false, __ATOMIC_RELAXED,
+                                                                __ATOMIC_RELAXED))) {
+                    }
+                    if (mine) {
+                      sc.edges.push_back({e * 16 + ee, std::vector<int32_t>((size_t)n)});
+                      std::vector<int32_t>& ed = sc.edges.back().dofs;
+                      for (int md = 0; md < n; ++md) {
+                        int ac[3];
+                        ac[d] = md;
+                        ac[u] = su * k;
+                        ac[v] = sv * k;
+                        ed[md] = out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])];
+                      }
+                    }
+                  }
+                  for (int bd = 0; bd < n; ++bd) {
+                    int ae[3];
+                    ae[d] = bd;
+                    ae[u] = au;
+                    ae[v] = av;
+                    const int li = ae[0] + n * (ae[1] + n * ae[2]);
+                    if (known(out->cell_dofs[e * n3 + li])) continue;
+                    if (is_node_of(c, node_key(e, ae[0], ae[1], ae[2]))) continue;
+                    const double* Wd = &W1[((size_t)cd * n + bd) * n];
+                    raw.clear();
+                    for (int md = 0; md < n; ++md) {
+                      int ac[3];
+                      ac[d] = md;
+                      ac[u] = su * k;
+                      ac[v] = sv * k;
+                      raw.push_back({out->cell_dofs[c * n3 + ac[0] + n * (ac[1] + n * ac[2])], Wd[md]});
+                    }
+                    add(out->cell_dofs[e * n3 + li], raw);
+                  }
+                }
+              }
+            }
+        }
+  
+      }
     }
+  });
+  for (const Scan& sc : scans)
+    if (sc.st != MFX_OK) return set_error(sc.st, sc.msg);
+  // merge: the first visit of each hanging node in leaf order, the others checked against it
+  std::vector<HangRec> recs;
+  for (Scan& sc : scans)
+    for (HangRec& r : sc.hang) recs.push_back(std::move(r));
+  std::sort(recs.begin(), recs.end(), [](const HangRec& x, const HangRec& y) {
+    return x.dof != y.dof ? x.dof < y.dof : x.order < y.order;
+  });
+  std::unordered_map<int32_t, std::vector<std::pair<int32_t, double>>> hanging;
+  hanging.reserve(recs.size());
+  std::vector<uint8_t> is_hanging(N, 0);
+  for (size_t i = 0; i < recs.size();) {
+    size_t j = i + 1;
+    for (; j < recs.size() && recs[j].dof == recs[i].dof; ++j) {
+      const auto& x = recs[i].masters;
+      const auto& y = recs[j].masters;
+      bool same = x.size() == y.size();
+      for (size_t q = 0; same && q < x.size(); ++q)
+        same = x[q].first == y[q].first && std::fabs(x[q].second - y[q].second) <= 1e-12;
+      if (!same) return set_error(MFX_EMESH, "inconsistent hanging-node constraints");
+    }
+    is_hanging[recs[i].dof] = 1;
+    hanging.emplace(recs[i].dof, std::move(recs[i].masters));
+    i = j;
   }
-  // compact per-cell lists; an edge on a hanging face of the same cell is left to the face
-  out->hoff.assign(C, 0);
-  out->hdofs.clear();
+  recs.clear();
+  // the coarse DoFs of the hanging faces and edges, sorted by (cell, face / edge)
+  std::vector<DofsRec> face_dofs, edge_dofs;
+  for (Scan& sc : scans) {
+    for (DofsRec& r : sc.faces) face_dofs.push_back(std::move(r));
+    for (DofsRec& r : sc.edges) edge_dofs.push_back(std::move(r));
+  }
+  scans.clear();
+  auto by_key = [](const DofsRec& x, const DofsRec& y) { return x.key < y.key; };
+  std::sort(face_dofs.begin(), face_dofs.end(), by_key);
+  std::sort(edge_dofs.begin(), edge_dofs.end(), by_key);
+  auto first_at = [](const std::vector<DofsRec>& v, int64_t key) {
+    return (size_t)(std::lower_bound(v.begin(), v.end(), key,
+                                     [](const DofsRec& r, int64_t k2) { return r.key < k2; }) -
+                    v.begin());
+  };
+  // compact per-cell lists; an edge on a hanging face of the same cell is left to the face.  Per chunk of
+  // cells: the kept edges and the list lengths, then (after the prefix over the cells) the lists
   auto coarse = [&](int32_t dof) { return (dirichlet[dof] || is_hanging[dof]) ? -1 : dof; };
-  for (int64_t c = 0; c < C; ++c) {
-    out->hoff[c] = (int64_t)out->hdofs.size();
-    const uint32_t hf = out->hface[c] & 0x3Fu;
-    uint32_t keep = 0u;
-    for (int ee = 0; ee < 12; ++ee) {
-      if (!(out->hedge[c] >> ee & 1u)) continue;
-      const int d = ee >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
-      const int su = ee & 1, sv = (ee >> 1) & 1;
-      if ((hf >> (2 * u + su) & 1u) || (hf >> (2 * v + sv) & 1u)) continue;
-      keep |= 1u << ee;
+  out->hoff.assign(C, 0);
+  const int64_t nn = (int64_t)n * n;
+  parallel_chunks(C, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi; ++c) {
+      const uint32_t hf = out->hface[c] & 0x3Fu;
+      uint32_t keep = 0u;
+      for (int ee = 0; ee < 12; ++ee) {
+        if (!(out->hedge[c] >> ee & 1u)) continue;
+        const int d = ee >> 2, u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+        const int su = ee & 1, sv = (ee >> 1) & 1;
+        if ((hf >> (2 * u + su) & 1u) || (hf >> (2 * v + sv) & 1u)) continue;
+        keep |= 1u << ee;
+      }
+      out->hedge[c] = keep | (out->hedge[c] & (keep << 12));
+      out->hoff[c] = nn * __builtin_popcount(hf) + (int64_t)n * __builtin_popcount(keep);
     }
-    out->hedge[c] = keep | (out->hedge[c] & (keep << 12));
-    for (int f = 0; f < 6; ++f)
-      if (hf >> f & 1u)
-        for (int32_t dof : face_dofs[c * 16 + f]) out->hdofs.push_back(coarse(dof));
-    for (int ee = 0; ee < 12; ++ee)
-      if (keep >> ee & 1u)
-        for (int32_t dof : edge_dofs[c * 16 + ee]) out->hdofs.push_back(coarse(dof));
+  });
+  int64_t total = 0;
+  for (int64_t c = 0; c < C; ++c) {  // exclusive prefix
+    const int64_t len = out->hoff[c];
+    out->hoff[c] = total;
+    total += len;
   }
+  out->hdofs.assign((size_t)total, 0);
+  parallel_chunks(C, [&](int64_t lo, int64_t hi) {
+    size_t fi = first_at(face_dofs, lo * 16), ei = first_at(edge_dofs, lo * 16);
+    for (int64_t c = lo; c < hi; ++c) {
+      int64_t o = out->hoff[c];
+      for (; fi < face_dofs.size() && face_dofs[fi].key < (c + 1) * 16; ++fi)
+        if (out->hface[c] >> (face_dofs[fi].key - c * 16) & 1u)
+          for (int32_t dof : face_dofs[fi].dofs) out->hdofs[o++] = coarse(dof);
+      for (; ei < edge_dofs.size() && edge_dofs[ei].key < (c + 1) * 16; ++ei)
+        if (out->hedge[c] >> (edge_dofs[ei].key - c * 16) & 1u)
+          for (int32_t dof : edge_dofs[ei].dofs) out->hdofs[o++] = coarse(dof);
+    }
+  });
   out->constrained.clear();
   size_t n_masters = 0;
   for (int64_t d = 0; d < N; ++d)

@@ -120,3 +120,22 @@ def test_autotuned_choice_is_a_compiled_pair(mfx):
     assert info["structured_kernel"] in kernels(mfx)
     e2, einf = errs(vmult(op, x, torch.float32), K @ x)
     assert e2 < TOL32 and einf < TOL32
+
+
+@pytest.mark.parametrize("k,cb,dims", [(4, 8, d) for d in ((1, 1, 1), (5, 1, 1), (9, 2, 1), (12, 1, 2))] +
+                         [(3, 16, d) for d in ((1, 1, 1), (4, 2, 2), (2, 3, 2), (2, 2, 2), (17, 1, 1))])
+def test_packed_rows_clipped_at_the_vector_end(mfx, k, cb, dims):
+    """The staged kernel moves tile rows with untiled bulk copies where it packs them (Q4 with 8 cells per
+    batch, Q3 with 16): the tile row that reaches past the end of the vector is clipped to whole 16-byte
+    words and its last 0..3 points go through plain loads and atomics.  At Q4 that row always keeps one
+    point beyond its words (lattice rows of 4 nx + 1 points); the Q3 cases give 0, 1, 2 and 3."""
+    nx, ny, nz = dims
+    Mx, My, Mz = k * nx + 1, k * ny + 1, k * nz + 1
+    n = Mx * My * Mz
+    x0 = k * ((nx - 1) // cb) * cb       # first lattice point of the last batch of the last row
+    g0 = (n - Mx + x0) & ~3              # 16-byte aligned start of the last tile row
+    assert n - g0 <= 4 * ((k * cb + 7) // 4)  # the row's box reaches past the vector's end
+    verts, om, K, x = oracle_case(nx, ny, nz, k, 900 + nx + 10 * ny + 100 * nz)
+    op = make_op(mfx, nx, ny, nz, k, verts, cb, mfx.KERNEL_FIVE_PHASE_STAGED)
+    e2, einf = errs(vmult(op, x, torch.float32), K @ x)
+    assert e2 < TOL32 and einf < TOL32, (dims, (n - g0) % 4, e2, einf)
