@@ -293,8 +293,11 @@ mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constra
  * interpolate to the Gauss points and take reference gradients by 1D
  * contractions, apply the stored metric, integrate back with the
  * transposed contractions, scatter-add; constrained rows copy src.
- * src, dst: device, n_dofs entries of the precision, must not alias.
- * Errors: MFX_EINVAL (null, precision not built), MFX_ECUDA (launch).
+ * src, dst: device, n_dofs entries of the precision, must not alias; on
+ * structured meshes the FP32 kernels move tile rows with the copy engine and
+ * need src and dst 16-byte aligned (as cudaMalloc and torch give them).
+ * Errors: MFX_EINVAL (null, precision not built, or an FP32 vector on a
+ * structured mesh not 16-byte aligned), MFX_ECUDA (launch).
  */
 mfx_status mfx_vmult(const mfx_op* op, mfx_prec prec, const void* src, void* dst, mfx_stream stream);
 /*
