@@ -139,3 +139,21 @@ def test_packed_rows_clipped_at_the_vector_end(mfx, k, cb, dims):
     op = make_op(mfx, nx, ny, nz, k, verts, cb, mfx.KERNEL_FIVE_PHASE_STAGED)
     e2, einf = errs(vmult(op, x, torch.float32), K @ x)
     assert e2 < TOL32 and einf < TOL32, (dims, (n - g0) % 4, e2, einf)
+
+
+def test_misaligned_vectors_rejected_before_launch(mfx):
+    """The FP32 structured kernels move tile rows with the copy engine, which needs 16-byte aligned
+    vectors: a view starting one float into an allocation is rejected with MFX_EINVAL on the host, before
+    anything is launched, and the aligned call still works."""
+    k, (nx, ny, nz) = 4, (9, 2, 2)
+    verts, om, K, x = oracle_case(nx, ny, nz, k, 950)
+    op = make_op(mfx, nx, ny, nz, k, verts, 8, mfx.KERNEL_FIVE_PHASE_STAGED)
+    big = torch.zeros(op.n_dofs + 4, device=DEV, dtype=torch.float32)
+    src = big[1:1 + op.n_dofs]
+    src.copy_(torch.tensor(x, device=DEV, dtype=torch.float32))
+    y = torch.empty(op.n_dofs, device=DEV, dtype=torch.float32)
+    with pytest.raises(mfx.MfxError) as e:
+        op.vmult(src, y)
+    assert e.value.code == mfx.EINVAL
+    e2, einf = errs(vmult(op, x, torch.float32), K @ x)
+    assert e2 < TOL32 and einf < TOL32
