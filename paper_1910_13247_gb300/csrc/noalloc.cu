@@ -55,12 +55,21 @@ __global__ void dot_noalloc_kernel(int64_t n, const Real* __restrict__ a, const 
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double s = 0.0;
-    for (unsigned int k = 0; k < gridDim.x; ++k) s += ((volatile double*)partials)[k];
-    *result = s;
-    *counter = 0u;
+  if (!last) return;
+  // the last CTA sums the partials: strided loads from L2 by all its threads, then a block sum
+  __threadfence();
+  double s = 0.0;
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) s += __ldcg(partials + k);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) warp_sums[warp] = s;  // its first use ended before the barrier that published `last`
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < kThreads / 32 ? warp_sums[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      *result = s;
+      *counter = 0u;
+    }
   }
 }
 

@@ -88,13 +88,18 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // the last CTA sums the partials: strided loads from L2 by all its threads, then a block sum (one
+  // thread walking them in turn waits on hundreds of dependent round trips: 40-80 us at 600 CTAs)
+  double t[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) t[j] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t[j] += __ldcg(partials + b * NV + j);
+  block_sum<NV>(t);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      double s = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[b * NV + j];
-      v[j] = s;
-    }
+    for (int j = 0; j < NV; ++j) v[j] = t[j];
     *counter = 0u;
   }
   return true;
