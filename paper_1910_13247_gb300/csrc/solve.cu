@@ -73,6 +73,25 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   }
 }
 
+// The (p, q), update and rz kernels of CG take four strides of the grid per step with all their loads
+// issued first (one stride per step held too few loads in flight: 1.5-2 TB/s), and add the step's four
+// products in the vectors' precision before one FP64 accumulation (GB300's FP64 rate is 1/64 of FP32).
+constexpr int kSteps = 4;
+
+template <typename Real>
+__device__ __forceinline__ void load_steps(const Real* __restrict__ a, int64_t i, int64_t S, Real (&v)[kSteps]) {
+#pragma unroll
+  for (int u = 0; u < kSteps; ++u) v[u] = a[i + u * S];
+}
+
+template <typename Real>
+__device__ __forceinline__ double dot_steps(const Real (&a)[kSteps], const Real (&b)[kSteps]) {
+  Real t = a[0] * b[0];
+#pragma unroll
+  for (int u = 1; u < kSteps; ++u) t += a[u] * b[u];
+  return (double)t;
+}
+
 // Writes the CTA partials; returns true in the last CTA, whose thread 0 then holds the totals.
 template <int NV>
 __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter) {
@@ -151,8 +170,15 @@ __global__ void cg_pq_kernel(int64_t n, const Real* __restrict__ p, const Real* 
                              double* partials, unsigned int* counter) {
   if (st->done) return;
   double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[0] += (double)p[i] * (double)q[i];
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kSteps - 1) * S < n; i += kSteps * S) {
+    Real a[kSteps], b[kSteps];
+    load_steps(p, i, S, a);
+    load_steps(q, i, S, b);
+    v[0] += dot_steps(a, b);
+  }
+  for (; i < n; i += S) v[0] += (double)p[i] * (double)q[i];
   if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) {
     st->pq = v[0];
     if (!(v[0] > 0.0) || !isfinite(v[0])) {
@@ -173,7 +199,26 @@ __global__ void cg_update_kernel(int64_t n, Real* __restrict__ x, Real* __restri
   if (st->done) return;
   const Real alpha = (Real)st->alpha;
   double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kSteps - 1) * S < n; i += kSteps * S) {
+    Real xv[kSteps], pv[kSteps], rv[kSteps], qv[kSteps], dv[kSteps];
+    load_steps(x, i, S, xv);
+    load_steps(p, i, S, pv);
+    load_steps(r, i, S, rv);
+    load_steps(q, i, S, qv);
+    if (jacobi) load_steps(dinv, i, S, dv);
+#pragma unroll
+    for (int u = 0; u < kSteps; ++u) {
+      x[i + u * S] = xv[u] + alpha * pv[u];
+      rv[u] = rv[u] - alpha * qv[u];
+      r[i + u * S] = rv[u];
+      if (jacobi) dv[u] *= rv[u];
+    }
+    v[0] += dot_steps(rv, rv);
+    if (jacobi) v[1] += dot_steps(rv, dv);
+  }
+  for (; i < n; i += S) {
     x[i] += alpha * p[i];
     const Real ri = r[i] - alpha * q[i];
     r[i] = ri;
@@ -207,8 +252,15 @@ __global__ void cg_rz_kernel(int64_t n, const Real* __restrict__ r, const Real* 
                              double* partials, unsigned int* counter) {
   if (st->done) return;
   double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[0] += (double)r[i] * (double)z[i];
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kSteps - 1) * S < n; i += kSteps * S) {
+    Real a[kSteps], b[kSteps];
+    load_steps(r, i, S, a);
+    load_steps(z, i, S, b);
+    v[0] += dot_steps(a, b);
+  }
+  for (; i < n; i += S) v[0] += (double)r[i] * (double)z[i];
   if (grid_sum<1>(v, partials, counter) && threadIdx.x == 0) {
     st->beta = v[0] / st->rz;
     st->rz = v[0];
