@@ -273,7 +273,23 @@ __global__ void cg_p_kernel(int64_t n, Real* __restrict__ p, const Real* __restr
                             const Real* __restrict__ dinv, const Real* __restrict__ z, const SolveState* st) {
   if (st->done) return;
   const Real beta = (Real)st->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kSteps - 1) * S < n; i += kSteps * S) {
+    Real pv[kSteps], a[kSteps], b[kSteps];
+    load_steps(p, i, S, pv);
+    if (z) {
+      load_steps(z, i, S, a);
+    } else {
+      load_steps(dinv, i, S, a);
+      load_steps(r, i, S, b);
+#pragma unroll
+      for (int u = 0; u < kSteps; ++u) a[u] *= b[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kSteps; ++u) p[i + u * S] = a[u] + beta * pv[u];
+  }
+  for (; i < n; i += S) {
     const Real zi = z ? z[i] : dinv[i] * r[i];
     p[i] = zi + beta * p[i];
   }
@@ -297,7 +313,23 @@ __global__ void cheb_step_kernel(int64_t n, const Real* __restrict__ r, const Re
                                  const Real* __restrict__ dinv, Real* __restrict__ d, Real* __restrict__ z, Real c1,
                                  Real c2, const int32_t* skip) {
   if (skip && *skip) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kSteps - 1) * S < n; i += kSteps * S) {
+    Real dv[kSteps], iv[kSteps], rv[kSteps], kv[kSteps], zv[kSteps];
+    load_steps(d, i, S, dv);
+    load_steps(dinv, i, S, iv);
+    load_steps(r, i, S, rv);
+    load_steps(kz, i, S, kv);
+    load_steps(z, i, S, zv);
+#pragma unroll
+    for (int u = 0; u < kSteps; ++u) {
+      const Real di = c1 * dv[u] + c2 * iv[u] * (rv[u] - kv[u]);
+      d[i + u * S] = di;
+      z[i + u * S] = zv[u] + di;
+    }
+  }
+  for (; i < n; i += S) {
     const Real di = c1 * d[i] + c2 * dinv[i] * (r[i] - kz[i]);
     d[i] = di;
     z[i] += di;
