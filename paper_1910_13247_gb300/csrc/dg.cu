@@ -55,6 +55,10 @@ struct DgArgs {
   // the FP64 kernel's runtime scalars as float pairs: per direction 1/h, 1/(2h), sigma interior,
   // sigma Dirichlet, a h_e h_f
   float dfs[3][5][2];
+  // the plane kernel's per-direction coefficients, each times s = a h_e h_f: h^-1 / 2 and h^-1 (end terms at
+  // interior and Dirichlet ends), the interior and Dirichlet penalties, and the cell stiffness s h^-1 K1
+  float fint[3], fbnd[3], sint[3], sbnd[3];
+  float K1s[3][kMaxN * kMaxN];
   // quadrature points and right-hand sides: the box's first vertex, Gauss points and weights on [0, 1],
   // S[q][i] = l_i(x_q)
   double origin[3], xq[kMaxN], wq[kMaxN], S[kMaxN * kMaxN];
@@ -252,6 +256,301 @@ __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ D
       for (int i = threadIdx.x; i < CH; i += 128)
         if (first + i < total) dst[first + i] = P[i] + Q[i];
     }
+  }
+}
+
+// FP32 plane kernel (degrees 1..5).  The same Kronecker sum, ordered so that two of the three
+// directions never leave registers:
+//   y = M_z C + D,   C = M_y (s_x L_x u) + M_x (s_y L_y u),   D = M_x M_y R,   R = s_z L_z u.
+// A CTA takes CB consecutive cells (CB N plane tasks, at most 128).  Three phases per batch:
+//   z-lines (one task per line of a cell): R from the cell's z-line, the z-neighbours' z-lines read
+//     straight from global memory (coalesced: a z-line task reads one point per plane);
+//   planes (one task per z-plane of a cell): the plane of u in registers, L_x along its rows and L_y
+//     along its columns with the x-neighbours' planes from the staged chunk (cells c0 - 1 .. c0 + CB)
+//     and the y-neighbours' planes from two more staged chunks (cells c0 -/+ nx ..), the masses M_y and
+//     M_x in registers; C and D written back over the tasks' own planes of the staging buffers;
+//   z-lines: y = M_z C + D, stored straight to dst.
+// The staged chunks are copied with 16-byte loads from a 16-byte aligned start below the chunk and
+// indexed from the shift; points outside the vector read as zero (and are never used: the face flags
+// of a cell select which neighbour data enter).
+template <int N>
+struct DgPlane {
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  static constexpr int CB = 128 / N;  // cells per batch: N z-planes per cell
+  static constexpr int region(int len) { return (len + 6 + 3) & ~3; }  // staged length + alignment shift
+  static constexpr int UL = region((CB + 2) * N3), YL = region(CB * N3), RL = (CB * N3 + 3) & ~3;
+  static constexpr size_t SMEM = (size_t)(UL + 2 * YL + RL) * sizeof(float) + 16 * ((CB + 3) / 4);
+};
+
+// Copy src[g0, g0 + len) (zero outside [0, total)) to s' = s + (g0 mod 4) with asynchronous 16-byte copies
+// (cp.async; the caller waits with cp.async.wait_all before its barrier) and plain stores for the quads at
+// the ends of the vector; returns s + (g0 mod 4), the chunk's first point.  src 16-byte aligned, s 16-byte
+// aligned with room for len + 6 floats.
+__device__ __forceinline__ float* dg_stage(float* s, const float* __restrict__ src, int64_t g0, int len,
+                                           int64_t total) {
+  const int64_t a0 = g0 & ~(int64_t)3;
+  const int sh = (int)(g0 - a0);
+  const int nq = (len + sh + 3) >> 2;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int64_t g = a0 + 4 * (int64_t)q;
+    if (g >= 0 && g + 4 <= total) {
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(s + 4 * q)),
+                   "l"(src + g)
+                   : "memory");
+    } else {
+      float4 v;
+      v.x = (g >= 0 && g < total) ? src[g] : 0.f;
+      v.y = (g + 1 >= 0 && g + 1 < total) ? src[g + 1] : 0.f;
+      v.z = (g + 2 >= 0 && g + 2 < total) ? src[g + 2] : 0.f;
+      v.w = (g + 3 >= 0 && g + 3 < total) ? src[g + 3] : 0.f;
+      reinterpret_cast<float4*>(s)[q] = v;
+    }
+  }
+  return s + sh;
+}
+
+__device__ __forceinline__ void dg_stage_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// One line x of the 1D SIPG operator of direction D, times the direction's scale s, in registers:
+//   y = s h^-1 K1 x + (lower end) d0 tl + e_0 (fl (g0 + gl) + sl jl) - (upper end) d1 th + e_K (sh jh - fh (g1 + gh)),
+// jl = x_0 - wl, tl = fl jl, g0 = d0 . x, jh = x_K - wh, th = fh jh, g1 = d1 . x; (fl, sl) are
+// (s h^-1 / 2, s sigma_int) at an interior end, (s h^-1, s sigma_Dirichlet) at a Dirichlet end and zero at
+// a natural end; (wl, gl) the lower neighbour's value at its upper end and d1 . w (zero without one),
+// (wh, gh) the upper neighbour's value at its lower end and d0 . w.  The scale is folded into the
+// stiffness table (K1s[D] = s h^-1 K1).
+template <int N, int D>
+__device__ __forceinline__ void dg_line_reg(const DgArgs& a, const float (&x)[N], float (&y)[N], float fl, float sl,
+                                            float wl, float gl, float fh, float shc, float wh, float gh) {
+  constexpr int K = N - 1;
+  float g0 = a.d0f[0] * x[0], g1 = a.d1f[0] * x[0];
+#pragma unroll
+  for (int j = 1; j < N; ++j) {
+    g0 = fmaf(a.d0f[j], x[j], g0);
+    g1 = fmaf(a.d1f[j], x[j], g1);
+  }
+  const float jl = x[0] - wl, jh = x[K] - wh;
+  const float tl = fl * jl, tn = -fh * jh;  // minus the upper end's factor
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s = fmaf(a.d1f[i], tn, a.d0f[i] * tl);
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = fmaf(a.K1s[D][i * N + j], x[j], s);
+    y[i] = s;
+  }
+  y[0] = fmaf(fl, g0 + gl, fmaf(sl, jl, y[0]));
+  y[K] = fmaf(shc, jh, fmaf(-fh, g1 + gh, y[K]));
+}
+
+// A neighbour line's contribution: its value at the shared end and its end derivative sum, or zeros
+// without the neighbour (a select, not a product: the staged cell beside a boundary face belongs to
+// another row of cells).
+template <int N, bool LOWER>
+__device__ __forceinline__ void dg_nb_end(const DgArgs& a, const float (&w)[N], bool has, float* wv, float* g) {
+  float s = (LOWER ? a.d1f[0] : a.d0f[0]) * w[0];
+#pragma unroll
+  for (int j = 1; j < N; ++j) s = fmaf(LOWER ? a.d1f[j] : a.d0f[j], w[j], s);
+  *g = has ? s : 0.f;
+  *wv = has ? (LOWER ? w[N - 1] : w[0]) : 0.f;
+}
+
+// End coefficients of direction d for a cell with face flags f (bit 2d: lower neighbour, 2d+1: upper).
+__device__ __forceinline__ void dg_end_coefs(const DgArgs& a, int d, int f, float* fl, float* sl, float* fh,
+                                             float* shc) {
+  const bool lo = (f >> (2 * d)) & 1, hi = (f >> (2 * d + 1)) & 1;
+  const bool dlo = (a.dmask >> (2 * d)) & 1u, dhi = (a.dmask >> (2 * d + 1)) & 1u;
+  *fl = lo ? a.fint[d] : (dlo ? a.fbnd[d] : 0.f);
+  *sl = lo ? a.sint[d] : (dlo ? a.sbnd[d] : 0.f);
+  *fh = hi ? a.fint[d] : (dhi ? a.fbnd[d] : 0.f);
+  *shc = hi ? a.sint[d] : (dhi ? a.sbnd[d] : 0.f);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
+    dg_vmult_plane_kernel(const __grid_constant__ DgArgs a, const float* __restrict__ src, float* __restrict__ dst) {
+  using Sh = DgPlane<N>;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3, CB = Sh::CB;
+  constexpr int RZ = (CB * N2 + 127) / 128;  // z-line tasks per thread
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) float dsm[];
+  float* const Us = dsm;            // cells c0 - 1 .. c0 + CB
+  float* const Yls = Us + Sh::UL;   // cells c0 - nx .., then C over the planes
+  float* const Yhs = Yls + Sh::YL;  // cells c0 + nx ..
+  float* const Rb = Yhs + Sh::YL;   // R, then D over the planes
+  int* const cflag = reinterpret_cast<int*>(Rb + Sh::RL);
+  const float* M = a.M1f;
+  const int64_t ncell = a.n_cells, total = ncell * N3;
+  const int zoff = (int)((int64_t)a.nx * a.ny * N3);  // fewer than 2^31 DoFs
+  const int64_t nbatch = (ncell + CB - 1) / CB;
+  // the plane task of this thread: z-plane pk of cell pc of the batch
+  const int pc = threadIdx.x / N, pk = threadIdx.x - pc * N;
+  const int poff = pc * N3 + N2 * pk;
+  for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+    const int64_t c0 = bt * CB;
+    const int nc = (int)std::min<int64_t>(CB, ncell - c0);  // cells in this batch
+    if (threadIdx.x < CB) {
+      // face flags: bit 2d lower neighbour in direction d, 2d + 1 upper (fewer than 2^31 cells)
+      const int64_t cell = c0 + threadIdx.x;
+      int f = 0;
+      if (cell < ncell) {
+        const unsigned c32 = (unsigned)cell, q = c32 / (unsigned)a.nx, cz = q / (unsigned)a.ny;
+        const unsigned cx = c32 - q * (unsigned)a.nx, cy = q - cz * (unsigned)a.ny;
+        f = (cx > 0) | ((cx + 1 < (unsigned)a.nx) << 1) | ((cy > 0) << 2) | ((cy + 1 < (unsigned)a.ny) << 3) |
+            ((cz > 0) << 4) | ((cz + 1 < (unsigned)a.nz) << 5);
+      }
+      cflag[threadIdx.x] = f;
+    }
+    float* const U = dg_stage(Us, src, (c0 - 1) * N3, (CB + 2) * N3, total) + N3;  // U: cell c0
+    float* const Yl = dg_stage(Yls, src, (c0 - a.nx) * N3, CB * N3, total);
+    float* const Yh = dg_stage(Yhs, src, (c0 + a.nx) * N3, CB * N3, total);
+    dg_stage_wait();
+    __syncthreads();
+    const float* const srcb = src + c0 * N3;
+    // z-lines: R = s_z L_z u; every global load of a thread's lines issued before the arithmetic
+    {
+      float wlo[RZ][N], whi[RZ][N];
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) {
+        const int t = threadIdx.x + 128 * r;
+        const int c = t / N2, o = c * N3 + (t - c * N2);
+        const int f = (c < nc) ? cflag[c] : 0;  // no neighbours read past the batch's last cell
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          wlo[r][k] = ((f >> 4) & 1) ? __ldg(srcb + (o - zoff + N2 * k)) : 0.f;
+          whi[r][k] = ((f >> 5) & 1) ? __ldg(srcb + (o + zoff + N2 * k)) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) {
+        const int t = threadIdx.x + 128 * r;
+        const int c = t / N2, o = c * N3 + (t - c * N2);
+        if (c < nc) {
+          const int f = cflag[c];
+          float x[N], y[N];
+#pragma unroll
+          for (int k = 0; k < N; ++k) x[k] = U[o + N2 * k];
+          float wl, gl, wh, gh;
+          dg_nb_end<N, true>(a, wlo[r], true, &wl, &gl);  // zeros already without a neighbour
+          dg_nb_end<N, false>(a, whi[r], true, &wh, &gh);
+          float fl, sl, fh, shc;
+          dg_end_coefs(a, 2, f, &fl, &sl, &fh, &shc);
+          dg_line_reg<N, 2>(a, x, y, fl, sl, wl, gl, fh, shc, wh, gh);
+#pragma unroll
+          for (int k = 0; k < N; ++k) Rb[o + N2 * k] = y[k];
+        }
+      }
+    }
+    __syncthreads();
+    // planes: D = M_x M_y R, C = M_y (s_x L_x u) + M_x (s_y L_y u), one z-plane per thread
+    if (threadIdx.x < CB * N && pc < nc) {
+      const int f = cflag[pc];
+      {
+        float* const rp = Rb + poff;
+        float t[N][N];  // M_y R, accumulated row by row of R
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+          float rr[N];
+#pragma unroll
+          for (int i = 0; i < N; ++i) rr[i] = rp[N * n + i];
+#pragma unroll
+          for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) t[j][i] = n == 0 ? M[j * N] * rr[i] : fmaf(M[j * N + n], rr[i], t[j][i]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            float s = M[i * N] * t[j][0];
+#pragma unroll
+            for (int m = 1; m < N; ++m) s = fmaf(M[i * N + m], t[j][m], s);
+            rp[N * j + i] = s;
+          }
+      }
+      const float* const up = U + poff;
+      float u[N][N], cacc[N][N];
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[j][i] = up[N * j + i];
+      {
+        // rows: P = s_x L_x u, accumulated into C = M_y P row by row of P; the x-neighbours' planes are the
+        // staged cells beside this one (always in the staging buffer, selected by the face flags)
+        float fl, sl, fh, shc;
+        dg_end_coefs(a, 0, f, &fl, &sl, &fh, &shc);
+        const bool xl = f & 1, xh = (f >> 1) & 1;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          float wn[N], p[N], wl, gl, wh, gh;
+#pragma unroll
+          for (int i = 0; i < N; ++i) wn[i] = up[N * m + i - N3];
+          dg_nb_end<N, true>(a, wn, xl, &wl, &gl);
+#pragma unroll
+          for (int i = 0; i < N; ++i) wn[i] = up[N * m + i + N3];
+          dg_nb_end<N, false>(a, wn, xh, &wh, &gh);
+          dg_line_reg<N, 0>(a, u[m], p, fl, sl, wl, gl, fh, shc, wh, gh);
+#pragma unroll
+          for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) cacc[j][i] = m == 0 ? M[j * N] * p[i] : fmaf(M[j * N + m], p[i], cacc[j][i]);
+        }
+      }
+      float* const ylp = Yl + poff;
+      {
+        // columns: Q = s_y L_y u, accumulated into C += M_x Q column by column of Q
+        float fl, sl, fh, shc;
+        dg_end_coefs(a, 1, f, &fl, &sl, &fh, &shc);
+        const bool yl = (f >> 2) & 1, yh = (f >> 3) & 1;
+        const float* const yhp = Yh + poff;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          float x[N], wn[N], q[N], wl, gl, wh, gh;
+#pragma unroll
+          for (int j = 0; j < N; ++j) x[j] = u[j][i];
+#pragma unroll
+          for (int j = 0; j < N; ++j) wn[j] = ylp[N * j + i];
+          dg_nb_end<N, true>(a, wn, yl, &wl, &gl);
+#pragma unroll
+          for (int j = 0; j < N; ++j) wn[j] = yhp[N * j + i];
+          dg_nb_end<N, false>(a, wn, yh, &wh, &gh);
+          dg_line_reg<N, 1>(a, x, q, fl, sl, wl, gl, fh, shc, wh, gh);
+#pragma unroll
+          for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int ii = 0; ii < N; ++ii) cacc[j][ii] = fmaf(M[ii * N + i], q[j], cacc[j][ii]);
+        }
+      }
+      // C over the task's own plane of the y-lower staging (read only by this task, all reads done)
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int i = 0; i < N; ++i) ylp[N * j + i] = cacc[j][i];
+    }
+    __syncthreads();
+    // z-lines: y = M_z C + D
+    {
+      float* const dstb = dst + c0 * N3;
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) {
+        const int t = threadIdx.x + 128 * r;
+        const int c = t / N2, o = c * N3 + (t - c * N2);
+        if (c < nc) {
+          float cc[N], dd[N];
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            cc[k] = Yl[o + N2 * k];
+            dd[k] = Rb[o + N2 * k];
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            float s = dd[k];
+#pragma unroll
+            for (int m = 0; m < N; ++m) s = fmaf(M[k * N + m], cc[m], s);
+            dstb[o + N2 * k] = s;
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -528,6 +827,12 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
   a.coef = op->dg_coef;
   a.dmask = op->dirichlet;
   for (int d = 0; d < 3; ++d) {
+    a.fint[d] = (float)(0.5 * a.hinv[d] * a.scale[d]);
+    a.fbnd[d] = (float)(a.hinv[d] * a.scale[d]);
+    a.sint[d] = (float)(a.sig_int[d] * a.scale[d]);
+    a.sbnd[d] = (float)(a.sig_bnd[d] * a.scale[d]);
+  }
+  for (int d = 0; d < 3; ++d) {
     const double v[5] = {a.hinv[d], 0.5 * a.hinv[d], a.sig_int[d], a.sig_bnd[d], a.scale[d]};
     for (int e = 0; e < 5; ++e) {
       a.dfs[d][e][0] = (float)v[e];
@@ -547,6 +852,8 @@ static DgArgs dg_args(const mfx_op* op, const int32_t* skip) {
       a.K1f[i * n + j] = (float)k1;
       a.M1f[i * n + j] = (float)m1;
     }
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < n * n; ++i) a.K1s[d][i] = (float)(a.K1[i] * a.hinv[d] * a.scale[d]);
   for (int i = 0; i < n; ++i) {
     a.d0[i] = lagrange_derivative(n, b.gll, i, 0.0);
     a.d1[i] = lagrange_derivative(n, b.gll, i, 1.0);
@@ -585,6 +892,25 @@ static mfx_status run_dg(const mfx_op* op, const Real* src, Real* dst, cudaStrea
 }
 
 template <int N>
+static mfx_status run_dg_plane(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  using Sh = DgPlane<N>;
+  auto kern = dg_vmult_plane_kernel<N>;
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+    int b = 0;
+    MFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, Sh::SMEM));
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  const DgArgs a = dg_args(op, skip);
+  const int64_t nbatch = (op->n_cells + Sh::CB - 1) / Sh::CB;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nbatch, (int64_t)device_sm_count() * blocks_per_sm));
+  kern<<<grid, 128, Sh::SMEM, s>>>(a, src, dst);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
+template <int N>
 static mfx_status run_dg_df(const mfx_op* op, const double* src, double* dst, cudaStream_t s, const int32_t* skip) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int CB = 128 / N2 > 0 ? 128 / N2 : 1;
@@ -607,6 +933,20 @@ static mfx_status run_dg_df(const mfx_op* op, const double* src, double* dst, cu
 
 template <typename Real>
 static mfx_status dg_dispatch(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+  // FP32 at degrees 1..5 with a 16-byte aligned source: the plane kernel (its staging loads are 16 bytes
+  // wide); otherwise the line kernel
+  if (sizeof(Real) == 4 && ((uintptr_t)src & 15) == 0) {
+    const float* x = (const float*)src;
+    float* y = (float*)dst;
+    switch (op->n) {
+      case 2: return run_dg_plane<2>(op, x, y, s, skip);
+      case 3: return run_dg_plane<3>(op, x, y, s, skip);
+      case 4: return run_dg_plane<4>(op, x, y, s, skip);
+      case 5: return run_dg_plane<5>(op, x, y, s, skip);
+      case 6: return run_dg_plane<6>(op, x, y, s, skip);
+      default: break;
+    }
+  }
   switch (op->n) {
     case 2: return run_dg<2, Real>(op, src, dst, s, skip);
     case 3: return run_dg<3, Real>(op, src, dst, s, skip);

@@ -76,16 +76,40 @@ def test_sipg_vmult_and_diagonal_equal_the_oracle(mfx, dims, k, lengths, faces, 
     assert np.array_equal(t["cell_dofs"].ravel(), np.arange(op.n_dofs)) and t["constrained"].size == 0
 
 
-@pytest.mark.parametrize("k", [2, 4])
-def test_sipg_many_cells_span_several_blocks_and_a_ragged_tail(mfx, k):
-    """More cells than one CTA batch and than one wave of the grid, with a partial last batch."""
-    dims = (7, 5, 3)
+@pytest.mark.parametrize("k,dims", [(1, (9, 8, 5)), (2, (7, 5, 3)), (3, (7, 5, 4)), (4, (7, 5, 3)), (5, (6, 5, 3)),
+                                    (6, (5, 3, 2))])
+def test_sipg_many_cells_span_several_blocks_and_a_ragged_tail(mfx, k, dims):
+    """More cells than one CTA batch, batches that start inside a row of cells and whose y and z
+    neighbours lie in other batches, and a partial last batch; FP64 and FP32 (the FP32 plane kernel at
+    degrees 1..5, the line kernel at 6) against the oracle matrix."""
     K = odg.dg_operator(*dims, k, (1.0, 1.2, 0.9), 0b011011)
     op = sipg(mfx, dims, k, (1.0, 1.2, 0.9), 0b011011)
     x = synthetic.uniform_vector(op.n_dofs, 41)
     ref = K @ x
+    scale = np.abs(ref).max()
     y = apply(op, x, torch.float64)
-    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(y - ref).max() <= 1e-12 * scale
+    y32 = apply(op, x, torch.float32)
+    assert np.abs(y32 - ref).max() <= 1e-5 * scale, np.abs(y32 - ref).max() / scale
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_sipg_fp32_source_not_16_byte_aligned(mfx, k):
+    """A source vector that starts 4 bytes past a 16-byte boundary takes the FP32 line kernel (the plane
+    kernel stages with 16-byte loads); both give the oracle's product."""
+    dims = (7, 5, 3)
+    K = odg.dg_operator(*dims, k, (1.0, 1.2, 0.9), 0b011011)
+    op = sipg(mfx, dims, k, (1.0, 1.2, 0.9), 0b011011)
+    x = synthetic.uniform_vector(op.n_dofs, 43)
+    ref = K @ x
+    buf = torch.zeros(op.n_dofs + 1, dtype=torch.float32, device=DEV)
+    src = buf[1:]
+    src.copy_(torch.tensor(x, dtype=torch.float32, device=DEV))
+    assert src.data_ptr() % 16 == 4
+    dst = torch.empty_like(src)
+    op.vmult(src, dst)
+    y32 = dst.cpu().double().numpy()
+    assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
 def test_sipg_pure_neumann_kernel_is_the_constants(mfx):
