@@ -262,17 +262,23 @@ __global__ void __launch_bounds__(128) dg_vmult_kernel(const __grid_constant__ D
 // FP32 plane kernel (degrees 1..5).  The same Kronecker sum, ordered so that two of the three
 // directions never leave registers:
 //   y = M_z C + D,   C = M_y (s_x L_x u) + M_x (s_y L_y u),   D = M_x M_y R,   R = s_z L_z u.
-// A CTA takes CB consecutive cells (CB N plane tasks, at most 128).  Three phases per batch:
-//   z-lines (one task per line of a cell): R from the cell's z-line, the z-neighbours' z-lines read
-//     straight from global memory (coalesced: a z-line task reads one point per plane);
-//   planes (one task per z-plane of a cell): the plane of u in registers, L_x along its rows and L_y
-//     along its columns with the x-neighbours' planes from the staged chunk (cells c0 - 1 .. c0 + CB)
-//     and the y-neighbours' planes from two more staged chunks (cells c0 -/+ nx ..), the masses M_y and
-//     M_x in registers; C and D written back over the tasks' own planes of the staging buffers;
+// A CTA takes CB consecutive cells (CB N plane tasks, at most 128 threads).  Three phases per batch:
+//   z-lines (one task per line of a cell, several per thread): R from the cell's z-line, with the
+//     z-neighbours' z-lines read from global memory (coalesced: a z-line task reads one point per
+//     plane), requested before the batch's staging completes;
+//   planes (one task per z-plane of a cell): L_x along the plane's rows and L_y along its columns, the
+//     x-neighbours' planes taken from the staged chunk (cells c0 - 1 .. c0 + CB) and the y-neighbours'
+//     planes from two more staged chunks (cells c0 -/+ nx ..), the masses M_y and M_x applied in
+//     registers row by row and column by column; C written over the task's own plane of the y-lower
+//     chunk, D over its plane of R;
 //   z-lines: y = M_z C + D, stored straight to dst.
-// The staged chunks are copied with 16-byte loads from a 16-byte aligned start below the chunk and
+// The staged chunks are asynchronous 16-byte copies from a 16-byte aligned start below the chunk,
 // indexed from the shift; points outside the vector read as zero (and are never used: the face flags
-// of a cell select which neighbour data enter).
+// of a cell select which neighbour data enter).  The next batch's own and y-upper chunks are requested
+// before the last phase of the current one, which reads neither.
+// Measured and dropped (p = 4, 65.5M DoFs, against 0.32 ms): two planes per thread as the lanes of packed
+// FFMA2 values (half the threads, twice the shared loads each: 0.36-0.43 ms), 21 cells per batch for five
+// CTAs per SM (0.36 ms).
 template <int N>
 struct DgPlane {
   static constexpr int N2 = N * N, N3 = N2 * N;
@@ -379,11 +385,21 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
   int* const cflag = reinterpret_cast<int*>(Rb + Sh::RL);
   const float* M = a.M1f;
   const int64_t ncell = a.n_cells, total = ncell * N3;
-  const int zoff = (int)((int64_t)a.nx * a.ny * N3);  // fewer than 2^31 DoFs
+  const int64_t sxy = (int64_t)a.nx * a.ny;
+  const int zoff = (int)(sxy * N3);  // fewer than 2^31 DoFs
   const int64_t nbatch = (ncell + CB - 1) / CB;
   // the plane task of this thread: z-plane pk of cell pc of the batch
   const int pc = threadIdx.x / N, pk = threadIdx.x - pc * N;
   const int poff = pc * N3 + N2 * pk;
+  // staging of the batch's own chunk (with the x-neighbours) and of its y-upper chunk is issued while the
+  // previous batch finishes (its last phase reads neither buffer)
+  float* U = nullptr;
+  float* Yh = nullptr;
+  if (blockIdx.x < nbatch) {
+    const int64_t c0 = (int64_t)blockIdx.x * CB;
+    U = dg_stage(Us, src, (c0 - 1) * N3, (CB + 2) * N3, total) + N3;  // U: cell c0
+    Yh = dg_stage(Yhs, src, (c0 + a.nx) * N3, CB * N3, total);
+  }
   for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
     const int64_t c0 = bt * CB;
     const int nc = (int)std::min<int64_t>(CB, ncell - c0);  // cells in this batch
@@ -399,44 +415,43 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
       }
       cflag[threadIdx.x] = f;
     }
-    float* const U = dg_stage(Us, src, (c0 - 1) * N3, (CB + 2) * N3, total) + N3;  // U: cell c0
     float* const Yl = dg_stage(Yls, src, (c0 - a.nx) * N3, CB * N3, total);
-    float* const Yh = dg_stage(Yhs, src, (c0 + a.nx) * N3, CB * N3, total);
+    const float* const srcb = src + c0 * N3;
+    // the z-neighbours' lines of this thread's z-line tasks, requested before the staging completes (a
+    // cell has a z-lower neighbour iff its index is at least nx ny, a z-upper one iff index + nx ny is
+    // below the cell count)
+    float wlo[RZ][N], whi[RZ][N];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+      const int t = threadIdx.x + 128 * r;
+      const int c = t / N2, o = c * N3 + (t - c * N2);
+      const bool lo = c < nc && c0 + c >= sxy, hi = c < nc && c0 + c + sxy < ncell;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        wlo[r][k] = lo ? __ldg(srcb + (o - zoff + N2 * k)) : 0.f;
+        whi[r][k] = hi ? __ldg(srcb + (o + zoff + N2 * k)) : 0.f;
+      }
+    }
     dg_stage_wait();
     __syncthreads();
-    const float* const srcb = src + c0 * N3;
-    // z-lines: R = s_z L_z u; every global load of a thread's lines issued before the arithmetic
-    {
-      float wlo[RZ][N], whi[RZ][N];
+    // z-lines: R = s_z L_z u
 #pragma unroll
-      for (int r = 0; r < RZ; ++r) {
-        const int t = threadIdx.x + 128 * r;
-        const int c = t / N2, o = c * N3 + (t - c * N2);
-        const int f = (c < nc) ? cflag[c] : 0;  // no neighbours read past the batch's last cell
+    for (int r = 0; r < RZ; ++r) {
+      const int t = threadIdx.x + 128 * r;
+      const int c = t / N2, o = c * N3 + (t - c * N2);
+      if (c < nc) {
+        const int f = cflag[c];
+        float x[N], y[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          wlo[r][k] = ((f >> 4) & 1) ? __ldg(srcb + (o - zoff + N2 * k)) : 0.f;
-          whi[r][k] = ((f >> 5) & 1) ? __ldg(srcb + (o + zoff + N2 * k)) : 0.f;
-        }
-      }
+        for (int k = 0; k < N; ++k) x[k] = U[o + N2 * k];
+        float wl, gl, wh, gh;
+        dg_nb_end<N, true>(a, wlo[r], true, &wl, &gl);  // zeros already without a neighbour
+        dg_nb_end<N, false>(a, whi[r], true, &wh, &gh);
+        float fl, sl, fh, shc;
+        dg_end_coefs(a, 2, f, &fl, &sl, &fh, &shc);
+        dg_line_reg<N, 2>(a, x, y, fl, sl, wl, gl, fh, shc, wh, gh);
 #pragma unroll
-      for (int r = 0; r < RZ; ++r) {
-        const int t = threadIdx.x + 128 * r;
-        const int c = t / N2, o = c * N3 + (t - c * N2);
-        if (c < nc) {
-          const int f = cflag[c];
-          float x[N], y[N];
-#pragma unroll
-          for (int k = 0; k < N; ++k) x[k] = U[o + N2 * k];
-          float wl, gl, wh, gh;
-          dg_nb_end<N, true>(a, wlo[r], true, &wl, &gl);  // zeros already without a neighbour
-          dg_nb_end<N, false>(a, whi[r], true, &wh, &gh);
-          float fl, sl, fh, shc;
-          dg_end_coefs(a, 2, f, &fl, &sl, &fh, &shc);
-          dg_line_reg<N, 2>(a, x, y, fl, sl, wl, gl, fh, shc, wh, gh);
-#pragma unroll
-          for (int k = 0; k < N; ++k) Rb[o + N2 * k] = y[k];
-        }
+        for (int k = 0; k < N; ++k) Rb[o + N2 * k] = y[k];
       }
     }
     __syncthreads();
@@ -526,6 +541,11 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
         for (int i = 0; i < N; ++i) ylp[N * j + i] = cacc[j][i];
     }
     __syncthreads();
+    if (bt + gridDim.x < nbatch) {
+      const int64_t n0 = (bt + gridDim.x) * CB;
+      U = dg_stage(Us, src, (n0 - 1) * N3, (CB + 2) * N3, total) + N3;
+      Yh = dg_stage(Yhs, src, (n0 + a.nx) * N3, CB * N3, total);
+    }
     // z-lines: y = M_z C + D
     {
       float* const dstb = dst + c0 * N3;
