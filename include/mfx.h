@@ -296,6 +296,9 @@ mfx_status mfx_get_tables(const mfx_op* op, int32_t* cell_dofs, int32_t* constra
  * src, dst: device, n_dofs entries of the precision, must not alias; on
  * structured meshes the FP32 kernels move tile rows with the copy engine and
  * need src and dst 16-byte aligned (as cudaMalloc and torch give them).
+ * SIPG operators take vectors of any alignment; in FP32 at degrees 1..5
+ * their fastest kernel stages src with 16-byte copies and runs when src is
+ * 16-byte aligned (otherwise the line kernel runs, same result to rounding).
  * Errors: MFX_EINVAL (null, precision not built, or an FP32 vector on a
  * structured mesh not 16-byte aligned), MFX_ECUDA (launch).
  */
