@@ -370,12 +370,67 @@ __device__ __forceinline__ void dg_end_coefs(const DgArgs& a, int d, int f, floa
   *shc = hi ? a.sint[d] : (dhi ? a.sbnd[d] : 0.f);
 }
 
+__device__ __forceinline__ float2 dg_f2(float v) { return make_float2(v, v); }
+
+// dg_line_reg on two lines at once (the lanes of each float2, each with its own end coefficients) with
+// packed multiply-adds; fhn is minus the upper end's factor.
+template <int N, int D>
+__device__ __forceinline__ void dg_line_reg2(const DgArgs& a, const float2 (&x)[N], float2 (&y)[N], float2 fl, float2 sl,
+                                             float2 wl, float2 gl, float2 fhn, float2 shc, float2 wh, float2 gh) {
+  constexpr int K = N - 1;
+  float2 g0 = __fmul2_rn(dg_f2(a.d0f[0]), x[0]);
+  float2 g1 = __fmul2_rn(dg_f2(a.d1f[0]), x[0]);
+#pragma unroll
+  for (int j = 1; j < N; ++j) {
+    g0 = __ffma2_rn(dg_f2(a.d0f[j]), x[j], g0);
+    g1 = __ffma2_rn(dg_f2(a.d1f[j]), x[j], g1);
+  }
+  const float2 jl = __ffma2_rn(dg_f2(-1.f), wl, x[0]);
+  const float2 jh = __ffma2_rn(dg_f2(-1.f), wh, x[K]);
+  const float2 tl = __fmul2_rn(fl, jl);
+  const float2 tn = __fmul2_rn(fhn, jh);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float2 s = __ffma2_rn(dg_f2(a.d1f[i]), tn, __fmul2_rn(dg_f2(a.d0f[i]), tl));
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = __ffma2_rn(dg_f2(a.K1s[D][i * N + j]), x[j], s);
+    y[i] = s;
+  }
+  y[0] = __ffma2_rn(fl, __ffma2_rn(dg_f2(1.f), g0, gl), __ffma2_rn(sl, jl, y[0]));
+  y[K] = __ffma2_rn(shc, jh, __ffma2_rn(fhn, __ffma2_rn(dg_f2(1.f), g1, gh), y[K]));
+}
+
+// dg_nb_end on two neighbour lines at once, each lane with its own neighbour flag.
+template <int N, bool LOWER>
+__device__ __forceinline__ void dg_nb_end2(const DgArgs& a, const float2 (&w)[N], bool hx, bool hy, float2* wv,
+                                           float2* g) {
+  float2 s = __fmul2_rn(dg_f2(LOWER ? a.d1f[0] : a.d0f[0]), w[0]);
+#pragma unroll
+  for (int j = 1; j < N; ++j) s = __ffma2_rn(dg_f2(LOWER ? a.d1f[j] : a.d0f[j]), w[j], s);
+  const float2 v = LOWER ? w[N - 1] : w[0];
+  *g = make_float2(hx ? s.x : 0.f, hy ? s.y : 0.f);
+  *wv = make_float2(hx ? v.x : 0.f, hy ? v.y : 0.f);
+}
+
+// End coefficients of direction d for the two lanes' cells (face flags fx, fy), the upper end's factor negated.
+__device__ __forceinline__ void dg_end_coefs2(const DgArgs& a, int d, int fx, int fy, float2* fl, float2* sl,
+                                              float2* fhn, float2* shc) {
+  float a0, a1, a2, a3, b0, b1, b2, b3;
+  dg_end_coefs(a, d, fx, &a0, &a1, &a2, &a3);
+  dg_end_coefs(a, d, fy, &b0, &b1, &b2, &b3);
+  *fl = make_float2(a0, b0);
+  *sl = make_float2(a1, b1);
+  *fhn = make_float2(-a2, -b2);
+  *shc = make_float2(a3, b3);
+}
+
 template <int N>
 __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
     dg_vmult_plane_kernel(const __grid_constant__ DgArgs a, const float* __restrict__ src, float* __restrict__ dst) {
   using Sh = DgPlane<N>;
   constexpr int N2 = Sh::N2, N3 = Sh::N3, CB = Sh::CB;
   constexpr int RZ = (CB * N2 + 127) / 128;  // z-line tasks per thread
+  constexpr int RP = RZ / 2 > 0 ? RZ / 2 : 1;  // pairs of them (RZ >= 2 at every degree)
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) float dsm[];
   float* const Us = dsm;            // cells c0 - 1 .. c0 + CB
@@ -419,8 +474,9 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
     const float* const srcb = src + c0 * N3;
     // the z-neighbours' lines of this thread's z-line tasks, requested before the staging completes (a
     // cell has a z-lower neighbour iff its index is at least nx ny, a z-upper one iff index + nx ny is
-    // below the cell count)
-    float wlo[RZ][N], whi[RZ][N];
+    // below the cell count); rounds 2p and 2p + 1 of a thread's tasks are the lanes of float2 values
+    float2 wlo[RP][N], whi[RP][N];
+    float wlo1[N], whi1[N];
 #pragma unroll
     for (int r = 0; r < RZ; ++r) {
       const int t = threadIdx.x + 128 * r;
@@ -428,16 +484,50 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
       const bool lo = c < nc && c0 + c >= sxy, hi = c < nc && c0 + c + sxy < ncell;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        wlo[r][k] = lo ? __ldg(srcb + (o - zoff + N2 * k)) : 0.f;
-        whi[r][k] = hi ? __ldg(srcb + (o + zoff + N2 * k)) : 0.f;
+        const float vl = lo ? __ldg(srcb + (o - zoff + N2 * k)) : 0.f;
+        const float vh = hi ? __ldg(srcb + (o + zoff + N2 * k)) : 0.f;
+        if (r < 2 * RP) {
+          if (r & 1) {
+            wlo[r / 2][k].y = vl;
+            whi[r / 2][k].y = vh;
+          } else {
+            wlo[r / 2][k].x = vl;
+            whi[r / 2][k].x = vh;
+          }
+        } else {
+          wlo1[k] = vl;
+          whi1[k] = vh;
+        }
       }
     }
     dg_stage_wait();
     __syncthreads();
-    // z-lines: R = s_z L_z u
+    // z-lines: R = s_z L_z u, two tasks at a time in packed arithmetic (the second lane repeats the first,
+    // never stored, where its task lies past the batch's last cell)
 #pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-      const int t = threadIdx.x + 128 * r;
+    for (int q = 0; q < RP; ++q) {
+      const int tX = threadIdx.x + 256 * q, tY = tX + 128;
+      const int cX = tX / N2, oX = cX * N3 + (tX - cX * N2);
+      const int cY = tY / N2, oY = cY * N3 + (tY - cY * N2);
+      const bool hy = cY < nc;
+      if (cX < nc) {
+        const int fX = cflag[cX], fY = hy ? cflag[cY] : fX, oYe = hy ? oY : oX;
+        float2 x[N], y[N], wl, gl, wh, gh, fl, sl, fhn, shc;
+#pragma unroll
+        for (int k = 0; k < N; ++k) x[k] = make_float2(U[oX + N2 * k], U[oYe + N2 * k]);
+        dg_nb_end2<N, true>(a, wlo[q], true, true, &wl, &gl);  // zeros already without a neighbour
+        dg_nb_end2<N, false>(a, whi[q], true, true, &wh, &gh);
+        dg_end_coefs2(a, 2, fX, fY, &fl, &sl, &fhn, &shc);
+        dg_line_reg2<N, 2>(a, x, y, fl, sl, wl, gl, fhn, shc, wh, gh);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          Rb[oX + N2 * k] = y[k].x;
+          if (hy) Rb[oY + N2 * k] = y[k].y;
+        }
+      }
+    }
+    if (RZ & 1) {
+      const int t = threadIdx.x + 128 * (RZ - 1);
       const int c = t / N2, o = c * N3 + (t - c * N2);
       if (c < nc) {
         const int f = cflag[c];
@@ -445,8 +535,8 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
 #pragma unroll
         for (int k = 0; k < N; ++k) x[k] = U[o + N2 * k];
         float wl, gl, wh, gh;
-        dg_nb_end<N, true>(a, wlo[r], true, &wl, &gl);  // zeros already without a neighbour
-        dg_nb_end<N, false>(a, whi[r], true, &wh, &gh);
+        dg_nb_end<N, true>(a, wlo1, true, &wl, &gl);
+        dg_nb_end<N, false>(a, whi1, true, &wh, &gh);
         float fl, sl, fh, shc;
         dg_end_coefs(a, 2, f, &fl, &sl, &fh, &shc);
         dg_line_reg<N, 2>(a, x, y, fl, sl, wl, gl, fh, shc, wh, gh);
@@ -546,12 +636,35 @@ __global__ void __launch_bounds__(128, N <= 3 ? 6 : (N <= 5 ? 4 : 2))
       U = dg_stage(Us, src, (n0 - 1) * N3, (CB + 2) * N3, total) + N3;
       Yh = dg_stage(Yhs, src, (n0 + a.nx) * N3, CB * N3, total);
     }
-    // z-lines: y = M_z C + D
+    // z-lines: y = M_z C + D, two tasks at a time in packed arithmetic
     {
       float* const dstb = dst + c0 * N3;
 #pragma unroll
-      for (int r = 0; r < RZ; ++r) {
-        const int t = threadIdx.x + 128 * r;
+      for (int q = 0; q < RP; ++q) {
+        const int tX = threadIdx.x + 256 * q, tY = tX + 128;
+        const int cX = tX / N2, oX = cX * N3 + (tX - cX * N2);
+        const int cY = tY / N2, oY = cY * N3 + (tY - cY * N2);
+        const bool hy = cY < nc;
+        if (cX < nc) {
+          const int oYe = hy ? oY : oX;
+          float2 cc[N], dd[N];
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            cc[k] = make_float2(Yl[oX + N2 * k], Yl[oYe + N2 * k]);
+            dd[k] = make_float2(Rb[oX + N2 * k], Rb[oYe + N2 * k]);
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            float2 s = dd[k];
+#pragma unroll
+            for (int m = 0; m < N; ++m) s = __ffma2_rn(dg_f2(M[k * N + m]), cc[m], s);
+            dstb[oX + N2 * k] = s.x;
+            if (hy) dstb[oY + N2 * k] = s.y;
+          }
+        }
+      }
+      if (RZ & 1) {
+        const int t = threadIdx.x + 128 * (RZ - 1);
         const int c = t / N2, o = c * N3 + (t - c * N2);
         if (c < nc) {
           float cc[N], dd[N];
