@@ -93,6 +93,22 @@ def test_sipg_many_cells_span_several_blocks_and_a_ragged_tail(mfx, k, dims):
     assert np.abs(y32 - ref).max() <= 1e-5 * scale, np.abs(y32 - ref).max() / scale
 
 
+@pytest.mark.parametrize("k,dims,faces", [(1, (1, 1, 1), 0x3F), (3, (1, 1, 1), 0b100110), (5, (1, 1, 1), 0),
+                                          (2, (1, 5, 7), 0x3F), (4, (6, 1, 4), 0b011001), (3, (5, 4, 1), 0x3F),
+                                          (4, (1, 30, 2), 0b110011), (2, (27, 1, 1), 0b000011)])
+def test_sipg_fp32_degenerate_boxes(mfx, k, dims, faces):
+    """Boxes one cell thick in some direction (no neighbours there; a batch of the FP32 plane kernel spans
+    several rows or planes of cells, and its staged neighbour chunks overlap its own), a single cell, and
+    natural faces: FP32 against the oracle matrix."""
+    K = odg.dg_operator(*dims, k, (1.0, 0.8, 1.1), faces)
+    op = sipg(mfx, dims, k, (1.0, 0.8, 1.1), faces)
+    x = synthetic.uniform_vector(op.n_dofs, 47 + k)
+    ref = K @ x
+    scale = np.abs(ref).max()
+    y32 = apply(op, x, torch.float32)
+    assert np.abs(y32 - ref).max() <= 1e-5 * scale, np.abs(y32 - ref).max() / scale
+
+
 @pytest.mark.parametrize("k", [2, 4])
 def test_sipg_fp32_source_not_16_byte_aligned(mfx, k):
     """A source vector that starts 4 bytes past a 16-byte boundary takes the FP32 line kernel (the plane
