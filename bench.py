@@ -412,6 +412,9 @@ def main():
             line["octree"] = octree_measurement(mfx, synthetic, torch, args.octree_degree)
             # the same refinement on 32^3 coarse cells (17.5M DoFs at Q4): the kernels at a serving-size mesh
             line["octree"]["large"] = octree_measurement(mfx, synthetic, torch, args.octree_degree, nb=32, fp64=False)
+            # the same leaves on the undeformed cube with a constant coefficient (the serving requests' form)
+            line["octree"]["large_box"] = octree_measurement(mfx, synthetic, torch, args.octree_degree, nb=32,
+                                                             fp64=False, box=True)
         if not args.no_sipg:
             line["sipg"] = sipg_measurement(mfx, synthetic, torch, np, tuple(args.sipg_dims), k=args.sipg_degree,
                                             solve=not args.sipg_vmult_only)
@@ -600,25 +603,32 @@ def mixed_solve_measurement(mfx, synthetic, torch, np):
     return out
 
 
-def octree_bytes(n_dofs, n_cells, k, s):
+def octree_bytes(n_dofs, n_cells, k, s, box=False):
     """Algorithmic bytes of an octree vmult: src read and dst written, the 6-entry metric per quadrature
-    point, the int32 cell DoF table; the hanging constraints' words and coarse-DoF lists are left out
-    (they are a few bytes per hanging cell)."""
+    point (box cells: 3 entries per cell), the int32 cell DoF table; the hanging constraints' words and
+    coarse-DoF lists are left out (they are a few bytes per hanging cell)."""
     n3 = (k + 1) ** 3
-    return 2 * s * n_dofs + 6 * s * n_cells * n3 + 4 * n_cells * n3
+    metric = 3 * s * n_cells if box else 6 * s * n_cells * n3
+    return 2 * s * n_dofs + metric + 4 * n_cells * n3
 
 
-def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2, fp64=True):
+def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2, fp64=True, box=False):
     """FP32 and FP64 vmult on an octree refined twice inside a ball (hanging nodes; the serving
-    workload's mesh family): nb^3 coarse cells of the deformed cube, the variable coefficient."""
+    workload's mesh family): nb^3 coarse cells of the deformed cube, the variable coefficient; box=True:
+    the undeformed cube and a constant coefficient (the serving requests' operator: every cell an
+    axis-aligned box, the FP32 metric one diagonal per cell)."""
     leaves = synthetic.octree_leaves(nb, levels, (0.5, 0.45, 0.55), 0.3)
-    mesh = mfx.Mesh.octree(nb, nb, nb, leaves, synthetic.deformed_vertices(nb, nb, nb))
-    op = mfx.Operator(mesh, k, mfx.COEF_TRIG, (1.0, 0.5))
+    if box:
+        op = mfx.Operator(mfx.Mesh.octree(nb, nb, nb, leaves), k)
+    else:
+        mesh = mfx.Mesh.octree(nb, nb, nb, leaves, synthetic.deformed_vertices(nb, nb, nb))
+        op = mfx.Operator(mesh, k, mfx.COEF_TRIG, (1.0, 0.5))
     info = op.info()
     n = op.n_dofs
     hbm, peak_kind = peaks()
-    out = {"workload": "octree, %d^3 coarse cells refined %d times in a ball, Q%d" % (nb, levels, k), "n_dofs": n,
-           "n_cells": info["n_cells"], "n_hanging": info["n_hanging"]}
+    out = {"workload": "octree, %d^3 coarse cells refined %d times in a ball, Q%d%s"
+                       % (nb, levels, k, ", undeformed, constant coefficient" if box else ""), "n_dofs": n,
+           "n_cells": info["n_cells"], "n_hanging": info["n_hanging"], "box_metric": info["box_metric"]}
     stream = torch.cuda.current_stream()
     for name, dt in (("vmult_fp32", torch.float32), ("vmult_fp64", torch.float64))[:2 if fp64 else 1]:
         x = torch.tensor(synthetic.uniform_vector(n, 71), device="cuda", dtype=dt)
@@ -632,7 +642,8 @@ def octree_measurement(mfx, synthetic, torch, k=4, nb=16, levels=2, fp64=True):
             e1.record(stream)
         torch.cuda.synchronize()
         ms = statistics.median(a.elapsed_time(b) for a, b in evs)
-        byt = octree_bytes(n, info["n_cells"], k, 4 if dt == torch.float32 else 8)
+        byt = octree_bytes(n, info["n_cells"], k, 4 if dt == torch.float32 else 8,
+                           box=bool(info["box_metric"]) and dt == torch.float32)
         out[name] = {"gdofs": n / (ms * 1e-3) / 1e9, "ms": ms,
                      "roofline": {"bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                                   "frac": byt / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": byt,

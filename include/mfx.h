@@ -263,14 +263,19 @@ typedef struct {
   int32_t degree, n_q_1d, structured, cells_per_block;
   int32_t discretization;  /* MFX_CONTINUOUS or MFX_SIPG */
   int32_t structured_kernel; /* MFX_KERNEL_* of the FP32 structured vmult (0 where none applies) */
+  int32_t box_metric;  /* 1: an octree operator whose cells are all axis-aligned boxes with a constant
+                          coefficient, whose FP32 kernels take the metric as one diagonal per cell */
+  int32_t reserved;
 } mfx_op_info;
 
 /*
  * Sizes and layout of an operator: the DoF count of the Q_k space on the mesh
  * (Sec. 3.1 and Sec. 3.4), the cells, the constrained DoFs and constraint
  * entries of the hanging-node and Dirichlet constraints (Sec. 3.3), the
- * device bytes, and the chosen batch size and FP32 kernel (the last three
- * have no counterpart in the paper).  Errors: MFX_EINVAL (null argument).
+ * device bytes, and the chosen batch size and FP32 kernel (these three
+ * have no counterpart in the paper), and whether the FP32 metric is stored
+ * per box cell (the specialised mapping of cells that are boxes with axes
+ * parallel to the coordinate axes, Sec. 2).  Errors: MFX_EINVAL (null argument).
  */
 mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info);
 

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -262,6 +263,13 @@ int brick_cells_for_degree(int k) {
 // Operator data is allocated in stream order on the creation stream (the operator is complete, and
 // usable from any stream, once mfx_operator_create returns) and freed in stream order: making or
 // dropping an operator never waits for the rest of the device.
+// MFX_BOX_METRIC=0 in the environment keeps the full FP32 metric on box-cell octree operators (to compare
+// the two forms); read at every operator creation.
+static bool box_metric_enabled() {
+  const char* v = std::getenv("MFX_BOX_METRIC");
+  return !(v && v[0] == '0');
+}
+
 template <typename T>
 static mfx_status dev_alloc(mfx_op* op, T** p, size_t count, cudaStream_t s) {
   *p = nullptr;
@@ -333,7 +341,7 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   if (!op) return;
   if (sync) cudaDeviceSynchronize();
   free_workspace(op, s);
-  void* ptrs[] = {op->d_vertices, op->d_leaves, op->d_metric64, op->d_metric32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
+  void* ptrs[] = {op->d_vertices, op->d_leaves, op->d_metric64, op->d_metric32, op->d_box32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
                   op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs, op->d_cells_plain,
@@ -726,6 +734,35 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (coef_tmp) cudaFreeAsync(coef_tmp, s);
   MFX_TRY(geo_st);
   MFX_TRY(launch_diagonal(op, s));
+  // octree cells that are all axis-aligned boxes with a constant coefficient: the FP32 kernels take the
+  // metric as one diagonal per cell (the specialised mapping for boxes parallel to the coordinate axes);
+  // not at k = 7, whose FP32 kernel reads the full metric; MFX_BOX_METRIC=0 keeps the full metric
+  if (!op->structured && !op->dg && op->has_f32 && k != 7 && box_metric_enabled()) {
+    float* box = nullptr;
+    int* flag = nullptr;
+    MFX_TRY(dev_alloc(op, &box, (size_t)op->n_cells * 3, s));
+    cudaError_t e = cudaMallocAsync((void**)&flag, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    mfx_status bst = e == cudaSuccess ? launch_box_check(op, box, flag, s) : cuda_error(e, "box metric");
+    int not_box = 1;
+    if (bst == MFX_OK) {
+      e = cudaMemcpyAsync(&not_box, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) bst = cuda_error(e, "box metric");
+    }
+    if (flag) cudaFreeAsync(flag, s);
+    if (bst == MFX_OK && not_box == 0) {
+      cudaFreeAsync(op->d_metric32, s);
+      op->bytes_device -= (int64_t)(metric32_entries * sizeof(float));
+      op->d_metric32 = nullptr;
+      op->d_box32 = box;
+      op->box32 = true;
+    } else {
+      cudaFreeAsync(box, s);
+      op->bytes_device -= (int64_t)((size_t)op->n_cells * 3 * sizeof(float));
+    }
+    MFX_TRY(bst);
+  }
   std::vector<int32_t>().swap(op->hang_job_cell);  // staged by the copies above: host copies no longer needed
   std::vector<int32_t>().swap(op->hang_job_master);
   std::vector<uint8_t>().swap(op->hang_simple);
@@ -768,6 +805,8 @@ mfx_status mfx_operator_info(const mfx_op* op, mfx_op_info* info) {
   info->discretization = op->dg ? MFX_SIPG : MFX_CONTINUOUS;
   if (op->dg) info->cells_per_block = std::max(1, 128 / (op->n * op->n));
   info->structured_kernel = (op->structured && !op->dg && !op->percell32) ? op->f32_kernel : 0;
+  info->box_metric = op->box32 ? 1 : 0;
+  info->reserved = 0;
   return MFX_OK;
 }
 

@@ -640,6 +640,38 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s) {
   return MFX_OK;
 }
 
+// Box cells (axis-aligned boxes with a constant coefficient): the metric at quadrature point q is
+// w_q a |det J| J^-1 J^-T with a constant diagonal J, i.e. w_q diag(D).  One thread per cell: D from the
+// first point, every point and entry checked against w_q diag(D) to 1e-12 of the largest entry of D.
+__global__ void box_check_kernel(const GeoArgs g, const double* __restrict__ m64, float* __restrict__ box,
+                                 int* __restrict__ not_box) {
+  const int n = g.n, n3 = n * n * n;
+  const int64_t st = metric_stride(g);
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < g.n_cells;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    const double w0 = g.wq[0] * g.wq[0] * g.wq[0];
+    const int64_t b0 = metric_offset(g, cell, 0);
+    const double D[3] = {m64[b0] / w0, m64[b0 + 3 * st] / w0, m64[b0 + 5 * st] / w0};
+    const double tol = 1e-12 * fmax(fabs(D[0]), fmax(fabs(D[1]), fabs(D[2])));
+    bool ok = true;
+    for (int q = 0; q < n3 && ok; ++q) {
+      const double w = g.wq[q % n] * g.wq[(q / n) % n] * g.wq[q / (n * n)];
+      const int64_t b = metric_offset(g, cell, q);
+      const double expect[6] = {D[0], 0.0, 0.0, D[1], 0.0, D[2]};
+      for (int e = 0; e < 6; ++e) ok = ok && fabs(m64[b + e * st] / w - expect[e]) <= tol;
+    }
+    if (!ok) atomicOr(not_box, 1);
+    for (int i = 0; i < 3; ++i) box[cell * 3 + i] = (float)D[i];
+  }
+}
+
+mfx_status launch_box_check(const mfx_op* op, float* box, int* not_box, cudaStream_t s) {
+  const GeoArgs g = geo_args(op);
+  box_check_kernel<<<grid_for(op->n_cells), 256, 0, s>>>(g, op->d_metric64, box, not_box);
+  MFX_CUDA_TRY(cudaGetLastError());
+  return MFX_OK;
+}
+
 // FP64 metric -> (hi, lo) float pairs in place (structured operators, after the FP64 diagonal).
 __global__ void metric_to_pairs_kernel(int64_t n, double* __restrict__ m) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {

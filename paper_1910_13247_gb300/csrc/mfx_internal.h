@@ -134,6 +134,11 @@ struct mfx_op {
   int32_t* d_leaves = nullptr;       // octree: the sorted leaves, (level, i, j, l) per cell
   double* d_metric64 = nullptr;      // FP64 metric; structured operators: float pairs after creation
   float* d_metric32 = nullptr;
+  // FP32 octree operators whose cells are all boxes with axes along the coordinate axes and whose
+  // coefficient is constant: the metric at quadrature point q of a cell is w_q diag(D) with one D per
+  // cell, stored as [cell][3] instead of the full FP32 metric (which is then not kept)
+  float* d_box32 = nullptr;
+  bool box32 = false;
   double* d_jxw = nullptr;           // n_cells x n^3 (for the right-hand side)
   int32_t* d_cell_dofs = nullptr;    // octree: encoded cell DoFs (n_cells x n^3)
   uint8_t* d_cmask = nullptr;        // octree: 1 on constrained DoFs
@@ -174,6 +179,9 @@ mfx_status launch_geometry(mfx_op* op, int coef_kind, const double* par, const d
 mfx_status launch_qpoints(const mfx_op* op, double* xq, cudaStream_t s);
 mfx_status launch_rhs(const mfx_op* op, const double* fq, double* b, cudaStream_t s);
 mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
+// Box-cell check of an octree operator's FP64 metric ([cell][6][q]): box[cell][3] = the diagonal over the
+// quadrature weight, *not_box set to 1 where a cell's metric is not w_q diag(D) to 1e-12.
+mfx_status launch_box_check(const mfx_op* op, float* box, int* not_box, cudaStream_t s);
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
 mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
 // SIPG operator (dg.cu).

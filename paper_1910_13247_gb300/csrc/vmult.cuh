@@ -52,6 +52,10 @@ struct VmultArgs {
   // optional: the launch processes the cells cell_list[0 .. n_list) instead of 0 .. n_cells
   const int32_t* cell_list;
   int64_t n_list;
+  // box cells (FP32 kernels built for them): the metric at quadrature point (q1, q2, q3) of a cell is
+  // wq[q1] wq[q2] wq[q3] diag(box[cell][0..2])
+  const float* box;
+  Real wq[N];
 };
 
 // The hanging face (0..5) or edge (6..17) of a cell that owns local node (a1, a2, a3): the first hanging

@@ -66,7 +66,7 @@ struct Cell5Scratch {
 
 // HANG: hanging constraints in tensor-product form (bounded to 80 registers for three CTAs per SM, as
 // the ten-phase kernel)
-template <int N, typename Real, bool HANG>
+template <int N, typename Real, bool HANG, bool BOX = false>
 __global__ void __launch_bounds__(256, HANG ? 3 : (sizeof(Real) == 4 ? 4 : 1)) vmult5_kernel(const __grid_constant__ VmultArgs<N, Real> a,
                                                                     const Real* __restrict__ src,
                                                                     Real* __restrict__ dst) {
@@ -243,22 +243,40 @@ __global__ void __launch_bounds__(256, HANG ? 3 : (sizeof(Real) == 4 ? 4 : 1)) v
         vb[j] = B[zl + j * N * NP];
         vc[j] = C[zl + j * N * NP];
       }
-      const Real* G = a.metric + cell * (6 * N3) + rb * N + ra;
       Real oa[N], ob[N], oc[N];
+      if constexpr (BOX) {
+        // box cell: metric w_q diag(D), one D per cell, the weights of the line's point (ra, rb) times
+        // the z-weight of each point
+        const float* Db = a.box + cell * 3;
+        const Real wab = a.wq[ra] * a.wq[rb];
+        const Real D0 = wab * __ldg(Db), D1 = wab * __ldg(Db + 1), D2 = wab * __ldg(Db + 2);
 #pragma unroll
-      for (int q3 = 0; q3 < N; ++q3) {
-        const Real u1 = row1<N, Real, MAT_S>(vc, q3);   // d/dx
-        const Real u2 = row1<N, Real, MAT_S>(vb, q3);   // d/dy
-        const Real u3 = row1<N, Real, MAT_SD>(va, q3);  // d/dz
-        const int off = q3 * N2;
-        const Real G00 = __ldg(G + off), G01 = __ldg(G + N3 + off), G02 = __ldg(G + 2 * N3 + off);
-        const Real G11 = __ldg(G + 3 * N3 + off), G12 = __ldg(G + 4 * N3 + off), G22 = __ldg(G + 5 * N3 + off);
-        const Real h1 = G00 * u1 + G01 * u2 + G02 * u3;
-        const Real h2 = G01 * u1 + G11 * u2 + G12 * u3;
-        const Real h3 = G02 * u1 + G12 * u2 + G22 * u3;
-        axpy_col1<N, Real, MAT_S>(oc, h1, q3, q3 == 0);
-        axpy_col1<N, Real, MAT_S>(ob, h2, q3, q3 == 0);
-        axpy_col1<N, Real, MAT_SD>(oa, h3, q3, q3 == 0);
+        for (int q3 = 0; q3 < N; ++q3) {
+          const Real u1 = row1<N, Real, MAT_S>(vc, q3);   // d/dx
+          const Real u2 = row1<N, Real, MAT_S>(vb, q3);   // d/dy
+          const Real u3 = row1<N, Real, MAT_SD>(va, q3);  // d/dz
+          const Real wz = a.wq[q3];
+          axpy_col1<N, Real, MAT_S>(oc, (D0 * wz) * u1, q3, q3 == 0);
+          axpy_col1<N, Real, MAT_S>(ob, (D1 * wz) * u2, q3, q3 == 0);
+          axpy_col1<N, Real, MAT_SD>(oa, (D2 * wz) * u3, q3, q3 == 0);
+        }
+      } else {
+        const Real* G = a.metric + cell * (6 * N3) + rb * N + ra;
+#pragma unroll
+        for (int q3 = 0; q3 < N; ++q3) {
+          const Real u1 = row1<N, Real, MAT_S>(vc, q3);   // d/dx
+          const Real u2 = row1<N, Real, MAT_S>(vb, q3);   // d/dy
+          const Real u3 = row1<N, Real, MAT_SD>(va, q3);  // d/dz
+          const int off = q3 * N2;
+          const Real G00 = __ldg(G + off), G01 = __ldg(G + N3 + off), G02 = __ldg(G + 2 * N3 + off);
+          const Real G11 = __ldg(G + 3 * N3 + off), G12 = __ldg(G + 4 * N3 + off), G22 = __ldg(G + 5 * N3 + off);
+          const Real h1 = G00 * u1 + G01 * u2 + G02 * u3;
+          const Real h2 = G01 * u1 + G11 * u2 + G12 * u3;
+          const Real h3 = G02 * u1 + G12 * u2 + G22 * u3;
+          axpy_col1<N, Real, MAT_S>(oc, h1, q3, q3 == 0);
+          axpy_col1<N, Real, MAT_S>(ob, h2, q3, q3 == 0);
+          axpy_col1<N, Real, MAT_SD>(oa, h3, q3, q3 == 0);
+        }
       }
 #pragma unroll
       for (int j = 0; j < N; ++j) {

@@ -48,6 +48,8 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
   a->hedge = op->d_hedge;
   a->hoff = op->d_hoff;
   a->hdofs = op->d_hdofs;
+  a->box = op->d_box32;
+  for (int q = 0; q < N; ++q) a->wq[q] = (Real)op->basis.wq[q];
   for (int c = 0; c < 2; ++c)
     for (int b = 0; b < N; ++b)
       for (int m = 0; m < N; ++m)
@@ -56,7 +58,7 @@ static void fill_vmult_args(const mfx_op* op, VmultArgs<N, Real>* a) {
 
 // One launch of the per-cell kernel over all cells, or over a cell list (prologue: dst = src on the
 // constrained rows and 0 elsewhere, before the first launch of a vmult).
-template <int N, typename Real, bool HANG>
+template <int N, typename Real, bool HANG, bool BOX = false>
 static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip,
                               const int32_t* list, int64_t n_list, bool prologue) {
   using Sh = VmultShape<N>;
@@ -70,7 +72,8 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
   // 0.2177 / 0.2128, k = 7 0.1666 / 0.1705, k = 8 0.2570 / 0.2307); FP64: the ten-phase kernel (the
   // five-phase one spills at the 80-register bound of the hanging variant: k = 4 0.750 / 0.914)
   constexpr bool five = sizeof(Real) == 4 && N != 8;
-  auto kern = five ? vmult5_kernel<N, Real, HANG> : vmult_kernel<N, Real, HANG>;
+  static_assert(!BOX || five, "the box-cell metric is read by the FP32 five-phase kernel only");
+  auto kern = five ? vmult5_kernel<N, Real, HANG, BOX> : vmult_kernel<N, Real, HANG>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -101,6 +104,17 @@ static mfx_status run_vmult_h(const mfx_op* op, const Real* src, Real* dst, cuda
 // expansion otherwise.
 template <int N, typename Real>
 static mfx_status run_vmult(const mfx_op* op, const Real* src, Real* dst, cudaStream_t s, const int32_t* skip) {
+  if constexpr (sizeof(Real) == 4 && N != 8) {
+    if (op->box32) {
+      if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_cells_hang) {
+        mfx_status st =
+            run_vmult_h<N, Real, false, true>(op, src, dst, s, skip, op->d_cells_plain, op->n_cells_plain, true);
+        if (st != MFX_OK) return st;
+        return run_vmult_h<N, Real, true, true>(op, src, dst, s, skip, op->d_cells_hang, op->n_cells_hang, false);
+      }
+      return run_vmult_h<N, Real, false, true>(op, src, dst, s, skip, nullptr, 0, true);
+    }
+  }
   if (N - 1 >= kTensorHangMinDegree && op->n_hanging > 0 && op->d_cells_hang) {
     // cells without hanging faces or edges in the plain kernel, the rest in the tensor-product one, one
     // launch after the other (side by side on two streams with grids split by work share measured slower:
@@ -355,14 +369,14 @@ int brick_kernel_candidates(int* out) {
   return n;
 }
 
-template <int N, int CB>
+template <int N, int CB, bool BOX>
 static mfx_status run_octree_pair(const mfx_op* op, const float* src, float* dst, cudaStream_t s,
                                   const int32_t* skip) {
   using Ps = PairShape<N, CB>;
   using Os = OctreePairShape<N, CB>;
   static int blocks_per_sm = -1;
   const size_t smem = Os::SMEM;
-  auto kern = octree_vmult_pair_kernel<N, CB>;
+  auto kern = octree_vmult_pair_kernel<N, CB, BOX>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -386,6 +400,8 @@ static mfx_status run_octree_pair(const mfx_op* op, const float* src, float* dst
   a.n_cells = op->n_cells;
   a.n_batches = (int)((op->n_cells + CB - 1) / CB);
   a.skip = skip;
+  a.box = op->d_box32;
+  for (int q = 0; q < N; ++q) a.wq[q] = (float)op->basis.wq[q];
   if (a.n_batches > 0) {
     const int grid = std::min(a.n_batches, sms * blocks_per_sm);
     kern<<<grid, Ps::THREADS, smem, s>>>(a, src, dst);
@@ -412,7 +428,9 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
   }
   // the paired octree kernel where the FP32 metric is laid out for it (k = 1; k = 8 without hanging nodes)
   if constexpr (OctreePairFor<N>::value)
-    if (op->metric_cb32 > 0) return run_octree_pair<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
+    if (op->metric_cb32 > 0)
+      return op->box32 ? run_octree_pair<N, CB0, true>(op, (const float*)src, (float*)dst, s, skip)
+                       : run_octree_pair<N, CB0, false>(op, (const float*)src, (float*)dst, s, skip);
   return run_vmult<N, float>(op, (const float*)src, (float*)dst, s, skip);
 }
 

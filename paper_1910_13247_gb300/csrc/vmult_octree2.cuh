@@ -39,6 +39,9 @@ struct OctreePairArgs {
   int64_t n_cells;
   int n_batches;
   const int32_t* skip;
+  // box cells: metric w_q diag(box[cell][0..2]), wq the 1D Gauss weights (BOX variant)
+  const float* box;
+  float wq[N];
 };
 
 template <int N, int CB>
@@ -71,7 +74,7 @@ __device__ __forceinline__ void scatter_node(const int32_t e, float v, float* __
     atomicAdd(dst + __ldg(cmaster + p), __ldg(cweight + p) * v);
 }
 
-template <int N, int CB>
+template <int N, int CB, bool BOX = false>
 __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::MIN_BLOCKS)
     octree_vmult_pair_kernel(const __grid_constant__ OctreePairArgs<N> a, const float* __restrict__ src,
                              float* __restrict__ dst) {
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   using Os = OctreePairShape<N, CB>;
   constexpr int PP = CB / 2;
   constexpr int K = Sh::K, NP = Sh::NP, P2 = Sh::P2, CELL = Sh::CELL, N3 = N * N * N;
-  constexpr bool PREFETCH = N <= 5;
+  constexpr bool PREFETCH = N <= 5 && !BOX;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* A = reinterpret_cast<float2*>(smem_raw);
@@ -106,8 +109,9 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
     const int m = rest < CB ? (int)rest : CB;
     const bool act = line_ok && 2 * c < m;
     const bool act1 = line_ok && 2 * c + 1 < m;
-    const float2* Gb =
-        reinterpret_cast<const float2*>(a.metric + (int64_t)b * (6 * N3 * CB) + (xa2 * N + xa3 * N * N) * CB + 2 * c);
+    const float2* Gb = BOX ? nullptr
+                           : reinterpret_cast<const float2*>(a.metric + (int64_t)b * (6 * N3 * CB) +
+                                                             (xa2 * N + xa3 * N * N) * CB + 2 * c);
     float2 G[PREFETCH ? 6 : 1][N];
     if (PREFETCH && act) {
 #pragma unroll
@@ -177,6 +181,23 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
     float2 t1[N];
     if (act) {
       float2 h1[N];
+      if constexpr (BOX) {
+        // box cells: metric w_q diag(D) per cell, the pair's two diagonals as the lanes (a missing second
+        // cell of a short batch repeats the first)
+        const int64_t c0 = cell0 + 2 * c, c1 = act1 ? c0 + 1 : c0;
+        const float wyz = a.wq[xa2] * a.wq[xa3];
+        const float2 D0 = make_float2(wyz * __ldg(a.box + c0 * 3), wyz * __ldg(a.box + c1 * 3));
+        const float2 D1 = make_float2(wyz * __ldg(a.box + c0 * 3 + 1), wyz * __ldg(a.box + c1 * 3 + 1));
+        const float2 D2 = make_float2(wyz * __ldg(a.box + c0 * 3 + 2), wyz * __ldg(a.box + c1 * 3 + 2));
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const float2 wx = make_float2(a.wq[q], a.wq[q]);
+          const float2 u1 = g1[q], u2 = B[xbase + q], u3 = C[xbase + q];
+          h1[q] = __fmul2_rn(__fmul2_rn(wx, D0), u1);
+          B[xbase + q] = __fmul2_rn(__fmul2_rn(wx, D1), u2);
+          C[xbase + q] = __fmul2_rn(__fmul2_rn(wx, D2), u3);
+        }
+      } else {
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         float2 G00, G01, G02, G11, G12, G22;
@@ -191,6 +212,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
         h1[q] = __ffma2_rn(G02, u3, __ffma2_rn(G01, u2, __fmul2_rn(G00, u1)));
         B[xbase + q] = __ffma2_rn(G12, u3, __ffma2_rn(G11, u2, __fmul2_rn(G01, u1)));
         C[xbase + q] = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
+      }
       }
       contract2_t<N, MAT_D>(h1, t1);
     }

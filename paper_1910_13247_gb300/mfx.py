@@ -51,7 +51,7 @@ class OpInfo(ctypes.Structure):
                 ("n_masters", ctypes.c_int64), ("n_hanging", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
                 ("degree", ctypes.c_int32), ("n_q_1d", ctypes.c_int32), ("structured", ctypes.c_int32),
                 ("cells_per_block", ctypes.c_int32), ("discretization", ctypes.c_int32),
-                ("structured_kernel", ctypes.c_int32)]
+                ("structured_kernel", ctypes.c_int32), ("box_metric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):

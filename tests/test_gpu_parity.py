@@ -172,6 +172,43 @@ def test_octree_tensor_product_hanging_constraints(mfx, seed, k, nb, radius):
     assert e32 < 1e-5, e32
 
 
+@pytest.mark.parametrize("k,nb,levels,radius", [(1, 4, 2, 0.3), (2, 3, 2, 0.3), (3, 3, 1, 0.3), (4, 3, 2, 0.25),
+                                              (6, 2, 1, 0.2), (7, 2, 1, 0.2), (8, 2, 1, 0.2), (8, 2, 1, 0.0)])
+def test_octree_box_cell_metric(mfx, k, nb, levels, radius, monkeypatch):
+    """Octree on the undeformed lattice with a constant coefficient: every cell is an axis-aligned box,
+    and the FP32 kernels take the metric as one diagonal per cell (the paired kernel at k = 1 and at k = 8
+    without hanging nodes, the five-phase kernel with and without hanging cells elsewhere; k = 7 keeps the
+    full metric). FP32 and FP64 against the oracle, and the FP32 result against the same operator with
+    the full metric (MFX_BOX_METRIC=0); a deformed lattice or a variable coefficient keeps the full metric."""
+    g = synthetic.rng(500 + k)
+    center = np.array([0.3, 0.3, 0.3]) if nb == 2 else g.uniform(0.3, 0.7, 3)
+    leaves = synthetic.octree_leaves(nb, levels, center, radius)
+    op = mfx.Operator(mfx.Mesh.octree(nb, nb, nb, leaves), k)
+    info = op.info()
+    assert (info["n_hanging"] > 0) == (radius > 0)
+    assert info["box_metric"] == (0 if k == 7 else 1)
+    om = omesh.octree_mesh(nb, nb, nb, k, leaves)
+    K = fem.assemble(om, k + 1)
+    x = synthetic.uniform_vector(om.n_dofs, 60 + k)
+    ref = K @ x
+    e2, einf = rel_err(run_vmult(op, x, torch.float64), ref)
+    assert e2 < 1e-12 and einf < 1e-12, (e2, einf)
+    y32 = run_vmult(op, x, torch.float32)
+    e32, e32inf = rel_err(y32, ref)
+    assert e32 < 1e-5 and e32inf < 1e-5, (e32, e32inf)
+    monkeypatch.setenv("MFX_BOX_METRIC", "0")
+    full = mfx.Operator(mfx.Mesh.octree(nb, nb, nb, leaves), k)
+    assert full.info()["box_metric"] == 0
+    if k != 7:
+        assert info["bytes_device"] < full.info()["bytes_device"]
+    assert rel_err(run_vmult(full, x, torch.float32), y32)[0] < 1e-6
+    monkeypatch.delenv("MFX_BOX_METRIC")
+    deformed = mfx.Operator(mfx.Mesh.octree(nb, nb, nb, leaves, synthetic.deformed_vertices(nb, nb, nb)), k)
+    assert deformed.info()["box_metric"] == 0
+    variable = mfx.Operator(mfx.Mesh.octree(nb, nb, nb, leaves), k, mfx.COEF_TRIG, (1.0, 0.5))
+    assert variable.info()["box_metric"] == 0
+
+
 @pytest.mark.parametrize("k", [5, 7, 8])
 def test_octree_diagonal_high_degree(mfx, k):
     """Diagonal and vmult on an octree at high degree: the diagonal's sum-factorised paths (cells with
