@@ -341,7 +341,8 @@ static void destroy_op(mfx_op* op, cudaStream_t s = cudaStreamPerThread, bool sy
   if (!op) return;
   if (sync) cudaDeviceSynchronize();
   free_workspace(op, s);
-  void* ptrs[] = {op->d_vertices, op->d_leaves, op->d_metric64, op->d_metric32, op->d_box32, op->d_jxw, op->d_cell_dofs, op->d_cmask,
+  void* ptrs[] = {op->d_vertices, op->d_leaves, op->d_metric64, op->d_metric32, op->d_box32, op->d_q1_start,
+                  op->d_q1_octdofs, op->d_q1_single, op->d_jxw, op->d_cell_dofs, op->d_cmask,
                   op->d_constrained, op->d_cptr, op->d_cmaster, op->d_cweight64, op->d_cweight32,
                   op->d_cell_hanging, op->d_diag64, op->d_diag32, op->d_scalars, op->d_partials, op->d_counter,
                   op->d_err, op->d_hface, op->d_hedge, op->d_hoff, op->d_hdofs, op->d_cells_plain,
@@ -757,6 +758,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       op->d_metric32 = nullptr;
       op->d_box32 = box;
       op->box32 = true;
+      if (k == 1) MFX_TRY(build_q1_octants(op, s));
     } else {
       cudaFreeAsync(box, s);
       op->bytes_device -= (int64_t)((size_t)op->n_cells * 3 * sizeof(float));

@@ -139,6 +139,13 @@ struct mfx_op {
   // cell, stored as [cell][3] instead of the full FP32 metric (which is then not kept)
   float* d_box32 = nullptr;
   bool box32 = false;
+  // k = 1 box-cell operators: the octants of the cell order (first cell of each and its 27 node entries)
+  // and the cells outside them
+  bool q1_split = false;
+  int64_t q1_n_oct = 0, q1_n_single = 0;
+  int32_t* d_q1_start = nullptr;
+  int32_t* d_q1_octdofs = nullptr;
+  int32_t* d_q1_single = nullptr;
   double* d_jxw = nullptr;           // n_cells x n^3 (for the right-hand side)
   int32_t* d_cell_dofs = nullptr;    // octree: encoded cell DoFs (n_cells x n^3)
   uint8_t* d_cmask = nullptr;        // octree: 1 on constrained DoFs
@@ -182,6 +189,10 @@ mfx_status launch_diagonal(mfx_op* op, cudaStream_t s);
 // Box-cell check of an octree operator's FP64 metric ([cell][6][q]): box[cell][3] = the diagonal over the
 // quadrature weight, *not_box set to 1 where a cell's metric is not w_q diag(D) to 1e-12.
 mfx_status launch_box_check(const mfx_op* op, float* box, int* not_box, cudaStream_t s);
+// k = 1 box-cell operators (vmult_k1.cu): the octant groups of the cell order, and the FP32 vmult that
+// gathers and scatters an octant group's 27 nodes once.
+mfx_status build_q1_octants(mfx_op* op, cudaStream_t s);
+mfx_status launch_octree_q1_box(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip);
 mfx_status launch_distribute(const mfx_op* op, double* x, cudaStream_t s);
 mfx_status launch_metric_to_pairs(mfx_op* op, int64_t entries, cudaStream_t s);
 // SIPG operator (dg.cu).

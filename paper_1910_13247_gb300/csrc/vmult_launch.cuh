@@ -426,6 +426,9 @@ mfx_status launch_vmult_n(const mfx_op* op, mfx_prec prec, const void* src, void
     if (CB1 != CB0 && op->metric_cb == CB1) return run_brick_f32<N, CB1>(op, (const float*)src, (float*)dst, s, skip);
     return run_brick_f32<N, CB0>(op, (const float*)src, (float*)dst, s, skip);
   }
+  // k = 1 box cells: one thread per cell, octant groups gathered and scattered once per node
+  if constexpr (N == 2)
+    if (op->box32 && op->q1_split) return launch_octree_q1_box(op, (const float*)src, (float*)dst, s, skip);
   // the paired octree kernel where the FP32 metric is laid out for it (k = 1; k = 8 without hanging nodes)
   if constexpr (OctreePairFor<N>::value)
     if (op->metric_cb32 > 0)
