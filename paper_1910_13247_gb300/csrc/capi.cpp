@@ -735,10 +735,11 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (coef_tmp) cudaFreeAsync(coef_tmp, s);
   MFX_TRY(geo_st);
   MFX_TRY(launch_diagonal(op, s));
-  // octree cells that are all axis-aligned boxes with a constant coefficient: the FP32 kernels take the
-  // metric as one diagonal per cell (the specialised mapping for boxes parallel to the coordinate axes);
-  // not at k = 7, whose FP32 kernel reads the full metric; MFX_BOX_METRIC=0 keeps the full metric
-  if (!op->structured && !op->dg && op->has_f32 && k != 7 && box_metric_enabled()) {
+  // octree cells (and structured ones from k = 6 on, which run the same per-cell kernels) that are all
+  // axis-aligned boxes with a constant coefficient: the FP32 kernels take the metric as one diagonal per
+  // cell (the specialised mapping for boxes parallel to the coordinate axes); not at k = 7, whose FP32
+  // kernel reads the full metric; MFX_BOX_METRIC=0 keeps the full metric
+  if ((!op->structured || op->percell32) && !op->dg && op->has_f32 && k != 7 && box_metric_enabled()) {
     float* box = nullptr;
     int* flag = nullptr;
     MFX_TRY(dev_alloc(op, &box, (size_t)op->n_cells * 3, s));
@@ -758,7 +759,7 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       op->d_metric32 = nullptr;
       op->d_box32 = box;
       op->box32 = true;
-      if (k == 1) MFX_TRY(build_q1_octants(op, s));
+      if (k == 1 && !op->structured) MFX_TRY(build_q1_octants(op, s));
     } else {
       cudaFreeAsync(box, s);
       op->bytes_device -= (int64_t)((size_t)op->n_cells * 3 * sizeof(float));

@@ -209,6 +209,27 @@ def test_octree_box_cell_metric(mfx, k, nb, levels, radius, monkeypatch):
     assert variable.info()["box_metric"] == 0
 
 
+@pytest.mark.parametrize("k,n", [(6, 3), (8, 2), (7, 2)])
+def test_structured_box_cell_metric_high_degree(mfx, k, n, monkeypatch):
+    """Structured meshes from k = 6 on run the per-cell kernels; on the undeformed cube with a constant
+    coefficient their FP32 metric is one diagonal per cell too (not at k = 7): FP32 against the oracle and
+    against the full metric."""
+    op = mfx.Operator(mfx.Mesh.structured_box(n, n, n), k)
+    assert op.info()["box_metric"] == (0 if k == 7 else 1)
+    om = omesh.structured_mesh(n, n, n, k)
+    K = fem.assemble(om, k + 1)
+    x = synthetic.uniform_vector(om.n_dofs, 80 + k)
+    ref = K @ x
+    y32 = run_vmult(op, x, torch.float32)
+    e2, einf = rel_err(y32, ref)
+    assert e2 < 1e-5 and einf < 1e-5, (e2, einf)
+    assert rel_err(run_vmult(op, x, torch.float64), ref)[0] < 1e-12
+    monkeypatch.setenv("MFX_BOX_METRIC", "0")
+    full = mfx.Operator(mfx.Mesh.structured_box(n, n, n), k)
+    assert full.info()["box_metric"] == 0
+    assert rel_err(run_vmult(full, x, torch.float32), y32)[0] < 1e-6
+
+
 @pytest.mark.parametrize("k", [5, 7, 8])
 def test_octree_diagonal_high_degree(mfx, k):
     """Diagonal and vmult on an octree at high degree: the diagonal's sum-factorised paths (cells with
