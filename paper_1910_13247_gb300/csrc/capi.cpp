@@ -735,11 +735,12 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
   if (coef_tmp) cudaFreeAsync(coef_tmp, s);
   MFX_TRY(geo_st);
   MFX_TRY(launch_diagonal(op, s));
-  // octree cells (and structured ones from k = 6 on, which run the same per-cell kernels) that are all
-  // axis-aligned boxes with a constant coefficient: the FP32 kernels take the metric as one diagonal per
-  // cell (the specialised mapping for boxes parallel to the coordinate axes); not at k = 7, whose FP32
-  // kernel reads the full metric; MFX_BOX_METRIC=0 keeps the full metric
-  if ((!op->structured || op->percell32) && !op->dg && op->has_f32 && k != 7 && box_metric_enabled()) {
+  // cells that are all axis-aligned boxes with a constant coefficient: the FP32 kernels take the metric
+  // as one diagonal per cell (the specialised mapping for boxes parallel to the coordinate axes) — the
+  // per-cell kernels (octrees; structured meshes from k = 6 on) from [cell][3], the structured row-batch
+  // kernels from the first point of each line of the full FP32 metric, which they keep; not at k = 7,
+  // whose FP32 kernel reads the full metric; MFX_BOX_METRIC=0 keeps the full metric everywhere
+  if (!op->dg && op->has_f32 && k != 7 && box_metric_enabled()) {
     float* box = nullptr;
     int* flag = nullptr;
     MFX_TRY(dev_alloc(op, &box, (size_t)op->n_cells * 3, s));
@@ -753,7 +754,11 @@ mfx_status mfx_operator_create(mfx_op** out, const mfx_mesh* mesh, const mfx_op_
       if (e != cudaSuccess) bst = cuda_error(e, "box metric");
     }
     if (flag) cudaFreeAsync(flag, s);
-    if (bst == MFX_OK && not_box == 0) {
+    if (bst == MFX_OK && not_box == 0 && op->structured && !op->percell32) {
+      cudaFreeAsync(box, s);
+      op->bytes_device -= (int64_t)((size_t)op->n_cells * 3 * sizeof(float));
+      op->box32 = true;
+    } else if (bst == MFX_OK && not_box == 0) {
       cudaFreeAsync(op->d_metric32, s);
       op->bytes_device -= (int64_t)(metric32_entries * sizeof(float));
       op->d_metric32 = nullptr;

@@ -269,9 +269,10 @@ __device__ __forceinline__ void c2_tt(const float2 (&a)[N], const float2 (&b)[N]
 // TB: input tiles (2: the next batch's rows are requested when a batch starts, 1: once phase 1 has read
 // the tile); MBF: staged metric buffers (2: the next batch's metric is requested when a batch starts);
 // EF: the metric stream carries the L2 evict-first policy
-template <int N, int CB, int MS, int MB, int TB, int MBF, int EF, int PK = 0>
+template <int N, int CB, int MS, int MB, int TB, int MBF, int EF, int PK = 0, bool BOXM = false>
 __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF, PK>::THREADS, MB)
     brick_vmult_f5_kernel(const __grid_constant__ TmaArgs<N> a) {
+  static_assert(!BOXM || MS == 0, "box cells read the metric from global memory");
   using Sh = BrickShape<N, CB, float>;  // cube paddings of CB cells = paddings of CB / 2 float pairs
   using Tm = TmaShape<N, CB>;
   using Fs = F5Shape<N, CB, MS, TB, MBF, PK>;
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF, PK>::THREADS, MB)
     // metric read from L2 (MS = 0): the TMA engine brings the next batch's metric into L2 (nothing waits
     // for it); with the staged metric the bulk copy alone measured faster (Q4 0.2585 -> 0.2503 ms, Q2
     // 0.3406 -> 0.3261 ms against an L2 prefetch two batches ahead)
-    if (!MS && tma_warp && lane >= 4 && lane < 7) {
+    if (!MS && !BOXM && tma_warp && lane >= 4 && lane < 7) {
       const int bn = b + (int)gridDim.x;
       if (bn < a.n_batches) {
         constexpr unsigned CHUNK = (MBYTES / 3 + 15u) & ~15u;
@@ -517,7 +518,21 @@ __global__ void __launch_bounds__(F5Shape<N, CB, MS, TB, MBF, PK>::THREADS, MB)
       const float2* Gm = MS ? reinterpret_cast<const float2*>(Msm) + gq
                             : reinterpret_cast<const float2*>(a.metric + (int64_t)b * Fs::METRIC) + gq;
       // the merged metric at Gauss point q of this x-line: h = G grad
+      // box cells: the metric on the line is w_q / w_0 times its first point's diagonal
+      float2 D0 = make_float2(0.f, 0.f), D1 = D0, D2 = D0;
+      if constexpr (BOXM) {
+        D0 = __ldg(Gm);
+        D1 = __ldg(Gm + 3 * N3 * PP);
+        D2 = __ldg(Gm + 5 * N3 * PP);
+      }
       auto qpoint = [&](int q, float2 u1, float2 u2, float2 u3, float2& h1, float2& h2, float2& h3) {
+        if constexpr (BOXM) {
+          const float2 rq = make_float2(a.wr[q], a.wr[q]);
+          h1 = __fmul2_rn(__fmul2_rn(rq, D0), u1);
+          h2 = __fmul2_rn(__fmul2_rn(rq, D1), u2);
+          h3 = __fmul2_rn(__fmul2_rn(rq, D2), u3);
+          return;
+        }
         float2 G00, G01, G02, G11, G12, G22;
         if constexpr (MS != 0) {
           G00 = Gm[(0 * N3 + q) * PP]; G01 = Gm[(1 * N3 + q) * PP]; G02 = Gm[(2 * N3 + q) * PP];

@@ -41,6 +41,9 @@ struct TmaArgs {
   const float* src;
   float* dst;
   int64_t n;
+  // box cells (the BOXM kernel variants): w_q / w_0 of the 1D Gauss weights; the metric along a line is
+  // these ratios times the line's first point's diagonal
+  float wr[N];
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

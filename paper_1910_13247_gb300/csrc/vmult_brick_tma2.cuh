@@ -60,7 +60,7 @@ __device__ __forceinline__ void contract2_t(const float2 (&in)[N], float2 (&out)
   }
 }
 
-template <int N, int CB>
+template <int N, int CB, bool BOXM = false>
 __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::MIN_BLOCKS)
     brick_vmult_tma2_kernel(const __grid_constant__ TmaArgs<N> a) {
   using Sh = BrickShape<N, CB, float>;  // cube paddings of CB cells = paddings of CB / 2 float pairs
@@ -73,13 +73,13 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
   // k = 2, 4: loaded where it is used, from L2 (the TMA engine prefetches each batch's metric one batch
   // ahead, below), which frees registers for more CTAs per SM: Q4 on 64^3 0.2871 -> 0.2708 ms, Q2 on
   // 128^3 0.3903 -> 0.3814 ms (Q3 measured slower that way: 0.304 -> 0.314 ms)
-  constexpr bool PREFETCH = N == 2 || N == 4;
+  constexpr bool PREFETCH = !BOXM && (N == 2 || N == 4);
   // k = 1: the next batch's metric is requested right after the current one is used (spreads the
   // metric stream over the whole batch); k = 3: at the start of the batch
   constexpr bool XPREF = PREFETCH && N <= 3;
   // L2 prefetch of the metric one batch ahead for k >= 2 (k = 8: 0.949 -> 0.863 ms on 40^3, Q3 on 86^3
   // 0.310 -> 0.304); with the register prefetch of k = 1 it measured slower
-  constexpr int MDIST = N >= 3 ? 1 : 0;
+  constexpr int MDIST = (!BOXM && N >= 3) ? 1 : 0;  // box cells read three entries of each line
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* in_tiles = reinterpret_cast<float*>(smem_raw);  // 2 x TILE
@@ -251,6 +251,18 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
     float2 t1[N];
     if (act) {
       float2 h1[N];
+      if constexpr (BOXM) {
+        // box cells: the metric on the line is w_q / w_0 times its first point's diagonal
+        const float2 D0 = __ldg(Gb), D1 = __ldg(Gb + 3 * N3 * PP), D2 = __ldg(Gb + 5 * N3 * PP);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const float2 rq = make_float2(a.wr[q], a.wr[q]);
+          const float2 u1 = g1[q], u2 = B[xbase + q], u3 = C[xbase + q];
+          h1[q] = __fmul2_rn(__fmul2_rn(rq, D0), u1);
+          B[xbase + q] = __fmul2_rn(__fmul2_rn(rq, D1), u2);
+          C[xbase + q] = __fmul2_rn(__fmul2_rn(rq, D2), u3);
+        }
+      } else {
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         float2 G00, G01, G02, G11, G12, G22;
@@ -265,6 +277,7 @@ __global__ void __launch_bounds__(PairShape<N, CB>::THREADS, PairShape<N, CB>::M
         h1[q] = __ffma2_rn(G02, u3, __ffma2_rn(G01, u2, __fmul2_rn(G00, u1)));
         B[xbase + q] = __ffma2_rn(G12, u3, __ffma2_rn(G11, u2, __fmul2_rn(G01, u1)));
         C[xbase + q] = __ffma2_rn(G22, u3, __ffma2_rn(G12, u2, __fmul2_rn(G02, u1)));
+      }
       }
       contract2_t<N, MAT_D>(h1, t1);
     }

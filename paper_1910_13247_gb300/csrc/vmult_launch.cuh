@@ -235,13 +235,13 @@ static mfx_status encode_1d_map(CUtensorMap* map, const void* ptr, int64_t n, in
   return MFX_OK;
 }
 
-template <int N, int CB>
+template <int N, int CB, bool BOXM = false>
 static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
   using Ps = PairShape<N, CB>;
   using Tm = TmaShape<N, CB>;
   static int blocks_per_sm = -1;
   const size_t smem = Ps::SMEM;
-  auto kern = brick_vmult_tma2_kernel<N, CB>;
+  auto kern = brick_vmult_tma2_kernel<N, CB, BOXM>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -266,6 +266,7 @@ static mfx_status run_brick_tma2(const mfx_op* op, const float* src, float* dst,
   a.err = op->d_err;
   a.skip = skip;
   a.dmask = op->dirichlet;
+  for (int q = 0; q < N; ++q) a.wr[q] = (float)(op->basis.wq[q] / op->basis.wq[0]);
   const int rows = a.My * a.Mz;
   init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
@@ -299,7 +300,7 @@ struct F5Config {
   static constexpr int PK = (MS && ((N == 5 && CB == 8) || (N == 4 && CB == 16))) ? 1 : 0;
 };
 
-template <int N, int CB, int MS>
+template <int N, int CB, int MS, bool BOXM = false>
 static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
   using Cf = F5Config<N, CB, MS>;
   constexpr int PK = Cf::PK;
@@ -312,7 +313,7 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
   constexpr int MB = MB0 < MBS ? MB0 : MBS;
   static int blocks_per_sm = -1;
   const size_t smem = Fs::SMEM;
-  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB, Cf::TB, Cf::MBF, Cf::EF, PK>;
+  auto kern = brick_vmult_f5_kernel<N, CB, MS, MB, Cf::TB, Cf::MBF, Cf::EF, PK, BOXM>;
   if (blocks_per_sm < 0) {
     MFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int b = 0;
@@ -340,6 +341,7 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
   a.err = op->d_err;
   a.skip = skip;
   a.dmask = op->dirichlet;
+  for (int q = 0; q < N; ++q) a.wr[q] = (float)(op->basis.wq[q] / op->basis.wq[0]);
   const int rows = a.My * a.Mz;
   init_rows_kernel<float><<<init_rows_grid(rows), 256, 0, s>>>(a.Mx, a.My, a.Mz, a.dmask, src, dst);
   const int grid = std::min(a.n_batches, device_sm_count() * blocks_per_sm);
@@ -351,6 +353,14 @@ static mfx_status run_brick_f5(const mfx_op* op, const float* src, float* dst, c
 
 template <int N, int CB>
 static mfx_status run_brick_f32(const mfx_op* op, const float* src, float* dst, cudaStream_t s, const int32_t* skip) {
+  // box cells: the chosen kernel's variant that reads three entries of each line's metric (the staged
+  // five-phase kernel in its unstaged form: there is nothing left to stage)
+  if (op->box32) {
+    if constexpr (F5For<N>::value)
+      if (op->f32_kernel == MFX_KERNEL_FIVE_PHASE || op->f32_kernel == MFX_KERNEL_FIVE_PHASE_STAGED)
+        return run_brick_f5<N, CB, 0, true>(op, src, dst, s, skip);
+    return run_brick_tma2<N, CB, true>(op, src, dst, s, skip);
+  }
   if constexpr (F5For<N>::value) {
     if (op->f32_kernel == MFX_KERNEL_FIVE_PHASE) return run_brick_f5<N, CB, 0>(op, src, dst, s, skip);
     if (op->f32_kernel == MFX_KERNEL_FIVE_PHASE_STAGED) return run_brick_f5<N, CB, 1>(op, src, dst, s, skip);

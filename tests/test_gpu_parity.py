@@ -209,6 +209,30 @@ def test_octree_box_cell_metric(mfx, k, nb, levels, radius, monkeypatch):
     assert variable.info()["box_metric"] == 0
 
 
+@pytest.mark.parametrize("k,kernel", [(1, "TEN_PHASE"), (2, "TEN_PHASE"), (3, "TEN_PHASE"), (4, "TEN_PHASE"),
+                                      (5, "TEN_PHASE"), (1, "FIVE_PHASE"), (2, "FIVE_PHASE_STAGED"),
+                                      (3, "FIVE_PHASE"), (4, "FIVE_PHASE_STAGED"), (4, "FIVE_PHASE")])
+def test_structured_box_cell_metric_row_batch(mfx, k, kernel, monkeypatch):
+    """Structured row-batch kernels on box cells with a constant coefficient read three entries of each
+    line's FP32 metric (its first point's diagonal) and scale them by the quadrature weights: rows of 35
+    cells (full and partial batches), FP32 against the oracle and against the full metric."""
+    dims = (35, 3, 2)
+    kid = getattr(mfx, "KERNEL_" + kernel)
+    op = mfx.Operator(mfx.Mesh.structured_box(*dims), k, structured_kernel=kid)
+    assert op.info()["box_metric"] == 1 and op.info()["structured_kernel"] == kid
+    om = omesh.structured_mesh(*dims, k)
+    K = fem.assemble(om, k + 1)
+    x = synthetic.uniform_vector(om.n_dofs, 90 + k)
+    ref = K @ x
+    y32 = run_vmult(op, x, torch.float32)
+    e2, einf = rel_err(y32, ref)
+    assert e2 < 1e-5 and einf < 1e-5, (e2, einf)
+    monkeypatch.setenv("MFX_BOX_METRIC", "0")
+    full = mfx.Operator(mfx.Mesh.structured_box(*dims), k, structured_kernel=kid)
+    assert full.info()["box_metric"] == 0
+    assert rel_err(run_vmult(full, x, torch.float32), y32)[0] < 1e-6
+
+
 @pytest.mark.parametrize("k,n", [(6, 3), (8, 2), (7, 2)])
 def test_structured_box_cell_metric_high_degree(mfx, k, n, monkeypatch):
     """Structured meshes from k = 6 on run the per-cell kernels; on the undeformed cube with a constant
