@@ -40,11 +40,11 @@ WORKLOAD = "64^3 deformed unit cube, Q4 GLL, 5-pt Gauss, a=1+0.5 sin(2pi x)cos(2
 # profiles/vmult_fp32_f5_staged_q4_48cube.md (48^3 case, five-phase kernel with the staged metric, 8 cells per
 # batch; 412.85 MB read + written, scaled by cells to 64^3).  Valid only for that kernel, batch size and the
 # kernel sources it was taken from: anything else reports null.
-TRAFFIC_BYTES = 977.9e6
+TRAFFIC_BYTES = 978.4e6
 TRAFFIC_KERNEL = (3, 8)  # (structured_kernel, cells_per_block): five-phase, staged metric, 8 cells per batch
-TRAFFIC_SOURCES = {"vmult_brick_f5.cuh": "03c347c468e9c9f5", "vmult_brick_tma2.cuh": "a9524b2424c4577c",
-                   "vmult_brick_tma.cuh": "c1f5022f3477b394", "vmult_brick.cuh": "d4348f1901d2181e",
-                   "vmult.cuh": "a6088d02147ee108", "vmult_launch.cuh": "69ab737b29ad0234"}
+TRAFFIC_SOURCES = {"vmult_brick_f5.cuh": "4f7d5a2e9488aa25", "vmult_brick_tma2.cuh": "0991fee5e2c07a72",
+                   "vmult_brick_tma.cuh": "25984cf632f8c607", "vmult_brick.cuh": "d4348f1901d2181e",
+                   "vmult.cuh": "a6088d02147ee108", "vmult_launch.cuh": "81978a63b553fbee"}
 KERNEL_NAMES = {1: "brick_vmult_tma2_kernel (ten phases)", 2: "brick_vmult_f5_kernel (five phases, metric from L2)",
                 3: "brick_vmult_f5_kernel (five phases, metric staged in shared memory)"}
 
